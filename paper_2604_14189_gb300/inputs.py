@@ -1,0 +1,135 @@
+"""Seeded synthetic inputs for the acoustic and elastic solvers.
+
+This module holds no solver arithmetic: it only draws models, wavelets and
+acquisition geometry (numpy + scipy on the host).  Both the CUDA path's tests
+and the CPU oracle's tests take their inputs from here.
+
+Workload recipes (the paper names no public dataset; every input is
+synthetic):
+
+* ``layered3`` -- 3 flat layers 1500/2500/3500 m/s with interfaces at
+  z = 60 and 130 cells (acoustic single-shot forward, 200 x 200 interior).
+* ``marmousi_like`` -- smooth layered gradient 1500 -> 4500 m/s with 8 seeded
+  undulating interfaces (+-150 m/s) plus 5 Gaussian anomalies (+-10 %,
+  sigma 15 cells); the starting model is the true one blurred with a 40-cell
+  Gaussian (acoustic forward + adjoint gradient, 301 x 901 interior).
+* ``elastic_layered`` -- Vp 1800 -> 5000 m/s linear in depth plus 10 seeded
+  layers (+-200 m/s), Vs = Vp / 1.73, Gardner density 310 Vp^0.25.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.ndimage import gaussian_filter
+
+
+def ricker(f0: float, dt: float, nt: int, t0: float | None = None,
+           shift: float = 0.0) -> np.ndarray:
+    """Ricker wavelet sampled at t_n = (n + shift) dt, delay t0 = 1.5 / f0."""
+    if t0 is None:
+        t0 = 1.5 / f0
+    t = (np.arange(nt) + shift) * dt - t0
+    a = (np.pi * f0 * t) ** 2
+    return (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def surface_line(nshot: int, z: int, xs) -> np.ndarray:
+    """[nshot][n][2] positions (z, x) with the same x list for every shot."""
+    xs = np.asarray(xs, dtype=np.int32)
+    pos = np.stack([np.full_like(xs, z), xs], axis=-1)
+    return np.broadcast_to(pos, (nshot,) + pos.shape).copy()
+
+
+def layered3(nz: int = 200, nx: int = 200) -> np.ndarray:
+    v = np.empty((nz, nx), dtype=np.float64)
+    z = np.arange(nz)[:, None]
+    v[:] = np.where(z < 60, 1500.0, np.where(z < 130, 2500.0, 3500.0))
+    return v
+
+
+def marmousi_like(nz: int, nx: int, seed: int, vmin=1500.0, vmax=4500.0,
+                  n_interfaces=8, n_anomalies=5):
+    """True and starting velocity models (float64 [nz][nx])."""
+    rng = np.random.default_rng(seed)
+    z = np.arange(nz, dtype=np.float64)[:, None]
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    v = vmin + (vmax - vmin) * z / max(nz - 1, 1) + 0.0 * x
+    depths = np.sort(rng.uniform(0.1 * nz, 0.9 * nz, n_interfaces))
+    for d in depths:
+        jump = rng.choice([-150.0, 150.0])
+        k = rng.uniform(1.0, 3.0) * 2 * np.pi / nx
+        ph = rng.uniform(0, 2 * np.pi)
+        surf = d + 5.0 * np.sin(k * x + ph)
+        v = v + jump * (z >= surf)
+    v = np.clip(v, vmin, vmax)
+    for _ in range(n_anomalies):
+        cz = rng.uniform(0.2, 0.8) * nz
+        cx = rng.uniform(0.2, 0.8) * nx
+        amp = rng.uniform(-0.1, 0.1)
+        v = v * (1.0 + amp * np.exp(-((z - cz) ** 2 + (x - cx) ** 2) / (2 * 15.0 ** 2)))
+    v0 = gaussian_filter(v, sigma=40.0, mode="nearest")
+    return v, v0
+
+
+def smooth_perturbations(nz: int, nx: int, v: np.ndarray, count: int, seed: int,
+                         sigma: float = 10.0, rel: float = 0.01) -> np.ndarray:
+    """[count][nz][nx] blurred white noise scaled to `rel` of v (max norm)."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((count, nz, nx))
+    for k in range(count):
+        w = gaussian_filter(rng.standard_normal((nz, nx)), sigma=sigma, mode="nearest")
+        out[k] = rel * v * w / np.abs(w).max()
+    return out
+
+
+def elastic_layered(nz: int, nx: int, seed: int, n_layers: int = 10):
+    """(vp, vs, rho) float64 [3][nz][nx]."""
+    rng = np.random.default_rng(seed)
+    z = np.arange(nz, dtype=np.float64)[:, None]
+    vp = 1800.0 + (5000.0 - 1800.0) * z / max(nz - 1, 1) + np.zeros((1, nx))
+    for d in np.sort(rng.uniform(0.05 * nz, 0.95 * nz, n_layers)):
+        vp = vp + rng.uniform(-200.0, 200.0) * (z >= d)
+    vp = np.clip(vp, 1800.0, 5000.0)
+    vs = vp / 1.73
+    rho = 310.0 * vp ** 0.25
+    return np.stack([vp, vs, rho])
+
+
+def pad_edge(model: np.ndarray, pml: int) -> np.ndarray:
+    """Edge-replicate the last two axes by `pml` cells (model layout helper)."""
+    pad = [(0, 0)] * (model.ndim - 2) + [(pml, pml), (pml, pml)]
+    return np.pad(model, pad, mode="edge")
+
+
+# --------------------------------------------------------------------------
+# Named workloads
+# --------------------------------------------------------------------------
+
+def workload_layered3():
+    """Acoustic forward, one shot: 200 x 200 + 40-cell CPML, nt = 1000."""
+    nz = nx = 200
+    return dict(nz=nz, nx=nx, pml=40, dx=10.0, dt=1e-3, nt=1000, f0=10.0,
+                model=layered3(nz, nx),
+                src=np.array([[2, 100]], dtype=np.int32),
+                rec=surface_line(1, 2, np.arange(200)))
+
+
+def workload_marmousi(nshot: int = 20, nt: int = 3000, seed: int = 1001):
+    """Acoustic forward + adjoint gradient: 301 x 901, nt = 3000, 20 shots."""
+    nz, nx = 301, 901
+    v_true, v0 = marmousi_like(nz, nx, seed)
+    sx = np.round(np.linspace(0, nx - 1, 20)).astype(np.int32)[:nshot]
+    src = np.stack([np.full_like(sx, 2), sx], axis=-1).astype(np.int32)
+    rec = surface_line(nshot, 2, np.arange(0, nx, 3))
+    return dict(nz=nz, nx=nx, pml=40, dx=10.0, dt=1e-3, nt=nt, f0=10.0,
+                v_true=v_true, model=v0, src=src, rec=rec)
+
+
+def workload_elastic(nshot: int = 64, nt: int = 4000, seed: int = 1002,
+                     nz: int = 500, nx: int = 1500):
+    """Elastic forward: 500 x 1500, dx = 5 m, dt = 0.5 ms, 64 shots, 750 receivers."""
+    m = elastic_layered(nz, nx, seed)
+    sx = np.round(np.linspace(0, nx - 1, 64)).astype(np.int32)[:nshot]
+    src = np.stack([np.full_like(sx, 2), sx], axis=-1).astype(np.int32)
+    rec = surface_line(nshot, 2, np.arange(0, nx, 2))
+    return dict(nz=nz, nx=nx, pml=40, dx=5.0, dt=5e-4, nt=nt, f0=15.0,
+                model=m, src=src, rec=rec)

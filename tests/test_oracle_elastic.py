@@ -1,0 +1,133 @@
+"""Pins of the FP64 elastic (velocity-stress, staggered) oracle.
+
+* exact conservation of the staggered-leapfrog energy
+  E^n = 1/2 <v^{n+1/2}, M v^{n-1/2}> + 1/2 <tau^n, C^{-1} tau^n>
+  without absorbing boundary (operators, averaging, Hooke's law);
+* with Vs = 0 the mean stress -1/2 (txx + tzz) is the acoustic pressure and
+  matches the closed-form 2D Green's function driven by -f'(t)
+  (scaling and timing of the explosive source);
+* in a homogeneous medium an explosive source radiates P waves only, so the
+  recorded particle velocities do not depend on Vs (signs of the shear terms);
+* the CPML absorbs (energy decays, no late growth).
+"""
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from paper_2604_14189_gb300 import inputs
+
+
+def _mats(vp, vs, rho):
+    """Mass and compliance of the staggered grid, as the engine defines them."""
+    lam = rho * (vp ** 2 - 2 * vs ** 2)
+    mu = rho * vs ** 2
+    rx = np.concatenate([rho[:, 1:], rho[:, -1:]], axis=1)
+    rz = np.concatenate([rho[1:, :], rho[-1:, :]], axis=0)
+    mx = 0.5 * (rho + rx)  # 1 / buoyancy at vx points
+    mz = 0.5 * (rho + rz)
+    m01 = np.concatenate([mu[:, 1:], mu[:, -1:]], axis=1)
+    m10 = np.concatenate([mu[1:, :], mu[-1:, :]], axis=0)
+    m11 = np.concatenate([m10[:, 1:], m10[:, -1:]], axis=1)
+    muxz = 4.0 / (1 / mu + 1 / m01 + 1 / m10 + 1 / m11)
+    return lam, mu, mx, mz, muxz
+
+
+def test_energy_conserved_without_pml():
+    rng = np.random.default_rng(17)
+    nz, nx, nt, dx, dt = 30, 36, 500, 5.0, 4e-4
+    vp = rng.uniform(2000, 3000, (nz, nx))
+    vs = vp / rng.uniform(1.6, 2.0, (nz, nx))
+    rho = rng.uniform(1800, 2600, (nz, nx))
+    w = np.zeros(nt)
+    w[:40] = inputs.ricker(60.0, dt, 40, t0=0.008)
+    p = oracle.make_problem(1, nz, nx, 0, dx, dt, nt, 1, 1, 30.0)
+    _, wf = oracle.elastic_forward(p, np.stack([vp, vs, rho]), w[None],
+                                   np.array([[15, 18]]), np.array([[[3, 3]]]),
+                                   wavefield=True)
+    f = wf[0]  # [nt+1][5][nz][nx]
+    lam, mu, mx, mz, muxz = _mats(vp, vs, rho)
+    l2m = lam + 2 * mu
+    det = l2m ** 2 - lam ** 2
+    E = []
+    for k in range(45, nt):
+        vx1, vz1 = f[k + 1, 0], f[k + 1, 1]   # v^{k+1/2}
+        vx0, vz0 = f[k, 0], f[k, 1]           # v^{k-1/2}
+        txx, tzz, txz = f[k, 2], f[k, 3], f[k, 4]  # tau^k
+        kin = 0.5 * np.sum(mx * vx1 * vx0 + mz * vz1 * vz0)
+        pot = 0.5 * np.sum((l2m * txx ** 2 - 2 * lam * txx * tzz + l2m * tzz ** 2) / det
+                           + txz ** 2 / muxz)
+        E.append(kin + pot)
+    E = np.array(E)
+    assert E[0] > 0
+    assert np.abs(E - E[0]).max() / E[0] < 1e-11
+
+
+def _green_pressure(fdot, r, v, ts):
+    """P(r,t) for P_tt = v^2 Lap P - f'(t) delta: the 2D Green's function with
+    source term v^2 g, g = -f'/v^2."""
+    out = np.zeros_like(ts)
+    for k, t in enumerate(ts):
+        if v * t > r:
+            val, _ = integrate.quad(lambda s: fdot(t - (r / v) * np.cosh(s)), 0.0,
+                                    np.arccosh(v * t / r), limit=200)
+            out[k] = -val / (2 * np.pi * v ** 2)
+    return out
+
+
+def test_zero_shear_pressure_matches_green_function():
+    f0, v, dx, T = 20.0, 2000.0, 5.0, 0.2
+    n = 161
+    dt = 2.5e-4
+    nt = int(round(T / dt))
+    vp = np.full((n, n), v)
+    model = np.stack([vp, 0 * vp, np.full((n, n), 1000.0)])
+    p = oracle.make_problem(1, n, n, 0, dx, dt, nt, 1, 1, f0)
+    # the stress update from n to n+1 is centred at (n + 1/2) dt
+    w = inputs.ricker(f0, dt, nt, shift=0.5)
+    _, wf = oracle.elastic_forward(p, model, w[None], np.array([[80, 80]]),
+                                   np.array([[[80, 120]]]), wavefield=True)
+    P = -0.5 * (wf[0, 1:, 2, 80, 120] + wf[0, 1:, 3, 80, 120])  # at t = (k+1) dt
+    ts = (np.arange(nt) + 1) * dt
+    t0 = 1.5 / f0
+
+    def rdot(t):
+        a = (np.pi * f0 * (t - t0)) ** 2
+        return np.exp(-a) * (-6 * np.pi ** 2 * f0 ** 2 * (t - t0) + 4 * np.pi ** 4
+                             * f0 ** 4 * (t - t0) ** 3)
+
+    a = _green_pressure(rdot, 40 * dx, v, ts)
+    err = np.linalg.norm(P - a) / np.linalg.norm(a)
+    assert err < 1.5e-2, err
+
+
+def test_explosive_source_traces_independent_of_vs():
+    f0, v, dx, dt, nt = 15.0, 2500.0, 5.0, 4e-4, 450
+    n = 120
+    out = []
+    for vs in (0.0, v / 1.73):
+        model = np.stack([np.full((n, n), v), np.full((n, n), vs), np.full((n, n), 2000.0)])
+        p = oracle.make_problem(1, n, n, 20, dx, dt, nt, 1, 3, f0)
+        d = oracle.elastic_forward(p, model, inputs.ricker(f0, dt, nt)[None],
+                                   np.array([[60, 60]]),
+                                   np.array([[[60, 100], [20, 60], [90, 90]]]))
+        out.append(d[0])
+    a, b = out
+    assert np.abs(a).max() > 0
+    assert np.linalg.norm(a - b) / np.linalg.norm(a) < 3e-2
+
+
+def test_elastic_cpml_absorbs():
+    nz = nx = 50
+    dx, dt, nt = 5.0, 4e-4, 2500
+    vp = np.full((nz, nx), 2500.0)
+    model = np.stack([vp, vp / 1.73, np.full((nz, nx), 2000.0)])
+    w = np.zeros(nt)
+    w[:200] = inputs.ricker(30.0, dt, 200)
+    p = oracle.make_problem(1, nz, nx, 20, dx, dt, nt, 1, 1, 30.0)
+    _, wf = oracle.elastic_forward(p, model, w[None], np.array([[25, 25]]),
+                                   np.array([[[0, 0]]]), wavefield=True)
+    e = np.array([np.sum(x[:2] ** 2) for x in wf[0]])
+    assert np.all(np.isfinite(e))
+    assert e[-1] < 1e-4 * e.max()
+    assert e[-1] < e[nt // 2]
