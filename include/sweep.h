@@ -1,0 +1,161 @@
+/*
+ * sweep.h -- C ABI of the GB300 (sm_103a) finite-difference wave solvers.
+ *
+ * The library implements the time-stepping hot path of SWEEP (Wang &
+ * Alkhalifah, "SWEEP: A Unified Solver Framework for Differentiable Wave
+ * Physics"): the Propagator / Source / Receiver modules of Sec. 2.1 for
+ *   - the constant-density acoustic equation, 2nd order in time (Sec. 3.1.2,
+ *     Eq. 2, stepped in the form of the Sec. 2.1 listing), 8th order in
+ *     space, with a convolutional PML;
+ *   - the isotropic elastic velocity-stress equations (Sec. 3.5, Eq. 12) on a
+ *     staggered grid, 4th order in space, with a convolutional PML;
+ * together with the exact discrete adjoint of the acoustic recurrence and the
+ * FWI velocity gradient of the L2 seismogram misfit (the adjoint-state use
+ * and dot-product test motivated in Sec. 1).  Batches of shots run in one
+ * launch per time step (Sec. 2.2).
+ *
+ * Conventions (the paper fixes none of them; these are the library's):
+ *   Grid      cell (z, x), row-major, x fastest, dz == dx.  The interior model
+ *             [nz][nx] is edge-replicated into a border of `pml` cells per
+ *             side, giving the padded grid NZ = nz + 2 pml, NX = nx + 2 pml.
+ *             Fields are zero outside the padded grid.
+ *   Acoustic  u^{n+1} = 2u^n - u^{n-1} + K (Lap_x + Lap_z), K = v^2 dt^2/dx^2,
+ *             where inside the border each axis term is
+ *             D2 u + D1 psi^{n-1} + zeta^n with
+ *             psi^n = a psi^{n-1} + b D1 u^n,
+ *             zeta^n = a zeta^{n-1} + b (D2 u + D1 psi^{n-1}).
+ *             Source: u^{n+1}(s) += K(s) f^n.  Trace sample n = u^{n+1}(r).
+ *   Elastic   vx at (z, x+1/2), vz at (z+1/2, x), txz at (z+1/2, x+1/2);
+ *             explosive source txx(s), tzz(s) += dt f^n / dx^2 after the
+ *             stress update of step n; trace sample n = (vx, vz)^{n+1/2}.
+ *   CPML      depth d (cells) into the border, rho = d / pml,
+ *             sigma = 3 vref ln(1000) / (2 pml dx) rho^2,
+ *             alpha = pi f_ref (1 - rho), a = exp(-(sigma + alpha) dt),
+ *             b = sigma / (sigma + alpha) (a - 1); vref = v_pml if > 0, else
+ *             the largest vp of the padded model.
+ *   Gradient  d misfit / d v on interior cells, padding and CPML profile held
+ *             fixed.  misfit = 1/2 sum (d - d_obs)^2, reduced in FP64.
+ *
+ * Memory: every array argument is a DEVICE pointer; only `prob` is a host
+ * pointer.  The caller owns all memory, including the workspace; the library
+ * never allocates device memory.  Calls are asynchronous on `stream` (a
+ * cudaStream_t, NULL = legacy default stream).
+ *
+ * Errors: a call returns SWEEP_OK or a negative code.  Errors visible on the
+ * host (sizes, NULL pointers, workspace too small, CFL with a given v_pml) are
+ * returned before any launch.  Errors that depend on device data (positions
+ * out of range, non-positive or non-finite model values, the CFL limit of the
+ * model's own maximum velocity, a non-finite misfit) are latched in the
+ * workspace status word by the kernels, which then skip all further work of
+ * that call; sweep_status() returns it.  Each call clears the status word of
+ * its workspace when it starts.  One workspace must not be used by two calls
+ * at once; different workspaces may be used concurrently.
+ */
+#ifndef SWEEP_H
+#define SWEEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { SWEEP_ACOUSTIC = 0, SWEEP_ELASTIC = 1 } sweep_physics;
+
+typedef enum {
+  SWEEP_MODE_FORWARD = 0,
+  SWEEP_MODE_ADJOINT = 1,
+  SWEEP_MODE_GRADIENT = 2
+} sweep_mode;
+
+/* model is passed on the padded grid [npar][NZ][NX] instead of [npar][nz][nx] */
+#define SWEEP_F_PADDED_MODEL 0x1
+/* sweep_gradient: d_obs holds the data residual r itself; the gradient is
+ * (dd/dv)^T r and misfit = 1/2 sum r^2 */
+#define SWEEP_F_RESIDUAL_IN 0x2
+
+enum {
+  SWEEP_OK = 0,
+  SWEEP_EINVAL = -1,      /* bad size, NULL pointer, unknown physics/mode  */
+  SWEEP_ECFL = -2,        /* v dt / dx above the scheme's stability limit  */
+  SWEEP_EBOUNDS = -3,     /* source or receiver outside the interior grid  */
+  SWEEP_EWORKSPACE = -4,  /* workspace NULL, misaligned or too small       */
+  SWEEP_ECUDA = -5,       /* a CUDA runtime call failed                    */
+  SWEEP_ETIMEOUT = -6,    /* a bounded device-side wait gave up            */
+  SWEEP_ENONFINITE = -7,  /* non-finite model value or misfit              */
+  SWEEP_EMODEL = -8,      /* non-positive velocity or density              */
+  SWEEP_EUNSUPPORTED = -9 /* combination not implemented                   */
+};
+
+typedef struct {
+  int32_t physics; /* sweep_physics                                          */
+  int32_t nz, nx;  /* interior grid, cells (>= 1)                            */
+  int32_t pml;     /* border width per side, cells (>= 0)                    */
+  float dx;        /* grid spacing, m (> 0); dz == dx                        */
+  float dt;        /* time step, s (> 0)                                     */
+  int32_t nt;      /* time steps == samples per trace (>= 1)                 */
+  int32_t nshot;   /* shots in the batch (>= 0)                              */
+  int32_t nrec;    /* receivers per shot (>= 0)                              */
+  float f_ref;     /* CPML alpha reference frequency, Hz (>= 0)              */
+  float v_pml;     /* CPML reference velocity, m/s; <= 0: max vp of model    */
+  int32_t flags;   /* SWEEP_F_*                                              */
+} sweep_problem;
+
+/* Bytes of device workspace a call of `mode` needs for `prob` (0 on invalid
+ * input).  The workspace must be 256-byte aligned. */
+size_t sweep_workspace_bytes(const sweep_problem* prob, int mode);
+
+/* Forward modelling (Sec. 2.1 Propagator + Source + Receiver; Eq. 2 or 12).
+ *   model    acoustic [nz][nx] vp (m/s); elastic [3][nz][nx] = (vp, vs, rho)
+ *            (m/s, m/s, kg/m^3); padded grid with SWEEP_F_PADDED_MODEL
+ *   wavelet  [nshot][nt] source time function samples f^n
+ *   src      [nshot][2] int32 (z, x) interior cell of each shot's source
+ *   rec      [nshot][nrec][2] int32 (z, x) interior receiver cells
+ *   data     out [nshot][ncomp][nrec][nt]; ncomp = 1 (u) or 2 (vx, vz)   */
+int sweep_forward(const sweep_problem* prob, const float* model,
+                  const float* wavelet, const int32_t* src, const int32_t* rec,
+                  float* data, void* ws, size_t ws_bytes, void* stream);
+
+/* Adjoint of the linear map wavelet -> data at fixed model (acoustic only):
+ * wavelet_grad[s][n] = sum_{r,m} adj_data[s][r][m] d data[s][r][m]/d f_s^n.
+ * The dot-product test <F f, d> = <f, F^T d> holds to rounding.            */
+int sweep_adjoint(const sweep_problem* prob, const float* model,
+                  const float* adj_data, const int32_t* src,
+                  const int32_t* rec, float* wavelet_grad, void* ws,
+                  size_t ws_bytes, void* stream);
+
+/* FWI velocity gradient (acoustic only): forward with boundary saving, L2
+ * residual, adjoint propagation with wavefield reconstruction and the imaging
+ * condition g = (2/v) sum_n mu^{n+1} (Lap u^n + f^n delta_s), mu = K lambda.
+ *   d_obs    [nshot][1][nrec][nt] observed data (or residual, see flags)
+ *   grad     out [nz][nx] dJ/dv, summed over shots (FP64 sum, FP32 result)
+ *   misfit   out device double, J = 1/2 sum r^2 (may be NULL)
+ *   illum    out [nz][nx] sum over shots and steps of u^2 (may be NULL)   */
+int sweep_gradient(const sweep_problem* prob, const float* model,
+                   const float* wavelet, const int32_t* src, const int32_t* rec,
+                   const float* d_obs, float* grad, double* misfit, float* illum,
+                   void* ws, size_t ws_bytes, void* stream);
+
+/* FP64 dot product sum_i a[i] b[i] of two device float arrays into the device
+ * double *out (for dot-product and finite-difference tests).  ws: at least
+ * sweep_dot_workspace_bytes() bytes of device scratch. */
+size_t sweep_dot_workspace_bytes(void);
+int sweep_dot(const float* a, const float* b, int64_t n, double* out, void* ws,
+              size_t ws_bytes, void* stream);
+
+/* Synchronises `stream` and returns the status word latched in `ws` by the
+ * last call that used it (SWEEP_OK or a negative code). */
+int sweep_status(void* ws, void* stream);
+
+/* Static description of a code. */
+const char* sweep_strerror(int code);
+
+/* Number of kernels this library has launched in this process so far
+ * (monotone counter, for accounting launches per step). */
+unsigned long long sweep_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,406 @@
+// Host side of the C ABI declared in include/sweep.h: argument validation,
+// workspace layout, and the time loops that launch the step kernels (the
+// Propagator of Sec. 2.1).  No device memory is allocated here: every buffer
+// is carved out of the caller's workspace.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+
+#include "sweep_internal.cuh"
+
+namespace sweep {
+
+std::atomic<unsigned long long> g_launches{0};
+void note_launches(int k) { g_launches.fetch_add((unsigned long long)k); }
+
+namespace {
+
+// Stability limits of the two schemes (leapfrog in time):
+//   acoustic 8th order: v dt/dx <= 2 / sqrt(2 * 6.5015873) (Nyquist symbol of D2)
+//   elastic 4th-order staggered: v dt/dx <= 1 / (sqrt(2) (9/8 + 1/24))
+constexpr float kCflAcoustic = 0.5546324f;
+constexpr float kCflElastic = 0.6060915f;
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t status = 0, partial = 0, vmax = 0, K = 0;
+  size_t ax = 0, bx = 0, az = 0, bz = 0, axh = 0, bxh = 0, azh = 0, bzh = 0;
+  size_t u[2] = {0, 0}, psx[2] = {0, 0}, psz[2] = {0, 0}, zex = 0, zez = 0;
+  size_t m[2] = {0, 0}, pbx[2] = {0, 0}, pbz[2] = {0, 0}, zbx[2] = {0, 0}, zbz[2] = {0, 0};
+  size_t data = 0, save = 0, graw = 0, iraw = 0;
+  size_t fwd_lo = 0, fwd_hi = 0;  // contiguous range of forward fields
+  size_t adj_lo = 0, adj_hi = 0;  // contiguous range of adjoint fields
+  size_t total = 0;
+};
+
+struct Bump {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  }
+};
+
+Geom make_geom(const sweep_problem* p) {
+  Geom g{};
+  g.nz = p->nz;
+  g.nx = p->nx;
+  g.P = p->pml;
+  g.NZ = p->nz + 2 * p->pml;
+  g.NX = p->nx + 2 * p->pml;
+  g.NXp = (g.NX + 31) / 32 * 32;
+  g.nshot = p->nshot;
+  g.nrec = p->nrec;
+  g.nt = p->nt;
+  g.ringw = p->pml < 4 ? p->pml : 4;
+  const int w = g.ringw;
+  g.nring = 2 * w * (g.nx + 2 * w) + 2 * g.nz * w;
+  g.fstride = (long long)g.NZ * g.NXp;
+  return g;
+}
+
+bool valid_problem(const sweep_problem* p) {
+  if (!p) return false;
+  if (p->physics != SWEEP_ACOUSTIC && p->physics != SWEEP_ELASTIC) return false;
+  if (p->nz < 1 || p->nx < 1 || p->pml < 0 || p->nt < 1 || p->nshot < 0 || p->nrec < 0)
+    return false;
+  if (!(p->dx > 0.f) || !std::isfinite(p->dx)) return false;
+  if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return false;
+  if (!(p->f_ref >= 0.f) || !std::isfinite(p->f_ref)) return false;
+  if (!std::isfinite(p->v_pml)) return false;
+  // keep every per-shot index within 32-bit loops where they are used
+  const long long NZ = (long long)p->nz + 2LL * p->pml, NX = (long long)p->nx + 2LL * p->pml;
+  if (NZ > (1 << 20) || NX > (1 << 20) || NZ * NX > (1LL << 31)) return false;
+  if (p->nshot > 65535) return false;  // gridDim.z
+  return true;
+}
+
+Layout layout(const sweep_problem* p, int mode) {
+  const Geom g = make_geom(p);
+  Layout L;
+  Bump b;
+  const size_t F = sizeof(float) * (size_t)g.fstride * (size_t)g.nshot;
+  L.status = b.take(sizeof(int) * 4);
+  L.vmax = b.take(sizeof(unsigned int));
+  L.partial = b.take(sizeof(double) * RED_BLOCKS);
+  L.K = b.take(sizeof(float) * (size_t)g.fstride);
+  L.ax = b.take(sizeof(float) * g.NXp);
+  L.bx = b.take(sizeof(float) * g.NXp);
+  L.az = b.take(sizeof(float) * g.NZ);
+  L.bz = b.take(sizeof(float) * g.NZ);
+  L.axh = b.take(sizeof(float) * g.NXp);
+  L.bxh = b.take(sizeof(float) * g.NXp);
+  L.azh = b.take(sizeof(float) * g.NZ);
+  L.bzh = b.take(sizeof(float) * g.NZ);
+  if (mode == SWEEP_MODE_FORWARD || mode == SWEEP_MODE_GRADIENT) {
+    L.fwd_lo = b.off;
+    L.u[0] = b.take(F);
+    L.u[1] = b.take(F);
+    L.psx[0] = b.take(F);
+    L.psx[1] = b.take(F);
+    L.psz[0] = b.take(F);
+    L.psz[1] = b.take(F);
+    L.zex = b.take(F);
+    L.zez = b.take(F);
+    L.fwd_hi = b.off;
+  }
+  if (mode == SWEEP_MODE_ADJOINT || mode == SWEEP_MODE_GRADIENT) {
+    L.adj_lo = b.off;
+    L.m[0] = b.take(F);
+    L.m[1] = b.take(F);
+    L.pbx[0] = b.take(F);
+    L.pbx[1] = b.take(F);
+    L.pbz[0] = b.take(F);
+    L.pbz[1] = b.take(F);
+    L.zbx[0] = b.take(F);
+    L.zbx[1] = b.take(F);
+    L.zbz[0] = b.take(F);
+    L.zbz[1] = b.take(F);
+    L.adj_hi = b.off;
+  }
+  if (mode == SWEEP_MODE_GRADIENT) {
+    const size_t nint = (size_t)g.nz * g.nx * (size_t)g.nshot;
+    L.data = b.take(sizeof(float) * (size_t)g.nshot * g.nrec * g.nt);
+    L.save = b.take(sizeof(float) * ((size_t)g.nt + 1) * g.nshot * g.nring);
+    L.graw = b.take(sizeof(float) * nint);
+    L.iraw = b.take(sizeof(float) * nint);
+  }
+  L.total = b.off;
+  return L;
+}
+
+template <class T>
+T* at(void* ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+int check_ws(const sweep_problem* p, int mode, void* ws, size_t ws_bytes) {
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return SWEEP_EWORKSPACE;
+  if (ws_bytes < layout(p, mode).total) return SWEEP_EWORKSPACE;
+  return SWEEP_OK;
+}
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? SWEEP_OK : SWEEP_ECUDA; }
+
+SetupArgs setup_args(const sweep_problem* p, const Layout& L, void* ws, const float* model,
+                     const int32_t* src, const int32_t* rec) {
+  SetupArgs s{};
+  s.g = make_geom(p);
+  s.physics = p->physics;
+  s.model = model;
+  s.padded = (p->flags & SWEEP_F_PADDED_MODEL) ? 1 : 0;
+  s.dx = p->dx;
+  s.dt = p->dt;
+  s.f_ref = p->f_ref;
+  s.v_pml = p->v_pml;
+  s.cfl_limit = p->physics == SWEEP_ELASTIC ? kCflElastic : kCflAcoustic;
+  s.src = src;
+  s.rec = rec;
+  s.K = at<float>(ws, L.K);
+  s.ax = at<float>(ws, L.ax);
+  s.bx = at<float>(ws, L.bx);
+  s.az = at<float>(ws, L.az);
+  s.bz = at<float>(ws, L.bz);
+  if (p->physics == SWEEP_ELASTIC) {
+    s.axh = at<float>(ws, L.axh);
+    s.bxh = at<float>(ws, L.bxh);
+    s.azh = at<float>(ws, L.azh);
+    s.bzh = at<float>(ws, L.bzh);
+  }
+  s.vmax_bits = at<unsigned int>(ws, L.vmax);
+  s.status = at<int>(ws, L.status);
+  return s;
+}
+
+// Forward time loop of the acoustic engine.  On return the workspace holds
+// u^{nt} in u[nt % 2] and u^{nt-1} in u[(nt + 1) % 2].
+void acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
+                           const float* wavelet, const int32_t* src, const int32_t* rec,
+                           float* data, bool save_ring, cudaStream_t st) {
+  const Geom g = make_geom(p);
+  cudaMemsetAsync(at<char>(ws, L.fwd_lo), 0, L.fwd_hi - L.fwd_lo, st);
+  AcFwdArgs a{};
+  a.g = g;
+  a.K = at<float>(ws, L.K);
+  a.zex = at<float>(ws, L.zex);
+  a.zez = at<float>(ws, L.zez);
+  a.ax = at<float>(ws, L.ax);
+  a.bx = at<float>(ws, L.bx);
+  a.az = at<float>(ws, L.az);
+  a.bz = at<float>(ws, L.bz);
+  a.wavelet = wavelet;
+  a.src = src;
+  a.rec = rec;
+  a.data = data;
+  a.status = at<int>(ws, L.status);
+  float* save = save_ring ? at<float>(ws, L.save) : nullptr;
+  if (save) cudaMemsetAsync(save, 0, sizeof(float) * (size_t)g.nshot * g.nring, st);
+  for (int n = 0; n < g.nt; ++n) {
+    a.n = n;
+    a.u = at<float>(ws, L.u[n & 1]);
+    a.un = at<float>(ws, L.u[(n + 1) & 1]);
+    a.psx_in = at<float>(ws, L.psx[n & 1]);
+    a.psx_out = at<float>(ws, L.psx[(n + 1) & 1]);
+    a.psz_in = at<float>(ws, L.psz[n & 1]);
+    a.psz_out = at<float>(ws, L.psz[(n + 1) & 1]);
+    a.save = save ? save + (size_t)(n + 1) * g.nshot * g.nring : nullptr;
+    launch_ac_fwd(a, st);
+  }
+  note_launches(g.nt);
+}
+
+// Backward loop: adjoint propagation from the residual `res`; optionally the
+// imaging condition with wavefield reconstruction (gradient) and/or the
+// adjoint source gather (wgrad).
+void acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
+                            const float* wavelet, const int32_t* src, const int32_t* rec,
+                            const float* res, float* wgrad, bool imaging, bool illum,
+                            cudaStream_t st) {
+  const Geom g = make_geom(p);
+  cudaMemsetAsync(at<char>(ws, L.adj_lo), 0, L.adj_hi - L.adj_lo, st);
+  const size_t nint = (size_t)g.nz * g.nx * (size_t)g.nshot;
+  if (imaging) {
+    cudaMemsetAsync(at<float>(ws, L.graw), 0, sizeof(float) * nint, st);
+    if (illum) cudaMemsetAsync(at<float>(ws, L.iraw), 0, sizeof(float) * nint, st);
+  }
+  AcBwdArgs a{};
+  a.g = g;
+  a.K = at<float>(ws, L.K);
+  a.ax = at<float>(ws, L.ax);
+  a.bx = at<float>(ws, L.bx);
+  a.az = at<float>(ws, L.az);
+  a.bz = at<float>(ws, L.bz);
+  a.wavelet = wavelet;
+  a.src = src;
+  a.rec = rec;
+  a.res = res;
+  a.graw = imaging ? at<float>(ws, L.graw) : nullptr;
+  a.illum = (imaging && illum) ? at<float>(ws, L.iraw) : nullptr;
+  a.wgrad = wgrad;
+  a.status = at<int>(ws, L.status);
+  float* save = imaging ? at<float>(ws, L.save) : nullptr;
+  for (int n = g.nt; n >= 0; --n) {
+    a.n = n;
+    a.do_adj = n >= 1;
+    a.do_img = imaging && n <= g.nt - 1;
+    a.do_rec = imaging && n >= 1 && n <= g.nt - 1;
+    a.uA = imaging ? at<float>(ws, L.u[n & 1]) : nullptr;
+    a.uB = imaging ? at<float>(ws, L.u[(n + 1) & 1]) : nullptr;
+    a.mA = at<float>(ws, L.m[(n + 1) & 1]);
+    a.mB = at<float>(ws, L.m[n & 1]);
+    a.pbx_in = at<float>(ws, L.pbx[n & 1]);
+    a.pbx_out = at<float>(ws, L.pbx[(n + 1) & 1]);
+    a.pbz_in = at<float>(ws, L.pbz[n & 1]);
+    a.pbz_out = at<float>(ws, L.pbz[(n + 1) & 1]);
+    a.zbx_in = at<float>(ws, L.zbx[n & 1]);
+    a.zbx_out = at<float>(ws, L.zbx[(n + 1) & 1]);
+    a.zbz_in = at<float>(ws, L.zbz[n & 1]);
+    a.zbz_out = at<float>(ws, L.zbz[(n + 1) & 1]);
+    a.save = (save && n >= 1) ? save + (size_t)(n - 1) * g.nshot * g.nring : nullptr;
+    launch_ac_bwd(a, st);
+  }
+  note_launches(g.nt + 1);
+}
+
+}  // namespace
+}  // namespace sweep
+
+using namespace sweep;
+
+extern "C" {
+
+size_t sweep_workspace_bytes(const sweep_problem* prob, int mode) {
+  if (!valid_problem(prob)) return 0;
+  if (mode < SWEEP_MODE_FORWARD || mode > SWEEP_MODE_GRADIENT) return 0;
+  return layout(prob, mode).total;
+}
+
+static int begin(const sweep_problem* p, int mode, void* ws, size_t ws_bytes,
+                 cudaStream_t st) {
+  if (!valid_problem(p)) return SWEEP_EINVAL;
+  int rc = check_ws(p, mode, ws, ws_bytes);
+  if (rc) return rc;
+  const Layout L = layout(p, mode);
+  return cuda_rc(cudaMemsetAsync(at<int>(ws, L.status), 0, sizeof(int), st));
+}
+
+int sweep_forward(const sweep_problem* p, const float* model, const float* wavelet,
+                  const int32_t* src, const int32_t* rec, float* data, void* ws,
+                  size_t ws_bytes, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = begin(p, SWEEP_MODE_FORWARD, ws, ws_bytes, st);
+  if (rc) return rc;
+  if (!model) return SWEEP_EINVAL;
+  if (p->nshot > 0 && (!wavelet || !src)) return SWEEP_EINVAL;
+  if (p->nshot > 0 && p->nrec > 0 && (!rec || !data)) return SWEEP_EINVAL;
+  if (p->physics != SWEEP_ACOUSTIC) return SWEEP_EUNSUPPORTED;
+  if (p->nshot == 0) return SWEEP_OK;
+  const Layout L = layout(p, SWEEP_MODE_FORWARD);
+  launch_setup(setup_args(p, L, ws, model, src, rec), st);
+  note_launches(2);
+  acoustic_forward_loop(p, L, ws, wavelet, src, rec, p->nrec > 0 ? data : nullptr, false, st);
+  return cuda_rc(cudaGetLastError());
+}
+
+int sweep_adjoint(const sweep_problem* p, const float* model, const float* adj_data,
+                  const int32_t* src, const int32_t* rec, float* wavelet_grad, void* ws,
+                  size_t ws_bytes, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = begin(p, SWEEP_MODE_ADJOINT, ws, ws_bytes, st);
+  if (rc) return rc;
+  if (!model) return SWEEP_EINVAL;
+  if (p->nshot > 0 && (!src || !wavelet_grad)) return SWEEP_EINVAL;
+  if (p->nshot > 0 && p->nrec > 0 && (!rec || !adj_data)) return SWEEP_EINVAL;
+  if (p->physics != SWEEP_ACOUSTIC) return SWEEP_EUNSUPPORTED;
+  if (p->nshot == 0) return SWEEP_OK;
+  const Layout L = layout(p, SWEEP_MODE_ADJOINT);
+  launch_setup(setup_args(p, L, ws, model, src, rec), st);
+  note_launches(2);
+  // no imaging: the backward kernel never reads the wavelet
+  acoustic_backward_loop(p, L, ws, nullptr, src, rec, adj_data, wavelet_grad, false, false, st);
+  return cuda_rc(cudaGetLastError());
+}
+
+int sweep_gradient(const sweep_problem* p, const float* model, const float* wavelet,
+                   const int32_t* src, const int32_t* rec, const float* d_obs, float* grad,
+                   double* misfit, float* illum, void* ws, size_t ws_bytes, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = begin(p, SWEEP_MODE_GRADIENT, ws, ws_bytes, st);
+  if (rc) return rc;
+  if (!model || !grad) return SWEEP_EINVAL;
+  if (p->nshot > 0 && (!wavelet || !src)) return SWEEP_EINVAL;
+  if (p->nshot > 0 && p->nrec > 0 && (!rec || !d_obs)) return SWEEP_EINVAL;
+  if (p->physics != SWEEP_ACOUSTIC) return SWEEP_EUNSUPPORTED;
+  const Geom g = make_geom(p);
+  if (p->nshot == 0) {
+    cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)g.nz * g.nx, st);
+    if (illum) cudaMemsetAsync(illum, 0, sizeof(float) * (size_t)g.nz * g.nx, st);
+    if (misfit) cudaMemsetAsync(misfit, 0, sizeof(double), st);
+    return cuda_rc(cudaGetLastError());
+  }
+  const Layout L = layout(p, SWEEP_MODE_GRADIENT);
+  launch_setup(setup_args(p, L, ws, model, src, rec), st);
+  note_launches(2);
+  float* d = at<float>(ws, L.data);
+  acoustic_forward_loop(p, L, ws, wavelet, src, rec, p->nrec > 0 ? d : nullptr, true, st);
+  const long long nd = (long long)g.nshot * g.nrec * g.nt;
+  launch_residual_misfit(d, d_obs, d, nd, (p->flags & SWEEP_F_RESIDUAL_IN) ? 1 : 0,
+                         at<double>(ws, L.partial), RED_BLOCKS, misfit, at<int>(ws, L.status),
+                         st);
+  note_launches(2);
+  acoustic_backward_loop(p, L, ws, wavelet, src, rec, d, nullptr, true, illum != nullptr, st);
+  launch_grad_reduce(g, at<float>(ws, L.graw), illum ? at<float>(ws, L.iraw) : nullptr, model,
+                     (p->flags & SWEEP_F_PADDED_MODEL) ? 1 : 0, grad, illum,
+                     at<int>(ws, L.status), st);
+  note_launches(1);
+  return cuda_rc(cudaGetLastError());
+}
+
+size_t sweep_dot_workspace_bytes(void) { return sizeof(double) * RED_BLOCKS; }
+
+int sweep_dot(const float* a, const float* b, int64_t n, double* out, void* ws,
+              size_t ws_bytes, void* stream) {
+  if (n < 0 || !out || (n > 0 && (!a || !b))) return SWEEP_EINVAL;
+  if (!ws || ws_bytes < sweep_dot_workspace_bytes() ||
+      (reinterpret_cast<uintptr_t>(ws) % 8) != 0)
+    return SWEEP_EWORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  launch_dot(a, b, n, static_cast<double*>(ws), RED_BLOCKS, out, st);
+  note_launches(2);
+  return cuda_rc(cudaGetLastError());
+}
+
+int sweep_status(void* ws, void* stream) {
+  if (!ws) return SWEEP_EWORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ws, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return SWEEP_ECUDA;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return SWEEP_ECUDA;
+  return h;
+}
+
+unsigned long long sweep_kernel_launches(void) { return g_launches.load(); }
+
+const char* sweep_strerror(int code) {
+  switch (code) {
+    case SWEEP_OK: return "ok";
+    case SWEEP_EINVAL: return "invalid argument";
+    case SWEEP_ECFL: return "time step above the stability (CFL) limit";
+    case SWEEP_EBOUNDS: return "source or receiver outside the interior grid";
+    case SWEEP_EWORKSPACE: return "workspace missing, misaligned or too small";
+    case SWEEP_ECUDA: return "CUDA runtime error";
+    case SWEEP_ETIMEOUT: return "bounded device-side wait timed out";
+    case SWEEP_ENONFINITE: return "non-finite model value or misfit";
+    case SWEEP_EMODEL: return "non-physical model value";
+    case SWEEP_EUNSUPPORTED: return "not implemented for this physics";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+"""Thin ctypes binding of the C ABI in ``include/sweep.h`` (``libsweep.so``).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Tensors must be CUDA tensors (float32 / int32, contiguous);
+PyTorch supplies device memory and the current stream.  There is no CPU
+fallback: importing this module fails if the library cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+ACOUSTIC = 0
+ELASTIC = 1
+MODE_FORWARD = 0
+MODE_ADJOINT = 1
+MODE_GRADIENT = 2
+F_PADDED_MODEL = 0x1
+F_RESIDUAL_IN = 0x2
+
+OK = 0
+EINVAL, ECFL, EBOUNDS, EWORKSPACE, ECUDA, ETIMEOUT, ENONFINITE, EMODEL, EUNSUPPORTED = (
+    -1, -2, -3, -4, -5, -6, -7, -8, -9)
+
+# Every symbol declared in include/sweep.h.
+EXPORTS = ("sweep_workspace_bytes", "sweep_forward", "sweep_adjoint", "sweep_gradient",
+           "sweep_dot_workspace_bytes", "sweep_dot", "sweep_status", "sweep_strerror",
+           "sweep_kernel_launches")
+
+
+class Problem(ctypes.Structure):
+    """Mirror of ``sweep_problem``."""
+    _fields_ = [
+        ("physics", ctypes.c_int32),
+        ("nz", ctypes.c_int32),
+        ("nx", ctypes.c_int32),
+        ("pml", ctypes.c_int32),
+        ("dx", ctypes.c_float),
+        ("dt", ctypes.c_float),
+        ("nt", ctypes.c_int32),
+        ("nshot", ctypes.c_int32),
+        ("nrec", ctypes.c_int32),
+        ("f_ref", ctypes.c_float),
+        ("v_pml", ctypes.c_float),
+        ("flags", ctypes.c_int32),
+    ]
+
+    def __repr__(self):
+        return "Problem(" + ", ".join(f"{n}={getattr(self, n)}" for n, _ in self._fields_) + ")"
+
+
+def problem(physics=ACOUSTIC, *, nz, nx, pml, dx, dt, nt, nshot, nrec, f_ref=10.0,
+            v_pml=0.0, flags=0) -> Problem:
+    return Problem(physics, nz, nx, pml, dx, dt, nt, nshot, nrec, f_ref, v_pml, flags)
+
+
+class SweepError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (code {code})")
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libsweep.so (building it first if missing)."""
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, sz, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+    P = ctypes.POINTER(Problem)
+    lib.sweep_workspace_bytes.argtypes = [P, i32]
+    lib.sweep_workspace_bytes.restype = sz
+    lib.sweep_forward.argtypes = [P, vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.sweep_forward.restype = i32
+    lib.sweep_adjoint.argtypes = [P, vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.sweep_adjoint.restype = i32
+    lib.sweep_gradient.argtypes = [P, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.sweep_gradient.restype = i32
+    lib.sweep_dot_workspace_bytes.argtypes = []
+    lib.sweep_dot_workspace_bytes.restype = sz
+    lib.sweep_dot.argtypes = [vp, vp, ctypes.c_int64, vp, vp, sz, vp]
+    lib.sweep_dot.restype = i32
+    lib.sweep_status.argtypes = [vp, vp]
+    lib.sweep_status.restype = i32
+    lib.sweep_strerror.argtypes = [i32]
+    lib.sweep_strerror.restype = ctypes.c_char_p
+    lib.sweep_kernel_launches.argtypes = []
+    lib.sweep_kernel_launches.restype = ctypes.c_ulonglong
+    return lib
+
+
+_lib = load_library()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return _lib.sweep_strerror(int(code)).decode()
+
+
+def kernel_launches() -> int:
+    return int(_lib.sweep_kernel_launches())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("sweep: tensors must live on the GPU")
+    if not t.is_contiguous():
+        raise ValueError("sweep: tensors must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_dtype(t, dt, name):
+    if t is not None and t.dtype != dt:
+        raise TypeError(f"sweep: {name} must be {dt}, got {t.dtype}")
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def workspace_bytes(p: Problem, mode: int) -> int:
+    n = int(_lib.sweep_workspace_bytes(ctypes.byref(p), mode))
+    if n == 0:
+        raise SweepError(EINVAL, "sweep_workspace_bytes")
+    return n
+
+
+def alloc_workspace(p: Problem, mode: int, device=None) -> torch.Tensor:
+    """A uint8 CUDA tensor big enough (and 256-byte aligned) for `mode`."""
+    n = workspace_bytes(p, mode)
+    ws = torch.empty(n + 256, dtype=torch.uint8, device=device or "cuda")
+    off = (-ws.data_ptr()) % 256
+    return ws[off:off + n]
+
+
+def _ws_args(ws):
+    return ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel())
+
+
+def status(ws: torch.Tensor, stream=None) -> int:
+    return int(_lib.sweep_status(ctypes.c_void_p(ws.data_ptr()), _stream(stream)))
+
+
+def _finish(rc, ws, where, stream, sync):
+    if rc != OK:
+        raise SweepError(rc, where)
+    if sync:
+        st = status(ws, stream)
+        if st != OK:
+            raise SweepError(st, where)
+
+
+def sweep_forward(p: Problem, model, wavelet, src, rec, data=None, ws=None, stream=None,
+                  sync=True):
+    """data [nshot][ncomp][nrec][nt] (float32, CUDA)."""
+    _check_dtype(model, torch.float32, "model")
+    _check_dtype(wavelet, torch.float32, "wavelet")
+    _check_dtype(src, torch.int32, "src")
+    _check_dtype(rec, torch.int32, "rec")
+    ncomp = 2 if p.physics == ELASTIC else 1
+    if data is None:
+        data = torch.empty((p.nshot, ncomp, p.nrec, p.nt), dtype=torch.float32,
+                           device=model.device)
+    if ws is None:
+        ws = alloc_workspace(p, MODE_FORWARD, model.device)
+    w, wn = _ws_args(ws)
+    rc = _lib.sweep_forward(ctypes.byref(p), _ptr(model), _ptr(wavelet), _ptr(src), _ptr(rec),
+                            _ptr(data), w, wn, _stream(stream))
+    _finish(rc, ws, "sweep_forward", stream, sync)
+    return data
+
+
+def sweep_adjoint(p: Problem, model, adj_data, src, rec, wavelet_grad=None, ws=None,
+                  stream=None, sync=True):
+    """wavelet_grad [nshot][nt]."""
+    _check_dtype(model, torch.float32, "model")
+    _check_dtype(adj_data, torch.float32, "adj_data")
+    if wavelet_grad is None:
+        wavelet_grad = torch.empty((p.nshot, p.nt), dtype=torch.float32, device=model.device)
+    if ws is None:
+        ws = alloc_workspace(p, MODE_ADJOINT, model.device)
+    w, wn = _ws_args(ws)
+    rc = _lib.sweep_adjoint(ctypes.byref(p), _ptr(model), _ptr(adj_data), _ptr(src), _ptr(rec),
+                            _ptr(wavelet_grad), w, wn, _stream(stream))
+    _finish(rc, ws, "sweep_adjoint", stream, sync)
+    return wavelet_grad
+
+
+def sweep_gradient(p: Problem, model, wavelet, src, rec, d_obs, grad=None, misfit=None,
+                   illum=None, want_illum=False, ws=None, stream=None, sync=True):
+    """Returns (grad [nz][nx], misfit (device float64 scalar), illum or None)."""
+    _check_dtype(model, torch.float32, "model")
+    _check_dtype(d_obs, torch.float32, "d_obs")
+    dev = model.device
+    if grad is None:
+        grad = torch.empty((p.nz, p.nx), dtype=torch.float32, device=dev)
+    if misfit is None:
+        misfit = torch.empty((), dtype=torch.float64, device=dev)
+    if illum is None and want_illum:
+        illum = torch.empty((p.nz, p.nx), dtype=torch.float32, device=dev)
+    if ws is None:
+        ws = alloc_workspace(p, MODE_GRADIENT, dev)
+    w, wn = _ws_args(ws)
+    rc = _lib.sweep_gradient(ctypes.byref(p), _ptr(model), _ptr(wavelet), _ptr(src), _ptr(rec),
+                             _ptr(d_obs), _ptr(grad), _ptr(misfit), _ptr(illum), w, wn,
+                             _stream(stream))
+    _finish(rc, ws, "sweep_gradient", stream, sync)
+    return grad, misfit, illum
+
+
+_dot_ws = {}
+
+
+def sweep_dot(a, b, out=None, stream=None):
+    """FP64 sum(a * b) of two float32 CUDA tensors, as a device float64 scalar."""
+    _check_dtype(a, torch.float32, "a")
+    _check_dtype(b, torch.float32, "b")
+    if a.numel() != b.numel():
+        raise ValueError("sweep_dot: size mismatch")
+    dev = a.device
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=dev)
+    key = (dev.index if dev.index is not None else torch.cuda.current_device())
+    ws = _dot_ws.get(key)
+    if ws is None:
+        ws = torch.empty(int(_lib.sweep_dot_workspace_bytes()), dtype=torch.uint8, device=dev)
+        _dot_ws[key] = ws
+    w, wn = _ws_args(ws)
+    rc = _lib.sweep_dot(_ptr(a), _ptr(b), ctypes.c_int64(a.numel()), _ptr(out), w, wn,
+                        _stream(stream))
+    if rc != OK:
+        raise SweepError(rc, "sweep_dot")
+    return out
