@@ -1,0 +1,383 @@
+"""Benchmark of the acoustic forward + adjoint gradient (one JSON line).
+
+Workload: acoustic FWI gradient on a 301 x 901 interior grid (+ 40-cell CPML
+per side, 381 x 981 padded), dx = 10 m, dt = 1 ms, nt = 3000, 20 shots at the
+surface, 301 receivers every 3 cells, 10 Hz Ricker; the model is the seeded
+layered + Gaussian-anomaly starting model, d_obs the forward data of the true
+model (synthetic).  One step = one sweep_gradient call: forward with ring
+saving, residual + FP64 misfit, backward with reconstruction + imaging, FP64
+shot sum.  value = padded cells x nt x shots x ranks / step time (Gpts/s).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sweep|reference]
+
+Under torchrun (N > 1) every rank runs its own 20-shot batch (weak scaling)
+and the gradients and misfits are summed over ranks with one all-reduce per
+step (the shot sum, the only exchange of the method).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2604_14189_gb300 import inputs  # noqa: E402
+
+METRIC = "Gpts/s fwd+adj"
+UNIT = "Gpts/s"
+FALLBACK_HBM_GBS = 6800.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ac_bwd_marmousi.txt")
+
+
+def workload_desc(w, nshot):
+    return (f"acoustic fwd+adj gradient {w['nz']}x{w['nx']} + {w['pml']}-cell CPML, "
+            f"dx {w['dx']:g} m, dt {w['dt'] * 1e3:g} ms, nt {w['nt']}, {nshot} shots, "
+            f"{w['rec'].shape[1]} receivers, {w['f0']:g} Hz Ricker")
+
+
+def counts(nz, nx, P):
+    """Cell counts of the padded grid: padded, interior, x-border strip
+    cells (2P x NZ), z-border strip cells (2P x NX), saved ring."""
+    NZ, NX = nz + 2 * P, nx + 2 * P
+    w = min(P, 4)
+    return dict(N_pad=NZ * NX, N_int=nz * nx, N_x=2 * P * NZ, N_z=2 * P * NX,
+                N_ring=2 * w * (nx + 2 * w) + 2 * nz * w)
+
+
+def alg_bytes_bwd(c):
+    """Algorithmic bytes of one backward step per shot (FP32): reconstruction
+    reads u^n, u^{n+1}, K and writes u^{n-1} on the interior; the adjoint
+    reads mu^{n+1}, mu^{n+2}, K and writes mu^n on the padded grid (K shared
+    with the reconstruction inside); g is read and written on the interior;
+    4 adjoint memory variables per border strip cell per axis; ring read."""
+    return (20 * c["N_int"] + 16 * c["N_pad"] + 16 * (c["N_x"] + c["N_z"]) + 4 * c["N_ring"])
+
+
+def alg_bytes_fwd(c):
+    return 16 * c["N_pad"] + 16 * (c["N_x"] + c["N_z"]) + 4 * c["N_ring"]
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2604_14189_gb300", "csrc"))):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(ROOT, "paper_2604_14189_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic():
+    """ncu DRAM bytes per launch of the backward kernel, if the committed
+    summary was taken on the current kernel sources."""
+    try:
+        kv = {}
+        for line in open(TRAFFIC_FILE):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_hash") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def peaks():
+    try:
+        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(m["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        loaded = [s for s in sm if smax and s > 0.3 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------- oracle
+def oracle_sample(w, nshot_max, nt_sample):
+    """Time the FP64 oracle gradient on a bounded sample of the workload: the
+    same grid and geometry, min(cores, 20) shots, nt_sample steps."""
+    import oracle
+    cores = os.cpu_count() or 1
+    ns = max(1, min(nshot_max, cores))
+    oracle.set_threads(cores)
+    q = oracle.make_problem(0, w["nz"], w["nx"], w["pml"], w["dx"], w["dt"], nt_sample, ns,
+                            w["rec"].shape[1], w["f0"])
+    wav = np.stack([inputs.ricker(w["f0"], w["dt"], nt_sample)] * ns)
+    d_obs = np.zeros((ns, w["rec"].shape[1], nt_sample))
+    t = time.perf_counter()
+    oracle.acoustic_gradient(q, w["model"], wav, w["src"][:ns], w["rec"][:ns], d_obs)
+    el = time.perf_counter() - t
+    c = counts(w["nz"], w["nx"], w["pml"])
+    gpts = c["N_pad"] * nt_sample * ns / el / 1e9
+    return gpts, el, min(ns, cores), (f"oracle gradient, {ns} shots x {nt_sample} steps of the "
+                                      f"{w['nz']}x{w['nx']} workload ({el:.1f} s)")
+
+
+def run_reference(args, w, rank):
+    """Reference arm: the FP64 oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    nt_sample = 60
+    for _ in range(args.warmup):
+        oracle_sample(w, 20, nt_sample)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g, el, cores, sample = oracle_sample(w, 20, nt_sample)
+        vals.append(g)
+    total = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(w, 20), "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------- sweep
+def run_sweep(args, w, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2604_14189_gb300 import sweep
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    nshot, nt = w["src"].shape[0], w["nt"]
+    nrec = w["rec"].shape[1]
+    p = sweep.problem(nz=w["nz"], nx=w["nx"], pml=w["pml"], dx=w["dx"], dt=w["dt"], nt=nt,
+                      nshot=nshot, nrec=nrec, f_ref=w["f0"])
+    wav_h = np.stack([inputs.ricker(w["f0"], w["dt"], nt)] * nshot).astype(np.float32)
+    v0 = torch.tensor(w["model"], dtype=torch.float32, device=dev)
+    vt = torch.tensor(w["v_true"], dtype=torch.float32, device=dev)
+    wav = torch.tensor(wav_h, device=dev)
+    src = torch.tensor(w["src"], device=dev)
+    rec = torch.tensor(w["rec"], device=dev)
+    d_obs = sweep.sweep_forward(p, vt, wav, src, rec)
+    ws = sweep.alloc_workspace(p, sweep.MODE_GRADIENT, dev)
+    grad = torch.empty((w["nz"], w["nx"]), dtype=torch.float32, device=dev)
+    mis = torch.empty((), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        sweep.sweep_gradient(p, v0, wav, src, rec, d_obs, grad=grad, misfit=mis, ws=ws,
+                             sync=False)
+        if world > 1:
+            dist.all_reduce(grad)
+            dist.all_reduce(mis)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    st = sweep.status(ws)
+    if st != sweep.OK:
+        raise sweep.SweepError(st, "warm-up")
+
+    sampler = ClockSampler(local_rank)
+    sweep.profile_enable(True)
+    l0 = sweep.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        if k:
+            flush.zero_()  # L2 flush between timed steps (inputs exceed L2 anyway)
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = sweep.kernel_launches() - l0
+    ms = e0.elapsed_time(e1)
+    bwd_ms, bwd_n = sweep.profile_read(sweep.K_AC_BWD)
+    fwd_ms, fwd_n = sweep.profile_read(sweep.K_AC_FWD)
+    sweep.profile_enable(False)
+    st = sweep.status(ws)
+    if st != sweep.OK:
+        raise sweep.SweepError(st, "timed region")
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    c = counts(w["nz"], w["nx"], w["pml"])
+    pts_step = c["N_pad"] * nt * nshot * world
+    value = pts_step / (ms_step * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers
+    d_obs_h = d_obs.cpu().pin_memory()
+    model_h = torch.tensor(w["model"], dtype=torch.float32).pin_memory()
+    wav_hh = torch.tensor(wav_h).pin_memory()
+    src_h = torch.tensor(w["src"]).pin_memory()
+    rec_h = torch.tensor(w["rec"]).pin_memory()
+    grad_h = torch.empty_like(grad, device="cpu").pin_memory()
+    mis_h = torch.empty((), dtype=torch.float64).pin_memory()
+    bufs = [torch.empty_like(t, device=dev) for t in (model_h, wav_hh, src_h, rec_h, d_obs_h)]
+    h2d = sum(t.numel() * t.element_size() for t in (model_h, wav_hh, src_h, rec_h, d_obs_h))
+    d2h = grad_h.numel() * grad_h.element_size() + 8
+
+    def e2e_step():
+        for dst, srcb in zip(bufs, (model_h, wav_hh, src_h, rec_h, d_obs_h)):
+            dst.copy_(srcb, non_blocking=True)
+        sweep.sweep_gradient(p, bufs[0], bufs[1], bufs[2], bufs[3], bufs[4], grad=grad,
+                             misfit=mis, ws=ws, sync=False)
+        if world > 1:
+            dist.all_reduce(grad)
+            dist.all_reduce(mis)
+        grad_h.copy_(grad, non_blocking=True)
+        mis_h.copy_(mis, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e_value = pts_step / (ms_e2e / args.steps * 1e-3) / 1e9
+    if not np.isfinite(float(mis_h)):
+        raise RuntimeError("non-finite misfit in the end-to-end run")
+
+    if rank != 0:
+        return
+    peak, peak_src = peaks()
+    bwd_avg_ms = bwd_ms / max(bwd_n, 1)
+    achieved = alg_bytes_bwd(c) * nshot / (bwd_avg_ms * 1e-3) / 1e9
+    traffic = read_traffic()
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        g, el, cores, sample = oracle_sample(w, nshot, 200)
+        cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_desc(w, nshot), "nz": w["nz"], "nx": w["nx"],
+                   "pml": w["pml"], "nt": nt, "shots_per_gpu": nshot, "nrec": nrec,
+                   "l2": "inputs larger than L2 (workspace %.2f GB per step); 256 MB L2 flush "
+                         "between timed steps" % (ws.numel() / 1e9),
+                   "reductions": "f64"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "acoustic backward step (adjoint + reconstruction + imaging)",
+                     "peak_source": peak_src,
+                     "frac_of_8000": achieved / 8000.0,
+                     "alg_bytes_per_launch": alg_bytes_bwd(c) * nshot,
+                     "avg_launch_ms": bwd_avg_ms},
+        "forward_kernel": {"avg_launch_ms": fwd_ms / max(fwd_n, 1),
+                           "achieved_gbs": alg_bytes_fwd(c) * nshot /
+                           (fwd_ms / max(fwd_n, 1) * 1e-3) / 1e9},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["sweep", "reference"], default="sweep")
+    ap.add_argument("--nt", type=int, default=3000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    w = inputs.workload_marmousi(nshot=20, nt=args.nt)
+    if args.impl == "reference":
+        run_reference(args, w, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_sweep(args, w, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

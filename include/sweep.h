@@ -155,6 +155,22 @@ const char* sweep_strerror(int code);
  * (monotone counter, for accounting launches per step). */
 unsigned long long sweep_kernel_launches(void);
 
+/* Kernel timing for benchmarks.  While enabled, every launch of a time-step
+ * kernel is bracketed by two CUDA events recorded on the launching stream.
+ * sweep_profile_enable(1) clears earlier records; (0) stops recording.
+ * sweep_profile_read() synchronises on the recorded events and returns, for
+ * kernel class `kernel` (SWEEP_K_*), the summed device time in ms and the
+ * number of launches.  Host-side cost: two event records per launch. */
+enum {
+  SWEEP_K_AC_FWD = 0,  /* acoustic forward step              */
+  SWEEP_K_AC_BWD = 1,  /* acoustic backward (adjoint) step   */
+  SWEEP_K_EL_VEL = 2,  /* elastic velocity half step         */
+  SWEEP_K_EL_STR = 3,  /* elastic stress step                */
+  SWEEP_K_COUNT = 4
+};
+int sweep_profile_enable(int on);
+int sweep_profile_read(int kernel, double* ms, long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -383,13 +383,17 @@ __global__ void __launch_bounds__(AC_THREADS) ac_bwd_kernel(const AcBwdArgs a) {
 void launch_ac_fwd(const AcFwdArgs& a, cudaStream_t st) {
   const Geom& g = a.g;
   dim3 grid((g.NXp + AC_BX - 1) / AC_BX, (g.NZ + AC_BZ - 1) / AC_BZ, g.nshot);
+  void* tok = profile_begin(SWEEP_K_AC_FWD, st);
   ac_fwd_kernel<<<grid, AC_THREADS, 0, st>>>(a);
+  profile_end(tok, st);
 }
 
 void launch_ac_bwd(const AcBwdArgs& a, cudaStream_t st) {
   const Geom& g = a.g;
   dim3 grid((g.NXp + AC_BX - 1) / AC_BX, (g.NZ + AC_BZ - 1) / AC_BZ, g.nshot);
+  void* tok = profile_begin(SWEEP_K_AC_BWD, st);
   ac_bwd_kernel<<<grid, AC_THREADS, 0, st>>>(a);
+  profile_end(tok, st);
 }
 
 }  // namespace sweep

@@ -128,6 +128,12 @@ void launch_dot(const float* a, const float* b, long long n, double* partial,
 
 constexpr int RED_BLOCKS = 1024;  // partial sums of the FP64 reductions
 
+// Launch accounting and optional per-launch event timing (profile.cu,
+// sweep_api.cu).
+void note_launches(int k);
+void* profile_begin(int kernel, cudaStream_t st);
+void profile_end(void* token, cudaStream_t st);
+
 __device__ __forceinline__ void latch(int* status, int code) {
   atomicCAS(status, 0, code);
 }

@@ -29,7 +29,8 @@ EINVAL, ECFL, EBOUNDS, EWORKSPACE, ECUDA, ETIMEOUT, ENONFINITE, EMODEL, EUNSUPPO
 # Every symbol declared in include/sweep.h.
 EXPORTS = ("sweep_workspace_bytes", "sweep_forward", "sweep_adjoint", "sweep_gradient",
            "sweep_dot_workspace_bytes", "sweep_dot", "sweep_status", "sweep_strerror",
-           "sweep_kernel_launches")
+           "sweep_kernel_launches", "sweep_profile_enable", "sweep_profile_read")
+K_AC_FWD, K_AC_BWD, K_EL_VEL, K_EL_STR = 0, 1, 2, 3
 
 
 class Problem(ctypes.Structure):
@@ -90,6 +91,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.sweep_strerror.restype = ctypes.c_char_p
     lib.sweep_kernel_launches.argtypes = []
     lib.sweep_kernel_launches.restype = ctypes.c_ulonglong
+    lib.sweep_profile_enable.argtypes = [i32]
+    lib.sweep_profile_enable.restype = i32
+    lib.sweep_profile_read.argtypes = [i32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_longlong)]
+    lib.sweep_profile_read.restype = i32
     return lib
 
 
@@ -106,6 +112,19 @@ def strerror(code: int) -> str:
 
 def kernel_launches() -> int:
     return int(_lib.sweep_kernel_launches())
+
+
+def profile_enable(on: bool) -> None:
+    _lib.sweep_profile_enable(1 if on else 0)
+
+
+def profile_read(kernel: int) -> tuple[float, int]:
+    """(summed device ms, launches) of a kernel class since profile_enable(True)."""
+    ms, n = ctypes.c_double(0.0), ctypes.c_longlong(0)
+    rc = _lib.sweep_profile_read(kernel, ctypes.byref(ms), ctypes.byref(n))
+    if rc != OK:
+        raise SweepError(rc, "sweep_profile_read")
+    return ms.value, n.value
 
 
 def _ptr(t):
