@@ -1,0 +1,358 @@
+// Interior acoustic step kernels: the plain 8th-order update on the cells
+// away from the absorbing border (forward), and the fused adjoint +
+// reconstruction + imaging update on interior cells at least 4 cells from
+// the border (backward).  See acoustic_common.cuh for the equations.
+//
+// Work is a list of (tile, shot) units, tile-major, split into contiguous
+// chunks over persistent CTAs.  Each CTA runs a two-stage TMA pipeline: while
+// it computes unit k from shared memory, the tiles of unit k+1 are in flight
+// (cp.async.bulk.tensor, completion on an mbarrier).  Halo tiles carry 4
+// extra cells per side; the TMA zero-fills outside the padded grid, which is
+// the Dirichlet condition.  Results go straight from registers to global
+// memory with 16-byte stores.
+#include "acoustic_common.cuh"
+#include "tma.cuh"
+
+namespace sweep {
+namespace {
+
+constexpr int HALO_F = IN_HW * IN_HH;  // floats in a halo tile
+constexpr int CEN_F = IN_BX * IN_BZ;   // floats in a centre tile
+static_assert((HALO_F * 4) % 128 == 0 && (CEN_F * 4) % 128 == 0, "tile alignment");
+
+struct __align__(128) FwdStage {
+  float u[HALO_F];   // u^n with halo
+  float up[CEN_F];   // u^{n-1}
+  float k[CEN_F];    // K
+};
+struct __align__(128) BwdStage {
+  float ua[HALO_F];  // u^n with halo
+  float ma[HALO_F];  // mu^{n+1} with halo
+  float ub[CEN_F];   // u^{n+1}
+  float mb[CEN_F];   // mu^{n+2}
+  float k[CEN_F];    // K
+};
+constexpr uint32_t kFwdBytes = (HALO_F + 2 * CEN_F) * 4;
+constexpr size_t kFwdSmem = 2 * sizeof(FwdStage) + 64;
+constexpr size_t kBwdSmem = 2 * sizeof(BwdStage) + 64;
+
+__device__ __forceinline__ float4 lds4(const float* t, int pitch, int r, int c) {
+  return *reinterpret_cast<const float4*>(t + r * pitch + c);
+}
+
+struct UnitPos {
+  int s, z0, x0;
+};
+
+__device__ __forceinline__ UnitPos unit_pos(const Region& R, int S, int ntx, int unit) {
+  const int tile = unit / S;
+  UnitPos p;
+  p.s = unit - tile * S;
+  const int tz = tile / ntx, tx = tile - tz * ntx;
+  p.z0 = R.z0 + tz * IN_BZ;
+  p.x0 = R.x0 + tx * IN_BX;
+  return p;
+}
+
+// -------------------------------------------------------------- forward
+__global__ void __launch_bounds__(IN_THREADS, 2)
+    ac_in_fwd_kernel(const __grid_constant__ AcInFwdArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  FwdStage* stg = reinterpret_cast<FwdStage*>(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * sizeof(FwdStage));
+  if (*a.status) return;
+  const Geom& g = a.g;
+  const Region& R = g.fin;
+  const int S = g.nshot;
+  const int ub = (int)((long long)a.units * blockIdx.x / gridDim.x);
+  const int ue = (int)((long long)a.units * (blockIdx.x + 1) / gridDim.x);
+  const int count = ue - ub;
+  if (count <= 0) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  auto issue = [&](int k) {
+    const UnitPos p = unit_pos(R, S, a.ntx, ub + k);
+    FwdStage& sg = stg[k & 1];
+    mbar_arrive_expect_tx(&bar[k & 1], kFwdBytes);
+    tma_load_3d(sg.u, &a.tu, &bar[k & 1], p.x0 - 4, p.z0 - 4, p.s);
+    tma_load_3d(sg.up, &a.tup, &bar[k & 1], p.x0, p.z0, p.s);
+    tma_load_2d(sg.k, &a.tK, &bar[k & 1], p.x0, p.z0);
+  };
+  if (threadIdx.x == 0) {
+    issue(0);
+    if (count > 1) issue(1);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lx = 4 * lane, r0 = warp * IN_RPW;
+  int k = 0;
+  for (; k < count; ++k) {
+    const bool got = mbar_wait(&bar[k & 1], (k >> 1) & 1);
+    if (__syncthreads_or(!got)) break;
+    const UnitPos p = unit_pos(R, S, a.ntx, ub + k);
+    const FwdStage& sg = stg[k & 1];
+    const long long so = (long long)p.s * g.fstride;
+    const int sz = a.src[2 * p.s] + g.P, sx = a.src[2 * p.s + 1] + g.P;
+    const float fn = a.wavelet[(long long)p.s * g.nt + a.n];
+    const int gx = p.x0 + lx;
+    float w[9][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f4a(lds4(sg.u, IN_HW, r0 + j, lx + 4), w[j]);
+#pragma unroll
+    for (int q = 0; q < IN_RPW; ++q) {
+      f4a(lds4(sg.u, IN_HW, r0 + q + 8, lx + 4), w[8]);
+      const int gz = p.z0 + r0 + q;
+      if (gz < R.z1 && gx < R.x1) {
+        float e[12], up[4], kk[4], out[4];
+        f4a(lds4(sg.u, IN_HW, r0 + q + 4, lx), e);
+        f4a(lds4(sg.u, IN_HW, r0 + q + 4, lx + 8), e + 8);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) e[4 + c] = w[4][c];
+        f4a(lds4(sg.up, IN_BX, r0 + q, lx), up);
+        f4a(lds4(sg.k, IN_BX, r0 + q, lx), kk);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float lap =
+              d2(e[c], e[c + 1], e[c + 2], e[c + 3], e[c + 4], e[c + 5], e[c + 6], e[c + 7],
+                 e[c + 8]) +
+              d2(w[0][c], w[1][c], w[2][c], w[3][c], w[4][c], w[5][c], w[6][c], w[7][c], w[8][c]);
+          out[c] = 2.f * w[4][c] - up[c] + kk[c] * lap;
+          if (gz == sz && gx + c == sx) out[c] += kk[c] * fn;
+        }
+        *reinterpret_cast<float4*>(a.un + so + (long long)gz * g.NXp + gx) =
+            make_float4(out[0], out[1], out[2], out[3]);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) w[j][c] = w[j + 1][c];
+      }
+    }
+    __syncthreads();  // stage k&1 fully read; this unit's stores visible
+    if (threadIdx.x == 0 && k + 2 < count) {
+      fence_proxy_async_smem();
+      issue(k + 2);
+    }
+    // receivers of this shot inside this tile (read back this CTA's stores)
+    if (a.data && tile_meets_box(a.rbox + 4 * p.s, p.z0, IN_BZ, p.x0, IN_BX)) {
+      for (int r = threadIdx.x; r < g.nrec; r += IN_THREADS) {
+        const int32_t* q = a.rec + 2 * ((long long)p.s * g.nrec + r);
+        const int rz = q[0] + g.P, rx = q[1] + g.P;
+        if (rz >= p.z0 && rz < p.z0 + IN_BZ && rx >= p.x0 && rx < p.x0 + IN_BX &&
+            in_region(R, rz, rx))
+          a.data[((long long)p.s * g.nrec + r) * g.nt + a.n] =
+              a.un[so + (long long)rz * g.NXp + rx];
+      }
+    }
+  }
+  if (k < count) {
+    // a transfer never landed: report, drain what is still in flight
+    if (threadIdx.x == 0) {
+      latch(a.status, SWEEP_ETIMEOUT);
+      for (int j = k; j < count && j < k + 2; ++j) mbar_wait(&bar[j & 1], (j >> 1) & 1);
+    }
+  }
+}
+
+// -------------------------------------------------------------- backward
+__global__ void __launch_bounds__(IN_THREADS, 1)
+    ac_in_bwd_kernel(const __grid_constant__ AcInBwdArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  BwdStage* stg = reinterpret_cast<BwdStage*>(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * sizeof(BwdStage));
+  if (*a.status) return;
+  const Geom& g = a.g;
+  const Region& R = g.bin;
+  const int S = g.nshot;
+  const int ub = (int)((long long)a.units * blockIdx.x / gridDim.x);
+  const int ue = (int)((long long)a.units * (blockIdx.x + 1) / gridDim.x);
+  const int count = ue - ub;
+  if (count <= 0) return;
+  const bool img = a.do_img != 0, adj = a.do_adj != 0, rec = a.do_rec != 0;
+  const uint32_t bytes = (HALO_F + CEN_F) * 4 + (img ? HALO_F * 4 : 0) +
+                         (rec ? CEN_F * 4 : 0) + (adj ? CEN_F * 4 : 0);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  auto issue = [&](int k) {
+    const UnitPos p = unit_pos(R, S, a.ntx, ub + k);
+    BwdStage& sg = stg[k & 1];
+    mbar_arrive_expect_tx(&bar[k & 1], bytes);
+    tma_load_3d(sg.ma, &a.tmA, &bar[k & 1], p.x0 - 4, p.z0 - 4, p.s);
+    tma_load_2d(sg.k, &a.tK, &bar[k & 1], p.x0, p.z0);
+    if (img) tma_load_3d(sg.ua, &a.tuA, &bar[k & 1], p.x0 - 4, p.z0 - 4, p.s);
+    if (rec) tma_load_3d(sg.ub, &a.tuB, &bar[k & 1], p.x0, p.z0, p.s);
+    if (adj) tma_load_3d(sg.mb, &a.tmB, &bar[k & 1], p.x0, p.z0, p.s);
+  };
+  if (threadIdx.x == 0) {
+    issue(0);
+    if (count > 1) issue(1);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lx = 4 * lane, r0 = warp * IN_RPW;
+  int k = 0;
+  for (; k < count; ++k) {
+    const bool got = mbar_wait(&bar[k & 1], (k >> 1) & 1);
+    if (__syncthreads_or(!got)) break;
+    const UnitPos p = unit_pos(R, S, a.ntx, ub + k);
+    const BwdStage& sg = stg[k & 1];
+    const long long so = (long long)p.s * g.fstride;
+    const int sz = a.src[2 * p.s] + g.P, sx = a.src[2 * p.s + 1] + g.P;
+    const float fn = img ? a.wavelet[(long long)p.s * g.nt + a.n] : 0.f;
+    const int gx = p.x0 + lx;
+    float wm[9][4], wu[9][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      f4a(lds4(sg.ma, IN_HW, r0 + j, lx + 4), wm[j]);
+      if (img) f4a(lds4(sg.ua, IN_HW, r0 + j, lx + 4), wu[j]);
+    }
+#pragma unroll
+    for (int q = 0; q < IN_RPW; ++q) {
+      f4a(lds4(sg.ma, IN_HW, r0 + q + 8, lx + 4), wm[8]);
+      if (img) f4a(lds4(sg.ua, IN_HW, r0 + q + 8, lx + 4), wu[8]);
+      const int gz = p.z0 + r0 + q;
+      if (gz < R.z1 && gx < R.x1) {
+        const long long ci = so + (long long)gz * g.NXp + gx;
+        float kk[4];
+        f4a(lds4(sg.k, IN_BX, r0 + q, lx), kk);
+        if (adj) {
+          float e[12], m2[4], out[4];
+          f4a(lds4(sg.ma, IN_HW, r0 + q + 4, lx), e);
+          f4a(lds4(sg.ma, IN_HW, r0 + q + 4, lx + 8), e + 8);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) e[4 + c] = wm[4][c];
+          f4a(lds4(sg.mb, IN_BX, r0 + q, lx), m2);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float lap =
+                d2(e[c], e[c + 1], e[c + 2], e[c + 3], e[c + 4], e[c + 5], e[c + 6], e[c + 7],
+                   e[c + 8]) +
+                d2(wm[0][c], wm[1][c], wm[2][c], wm[3][c], wm[4][c], wm[5][c], wm[6][c],
+                   wm[7][c], wm[8][c]);
+            out[c] = 2.f * wm[4][c] - m2[c] + kk[c] * lap;
+          }
+          *reinterpret_cast<float4*>(a.mB + ci) = make_float4(out[0], out[1], out[2], out[3]);
+        }
+        if (img) {
+          float e[12], lap[4];
+          f4a(lds4(sg.ua, IN_HW, r0 + q + 4, lx), e);
+          f4a(lds4(sg.ua, IN_HW, r0 + q + 4, lx + 8), e + 8);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) e[4 + c] = wu[4][c];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            lap[c] = d2(e[c], e[c + 1], e[c + 2], e[c + 3], e[c + 4], e[c + 5], e[c + 6],
+                        e[c + 7], e[c + 8]) +
+                     d2(wu[0][c], wu[1][c], wu[2][c], wu[3][c], wu[4][c], wu[5][c], wu[6][c],
+                        wu[7][c], wu[8][c]);
+            if (gz == sz && gx + c == sx) lap[c] += fn;
+          }
+          float4* gp = reinterpret_cast<float4*>(a.graw + ci);
+          float4 gv = *gp;
+          gv.x += wm[4][0] * lap[0];
+          gv.y += wm[4][1] * lap[1];
+          gv.z += wm[4][2] * lap[2];
+          gv.w += wm[4][3] * lap[3];
+          *gp = gv;
+          if (a.illum) {
+            float4* ip = reinterpret_cast<float4*>(a.illum + ci);
+            float4 iv = *ip;
+            iv.x += wu[4][0] * wu[4][0];
+            iv.y += wu[4][1] * wu[4][1];
+            iv.z += wu[4][2] * wu[4][2];
+            iv.w += wu[4][3] * wu[4][3];
+            *ip = iv;
+          }
+          if (rec) {
+            float u1[4], out[4];
+            f4a(lds4(sg.ub, IN_BX, r0 + q, lx), u1);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) out[c] = 2.f * wu[4][c] - u1[c] + kk[c] * lap[c];
+            *reinterpret_cast<float4*>(a.uB + ci) = make_float4(out[0], out[1], out[2], out[3]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          wm[j][c] = wm[j + 1][c];
+          wu[j][c] = wu[j + 1][c];
+        }
+      }
+    }
+    // adjoint source gather: f-bar^n = mu^{n+1}(s)
+    if (a.wgrad && threadIdx.x == 0 && a.n < g.nt && sz >= p.z0 && sz < p.z0 + IN_BZ &&
+        sx >= p.x0 && sx < p.x0 + IN_BX && in_region(R, sz, sx))
+      a.wgrad[(long long)p.s * g.nt + a.n] = sg.ma[(sz - p.z0 + 4) * IN_HW + (sx - p.x0 + 4)];
+    __syncthreads();  // stage k&1 fully read; mu^n stores visible to this CTA
+    if (threadIdx.x == 0 && k + 2 < count) {
+      fence_proxy_async_smem();
+      issue(k + 2);
+    }
+    // residual injection mu^n(r) += K(r) r^{n-1} for receivers in this tile
+    if (adj && a.n >= 1 && tile_meets_box(a.rbox + 4 * p.s, p.z0, IN_BZ, p.x0, IN_BX)) {
+      for (int r = threadIdx.x; r < g.nrec; r += IN_THREADS) {
+        const int32_t* q = a.rec + 2 * ((long long)p.s * g.nrec + r);
+        const int rz = q[0] + g.P, rx = q[1] + g.P;
+        if (rz >= p.z0 && rz < p.z0 + IN_BZ && rx >= p.x0 && rx < p.x0 + IN_BX &&
+            in_region(R, rz, rx)) {
+          const float rv = a.res[((long long)p.s * g.nrec + r) * g.nt + (a.n - 1)];
+          atomicAdd(a.mB + so + (long long)rz * g.NXp + rx,
+                    a.K[(long long)rz * g.NXp + rx] * rv);
+        }
+      }
+    }
+  }
+  if (k < count) {
+    if (threadIdx.x == 0) {
+      latch(a.status, SWEEP_ETIMEOUT);
+      for (int j = k; j < count && j < k + 2; ++j) mbar_wait(&bar[j & 1], (j >> 1) & 1);
+    }
+  }
+}
+
+}  // namespace
+
+int device_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st) {
+  if (a.units <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(ac_in_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kFwdSmem);
+    attr = true;
+  }
+  int grid = 2 * device_sms();
+  if (grid > a.units) grid = a.units;
+  ac_in_fwd_kernel<<<grid, IN_THREADS, kFwdSmem, st>>>(a);
+  note_launches(1);
+}
+
+void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st) {
+  if (a.units <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(ac_in_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kBwdSmem);
+    attr = true;
+  }
+  int grid = device_sms();
+  if (grid > a.units) grid = a.units;
+  ac_in_bwd_kernel<<<grid, IN_THREADS, kBwdSmem, st>>>(a);
+  note_launches(1);
+}
+
+}  // namespace sweep

@@ -71,15 +71,17 @@ __global__ void __launch_bounds__(RT) grad_reduce_kernel(const Geom g,
                                                          int padded, float* grad,
                                                          float* illum, const int* status) {
   if (*status) return;
+  // graw / iraw: per shot on the padded grid [S][NZ][NXp]
   const long long nint = (long long)g.nz * g.nx;
   for (long long c = blockIdx.x * (long long)RT + threadIdx.x; c < nint;
        c += (long long)gridDim.x * RT) {
+    const int z = (int)(c / g.nx), x = (int)(c - (long long)z * g.nx);
+    const long long pc = (long long)(z + g.P) * g.NXp + (x + g.P);
     double acc = 0.0, ill = 0.0;
     for (int s = 0; s < g.nshot; ++s) {
-      acc += (double)graw[(long long)s * nint + c];
-      if (iraw) ill += (double)iraw[(long long)s * nint + c];
+      acc += (double)graw[(long long)s * g.fstride + pc];
+      if (iraw) ill += (double)iraw[(long long)s * g.fstride + pc];
     }
-    const int z = (int)(c / g.nx), x = (int)(c - (long long)z * g.nx);
     const float v = padded ? model[(long long)(z + g.P) * g.NX + (x + g.P)] : model[c];
     grad[c] = (float)(2.0 * acc / (double)v);
     if (illum) illum[c] = (float)ill;

@@ -1,17 +1,54 @@
 // Host side of the C ABI declared in include/sweep.h: argument validation,
-// workspace layout, and the time loops that launch the step kernels (the
-// Propagator of Sec. 2.1).  No device memory is allocated here: every buffer
-// is carved out of the caller's workspace.
+// workspace layout, TMA descriptors, and the time loops that launch the step
+// kernels (the Propagator of Sec. 2.1).  No device memory is allocated here:
+// every buffer is carved out of the caller's workspace.
+#include <cudaTypedefs.h>
+
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "sweep_internal.cuh"
+#include "tma.cuh"
 
 namespace sweep {
 
 std::atomic<unsigned long long> g_launches{0};
 void note_launches(int k) { g_launches.fetch_add((unsigned long long)k); }
+
+// ------------------------------------------------------------- tensor maps
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+}  // namespace
+
+bool make_tensor_map(CUtensorMap* map, const float* base, int rank, uint64_t dim0,
+                     uint64_t dim1, uint64_t dim2, uint64_t pitch0, uint64_t pitch1,
+                     uint32_t box0, uint32_t box1, uint32_t box2) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {dim0, dim1, dim2};
+  cuuint64_t strides[2] = {pitch0 * sizeof(float), pitch1 * sizeof(float)};
+  cuuint32_t box[3] = {box0, box1, box2};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
+                  const_cast<float*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
 
 namespace {
 
@@ -26,7 +63,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t status = 0, partial = 0, vmax = 0, K = 0;
+  size_t status = 0, partial = 0, vmax = 0, rbox = 0, K = 0;
   size_t ax = 0, bx = 0, az = 0, bz = 0, axh = 0, bxh = 0, azh = 0, bzh = 0;
   size_t u[2] = {0, 0}, psx[2] = {0, 0}, psz[2] = {0, 0}, zex = 0, zez = 0;
   size_t m[2] = {0, 0}, pbx[2] = {0, 0}, pbz[2] = {0, 0}, zbx[2] = {0, 0}, zbz[2] = {0, 0};
@@ -45,6 +82,9 @@ struct Bump {
   }
 };
 
+int up4(int v) { return (v + 3) & ~3; }
+int down4(int v) { return v & ~3; }
+
 Geom make_geom(const sweep_problem* p) {
   Geom g{};
   g.nz = p->nz;
@@ -60,6 +100,9 @@ Geom make_geom(const sweep_problem* p) {
   const int w = g.ringw;
   g.nring = 2 * w * (g.nx + 2 * w) + 2 * g.nz * w;
   g.fstride = (long long)g.NZ * g.NXp;
+  const int P = g.P;
+  g.fin = Region{P, P + g.nz, up4(P), down4(P + g.nx)};
+  g.bin = Region{P + 4, P + g.nz - 4, up4(P + 4), down4(P + g.nx - 4)};
   return g;
 }
 
@@ -75,7 +118,7 @@ bool valid_problem(const sweep_problem* p) {
   // keep every per-shot index within 32-bit loops where they are used
   const long long NZ = (long long)p->nz + 2LL * p->pml, NX = (long long)p->nx + 2LL * p->pml;
   if (NZ > (1 << 20) || NX > (1 << 20) || NZ * NX > (1LL << 31)) return false;
-  if (p->nshot > 65535) return false;  // gridDim.z
+  if (p->nshot > 65535) return false;  // gridDim.y / z
   return true;
 }
 
@@ -87,6 +130,7 @@ Layout layout(const sweep_problem* p, int mode) {
   L.status = b.take(sizeof(int) * 4);
   L.vmax = b.take(sizeof(unsigned int));
   L.partial = b.take(sizeof(double) * RED_BLOCKS);
+  L.rbox = b.take(sizeof(int32_t) * 4 * (size_t)(g.nshot > 0 ? g.nshot : 1));
   L.K = b.take(sizeof(float) * (size_t)g.fstride);
   L.ax = b.take(sizeof(float) * g.NXp);
   L.bx = b.take(sizeof(float) * g.NXp);
@@ -123,11 +167,10 @@ Layout layout(const sweep_problem* p, int mode) {
     L.adj_hi = b.off;
   }
   if (mode == SWEEP_MODE_GRADIENT) {
-    const size_t nint = (size_t)g.nz * g.nx * (size_t)g.nshot;
     L.data = b.take(sizeof(float) * (size_t)g.nshot * g.nrec * g.nt);
     L.save = b.take(sizeof(float) * ((size_t)g.nt + 1) * g.nshot * g.nring);
-    L.graw = b.take(sizeof(float) * nint);
-    L.iraw = b.take(sizeof(float) * nint);
+    L.graw = b.take(F);
+    L.iraw = b.take(F);
   }
   L.total = b.off;
   return L;
@@ -171,99 +214,207 @@ SetupArgs setup_args(const sweep_problem* p, const Layout& L, void* ws, const fl
     s.azh = at<float>(ws, L.azh);
     s.bzh = at<float>(ws, L.bzh);
   }
+  s.rbox = at<int32_t>(ws, L.rbox);
   s.vmax_bits = at<unsigned int>(ws, L.vmax);
   s.status = at<int>(ws, L.status);
   return s;
 }
 
+// TMA descriptors of one per-shot field [S][NZ][NXp]: halo box and centre box.
+bool field_maps(const Geom& g, const float* base, CUtensorMap* halo, CUtensorMap* centre) {
+  const uint64_t S = (uint64_t)(g.nshot > 0 ? g.nshot : 1);
+  bool ok = true;
+  if (halo)
+    ok = ok && make_tensor_map(halo, base, 3, g.NX, g.NZ, S, g.NXp, (uint64_t)g.fstride, IN_HW,
+                               IN_HH, 1);
+  if (centre)
+    ok = ok && make_tensor_map(centre, base, 3, g.NX, g.NZ, S, g.NXp, (uint64_t)g.fstride, IN_BX,
+                               IN_BZ, 1);
+  return ok;
+}
+
+int region_units(const Region& R, int nshot, int* ntx) {
+  if (R.z1 <= R.z0 || R.x1 <= R.x0) {
+    *ntx = 0;
+    return 0;
+  }
+  *ntx = (R.x1 - R.x0 + IN_BX - 1) / IN_BX;
+  const int ntz = (R.z1 - R.z0 + IN_BZ - 1) / IN_BZ;
+  return *ntx * ntz * nshot;
+}
+
 // Forward time loop of the acoustic engine.  On return the workspace holds
 // u^{nt} in u[nt % 2] and u^{nt-1} in u[(nt + 1) % 2].
-void acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
-                           const float* wavelet, const int32_t* src, const int32_t* rec,
-                           float* data, bool save_ring, cudaStream_t st) {
+int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
+                          const float* wavelet, const int32_t* src, const int32_t* rec,
+                          float* data, bool save_ring, cudaStream_t st) {
   const Geom g = make_geom(p);
   cudaMemsetAsync(at<char>(ws, L.fwd_lo), 0, L.fwd_hi - L.fwd_lo, st);
-  AcFwdArgs a{};
-  a.g = g;
-  a.K = at<float>(ws, L.K);
-  a.zex = at<float>(ws, L.zex);
-  a.zez = at<float>(ws, L.zez);
-  a.ax = at<float>(ws, L.ax);
-  a.bx = at<float>(ws, L.bx);
-  a.az = at<float>(ws, L.az);
-  a.bz = at<float>(ws, L.bz);
-  a.wavelet = wavelet;
-  a.src = src;
-  a.rec = rec;
-  a.data = data;
-  a.status = at<int>(ws, L.status);
   float* save = save_ring ? at<float>(ws, L.save) : nullptr;
   if (save) cudaMemsetAsync(save, 0, sizeof(float) * (size_t)g.nshot * g.nring, st);
-  for (int n = 0; n < g.nt; ++n) {
-    a.n = n;
-    a.u = at<float>(ws, L.u[n & 1]);
-    a.un = at<float>(ws, L.u[(n + 1) & 1]);
-    a.psx_in = at<float>(ws, L.psx[n & 1]);
-    a.psx_out = at<float>(ws, L.psx[(n + 1) & 1]);
-    a.psz_in = at<float>(ws, L.psz[n & 1]);
-    a.psz_out = at<float>(ws, L.psz[(n + 1) & 1]);
-    a.save = save ? save + (size_t)(n + 1) * g.nshot * g.nring : nullptr;
-    launch_ac_fwd(a, st);
+  int* status = at<int>(ws, L.status);
+  const int32_t* rbox = at<int32_t>(ws, L.rbox);
+
+  AcInFwdArgs in{};
+  in.g = g;
+  in.units = region_units(g.fin, g.nshot, &in.ntx);
+  CUtensorMap tu_h[2], tu_c[2];
+  if (in.units > 0) {
+    for (int b = 0; b < 2; ++b)
+      if (!field_maps(g, at<float>(ws, L.u[b]), &tu_h[b], &tu_c[b])) return SWEEP_ECUDA;
+    if (!make_tensor_map(&in.tK, at<float>(ws, L.K), 2, g.NX, g.NZ, 1, g.NXp, (uint64_t)g.fstride,
+                         IN_BX, IN_BZ, 1))
+      return SWEEP_ECUDA;
   }
-  note_launches(g.nt);
+  in.wavelet = wavelet;
+  in.src = src;
+  in.rec = rec;
+  in.rbox = rbox;
+  in.data = data;
+  in.status = status;
+
+  AcFrFwdArgs fr{};
+  fr.g = g;
+  fr.fr = frame_rects(g, g.fin);
+  fr.K = at<float>(ws, L.K);
+  fr.zex = at<float>(ws, L.zex);
+  fr.zez = at<float>(ws, L.zez);
+  fr.ax = at<float>(ws, L.ax);
+  fr.bx = at<float>(ws, L.bx);
+  fr.az = at<float>(ws, L.az);
+  fr.bz = at<float>(ws, L.bz);
+  fr.wavelet = wavelet;
+  fr.src = src;
+  fr.rec = rec;
+  fr.rbox = rbox;
+  fr.data = data;
+  fr.status = status;
+  for (int n = 0; n < g.nt; ++n) {
+    const int A = n & 1, B = (n + 1) & 1;
+    void* tok = profile_begin(SWEEP_K_AC_FWD, st);
+    if (in.units > 0) {
+      in.n = n;
+      in.tu = tu_h[A];
+      in.tup = tu_c[B];
+      in.un = at<float>(ws, L.u[B]);
+      launch_ac_in_fwd(in, st);
+    }
+    fr.n = n;
+    fr.u = at<float>(ws, L.u[A]);
+    fr.un = at<float>(ws, L.u[B]);
+    fr.psx_in = at<float>(ws, L.psx[A]);
+    fr.psx_out = at<float>(ws, L.psx[B]);
+    fr.psz_in = at<float>(ws, L.psz[A]);
+    fr.psz_out = at<float>(ws, L.psz[B]);
+    fr.save = save ? save + (size_t)(n + 1) * g.nshot * g.nring : nullptr;
+    launch_ac_fr_fwd(fr, st);
+    profile_end(tok, st);
+  }
+  return SWEEP_OK;
 }
 
 // Backward loop: adjoint propagation from the residual `res`; optionally the
 // imaging condition with wavefield reconstruction (gradient) and/or the
 // adjoint source gather (wgrad).
-void acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
-                            const float* wavelet, const int32_t* src, const int32_t* rec,
-                            const float* res, float* wgrad, bool imaging, bool illum,
-                            cudaStream_t st) {
+int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
+                           const float* wavelet, const int32_t* src, const int32_t* rec,
+                           const float* res, float* wgrad, bool imaging, bool illum,
+                           cudaStream_t st) {
   const Geom g = make_geom(p);
   cudaMemsetAsync(at<char>(ws, L.adj_lo), 0, L.adj_hi - L.adj_lo, st);
-  const size_t nint = (size_t)g.nz * g.nx * (size_t)g.nshot;
+  const size_t F = sizeof(float) * (size_t)g.fstride * (size_t)g.nshot;
   if (imaging) {
-    cudaMemsetAsync(at<float>(ws, L.graw), 0, sizeof(float) * nint, st);
-    if (illum) cudaMemsetAsync(at<float>(ws, L.iraw), 0, sizeof(float) * nint, st);
+    cudaMemsetAsync(at<float>(ws, L.graw), 0, F, st);
+    if (illum) cudaMemsetAsync(at<float>(ws, L.iraw), 0, F, st);
   }
-  AcBwdArgs a{};
-  a.g = g;
-  a.K = at<float>(ws, L.K);
-  a.ax = at<float>(ws, L.ax);
-  a.bx = at<float>(ws, L.bx);
-  a.az = at<float>(ws, L.az);
-  a.bz = at<float>(ws, L.bz);
-  a.wavelet = wavelet;
-  a.src = src;
-  a.rec = rec;
-  a.res = res;
-  a.graw = imaging ? at<float>(ws, L.graw) : nullptr;
-  a.illum = (imaging && illum) ? at<float>(ws, L.iraw) : nullptr;
-  a.wgrad = wgrad;
-  a.status = at<int>(ws, L.status);
+  int* status = at<int>(ws, L.status);
+  const int32_t* rbox = at<int32_t>(ws, L.rbox);
   float* save = imaging ? at<float>(ws, L.save) : nullptr;
-  for (int n = g.nt; n >= 0; --n) {
-    a.n = n;
-    a.do_adj = n >= 1;
-    a.do_img = imaging && n <= g.nt - 1;
-    a.do_rec = imaging && n >= 1 && n <= g.nt - 1;
-    a.uA = imaging ? at<float>(ws, L.u[n & 1]) : nullptr;
-    a.uB = imaging ? at<float>(ws, L.u[(n + 1) & 1]) : nullptr;
-    a.mA = at<float>(ws, L.m[(n + 1) & 1]);
-    a.mB = at<float>(ws, L.m[n & 1]);
-    a.pbx_in = at<float>(ws, L.pbx[n & 1]);
-    a.pbx_out = at<float>(ws, L.pbx[(n + 1) & 1]);
-    a.pbz_in = at<float>(ws, L.pbz[n & 1]);
-    a.pbz_out = at<float>(ws, L.pbz[(n + 1) & 1]);
-    a.zbx_in = at<float>(ws, L.zbx[n & 1]);
-    a.zbx_out = at<float>(ws, L.zbx[(n + 1) & 1]);
-    a.zbz_in = at<float>(ws, L.zbz[n & 1]);
-    a.zbz_out = at<float>(ws, L.zbz[(n + 1) & 1]);
-    a.save = (save && n >= 1) ? save + (size_t)(n - 1) * g.nshot * g.nring : nullptr;
-    launch_ac_bwd(a, st);
+
+  AcInBwdArgs in{};
+  in.g = g;
+  in.units = region_units(g.bin, g.nshot, &in.ntx);
+  CUtensorMap tu_h[2], tu_c[2], tm_h[2], tm_c[2];
+  if (in.units > 0) {
+    for (int b = 0; b < 2; ++b) {
+      if (imaging && !field_maps(g, at<float>(ws, L.u[b]), &tu_h[b], &tu_c[b]))
+        return SWEEP_ECUDA;
+      if (!field_maps(g, at<float>(ws, L.m[b]), &tm_h[b], &tm_c[b])) return SWEEP_ECUDA;
+    }
+    if (!make_tensor_map(&in.tK, at<float>(ws, L.K), 2, g.NX, g.NZ, 1, g.NXp, (uint64_t)g.fstride,
+                         IN_BX, IN_BZ, 1))
+      return SWEEP_ECUDA;
   }
-  note_launches(g.nt + 1);
+  in.graw = imaging ? at<float>(ws, L.graw) : nullptr;
+  in.illum = (imaging && illum) ? at<float>(ws, L.iraw) : nullptr;
+  in.K = at<float>(ws, L.K);
+  in.wavelet = wavelet;
+  in.src = src;
+  in.rec = rec;
+  in.rbox = rbox;
+  in.res = res;
+  in.wgrad = wgrad;
+  in.status = status;
+
+  AcFrBwdArgs fr{};
+  fr.g = g;
+  fr.fr = frame_rects(g, g.bin);
+  fr.K = at<float>(ws, L.K);
+  fr.ax = at<float>(ws, L.ax);
+  fr.bx = at<float>(ws, L.bx);
+  fr.az = at<float>(ws, L.az);
+  fr.bz = at<float>(ws, L.bz);
+  fr.wavelet = wavelet;
+  fr.src = src;
+  fr.rec = rec;
+  fr.rbox = rbox;
+  fr.res = res;
+  fr.graw = in.graw;
+  fr.illum = in.illum;
+  fr.wgrad = wgrad;
+  fr.status = status;
+  for (int n = g.nt; n >= 0; --n) {
+    const int A = n & 1, B = (n + 1) & 1;  // u^n in u[A]; mu^{n+1} in m[B]
+    const int do_adj = n >= 1;
+    const int do_img = imaging && n <= g.nt - 1;
+    const int do_rec = imaging && n >= 1 && n <= g.nt - 1;
+    void* tok = profile_begin(SWEEP_K_AC_BWD, st);
+    if (in.units > 0 && (do_adj || do_img || wgrad)) {
+      in.n = n;
+      in.do_adj = do_adj;
+      in.do_img = do_img;
+      in.do_rec = do_rec;
+      if (imaging) {
+        in.tuA = tu_h[A];
+        in.tuB = tu_c[B];
+      }
+      in.tmA = tm_h[B];
+      in.tmB = tm_c[A];
+      in.uB = imaging ? at<float>(ws, L.u[B]) : nullptr;
+      in.mB = at<float>(ws, L.m[A]);
+      launch_ac_in_bwd(in, st);
+    }
+    fr.n = n;
+    fr.do_adj = do_adj;
+    fr.do_img = do_img;
+    fr.do_rec = do_rec;
+    fr.uA = imaging ? at<float>(ws, L.u[A]) : nullptr;
+    fr.uB = imaging ? at<float>(ws, L.u[B]) : nullptr;
+    fr.mA = at<float>(ws, L.m[B]);
+    fr.mB = at<float>(ws, L.m[A]);
+    fr.pbx_in = at<float>(ws, L.pbx[A]);
+    fr.pbx_out = at<float>(ws, L.pbx[B]);
+    fr.pbz_in = at<float>(ws, L.pbz[A]);
+    fr.pbz_out = at<float>(ws, L.pbz[B]);
+    fr.zbx_in = at<float>(ws, L.zbx[A]);
+    fr.zbx_out = at<float>(ws, L.zbx[B]);
+    fr.zbz_in = at<float>(ws, L.zbz[A]);
+    fr.zbz_out = at<float>(ws, L.zbz[B]);
+    fr.save = (save && n >= 1) ? save + (size_t)(n - 1) * g.nshot * g.nring : nullptr;
+    launch_ac_fr_bwd(fr, st);
+    profile_end(tok, st);
+  }
+  return SWEEP_OK;
 }
 
 }  // namespace
@@ -301,8 +452,9 @@ int sweep_forward(const sweep_problem* p, const float* model, const float* wavel
   if (p->nshot == 0) return SWEEP_OK;
   const Layout L = layout(p, SWEEP_MODE_FORWARD);
   launch_setup(setup_args(p, L, ws, model, src, rec), st);
-  note_launches(2);
-  acoustic_forward_loop(p, L, ws, wavelet, src, rec, p->nrec > 0 ? data : nullptr, false, st);
+  rc = acoustic_forward_loop(p, L, ws, wavelet, src, rec, p->nrec > 0 ? data : nullptr, false,
+                             st);
+  if (rc) return rc;
   return cuda_rc(cudaGetLastError());
 }
 
@@ -319,9 +471,10 @@ int sweep_adjoint(const sweep_problem* p, const float* model, const float* adj_d
   if (p->nshot == 0) return SWEEP_OK;
   const Layout L = layout(p, SWEEP_MODE_ADJOINT);
   launch_setup(setup_args(p, L, ws, model, src, rec), st);
-  note_launches(2);
-  // no imaging: the backward kernel never reads the wavelet
-  acoustic_backward_loop(p, L, ws, nullptr, src, rec, adj_data, wavelet_grad, false, false, st);
+  // no imaging: the backward kernels never read the wavelet
+  rc = acoustic_backward_loop(p, L, ws, nullptr, src, rec, adj_data, wavelet_grad, false, false,
+                              st);
+  if (rc) return rc;
   return cuda_rc(cudaGetLastError());
 }
 
@@ -344,15 +497,17 @@ int sweep_gradient(const sweep_problem* p, const float* model, const float* wave
   }
   const Layout L = layout(p, SWEEP_MODE_GRADIENT);
   launch_setup(setup_args(p, L, ws, model, src, rec), st);
-  note_launches(2);
   float* d = at<float>(ws, L.data);
-  acoustic_forward_loop(p, L, ws, wavelet, src, rec, p->nrec > 0 ? d : nullptr, true, st);
+  rc = acoustic_forward_loop(p, L, ws, wavelet, src, rec, p->nrec > 0 ? d : nullptr, true, st);
+  if (rc) return rc;
   const long long nd = (long long)g.nshot * g.nrec * g.nt;
   launch_residual_misfit(d, d_obs, d, nd, (p->flags & SWEEP_F_RESIDUAL_IN) ? 1 : 0,
                          at<double>(ws, L.partial), RED_BLOCKS, misfit, at<int>(ws, L.status),
                          st);
   note_launches(2);
-  acoustic_backward_loop(p, L, ws, wavelet, src, rec, d, nullptr, true, illum != nullptr, st);
+  rc = acoustic_backward_loop(p, L, ws, wavelet, src, rec, d, nullptr, true, illum != nullptr,
+                              st);
+  if (rc) return rc;
   launch_grad_reduce(g, at<float>(ws, L.graw), illum ? at<float>(ws, L.iraw) : nullptr, model,
                      (p->flags & SWEEP_F_PADDED_MODEL) ? 1 : 0, grad, illum,
                      at<int>(ws, L.status), st);

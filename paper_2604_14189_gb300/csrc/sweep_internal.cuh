@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 solver library (CUDA side only).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -8,8 +9,14 @@
 
 namespace sweep {
 
+// Rectangle [z0, z1) x [x0, x1) of the padded grid (empty if z1 <= z0 or
+// x1 <= x0).
+struct Region {
+  int z0, z1, x0, x1;
+};
+
 // ---------------------------------------------------------------------------
-// Geometry of one acoustic problem on the padded grid.
+// Geometry of one problem on the padded grid.
 // Fields are stored per shot as [NZ][NXp] floats, NXp = NX rounded up to a
 // multiple of 32 (128-byte rows); columns NX..NXp-1 hold zeros at all times.
 // ---------------------------------------------------------------------------
@@ -20,51 +27,113 @@ struct Geom {
   int ringw;          // width of the saved ring, min(P, 4)
   int nring;          // cells in the ring
   long long fstride;  // floats per shot per field = NZ * NXp
+  // Cells whose update is the plain stencil: forward = interior cells
+  // (columns aligned to 4); backward = interior cells at least 4 away from
+  // the border.  The frame kernels update every other cell.
+  Region fin, bin;
 };
 
-// Tile shape of the acoustic step kernels: BX cells along x (one warp, 4
-// cells per lane), BZ rows; RPW rows per warp.
-constexpr int AC_BX = 128;
-constexpr int AC_BZ = 32;
-constexpr int AC_RPW = 8;
-constexpr int AC_THREADS = 32 * (AC_BZ / AC_RPW);
+// ------------------------------------------------------------------ interior
+// Tiles of IN_BZ x IN_BX cells; IN_THREADS threads: each warp owns IN_RPW
+// rows, each lane 4 consecutive cells of a row.
+constexpr int IN_BX = 128;
+constexpr int IN_BZ = 32;
+constexpr int IN_THREADS = 256;
+constexpr int IN_RPW = IN_BZ / (IN_THREADS / 32);
+constexpr int IN_HW = IN_BX + 8;  // halo tile width
+constexpr int IN_HH = IN_BZ + 8;  // halo tile height
 
-struct AcFwdArgs {
+struct AcInFwdArgs {
   Geom g;
-  const float* u;     // u^n            [S][NZ][NXp]
+  CUtensorMap tu;    // u^n, halo box     [S][NZ][NX]
+  CUtensorMap tup;   // u^{n-1}, centre box
+  CUtensorMap tK;    // K [NZ][NX], centre box
+  float* un;         // out u^{n+1} (the u^{n-1} buffer)
+  const float* wavelet;
+  const int32_t* src;
+  const int32_t* rec;
+  const int32_t* rbox;  // [S][4] receiver bounding box (z0, z1, x0, x1) padded
+  float* data;          // [S][R][nt] or null
+  int* status;
+  int n;
+  int units, ntx;       // (tile, shot) units; tiles along x
+};
+
+struct AcInBwdArgs {
+  Geom g;
+  CUtensorMap tuA;   // u^n, halo box
+  CUtensorMap tmA;   // mu^{n+1}, halo box
+  CUtensorMap tuB;   // u^{n+1}, centre box
+  CUtensorMap tmB;   // mu^{n+2}, centre box
+  CUtensorMap tK;
+  float* uB;         // out u^{n-1}
+  float* mB;         // out mu^n
+  float* graw;       // [S][NZ][NXp]
+  float* illum;      // [S][NZ][NXp] or null
+  const float* K;
+  const float* wavelet;
+  const int32_t* src;
+  const int32_t* rec;
+  const int32_t* rbox;
+  const float* res;  // [S][R][nt]
+  float* wgrad;      // [S][nt] or null
+  int* status;
+  int n;
+  int do_adj, do_img, do_rec;
+  int units, ntx;
+};
+
+// --------------------------------------------------------------------- frame
+constexpr int FR_TZ = 16;
+constexpr int FR_TX = 64;
+constexpr int FR_THREADS = 128;
+
+struct FrameRects {
+  int n;               // rectangles (<= 4)
+  int z0[4], z1[4], x0[4], x1[4];
+  int ntx[4];          // tiles along x per rectangle
+  int first[5];        // prefix sum of tiles
+};
+
+struct AcFrFwdArgs {
+  Geom g;
+  FrameRects fr;
+  const float* u;     // u^n
   float* un;          // in u^{n-1}, out u^{n+1}
-  const float* K;     // [NZ][NXp]  v^2 dt^2 / dx^2
+  const float* K;
   const float* psx_in;
-  float* psx_out;     // psi_x^{n-1} -> psi_x^n   [S][NZ][NXp]
+  float* psx_out;
   const float* psz_in;
   float* psz_out;
-  float* zex;         // zeta_x, updated in place  [S][NZ][NXp]
+  float* zex;
   float* zez;
-  const float* ax;    // profiles [NXp] / [NZ]
+  const float* ax;
   const float* bx;
   const float* az;
   const float* bz;
-  const float* wavelet;  // [S][nt]
-  const int32_t* src;    // [S][2]
-  const int32_t* rec;    // [S][R][2]
-  float* data;           // [S][R][nt] or null
-  float* save;           // ring slot of u^{n+1}: [S][nring] or null
-  const int* status;
+  const float* wavelet;
+  const int32_t* src;
+  const int32_t* rec;
+  const int32_t* rbox;
+  float* data;
+  float* save;        // ring slot of u^{n+1} [S][nring] or null
+  int* status;
   int n;
 };
 
-struct AcBwdArgs {
+struct AcFrBwdArgs {
   Geom g;
-  const float* uA;    // u^n (interior + ring valid)
-  float* uB;          // in u^{n+1}, out u^{n-1} (interior + ring)
+  FrameRects fr;
+  const float* uA;    // u^n
+  float* uB;          // in u^{n+1}, out u^{n-1}
   const float* mA;    // mu^{n+1}
   float* mB;          // in mu^{n+2}, out mu^n
   const float* pbx_in;
-  float* pbx_out;     // adjoint psi_x: ^n -> ^{n-1}
+  float* pbx_out;
   const float* pbz_in;
   float* pbz_out;
   const float* zbx_in;
-  float* zbx_out;     // adjoint zeta_x: ^n -> ^{n-1}
+  float* zbx_out;
   const float* zbz_in;
   float* zbz_out;
   const float* K;
@@ -72,24 +141,27 @@ struct AcBwdArgs {
   const float* bx;
   const float* az;
   const float* bz;
-  const float* wavelet;  // [S][nt]
+  const float* wavelet;
   const int32_t* src;
   const int32_t* rec;
-  const float* res;      // residual [S][R][nt] (injected at sample n-1)
-  const float* save;     // ring slot of u^{n-1}: [S][nring] (or null)
-  float* graw;           // [S][nz][nx] sum mu^{n+1} (Lap u^n + f delta)
-  float* illum;          // [S][nz][nx] sum (u^n)^2, or null
-  float* wgrad;          // [S][nt] adjoint source gather, or null
-  const int* status;
+  const int32_t* rbox;
+  const float* res;
+  const float* save;  // ring slot of u^{n-1} or null
+  float* graw;        // [S][NZ][NXp]
+  float* illum;
+  float* wgrad;
+  int* status;
   int n;
-  int do_adj;            // compute mu^n (and inject r^{n-1})
-  int do_img;            // imaging with mu^{n+1}, u^n
-  int do_rec;            // reconstruct u^{n-1} (+ ring restore)
+  int do_adj, do_img, do_rec;
 };
 
-// Kernel launchers (acoustic.cu)
-void launch_ac_fwd(const AcFwdArgs& a, cudaStream_t st);
-void launch_ac_bwd(const AcBwdArgs& a, cudaStream_t st);
+// Kernel launchers (acoustic_interior.cu, acoustic_frame.cu)
+void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st);
+void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st);
+void launch_ac_fr_fwd(const AcFrFwdArgs& a, cudaStream_t st);
+void launch_ac_fr_bwd(const AcFrBwdArgs& a, cudaStream_t st);
+FrameRects frame_rects(const Geom& g, const Region& inner);
+int device_sms();
 
 // Setup (setup.cu)
 struct SetupArgs {
@@ -110,6 +182,7 @@ struct SetupArgs {
   float* bxh;
   float* azh;
   float* bzh;
+  int32_t* rbox;       // out [S][4] receiver bounding boxes (padded coords)
   unsigned int* vmax_bits;  // scratch: max vp as float bits
   int* status;
 };
