@@ -162,11 +162,15 @@ unsigned long long sweep_kernel_launches(void);
  * kernel class `kernel` (SWEEP_K_*), the summed device time in ms and the
  * number of launches.  Host-side cost: two event records per launch. */
 enum {
-  SWEEP_K_AC_FWD = 0,  /* acoustic forward step              */
-  SWEEP_K_AC_BWD = 1,  /* acoustic backward (adjoint) step   */
-  SWEEP_K_EL_VEL = 2,  /* elastic velocity half step         */
-  SWEEP_K_EL_STR = 3,  /* elastic stress step                */
-  SWEEP_K_COUNT = 4
+  SWEEP_K_AC_FWD = 0,     /* acoustic forward step (all its kernels)   */
+  SWEEP_K_AC_BWD = 1,     /* acoustic backward step (all its kernels)  */
+  SWEEP_K_EL_VEL = 2,     /* elastic velocity half step                */
+  SWEEP_K_EL_STR = 3,     /* elastic stress step                       */
+  SWEEP_K_AC_FWD_IN = 4,  /* acoustic forward, interior kernel         */
+  SWEEP_K_AC_FWD_FR = 5,  /* acoustic forward, border-frame kernel     */
+  SWEEP_K_AC_BWD_IN = 6,  /* acoustic backward, interior kernel        */
+  SWEEP_K_AC_BWD_FR = 7,  /* acoustic backward, border-frame kernel    */
+  SWEEP_K_COUNT = 8
 };
 int sweep_profile_enable(int on);
 int sweep_profile_read(int kernel, double* ms, long long* launches);

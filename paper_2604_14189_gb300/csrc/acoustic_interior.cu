@@ -3,38 +3,48 @@
 // reconstruction + imaging update on interior cells at least 4 cells from
 // the border (backward).  See acoustic_common.cuh for the equations.
 //
-// Work is a list of (tile, shot) units, tile-major, split into contiguous
-// chunks over persistent CTAs.  Each CTA runs a two-stage TMA pipeline: while
-// it computes unit k from shared memory, the tiles of unit k+1 are in flight
-// (cp.async.bulk.tensor, completion on an mbarrier).  Halo tiles carry 4
-// extra cells per side; the TMA zero-fills outside the padded grid, which is
-// the Dirichlet condition.  Results go straight from registers to global
-// memory with 16-byte stores.
+// Work is a list of (tile, shot) units taken round-robin by persistent CTAs
+// (one per SM).  Each CTA runs a multi-stage TMA pipeline: while it computes
+// unit k from shared memory, the tiles of the next units are in flight
+// (cp.async.bulk.tensor, completion on one mbarrier per stage).  Halo tiles
+// carry 4 extra cells per side; the TMA zero-fills outside the padded grid,
+// which is the Dirichlet condition.  A warp covers the 128-cell tile width
+// (4 cells per lane, 16-byte shared-memory reads), walks its rows with a
+// register window for the z stencil, and stores results with 16-byte global
+// stores.
 #include "acoustic_common.cuh"
 #include "tma.cuh"
 
 namespace sweep {
 namespace {
 
-constexpr int HALO_F = IN_HW * IN_HH;  // floats in a halo tile
-constexpr int CEN_F = IN_BX * IN_BZ;   // floats in a centre tile
-static_assert((HALO_F * 4) % 128 == 0 && (CEN_F * 4) % 128 == 0, "tile alignment");
+constexpr int RPW_F = IN_BZ_F / (IN_THREADS / 32);  // rows per warp, forward
+constexpr int RPW_B = IN_BZ_B / (IN_THREADS / 32);  // rows per warp, backward
+constexpr int HF_F = IN_HW * (IN_BZ_F + 8);          // floats, forward halo tile
+constexpr int CF_F = IN_BX * IN_BZ_F;                // floats, forward centre tile
+constexpr int HF_B = IN_HW * (IN_BZ_B + 8);
+constexpr int CF_B = IN_BX * IN_BZ_B;
+static_assert((HF_F * 4) % 128 == 0 && (CF_F * 4) % 128 == 0, "alignment");
+static_assert((HF_B * 4) % 128 == 0 && (CF_B * 4) % 128 == 0, "alignment");
 
 struct __align__(128) FwdStage {
-  float u[HALO_F];   // u^n with halo
-  float up[CEN_F];   // u^{n-1}
-  float k[CEN_F];    // K
+  float u[HF_F];   // u^n with halo
+  float up[CF_F];  // u^{n-1}
+  float k[CF_F];   // K
 };
 struct __align__(128) BwdStage {
-  float ua[HALO_F];  // u^n with halo
-  float ma[HALO_F];  // mu^{n+1} with halo
-  float ub[CEN_F];   // u^{n+1}
-  float mb[CEN_F];   // mu^{n+2}
-  float k[CEN_F];    // K
+  float ua[HF_B];  // u^n with halo
+  float ma[HF_B];  // mu^{n+1} with halo
+  float ub[CF_B];  // u^{n+1}
+  float mb[CF_B];  // mu^{n+2}
+  float k[CF_B];   // K
+  float gr[CF_B];  // imaging accumulator of this shot
 };
-constexpr uint32_t kFwdBytes = (HALO_F + 2 * CEN_F) * 4;
-constexpr size_t kFwdSmem = 2 * sizeof(FwdStage) + 64;
-constexpr size_t kBwdSmem = 2 * sizeof(BwdStage) + 64;
+constexpr int FWD_STAGES = 4;
+constexpr int BWD_STAGES = 3;
+constexpr uint32_t kFwdBytes = (HF_F + 2 * CF_F) * 4;
+constexpr size_t kFwdSmem = FWD_STAGES * sizeof(FwdStage) + 8 * FWD_STAGES;
+constexpr size_t kBwdSmem = BWD_STAGES * sizeof(BwdStage) + 8 * BWD_STAGES;
 
 __device__ __forceinline__ float4 lds4(const float* t, int pitch, int r, int c) {
   return *reinterpret_cast<const float4*>(t + r * pitch + c);
@@ -44,65 +54,64 @@ struct UnitPos {
   int s, z0, x0;
 };
 
-__device__ __forceinline__ UnitPos unit_pos(const Region& R, int S, int ntx, int unit) {
+__device__ __forceinline__ UnitPos unit_pos(const Region& R, int S, int ntx, int bz, int unit) {
   const int tile = unit / S;
   UnitPos p;
   p.s = unit - tile * S;
   const int tz = tile / ntx, tx = tile - tz * ntx;
-  p.z0 = R.z0 + tz * IN_BZ;
+  p.z0 = R.z0 + tz * bz;
   p.x0 = R.x0 + tx * IN_BX;
   return p;
 }
 
 // -------------------------------------------------------------- forward
-__global__ void __launch_bounds__(IN_THREADS, 2)
+__global__ void __launch_bounds__(IN_THREADS, 1)
     ac_in_fwd_kernel(const __grid_constant__ AcInFwdArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ ShotTable T;
+  constexpr int D = FWD_STAGES;
   FwdStage* stg = reinterpret_cast<FwdStage*>(smem_raw);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * sizeof(FwdStage));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(FwdStage));
   if (*a.status) return;
   const Geom& g = a.g;
   const Region& R = g.fin;
   const int S = g.nshot;
-  const int ub = (int)((long long)a.units * blockIdx.x / gridDim.x);
-  const int ue = (int)((long long)a.units * (blockIdx.x + 1) / gridDim.x);
-  const int count = ue - ub;
+  const int G = gridDim.x;
+  const int count = (a.units - (int)blockIdx.x + G - 1) / G;  // units b, b+G, ...
   if (count <= 0) return;
+  load_shot_table(T, g, a.src, a.wavelet, a.rbox, a.n);
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
     fence_barrier_init();
   }
   __syncthreads();
   auto issue = [&](int k) {
-    const UnitPos p = unit_pos(R, S, a.ntx, ub + k);
-    FwdStage& sg = stg[k & 1];
-    mbar_arrive_expect_tx(&bar[k & 1], kFwdBytes);
-    tma_load_3d(sg.u, &a.tu, &bar[k & 1], p.x0 - 4, p.z0 - 4, p.s);
-    tma_load_3d(sg.up, &a.tup, &bar[k & 1], p.x0, p.z0, p.s);
-    tma_load_2d(sg.k, &a.tK, &bar[k & 1], p.x0, p.z0);
+    const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_F, blockIdx.x + k * G);
+    FwdStage& sg = stg[k % D];
+    uint64_t* b = &bar[k % D];
+    mbar_arrive_expect_tx(b, kFwdBytes);
+    tma_load_3d(sg.u, &a.tu, b, p.x0 - 4, p.z0 - 4, p.s);
+    tma_load_3d(sg.up, &a.tup, b, p.x0, p.z0, p.s);
+    tma_load_2d(sg.k, &a.tK, b, p.x0, p.z0);
   };
-  if (threadIdx.x == 0) {
-    issue(0);
-    if (count > 1) issue(1);
-  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < D && k < count; ++k) issue(k);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int lx = 4 * lane, r0 = warp * IN_RPW;
+  const int lx = 4 * lane, r0 = warp * RPW_F;
   int k = 0;
   for (; k < count; ++k) {
-    const bool got = mbar_wait(&bar[k & 1], (k >> 1) & 1);
+    const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
     if (__syncthreads_or(!got)) break;
-    const UnitPos p = unit_pos(R, S, a.ntx, ub + k);
-    const FwdStage& sg = stg[k & 1];
+    const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_F, blockIdx.x + k * G);
+    const ShotInfo si = shot_info(T, g, a.src, a.wavelet, a.rbox, a.n, p.s);
+    const FwdStage& sg = stg[k % D];
     const long long so = (long long)p.s * g.fstride;
-    const int sz = a.src[2 * p.s] + g.P, sx = a.src[2 * p.s + 1] + g.P;
-    const float fn = a.wavelet[(long long)p.s * g.nt + a.n];
     const int gx = p.x0 + lx;
     float w[9][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) f4a(lds4(sg.u, IN_HW, r0 + j, lx + 4), w[j]);
 #pragma unroll
-    for (int q = 0; q < IN_RPW; ++q) {
+    for (int q = 0; q < RPW_F; ++q) {
       f4a(lds4(sg.u, IN_HW, r0 + q + 8, lx + 4), w[8]);
       const int gz = p.z0 + r0 + q;
       if (gz < R.z1 && gx < R.x1) {
@@ -120,7 +129,7 @@ __global__ void __launch_bounds__(IN_THREADS, 2)
                  e[c + 8]) +
               d2(w[0][c], w[1][c], w[2][c], w[3][c], w[4][c], w[5][c], w[6][c], w[7][c], w[8][c]);
           out[c] = 2.f * w[4][c] - up[c] + kk[c] * lap;
-          if (gz == sz && gx + c == sx) out[c] += kk[c] * fn;
+          if (gz == si.sz && gx + c == si.sx) out[c] += kk[c] * si.fn;
         }
         *reinterpret_cast<float4*>(a.un + so + (long long)gz * g.NXp + gx) =
             make_float4(out[0], out[1], out[2], out[3]);
@@ -131,29 +140,27 @@ __global__ void __launch_bounds__(IN_THREADS, 2)
         for (int c = 0; c < 4; ++c) w[j][c] = w[j + 1][c];
       }
     }
-    __syncthreads();  // stage k&1 fully read; this unit's stores visible
-    if (threadIdx.x == 0 && k + 2 < count) {
+    __syncthreads();  // stage released; this unit's stores visible to the CTA
+    if (threadIdx.x == 0 && k + D < count) {
       fence_proxy_async_smem();
-      issue(k + 2);
+      issue(k + D);
     }
     // receivers of this shot inside this tile (read back this CTA's stores)
-    if (a.data && tile_meets_box(a.rbox + 4 * p.s, p.z0, IN_BZ, p.x0, IN_BX)) {
+    if (a.data && tile_meets(si.box, p.z0, IN_BZ_F, p.x0, IN_BX)) {
       for (int r = threadIdx.x; r < g.nrec; r += IN_THREADS) {
         const int32_t* q = a.rec + 2 * ((long long)p.s * g.nrec + r);
         const int rz = q[0] + g.P, rx = q[1] + g.P;
-        if (rz >= p.z0 && rz < p.z0 + IN_BZ && rx >= p.x0 && rx < p.x0 + IN_BX &&
+        if (rz >= p.z0 && rz < p.z0 + IN_BZ_F && rx >= p.x0 && rx < p.x0 + IN_BX &&
             in_region(R, rz, rx))
           a.data[((long long)p.s * g.nrec + r) * g.nt + a.n] =
               a.un[so + (long long)rz * g.NXp + rx];
       }
     }
   }
-  if (k < count) {
+  if (k < count && threadIdx.x == 0) {
     // a transfer never landed: report, drain what is still in flight
-    if (threadIdx.x == 0) {
-      latch(a.status, SWEEP_ETIMEOUT);
-      for (int j = k; j < count && j < k + 2; ++j) mbar_wait(&bar[j & 1], (j >> 1) & 1);
-    }
+    latch(a.status, SWEEP_ETIMEOUT);
+    for (int j = k; j < count && j < k + D; ++j) mbar_wait(&bar[j % D], (j / D) & 1);
   }
 }
 
@@ -161,50 +168,52 @@ __global__ void __launch_bounds__(IN_THREADS, 2)
 __global__ void __launch_bounds__(IN_THREADS, 1)
     ac_in_bwd_kernel(const __grid_constant__ AcInBwdArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ ShotTable T;
+  constexpr int D = BWD_STAGES;
   BwdStage* stg = reinterpret_cast<BwdStage*>(smem_raw);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * sizeof(BwdStage));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(BwdStage));
   if (*a.status) return;
   const Geom& g = a.g;
   const Region& R = g.bin;
   const int S = g.nshot;
-  const int ub = (int)((long long)a.units * blockIdx.x / gridDim.x);
-  const int ue = (int)((long long)a.units * (blockIdx.x + 1) / gridDim.x);
-  const int count = ue - ub;
+  const int G = gridDim.x;
+  const int count = (a.units - (int)blockIdx.x + G - 1) / G;
   if (count <= 0) return;
   const bool img = a.do_img != 0, adj = a.do_adj != 0, rec = a.do_rec != 0;
-  const uint32_t bytes = (HALO_F + CEN_F) * 4 + (img ? HALO_F * 4 : 0) +
-                         (rec ? CEN_F * 4 : 0) + (adj ? CEN_F * 4 : 0);
+  const uint32_t bytes = (HF_B + CF_B) * 4 + (img ? (HF_B + CF_B) * 4 : 0) +
+                         (rec ? CF_B * 4 : 0) + (adj ? CF_B * 4 : 0);
+  load_shot_table(T, g, a.src, img ? a.wavelet : nullptr, a.rbox, a.n);
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
     fence_barrier_init();
   }
   __syncthreads();
   auto issue = [&](int k) {
-    const UnitPos p = unit_pos(R, S, a.ntx, ub + k);
-    BwdStage& sg = stg[k & 1];
-    mbar_arrive_expect_tx(&bar[k & 1], bytes);
-    tma_load_3d(sg.ma, &a.tmA, &bar[k & 1], p.x0 - 4, p.z0 - 4, p.s);
-    tma_load_2d(sg.k, &a.tK, &bar[k & 1], p.x0, p.z0);
-    if (img) tma_load_3d(sg.ua, &a.tuA, &bar[k & 1], p.x0 - 4, p.z0 - 4, p.s);
-    if (rec) tma_load_3d(sg.ub, &a.tuB, &bar[k & 1], p.x0, p.z0, p.s);
-    if (adj) tma_load_3d(sg.mb, &a.tmB, &bar[k & 1], p.x0, p.z0, p.s);
+    const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_B, blockIdx.x + k * G);
+    BwdStage& sg = stg[k % D];
+    uint64_t* b = &bar[k % D];
+    mbar_arrive_expect_tx(b, bytes);
+    tma_load_3d(sg.ma, &a.tmA, b, p.x0 - 4, p.z0 - 4, p.s);
+    tma_load_2d(sg.k, &a.tK, b, p.x0, p.z0);
+    if (img) {
+      tma_load_3d(sg.ua, &a.tuA, b, p.x0 - 4, p.z0 - 4, p.s);
+      tma_load_3d(sg.gr, &a.tG, b, p.x0, p.z0, p.s);
+    }
+    if (rec) tma_load_3d(sg.ub, &a.tuB, b, p.x0, p.z0, p.s);
+    if (adj) tma_load_3d(sg.mb, &a.tmB, b, p.x0, p.z0, p.s);
   };
-  if (threadIdx.x == 0) {
-    issue(0);
-    if (count > 1) issue(1);
-  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < D && k < count; ++k) issue(k);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int lx = 4 * lane, r0 = warp * IN_RPW;
+  const int lx = 4 * lane, r0 = warp * RPW_B;
   int k = 0;
   for (; k < count; ++k) {
-    const bool got = mbar_wait(&bar[k & 1], (k >> 1) & 1);
+    const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
     if (__syncthreads_or(!got)) break;
-    const UnitPos p = unit_pos(R, S, a.ntx, ub + k);
-    const BwdStage& sg = stg[k & 1];
+    const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_B, blockIdx.x + k * G);
+    const ShotInfo si = shot_info(T, g, a.src, img ? a.wavelet : nullptr, a.rbox, a.n, p.s);
+    const BwdStage& sg = stg[k % D];
     const long long so = (long long)p.s * g.fstride;
-    const int sz = a.src[2 * p.s] + g.P, sx = a.src[2 * p.s + 1] + g.P;
-    const float fn = img ? a.wavelet[(long long)p.s * g.nt + a.n] : 0.f;
     const int gx = p.x0 + lx;
     float wm[9][4], wu[9][4];
 #pragma unroll
@@ -213,7 +222,7 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
       if (img) f4a(lds4(sg.ua, IN_HW, r0 + j, lx + 4), wu[j]);
     }
 #pragma unroll
-    for (int q = 0; q < IN_RPW; ++q) {
+    for (int q = 0; q < RPW_B; ++q) {
       f4a(lds4(sg.ma, IN_HW, r0 + q + 8, lx + 4), wm[8]);
       if (img) f4a(lds4(sg.ua, IN_HW, r0 + q + 8, lx + 4), wu[8]);
       const int gz = p.z0 + r0 + q;
@@ -251,15 +260,14 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
                         e[c + 7], e[c + 8]) +
                      d2(wu[0][c], wu[1][c], wu[2][c], wu[3][c], wu[4][c], wu[5][c], wu[6][c],
                         wu[7][c], wu[8][c]);
-            if (gz == sz && gx + c == sx) lap[c] += fn;
+            if (gz == si.sz && gx + c == si.sx) lap[c] += si.fn;
           }
-          float4* gp = reinterpret_cast<float4*>(a.graw + ci);
-          float4 gv = *gp;
+          float4 gv = lds4(sg.gr, IN_BX, r0 + q, lx);
           gv.x += wm[4][0] * lap[0];
           gv.y += wm[4][1] * lap[1];
           gv.z += wm[4][2] * lap[2];
           gv.w += wm[4][3] * lap[3];
-          *gp = gv;
+          *reinterpret_cast<float4*>(a.graw + ci) = gv;
           if (a.illum) {
             float4* ip = reinterpret_cast<float4*>(a.illum + ci);
             float4 iv = *ip;
@@ -288,20 +296,21 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
       }
     }
     // adjoint source gather: f-bar^n = mu^{n+1}(s)
-    if (a.wgrad && threadIdx.x == 0 && a.n < g.nt && sz >= p.z0 && sz < p.z0 + IN_BZ &&
-        sx >= p.x0 && sx < p.x0 + IN_BX && in_region(R, sz, sx))
-      a.wgrad[(long long)p.s * g.nt + a.n] = sg.ma[(sz - p.z0 + 4) * IN_HW + (sx - p.x0 + 4)];
-    __syncthreads();  // stage k&1 fully read; mu^n stores visible to this CTA
-    if (threadIdx.x == 0 && k + 2 < count) {
+    if (a.wgrad && threadIdx.x == 0 && a.n < g.nt && si.sz >= p.z0 && si.sz < p.z0 + IN_BZ_B &&
+        si.sx >= p.x0 && si.sx < p.x0 + IN_BX && in_region(R, si.sz, si.sx))
+      a.wgrad[(long long)p.s * g.nt + a.n] =
+          sg.ma[(si.sz - p.z0 + 4) * IN_HW + (si.sx - p.x0 + 4)];
+    __syncthreads();  // stage released; mu^n stores visible to this CTA
+    if (threadIdx.x == 0 && k + D < count) {
       fence_proxy_async_smem();
-      issue(k + 2);
+      issue(k + D);
     }
     // residual injection mu^n(r) += K(r) r^{n-1} for receivers in this tile
-    if (adj && a.n >= 1 && tile_meets_box(a.rbox + 4 * p.s, p.z0, IN_BZ, p.x0, IN_BX)) {
+    if (adj && a.n >= 1 && tile_meets(si.box, p.z0, IN_BZ_B, p.x0, IN_BX)) {
       for (int r = threadIdx.x; r < g.nrec; r += IN_THREADS) {
         const int32_t* q = a.rec + 2 * ((long long)p.s * g.nrec + r);
         const int rz = q[0] + g.P, rx = q[1] + g.P;
-        if (rz >= p.z0 && rz < p.z0 + IN_BZ && rx >= p.x0 && rx < p.x0 + IN_BX &&
+        if (rz >= p.z0 && rz < p.z0 + IN_BZ_B && rx >= p.x0 && rx < p.x0 + IN_BX &&
             in_region(R, rz, rx)) {
           const float rv = a.res[((long long)p.s * g.nrec + r) * g.nt + (a.n - 1)];
           atomicAdd(a.mB + so + (long long)rz * g.NXp + rx,
@@ -310,21 +319,23 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
       }
     }
   }
-  if (k < count) {
-    if (threadIdx.x == 0) {
-      latch(a.status, SWEEP_ETIMEOUT);
-      for (int j = k; j < count && j < k + 2; ++j) mbar_wait(&bar[j & 1], (j >> 1) & 1);
-    }
+  if (k < count && threadIdx.x == 0) {
+    latch(a.status, SWEEP_ETIMEOUT);
+    for (int j = k; j < count && j < k + D; ++j) mbar_wait(&bar[j % D], (j / D) & 1);
   }
 }
 
 }  // namespace
 
 int device_sms() {
-  int dev = 0, n = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-  return n > 0 ? n : 1;
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    n = v > 0 ? v : 1;
+  }
+  return n;
 }
 
 void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st) {
@@ -335,9 +346,11 @@ void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st) {
                          (int)kFwdSmem);
     attr = true;
   }
-  int grid = 2 * device_sms();
+  int grid = device_sms();
   if (grid > a.units) grid = a.units;
+  void* tok = profile_begin(SWEEP_K_AC_FWD_IN, st);
   ac_in_fwd_kernel<<<grid, IN_THREADS, kFwdSmem, st>>>(a);
+  profile_end(tok, st);
   note_launches(1);
 }
 
@@ -351,7 +364,9 @@ void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st) {
   }
   int grid = device_sms();
   if (grid > a.units) grid = a.units;
+  void* tok = profile_begin(SWEEP_K_AC_BWD_IN, st);
   ac_in_bwd_kernel<<<grid, IN_THREADS, kBwdSmem, st>>>(a);
+  profile_end(tok, st);
   note_launches(1);
 }
 

@@ -220,26 +220,38 @@ SetupArgs setup_args(const sweep_problem* p, const Layout& L, void* ws, const fl
   return s;
 }
 
-// TMA descriptors of one per-shot field [S][NZ][NXp]: halo box and centre box.
-bool field_maps(const Geom& g, const float* base, CUtensorMap* halo, CUtensorMap* centre) {
+// TMA descriptors of one per-shot field [S][NZ][NXp] for interior tiles of
+// bz rows: halo box and centre box.
+bool field_maps(const Geom& g, const float* base, CUtensorMap* halo, CUtensorMap* centre,
+                int bz) {
   const uint64_t S = (uint64_t)(g.nshot > 0 ? g.nshot : 1);
   bool ok = true;
   if (halo)
     ok = ok && make_tensor_map(halo, base, 3, g.NX, g.NZ, S, g.NXp, (uint64_t)g.fstride, IN_HW,
-                               IN_HH, 1);
+                               bz + 8, 1);
   if (centre)
     ok = ok && make_tensor_map(centre, base, 3, g.NX, g.NZ, S, g.NXp, (uint64_t)g.fstride, IN_BX,
-                               IN_BZ, 1);
+                               bz, 1);
   return ok;
 }
 
-int region_units(const Region& R, int nshot, int* ntx) {
+// Per-shot field [S][NZ][NXp] with an arbitrary box (bx, bz, 1).
+bool map3(CUtensorMap* m, const Geom& g, const float* base, uint32_t bx, uint32_t bz) {
+  const uint64_t S = (uint64_t)(g.nshot > 0 ? g.nshot : 1);
+  return make_tensor_map(m, base, 3, g.NX, g.NZ, S, g.NXp, (uint64_t)g.fstride, bx, bz, 1);
+}
+// The shared K grid [NZ][NXp] with box (bx, bz).
+bool map2(CUtensorMap* m, const Geom& g, const float* base, uint32_t bx, uint32_t bz) {
+  return make_tensor_map(m, base, 2, g.NX, g.NZ, 1, g.NXp, (uint64_t)g.fstride, bx, bz, 1);
+}
+
+int region_units(const Region& R, int nshot, int bz, int* ntx) {
   if (R.z1 <= R.z0 || R.x1 <= R.x0) {
     *ntx = 0;
     return 0;
   }
   *ntx = (R.x1 - R.x0 + IN_BX - 1) / IN_BX;
-  const int ntz = (R.z1 - R.z0 + IN_BZ - 1) / IN_BZ;
+  const int ntz = (R.z1 - R.z0 + bz - 1) / bz;
   return *ntx * ntz * nshot;
 }
 
@@ -257,14 +269,12 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
 
   AcInFwdArgs in{};
   in.g = g;
-  in.units = region_units(g.fin, g.nshot, &in.ntx);
+  in.units = region_units(g.fin, g.nshot, IN_BZ_F, &in.ntx);
   CUtensorMap tu_h[2], tu_c[2];
   if (in.units > 0) {
     for (int b = 0; b < 2; ++b)
-      if (!field_maps(g, at<float>(ws, L.u[b]), &tu_h[b], &tu_c[b])) return SWEEP_ECUDA;
-    if (!make_tensor_map(&in.tK, at<float>(ws, L.K), 2, g.NX, g.NZ, 1, g.NXp, (uint64_t)g.fstride,
-                         IN_BX, IN_BZ, 1))
-      return SWEEP_ECUDA;
+      if (!field_maps(g, at<float>(ws, L.u[b]), &tu_h[b], &tu_c[b], IN_BZ_F)) return SWEEP_ECUDA;
+    if (!map2(&in.tK, g, at<float>(ws, L.K), IN_BX, IN_BZ_F)) return SWEEP_ECUDA;
   }
   in.wavelet = wavelet;
   in.src = src;
@@ -276,6 +286,19 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
   AcFrFwdArgs fr{};
   fr.g = g;
   fr.fr = frame_rects(g, g.fin);
+  fr.units = fr.fr.first[fr.fr.n] * g.nshot;
+  CUtensorMap fu_h[2], fu_c[2], fpx[2], fpz[2];
+  for (int b = 0; b < 2; ++b) {
+    if (!map3(&fu_h[b], g, at<float>(ws, L.u[b]), FR_HW, FR_HH) ||
+        !map3(&fu_c[b], g, at<float>(ws, L.u[b]), FR_TX, FR_TZ) ||
+        !map3(&fpx[b], g, at<float>(ws, L.psx[b]), FR_HW, FR_TZ) ||
+        !map3(&fpz[b], g, at<float>(ws, L.psz[b]), FR_TX, FR_HH))
+      return SWEEP_ECUDA;
+  }
+  if (!map2(&fr.tK, g, at<float>(ws, L.K), FR_TX, FR_TZ) ||
+      !map3(&fr.tzx, g, at<float>(ws, L.zex), FR_TX, FR_TZ) ||
+      !map3(&fr.tzz, g, at<float>(ws, L.zez), FR_TX, FR_TZ))
+    return SWEEP_ECUDA;
   fr.K = at<float>(ws, L.K);
   fr.zex = at<float>(ws, L.zex);
   fr.zez = at<float>(ws, L.zez);
@@ -300,6 +323,10 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
       launch_ac_in_fwd(in, st);
     }
     fr.n = n;
+    fr.tu = fu_h[A];
+    fr.tup = fu_c[B];
+    fr.tpx = fpx[A];
+    fr.tpz = fpz[A];
     fr.u = at<float>(ws, L.u[A]);
     fr.un = at<float>(ws, L.u[B]);
     fr.psx_in = at<float>(ws, L.psx[A]);
@@ -333,16 +360,16 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
 
   AcInBwdArgs in{};
   in.g = g;
-  in.units = region_units(g.bin, g.nshot, &in.ntx);
+  in.units = region_units(g.bin, g.nshot, IN_BZ_B, &in.ntx);
   CUtensorMap tu_h[2], tu_c[2], tm_h[2], tm_c[2];
   if (in.units > 0) {
     for (int b = 0; b < 2; ++b) {
-      if (imaging && !field_maps(g, at<float>(ws, L.u[b]), &tu_h[b], &tu_c[b]))
+      if (imaging && !field_maps(g, at<float>(ws, L.u[b]), &tu_h[b], &tu_c[b], IN_BZ_B))
         return SWEEP_ECUDA;
-      if (!field_maps(g, at<float>(ws, L.m[b]), &tm_h[b], &tm_c[b])) return SWEEP_ECUDA;
+      if (!field_maps(g, at<float>(ws, L.m[b]), &tm_h[b], &tm_c[b], IN_BZ_B)) return SWEEP_ECUDA;
     }
-    if (!make_tensor_map(&in.tK, at<float>(ws, L.K), 2, g.NX, g.NZ, 1, g.NXp, (uint64_t)g.fstride,
-                         IN_BX, IN_BZ, 1))
+    if (!map2(&in.tK, g, at<float>(ws, L.K), IN_BX, IN_BZ_B)) return SWEEP_ECUDA;
+    if (imaging && !field_maps(g, at<float>(ws, L.graw), nullptr, &in.tG, IN_BZ_B))
       return SWEEP_ECUDA;
   }
   in.graw = imaging ? at<float>(ws, L.graw) : nullptr;
@@ -359,6 +386,24 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
   AcFrBwdArgs fr{};
   fr.g = g;
   fr.fr = frame_rects(g, g.bin);
+  fr.units = fr.fr.first[fr.fr.n] * g.nshot;
+  CUtensorMap fm_h[2], fm_c[2], fu_h[2], fu_c[2], fzbx[2], fpbx[2], fzbz[2], fpbz[2];
+  for (int b = 0; b < 2; ++b) {
+    if (!map3(&fm_h[b], g, at<float>(ws, L.m[b]), FR_HW, FR_HH) ||
+        !map3(&fm_c[b], g, at<float>(ws, L.m[b]), FR_TX, FR_TZ) ||
+        !map3(&fzbx[b], g, at<float>(ws, L.zbx[b]), FR_HW, FR_TZ) ||
+        !map3(&fpbx[b], g, at<float>(ws, L.pbx[b]), FR_HW, FR_TZ) ||
+        !map3(&fzbz[b], g, at<float>(ws, L.zbz[b]), FR_TX, FR_HH) ||
+        !map3(&fpbz[b], g, at<float>(ws, L.pbz[b]), FR_TX, FR_HH))
+      return SWEEP_ECUDA;
+    if (imaging && (!map3(&fu_h[b], g, at<float>(ws, L.u[b]), FR_HW, FR_HH) ||
+                    !map3(&fu_c[b], g, at<float>(ws, L.u[b]), FR_TX, FR_TZ)))
+      return SWEEP_ECUDA;
+  }
+  if (!map2(&fr.tK, g, at<float>(ws, L.K), FR_TX, FR_TZ)) return SWEEP_ECUDA;
+  if (imaging && !map3(&fr.tG, g, at<float>(ws, L.graw), FR_TX, FR_TZ)) return SWEEP_ECUDA;
+  if (imaging && illum && !map3(&fr.tI, g, at<float>(ws, L.iraw), FR_TX, FR_TZ))
+    return SWEEP_ECUDA;
   fr.K = at<float>(ws, L.K);
   fr.ax = at<float>(ws, L.ax);
   fr.bx = at<float>(ws, L.bx);
@@ -398,6 +443,16 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
     fr.do_adj = do_adj;
     fr.do_img = do_img;
     fr.do_rec = do_rec;
+    fr.tmA = fm_h[B];
+    fr.tmB = fm_c[A];
+    if (imaging) {
+      fr.tuA = fu_h[A];
+      fr.tuB = fu_c[B];
+    }
+    fr.tzbx = fzbx[A];
+    fr.tpbx = fpbx[A];
+    fr.tzbz = fzbz[A];
+    fr.tpbz = fpbz[A];
     fr.uA = imaging ? at<float>(ws, L.u[A]) : nullptr;
     fr.uB = imaging ? at<float>(ws, L.u[B]) : nullptr;
     fr.mA = at<float>(ws, L.m[B]);

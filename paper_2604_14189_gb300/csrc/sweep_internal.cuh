@@ -34,14 +34,14 @@ struct Geom {
 };
 
 // ------------------------------------------------------------------ interior
-// Tiles of IN_BZ x IN_BX cells; IN_THREADS threads: each warp owns IN_RPW
-// rows, each lane 4 consecutive cells of a row.
+// Tiles of IN_BZ_F (forward) or IN_BZ_B (backward) rows x IN_BX cells;
+// IN_THREADS threads: each warp owns a band of rows, each lane 4 consecutive
+// cells of a row.  Halo tiles are IN_HW wide and 8 rows taller.
 constexpr int IN_BX = 128;
-constexpr int IN_BZ = 32;
+constexpr int IN_BZ_F = 32;
+constexpr int IN_BZ_B = 16;
 constexpr int IN_THREADS = 256;
-constexpr int IN_RPW = IN_BZ / (IN_THREADS / 32);
 constexpr int IN_HW = IN_BX + 8;  // halo tile width
-constexpr int IN_HH = IN_BZ + 8;  // halo tile height
 
 struct AcInFwdArgs {
   Geom g;
@@ -66,6 +66,7 @@ struct AcInBwdArgs {
   CUtensorMap tuB;   // u^{n+1}, centre box
   CUtensorMap tmB;   // mu^{n+2}, centre box
   CUtensorMap tK;
+  CUtensorMap tG;    // imaging accumulator graw, centre box
   float* uB;         // out u^{n-1}
   float* mB;         // out mu^n
   float* graw;       // [S][NZ][NXp]
@@ -84,9 +85,13 @@ struct AcInBwdArgs {
 };
 
 // --------------------------------------------------------------------- frame
+// Tiles of FR_TZ x FR_TX cells; each thread owns one column of FR_TZ /
+// (FR_THREADS / FR_TX) rows.
 constexpr int FR_TZ = 16;
 constexpr int FR_TX = 64;
-constexpr int FR_THREADS = 128;
+constexpr int FR_THREADS = 512;
+constexpr int FR_HW = FR_TX + 8;  // halo tile width
+constexpr int FR_HH = FR_TZ + 8;  // halo tile height
 
 struct FrameRects {
   int n;               // rectangles (<= 4)
@@ -95,9 +100,20 @@ struct FrameRects {
   int first[5];        // prefix sum of tiles
 };
 
+// The frame kernels are persistent TMA pipelines over (frame tile, shot)
+// units, like the interior kernels; boxes: halo (FR_HW, FR_HH), centre
+// (FR_TX, FR_TZ), x halo (FR_HW, FR_TZ), z halo (FR_TX, FR_HH).
 struct AcFrFwdArgs {
   Geom g;
   FrameRects fr;
+  CUtensorMap tu;     // u^n, halo box
+  CUtensorMap tup;    // u^{n-1}, centre box
+  CUtensorMap tK;     // K, centre box (2D)
+  CUtensorMap tpx;    // psi_x^{n-1}, x-halo box
+  CUtensorMap tpz;    // psi_z^{n-1}, z-halo box
+  CUtensorMap tzx;    // zeta_x, centre box
+  CUtensorMap tzz;    // zeta_z, centre box
+  int units;
   const float* u;     // u^n
   float* un;          // in u^{n-1}, out u^{n+1}
   const float* K;
@@ -124,6 +140,18 @@ struct AcFrFwdArgs {
 struct AcFrBwdArgs {
   Geom g;
   FrameRects fr;
+  CUtensorMap tmA;    // mu^{n+1}, halo box
+  CUtensorMap tuA;    // u^n, halo box
+  CUtensorMap tK;     // K, centre box (2D)
+  CUtensorMap tmB;    // mu^{n+2}, centre box
+  CUtensorMap tuB;    // u^{n+1}, centre box
+  CUtensorMap tG;     // graw, centre box
+  CUtensorMap tI;     // illumination, centre box
+  CUtensorMap tzbx;   // zetabar_x^n, x-halo box
+  CUtensorMap tpbx;   // psibar_x^n, x-halo box
+  CUtensorMap tzbz;   // zetabar_z^n, z-halo box
+  CUtensorMap tpbz;   // psibar_z^n, z-halo box
+  int units;
   const float* uA;    // u^n
   float* uB;          // in u^{n+1}, out u^{n-1}
   const float* mA;    // mu^{n+1}
