@@ -68,6 +68,9 @@ struct Layout {
   size_t u[2] = {0, 0}, psx[2] = {0, 0}, psz[2] = {0, 0}, zex = 0, zez = 0;
   size_t m[2] = {0, 0}, pbx[2] = {0, 0}, pbz[2] = {0, 0}, zbx[2] = {0, 0}, zbz[2] = {0, 0};
   size_t data = 0, save = 0, graw = 0, iraw = 0;
+  size_t el_par[5] = {0, 0, 0, 0, 0};  // elastic coefficients
+  size_t el_f[5] = {0, 0, 0, 0, 0};    // vx, vz, txx, tzz, txz
+  size_t el_p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   size_t fwd_lo = 0, fwd_hi = 0;  // contiguous range of forward fields
   size_t adj_lo = 0, adj_hi = 0;  // contiguous range of adjoint fields
   size_t total = 0;
@@ -140,6 +143,15 @@ Layout layout(const sweep_problem* p, int mode) {
   L.bxh = b.take(sizeof(float) * g.NXp);
   L.azh = b.take(sizeof(float) * g.NZ);
   L.bzh = b.take(sizeof(float) * g.NZ);
+  if (p->physics == SWEEP_ELASTIC) {
+    for (int i = 0; i < 5; ++i) L.el_par[i] = b.take(sizeof(float) * (size_t)g.fstride);
+    L.fwd_lo = b.off;
+    for (int i = 0; i < 5; ++i) L.el_f[i] = b.take(F);
+    for (int i = 0; i < 8; ++i) L.el_p[i] = b.take(F);
+    L.fwd_hi = b.off;
+    L.total = b.off;
+    return L;
+  }
   if (mode == SWEEP_MODE_FORWARD || mode == SWEEP_MODE_GRADIENT) {
     L.fwd_lo = b.off;
     L.u[0] = b.take(F);
@@ -472,6 +484,60 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
   return SWEEP_OK;
 }
 
+// Elastic forward time loop: velocity then stress kernel per step.
+int elastic_forward_loop(const sweep_problem* p, const Layout& L, void* ws, const float* model,
+                         const float* wavelet, const int32_t* src, const int32_t* rec,
+                         float* data, cudaStream_t st) {
+  const Geom g = make_geom(p);
+  cudaMemsetAsync(at<char>(ws, L.fwd_lo), 0, L.fwd_hi - L.fwd_lo, st);
+  ElParamArgs pa{};
+  pa.g = g;
+  pa.model = model;
+  pa.padded = (p->flags & SWEEP_F_PADDED_MODEL) ? 1 : 0;
+  pa.dx = p->dx;
+  pa.dt = p->dt;
+  pa.cbx = at<float>(ws, L.el_par[0]);
+  pa.cbz = at<float>(ws, L.el_par[1]);
+  pa.cl2m = at<float>(ws, L.el_par[2]);
+  pa.clam = at<float>(ws, L.el_par[3]);
+  pa.cmu = at<float>(ws, L.el_par[4]);
+  launch_el_params(pa, st);
+  ElStepArgs a{};
+  a.g = g;
+  a.vx = at<float>(ws, L.el_f[0]);
+  a.vz = at<float>(ws, L.el_f[1]);
+  a.txx = at<float>(ws, L.el_f[2]);
+  a.tzz = at<float>(ws, L.el_f[3]);
+  a.txz = at<float>(ws, L.el_f[4]);
+  float** ps[8] = {&a.p1, &a.p2, &a.p3, &a.p4, &a.p5, &a.p6, &a.p7, &a.p8};
+  for (int i = 0; i < 8; ++i) *ps[i] = at<float>(ws, L.el_p[i]);
+  a.cbx = pa.cbx;
+  a.cbz = pa.cbz;
+  a.cl2m = pa.cl2m;
+  a.clam = pa.clam;
+  a.cmu = pa.cmu;
+  a.ax = at<float>(ws, L.ax);
+  a.bx = at<float>(ws, L.bx);
+  a.axh = at<float>(ws, L.axh);
+  a.bxh = at<float>(ws, L.bxh);
+  a.az = at<float>(ws, L.az);
+  a.bz = at<float>(ws, L.bz);
+  a.azh = at<float>(ws, L.azh);
+  a.bzh = at<float>(ws, L.bzh);
+  a.wavelet = wavelet;
+  a.src = src;
+  a.rec = rec;
+  a.rbox = at<int32_t>(ws, L.rbox);
+  a.data = data;
+  a.src_scale = (float)((double)p->dt / ((double)p->dx * p->dx));
+  a.status = at<int>(ws, L.status);
+  for (int n = 0; n < g.nt; ++n) {
+    a.n = n;
+    launch_el_step(a, st);
+  }
+  return SWEEP_OK;
+}
+
 }  // namespace
 }  // namespace sweep
 
@@ -503,9 +569,17 @@ int sweep_forward(const sweep_problem* p, const float* model, const float* wavel
   if (!model) return SWEEP_EINVAL;
   if (p->nshot > 0 && (!wavelet || !src)) return SWEEP_EINVAL;
   if (p->nshot > 0 && p->nrec > 0 && (!rec || !data)) return SWEEP_EINVAL;
-  if (p->physics != SWEEP_ACOUSTIC) return SWEEP_EUNSUPPORTED;
   if (p->nshot == 0) return SWEEP_OK;
   const Layout L = layout(p, SWEEP_MODE_FORWARD);
+  if (p->physics == SWEEP_ELASTIC) {
+    SetupArgs sa = setup_args(p, L, ws, model, src, rec);
+    sa.K = nullptr;  // no acoustic K for the elastic engine
+    launch_setup(sa, st);
+    rc = elastic_forward_loop(p, L, ws, model, wavelet, src, rec, p->nrec > 0 ? data : nullptr,
+                              st);
+    if (rc) return rc;
+    return cuda_rc(cudaGetLastError());
+  }
   launch_setup(setup_args(p, L, ws, model, src, rec), st);
   rc = acoustic_forward_loop(p, L, ws, wavelet, src, rec, p->nrec > 0 ? data : nullptr, false,
                              st);

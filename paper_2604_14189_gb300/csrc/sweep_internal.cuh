@@ -183,6 +183,42 @@ struct AcFrBwdArgs {
   int do_adj, do_img, do_rec;
 };
 
+// ------------------------------------------------------------------- elastic
+// Coefficients on the padded grid [NZ][NXp], pre-scaled by dt / dx:
+// cbx, cbz = buoyancy at vx / vz points; cl2m = lambda + 2 mu, clam = lambda
+// at normal-stress points; cmu = mu at txz points.
+struct ElParamArgs {
+  Geom g;
+  const float* model;  // [3][nz][nx] (vp, vs, rho) or padded
+  int padded;
+  float dx, dt;
+  float* cbx;
+  float* cbz;
+  float* cl2m;
+  float* clam;
+  float* cmu;
+};
+
+struct ElStepArgs {
+  Geom g;
+  float *vx, *vz, *txx, *tzz, *txz;        // [S][NZ][NXp]
+  float *p1, *p2, *p3, *p4;                // velocity CPML memory variables
+  float *p5, *p6, *p7, *p8;                // stress CPML memory variables
+  const float *cbx, *cbz, *cl2m, *clam, *cmu;
+  const float *ax, *bx, *axh, *bxh;        // x profiles (integer, half points)
+  const float *az, *bz, *azh, *bzh;        // z profiles
+  const float* wavelet;
+  const int32_t* src;
+  const int32_t* rec;
+  const int32_t* rbox;
+  float* data;                             // [S][2][R][nt] or null
+  float src_scale;                         // dt / dx^2
+  const int* status;
+  int n;
+};
+void launch_el_params(const ElParamArgs& a, cudaStream_t st);
+void launch_el_step(const ElStepArgs& a, cudaStream_t st);
+
 // Kernel launchers (acoustic_interior.cu, acoustic_frame.cu)
 void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st);
 void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st);

@@ -1,0 +1,117 @@
+"""Parity of the CUDA elastic (velocity-stress, staggered) forward with the
+FP64 oracle, through the C ABI.  Tolerance: seismograms relative L2 <= 1e-4."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2604_14189_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_14189_gb300 import sweep
+    return sweep
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def run_both(sw, model, nz, nx, pml, dx, dt, nt, f0, src, rec, flags=0):
+    nshot, nrec = src.shape[0], rec.shape[1]
+    w = np.stack([inputs.ricker(f0 * (1 + 0.05 * k), dt, nt) for k in range(nshot)])
+    p = sw.problem(sw.ELASTIC, nz=nz, nx=nx, pml=pml, dx=dx, dt=dt, nt=nt, nshot=nshot,
+                   nrec=nrec, f_ref=f0, flags=flags)
+    q = oracle.make_problem(1, nz, nx, pml, np.float32(dx), np.float32(dt), nt, nshot, nrec,
+                            np.float32(f0), flags)
+    dev = "cuda"
+    d = sw.sweep_forward(p, torch.tensor(model, dtype=torch.float32, device=dev),
+                         torch.tensor(w, dtype=torch.float32, device=dev),
+                         torch.tensor(src, dtype=torch.int32, device=dev),
+                         torch.tensor(rec, dtype=torch.int32, device=dev)).cpu().numpy()
+    ref = oracle.elastic_forward(q, f32(model), f32(w), src, rec)
+    return d, ref
+
+
+def random_model(nz, nx, seed):
+    rng = np.random.default_rng(seed)
+    z = np.arange(nz)[:, None]
+    vp = 2000.0 + 1500.0 * z / nz + 100.0 * rng.standard_normal((nz, nx))
+    vs = vp / rng.uniform(1.6, 2.0, (nz, nx))
+    rho = 310.0 * vp ** 0.25
+    return np.stack([vp, vs, rho])
+
+
+@pytest.mark.parametrize("shape", [(37, 45, 6, 300, 2, 5), (70, 150, 20, 400, 3, 20),
+                                   (9, 11, 4, 150, 1, 3)])
+def test_elastic_forward_matches_oracle(sw, shape):
+    nz, nx, pml, nt, nshot, nrec = shape
+    rng = np.random.default_rng(sum(shape))
+    m = random_model(nz, nx, sum(shape))
+    src = np.stack([rng.integers(0, nz, nshot), rng.integers(0, nx, nshot)], -1)
+    rec = np.stack([rng.integers(0, nz, (nshot, nrec)), rng.integers(0, nx, (nshot, nrec))], -1)
+    d, ref = run_both(sw, m, nz, nx, pml, 5.0, 4e-4, nt, 25.0, src, rec)
+    assert np.abs(ref).max() > 0
+    assert rel(d, ref) <= 1e-4, rel(d, ref)
+
+
+def test_elastic_three_layer_fluid_top(sw):
+    """The paper's acoustic-elastic three-layer setting: Vp 1500/2000/2500,
+    Vs 0/1200/1400, rho 1000/1600/2000, 10 Hz Ricker (no-shear top layer)."""
+    nz, nx = 90, 120
+    z = np.arange(nz)[:, None] + np.zeros((1, nx))
+    vp = np.where(z < 30, 1500.0, np.where(z < 60, 2000.0, 2500.0))
+    vs = np.where(z < 30, 0.0, np.where(z < 60, 1200.0, 1400.0))
+    rho = np.where(z < 30, 1000.0, np.where(z < 60, 1600.0, 2000.0))
+    src = np.array([[10, 60]])
+    rec = inputs.surface_line(1, 5, np.arange(0, nx, 4))
+    d, ref = run_both(sw, np.stack([vp, vs, rho]), nz, nx, 20, 10.0, 1e-3, 500, 10.0, src, rec)
+    assert rel(d, ref) <= 1e-4, rel(d, ref)
+
+
+def test_elastic_padded_model_and_errors(sw):
+    nz, nx, pml = 30, 40, 8
+    m = random_model(nz, nx, 5)
+    mp = inputs.pad_edge(m, pml)
+    mp[2, :4] *= 1.2  # padding values are used
+    src = np.array([[3, 7], [20, 30]])
+    rec = np.array([[[0, 0], [10, 10]], [[29, 39], [5, 5]]])
+    d, ref = run_both(sw, mp, nz, nx, pml, 5.0, 4e-4, 200, 25.0, src, rec,
+                      flags=sw.F_PADDED_MODEL)
+    assert rel(d, ref) <= 1e-4
+    p = sw.problem(sw.ELASTIC, nz=nz, nx=nx, pml=pml, dx=5.0, dt=2e-3, nt=10, nshot=2, nrec=2)
+    with pytest.raises(sw.SweepError) as e:  # 4000 m/s * 2 ms / 5 m > 0.606
+        sw.sweep_forward(p, torch.tensor(m, dtype=torch.float32, device="cuda"),
+                         torch.zeros((2, 10), device="cuda"),
+                         torch.tensor(src, dtype=torch.int32, device="cuda"),
+                         torch.tensor(rec, dtype=torch.int32, device="cuda"))
+    assert e.value.code == sw.ECFL
+    bad = m.copy()
+    bad[1, 3, 3] = bad[0, 3, 3]  # vs = vp: negative lambda
+    p2 = sw.problem(sw.ELASTIC, nz=nz, nx=nx, pml=pml, dx=5.0, dt=4e-4, nt=10, nshot=2, nrec=2)
+    with pytest.raises(sw.SweepError) as e:
+        sw.sweep_forward(p2, torch.tensor(bad, dtype=torch.float32, device="cuda"),
+                         torch.zeros((2, 10), device="cuda"),
+                         torch.tensor(src, dtype=torch.int32, device="cuda"),
+                         torch.tensor(rec, dtype=torch.int32, device="cuda"))
+    assert e.value.code == sw.EMODEL
+
+
+def test_elastic_workload_grid_reduced_shots(sw):
+    """The 500 x 1500 (dx 5 m, dt 0.5 ms, 15 Hz, 40-cell CPML) elastic grid
+    with 2 of its 64 shots and 300 of its 4000 steps, 750 receivers."""
+    wl = inputs.workload_elastic(nshot=2, nt=300)
+    src = wl["src"][[0, 1]]
+    src[1] = [2, 750]
+    d, ref = run_both(sw, wl["model"], wl["nz"], wl["nx"], wl["pml"], wl["dx"], wl["dt"],
+                      wl["nt"], wl["f0"], src, wl["rec"])
+    assert rel(d, ref) <= 1e-4, rel(d, ref)
