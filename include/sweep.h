@@ -85,7 +85,8 @@ enum {
   SWEEP_ETIMEOUT = -6,    /* a bounded device-side wait gave up            */
   SWEEP_ENONFINITE = -7,  /* non-finite model value or misfit              */
   SWEEP_EMODEL = -8,      /* non-positive velocity or density              */
-  SWEEP_EUNSUPPORTED = -9 /* combination not implemented                   */
+  SWEEP_EUNSUPPORTED = -9, /* combination not implemented                  */
+  SWEEP_ETOOBIG = -10     /* size above a fixed internal capacity          */
 };
 
 typedef struct {
@@ -143,6 +144,21 @@ int sweep_gradient(const sweep_problem* prob, const float* model,
 size_t sweep_dot_workspace_bytes(void);
 int sweep_dot(const float* a, const float* b, int64_t n, double* out, void* ws,
               size_t ws_bytes, void* stream);
+
+/* The same FP64 dot product for callers that cannot allocate device memory
+ * (a plugin whose host application owns the device-memory budget, a loop
+ * that must not allocate after start-up).  The paper has no counterpart; this
+ * is a library convenience.  No workspace: the partial sums live in a fixed
+ * 64 KiB device array inside the library, held by every GPU that loads it
+ * until the process exits.  n <= SWEEP_DOT_NOALLOC_MAX_N (32 Mi elements),
+ * else SWEEP_ETOOBIG before any launch.  a, b, out are device pointers on the
+ * device current on the calling thread.  The first call on a device looks up
+ * the array's device address and caches it; make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * race (serialise them on one stream).  Asynchronous on `stream`. */
+#define SWEEP_DOT_NOALLOC_MAX_N 33554432LL
+int sweep_dot_noalloc(const float* a, const float* b, int64_t n, double* out,
+                      void* stream);
 
 /* Synchronises `stream` and returns the status word latched in `ws` by the
  * last call that used it (SWEEP_OK or a negative code). */

@@ -683,6 +683,7 @@ const char* sweep_strerror(int code) {
     case SWEEP_ENONFINITE: return "non-finite model value or misfit";
     case SWEEP_EMODEL: return "non-physical model value";
     case SWEEP_EUNSUPPORTED: return "not implemented for this physics";
+    case SWEEP_ETOOBIG: return "size above a fixed internal capacity";
     default: return "unknown error";
   }
 }

@@ -25,11 +25,14 @@ F_RESIDUAL_IN = 0x2
 OK = 0
 EINVAL, ECFL, EBOUNDS, EWORKSPACE, ECUDA, ETIMEOUT, ENONFINITE, EMODEL, EUNSUPPORTED = (
     -1, -2, -3, -4, -5, -6, -7, -8, -9)
+ETOOBIG = -10
+DOT_NOALLOC_MAX_N = 33554432
 
 # Every symbol declared in include/sweep.h.
 EXPORTS = ("sweep_workspace_bytes", "sweep_forward", "sweep_adjoint", "sweep_gradient",
            "sweep_dot_workspace_bytes", "sweep_dot", "sweep_status", "sweep_strerror",
-           "sweep_kernel_launches", "sweep_profile_enable", "sweep_profile_read")
+           "sweep_kernel_launches", "sweep_profile_enable", "sweep_profile_read",
+           "sweep_dot_noalloc")
 K_AC_FWD, K_AC_BWD, K_EL_VEL, K_EL_STR = 0, 1, 2, 3
 
 
@@ -85,6 +88,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.sweep_dot_workspace_bytes.restype = sz
     lib.sweep_dot.argtypes = [vp, vp, ctypes.c_int64, vp, vp, sz, vp]
     lib.sweep_dot.restype = i32
+    lib.sweep_dot_noalloc.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    lib.sweep_dot_noalloc.restype = i32
     lib.sweep_status.argtypes = [vp, vp]
     lib.sweep_status.restype = i32
     lib.sweep_strerror.argtypes = [i32]
