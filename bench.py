@@ -201,7 +201,7 @@ def run_sweep(args, w, rank, world, local_rank):
     import torch
     import torch.distributed as dist
 
-    from paper_2604_14189_gb300 import sweep
+    from paper_2604_14189_gb300 import shots, sweep
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -225,9 +225,7 @@ def run_sweep(args, w, rank, world, local_rank):
     def step():
         sweep.sweep_gradient(p, v0, wav, src, rec, d_obs, grad=grad, misfit=mis, ws=ws,
                              sync=False)
-        if world > 1:
-            dist.all_reduce(grad)
-            dist.all_reduce(mis)
+        shots.reduce_gradient(grad, mis)
 
     def barrier():
         if world > 1:
@@ -290,9 +288,7 @@ def run_sweep(args, w, rank, world, local_rank):
             dst.copy_(srcb, non_blocking=True)
         sweep.sweep_gradient(p, bufs[0], bufs[1], bufs[2], bufs[3], bufs[4], grad=grad,
                              misfit=mis, ws=ws, sync=False)
-        if world > 1:
-            dist.all_reduce(grad)
-            dist.all_reduce(mis)
+        shots.reduce_gradient(grad, mis)
         grad_h.copy_(grad, non_blocking=True)
         mis_h.copy_(mis, non_blocking=True)
 
