@@ -54,6 +54,26 @@ struct UnitPos {
   int s, z0, x0;
 };
 
+// What a backward unit touches: interior cells (imaging, reconstruction) and
+// ring cells (restore from the forward save).
+struct BwdFlags {
+  bool imgt, ringt, needu1;
+};
+__device__ __forceinline__ BwdFlags bwd_flags(const Geom& g, bool img, bool rec, bool has_save,
+                                              const UnitPos& p) {
+  const int z1 = p.z0 + IN_BZ_B, x1 = p.x0 + IN_BX;
+  const int w = g.ringw;
+  const bool touch_int = z1 > g.P && p.z0 < g.P + g.nz && x1 > g.P && p.x0 < g.P + g.nx;
+  const bool inside = p.z0 >= g.P && z1 <= g.P + g.nz && p.x0 >= g.P && x1 <= g.P + g.nx;
+  const bool touch_ring = w > 0 && !inside && z1 > g.P - w && p.z0 < g.P + g.nz + w &&
+                          x1 > g.P - w && p.x0 < g.P + g.nx + w;
+  BwdFlags f;
+  f.imgt = img && touch_int;
+  f.ringt = rec && has_save && touch_ring;
+  f.needu1 = rec && (f.imgt || f.ringt);
+  return f;
+}
+
 __device__ __forceinline__ UnitPos unit_pos(const Region& R, int S, int ntx, int bz, int unit) {
   const int tile = unit / S;
   UnitPos p;
@@ -180,8 +200,6 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
   const int count = (a.units - (int)blockIdx.x + G - 1) / G;
   if (count <= 0) return;
   const bool img = a.do_img != 0, adj = a.do_adj != 0, rec = a.do_rec != 0;
-  const uint32_t bytes = (HF_B + CF_B) * 4 + (img ? (HF_B + CF_B) * 4 : 0) +
-                         (rec ? CF_B * 4 : 0) + (adj ? CF_B * 4 : 0);
   load_shot_table(T, g, a.src, img ? a.wavelet : nullptr, a.rbox, a.n);
   if (threadIdx.x == 0) {
     for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
@@ -190,16 +208,18 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
   __syncthreads();
   auto issue = [&](int k) {
     const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_B, blockIdx.x + k * G);
+    const BwdFlags f = bwd_flags(g, img, rec, a.save != nullptr, p);
     BwdStage& sg = stg[k % D];
     uint64_t* b = &bar[k % D];
-    mbar_arrive_expect_tx(b, bytes);
+    mbar_arrive_expect_tx(b, (HF_B + CF_B) * 4 + (f.imgt ? (HF_B + CF_B) * 4 : 0) +
+                                 (f.needu1 ? CF_B * 4 : 0) + (adj ? CF_B * 4 : 0));
     tma_load_3d(sg.ma, &a.tmA, b, p.x0 - 4, p.z0 - 4, p.s);
     tma_load_2d(sg.k, &a.tK, b, p.x0, p.z0);
-    if (img) {
+    if (f.imgt) {
       tma_load_3d(sg.ua, &a.tuA, b, p.x0 - 4, p.z0 - 4, p.s);
       tma_load_3d(sg.gr, &a.tG, b, p.x0, p.z0, p.s);
     }
-    if (rec) tma_load_3d(sg.ub, &a.tuB, b, p.x0, p.z0, p.s);
+    if (f.needu1) tma_load_3d(sg.ub, &a.tuB, b, p.x0, p.z0, p.s);
     if (adj) tma_load_3d(sg.mb, &a.tmB, b, p.x0, p.z0, p.s);
   };
   if (threadIdx.x == 0)
@@ -208,9 +228,27 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
   const int lx = 4 * lane, r0 = warp * RPW_B;
   int k = 0;
   for (; k < count; ++k) {
+    const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_B, blockIdx.x + k * G);
+    const BwdFlags f = bwd_flags(g, img, rec, a.save != nullptr, p);
+    // saved ring values of u^{n-1} of this thread's cells, fetched before the
+    // wait so that their latency overlaps the stage's transfer
+    float rv[RPW_B][4];
+    unsigned rmask = 0;
+    if (f.ringt) {
+      const int gx0 = p.x0 + lx;
+#pragma unroll
+      for (int q = 0; q < RPW_B; ++q) {
+        const int gz = p.z0 + r0 + q;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int ri = (gz < R.z1 && gx0 + c < R.x1) ? ring_index(g, gz, gx0 + c) : -1;
+          rv[q][c] = ri >= 0 ? a.save[(long long)p.s * g.nring + ri] : 0.f;
+          if (ri >= 0) rmask |= 1u << (4 * q + c);
+        }
+      }
+    }
     const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
     if (__syncthreads_or(!got)) break;
-    const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_B, blockIdx.x + k * G);
     const ShotInfo si = shot_info(T, g, a.src, img ? a.wavelet : nullptr, a.rbox, a.n, p.s);
     const BwdStage& sg = stg[k % D];
     const long long so = (long long)p.s * g.fstride;
@@ -219,12 +257,12 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       f4a(lds4(sg.ma, IN_HW, r0 + j, lx + 4), wm[j]);
-      if (img) f4a(lds4(sg.ua, IN_HW, r0 + j, lx + 4), wu[j]);
+      if (f.imgt) f4a(lds4(sg.ua, IN_HW, r0 + j, lx + 4), wu[j]);
     }
 #pragma unroll
     for (int q = 0; q < RPW_B; ++q) {
       f4a(lds4(sg.ma, IN_HW, r0 + q + 8, lx + 4), wm[8]);
-      if (img) f4a(lds4(sg.ua, IN_HW, r0 + q + 8, lx + 4), wu[8]);
+      if (f.imgt) f4a(lds4(sg.ua, IN_HW, r0 + q + 8, lx + 4), wu[8]);
       const int gz = p.z0 + r0 + q;
       if (gz < R.z1 && gx < R.x1) {
         const long long ci = so + (long long)gz * g.NXp + gx;
@@ -248,42 +286,51 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
           }
           *reinterpret_cast<float4*>(a.mB + ci) = make_float4(out[0], out[1], out[2], out[3]);
         }
-        if (img) {
-          float e[12], lap[4];
+        float lap[4] = {0.f, 0.f, 0.f, 0.f};
+        bool ins[4] = {false, false, false, false};
+        if (f.imgt) {
+          // imaging on interior cells: graw += mu^{n+1} (Lap u^n + f^n delta_s)
+          float e[12];
           f4a(lds4(sg.ua, IN_HW, r0 + q + 4, lx), e);
           f4a(lds4(sg.ua, IN_HW, r0 + q + 4, lx + 8), e + 8);
 #pragma unroll
           for (int c = 0; c < 4; ++c) e[4 + c] = wu[4][c];
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
+            ins[c] = interior(g, gz, gx + c);
             lap[c] = d2(e[c], e[c + 1], e[c + 2], e[c + 3], e[c + 4], e[c + 5], e[c + 6],
                         e[c + 7], e[c + 8]) +
                      d2(wu[0][c], wu[1][c], wu[2][c], wu[3][c], wu[4][c], wu[5][c], wu[6][c],
                         wu[7][c], wu[8][c]);
             if (gz == si.sz && gx + c == si.sx) lap[c] += si.fn;
           }
-          float4 gv = lds4(sg.gr, IN_BX, r0 + q, lx);
-          gv.x += wm[4][0] * lap[0];
-          gv.y += wm[4][1] * lap[1];
-          gv.z += wm[4][2] * lap[2];
-          gv.w += wm[4][3] * lap[3];
-          *reinterpret_cast<float4*>(a.graw + ci) = gv;
-          if (a.illum) {
-            float4* ip = reinterpret_cast<float4*>(a.illum + ci);
-            float4 iv = *ip;
-            iv.x += wu[4][0] * wu[4][0];
-            iv.y += wu[4][1] * wu[4][1];
-            iv.z += wu[4][2] * wu[4][2];
-            iv.w += wu[4][3] * wu[4][3];
-            *ip = iv;
-          }
-          if (rec) {
-            float u1[4], out[4];
-            f4a(lds4(sg.ub, IN_BX, r0 + q, lx), u1);
+          float gvv[4];
+          f4a(lds4(sg.gr, IN_BX, r0 + q, lx), gvv);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) out[c] = 2.f * wu[4][c] - u1[c] + kk[c] * lap[c];
-            *reinterpret_cast<float4*>(a.uB + ci) = make_float4(out[0], out[1], out[2], out[3]);
+          for (int c = 0; c < 4; ++c)
+            if (ins[c]) gvv[c] += wm[4][c] * lap[c];
+          *reinterpret_cast<float4*>(a.graw + ci) = make_float4(gvv[0], gvv[1], gvv[2], gvv[3]);
+          if (a.illum) {
+            float iv[4];
+            f4a(*reinterpret_cast<const float4*>(a.illum + ci), iv);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (ins[c]) iv[c] += wu[4][c] * wu[4][c];
+            *reinterpret_cast<float4*>(a.illum + ci) = make_float4(iv[0], iv[1], iv[2], iv[3]);
           }
+        }
+        if (f.needu1) {
+          // u^{n-1}: reconstructed on interior cells, restored on the ring
+          float u1[4], out[4];
+          f4a(lds4(sg.ub, IN_BX, r0 + q, lx), u1);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (ins[c])
+              out[c] = 2.f * wu[4][c] - u1[c] + kk[c] * lap[c];
+            else
+              out[c] = (rmask >> (4 * q + c)) & 1u ? rv[q][c] : u1[c];
+          }
+          *reinterpret_cast<float4*>(a.uB + ci) = make_float4(out[0], out[1], out[2], out[3]);
         }
       }
 #pragma unroll

@@ -85,9 +85,6 @@ struct Bump {
   }
 };
 
-int up4(int v) { return (v + 3) & ~3; }
-int down4(int v) { return v & ~3; }
-
 Geom make_geom(const sweep_problem* p) {
   Geom g{};
   g.nz = p->nz;
@@ -103,9 +100,10 @@ Geom make_geom(const sweep_problem* p) {
   const int w = g.ringw;
   g.nring = 2 * w * (g.nx + 2 * w) + 2 * g.nz * w;
   g.fstride = (long long)g.NZ * g.NXp;
-  const int P = g.P;
-  g.fin = Region{P, P + g.nz, up4(P), down4(P + g.nx)};
-  g.bin = Region{P + 4, P + g.nz - 4, up4(P + 4), down4(P + g.nx - 4)};
+  // the plain-stencil kernels cover the whole padded grid; the CPML terms
+  // are added by the correction kernels
+  g.fin = Region{0, g.NZ, 0, g.NXp};
+  g.bin = Region{0, g.NZ, 0, g.NXp};
   return g;
 }
 
@@ -247,11 +245,6 @@ bool field_maps(const Geom& g, const float* base, CUtensorMap* halo, CUtensorMap
   return ok;
 }
 
-// Per-shot field [S][NZ][NXp] with an arbitrary box (bx, bz, 1).
-bool map3(CUtensorMap* m, const Geom& g, const float* base, uint32_t bx, uint32_t bz) {
-  const uint64_t S = (uint64_t)(g.nshot > 0 ? g.nshot : 1);
-  return make_tensor_map(m, base, 3, g.NX, g.NZ, S, g.NXp, (uint64_t)g.fstride, bx, bz, 1);
-}
 // The shared K grid [NZ][NXp] with box (bx, bz).
 bool map2(CUtensorMap* m, const Geom& g, const float* base, uint32_t bx, uint32_t bz) {
   return make_tensor_map(m, base, 2, g.NX, g.NZ, 1, g.NXp, (uint64_t)g.fstride, bx, bz, 1);
@@ -267,8 +260,10 @@ int region_units(const Region& R, int nshot, int bz, int* ntx) {
   return *ntx * ntz * nshot;
 }
 
-// Forward time loop of the acoustic engine.  On return the workspace holds
-// u^{nt} in u[nt % 2] and u^{nt-1} in u[(nt + 1) % 2].
+// Forward time loop of the acoustic engine: per step the plain-stencil
+// kernel over the whole padded grid, then the z and x CPML corrections.  On
+// return the workspace holds u^{nt} in u[nt % 2] and u^{nt-1} in
+// u[(nt + 1) % 2].
 int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
                           const float* wavelet, const int32_t* src, const int32_t* rec,
                           float* data, bool save_ring, cudaStream_t st) {
@@ -277,76 +272,47 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
   float* save = save_ring ? at<float>(ws, L.save) : nullptr;
   if (save) cudaMemsetAsync(save, 0, sizeof(float) * (size_t)g.nshot * g.nring, st);
   int* status = at<int>(ws, L.status);
-  const int32_t* rbox = at<int32_t>(ws, L.rbox);
 
   AcInFwdArgs in{};
   in.g = g;
   in.units = region_units(g.fin, g.nshot, IN_BZ_F, &in.ntx);
   CUtensorMap tu_h[2], tu_c[2];
-  if (in.units > 0) {
-    for (int b = 0; b < 2; ++b)
-      if (!field_maps(g, at<float>(ws, L.u[b]), &tu_h[b], &tu_c[b], IN_BZ_F)) return SWEEP_ECUDA;
-    if (!map2(&in.tK, g, at<float>(ws, L.K), IN_BX, IN_BZ_F)) return SWEEP_ECUDA;
-  }
+  for (int b = 0; b < 2; ++b)
+    if (!field_maps(g, at<float>(ws, L.u[b]), &tu_h[b], &tu_c[b], IN_BZ_F)) return SWEEP_ECUDA;
+  if (!map2(&in.tK, g, at<float>(ws, L.K), IN_BX, IN_BZ_F)) return SWEEP_ECUDA;
   in.wavelet = wavelet;
   in.src = src;
   in.rec = rec;
-  in.rbox = rbox;
+  in.rbox = at<int32_t>(ws, L.rbox);
   in.data = data;
   in.status = status;
 
-  AcFrFwdArgs fr{};
-  fr.g = g;
-  fr.fr = frame_rects(g, g.fin);
-  fr.units = fr.fr.first[fr.fr.n] * g.nshot;
-  CUtensorMap fu_h[2], fu_c[2], fpx[2], fpz[2];
-  for (int b = 0; b < 2; ++b) {
-    if (!map3(&fu_h[b], g, at<float>(ws, L.u[b]), FR_HW, FR_HH) ||
-        !map3(&fu_c[b], g, at<float>(ws, L.u[b]), FR_TX, FR_TZ) ||
-        !map3(&fpx[b], g, at<float>(ws, L.psx[b]), FR_HW, FR_TZ) ||
-        !map3(&fpz[b], g, at<float>(ws, L.psz[b]), FR_TX, FR_HH))
-      return SWEEP_ECUDA;
-  }
-  if (!map2(&fr.tK, g, at<float>(ws, L.K), FR_TX, FR_TZ) ||
-      !map3(&fr.tzx, g, at<float>(ws, L.zex), FR_TX, FR_TZ) ||
-      !map3(&fr.tzz, g, at<float>(ws, L.zez), FR_TX, FR_TZ))
-    return SWEEP_ECUDA;
-  fr.K = at<float>(ws, L.K);
-  fr.zex = at<float>(ws, L.zex);
-  fr.zez = at<float>(ws, L.zez);
-  fr.ax = at<float>(ws, L.ax);
-  fr.bx = at<float>(ws, L.bx);
-  fr.az = at<float>(ws, L.az);
-  fr.bz = at<float>(ws, L.bz);
-  fr.wavelet = wavelet;
-  fr.src = src;
-  fr.rec = rec;
-  fr.rbox = rbox;
-  fr.data = data;
-  fr.status = status;
+  AcCorrArgs cz{}, cx{};
+  cz.g = cx.g = g;
+  cz.K = cx.K = at<float>(ws, L.K);
+  cz.ax = cx.ax = at<float>(ws, L.ax);
+  cz.bx = cx.bx = at<float>(ws, L.bx);
+  cz.az = cx.az = at<float>(ws, L.az);
+  cz.bz = cx.bz = at<float>(ws, L.bz);
+  cz.zeta = at<float>(ws, L.zez);
+  cx.zeta = at<float>(ws, L.zex);
+  cz.status = cx.status = status;
   for (int n = 0; n < g.nt; ++n) {
     const int A = n & 1, B = (n + 1) & 1;
     void* tok = profile_begin(SWEEP_K_AC_FWD, st);
-    if (in.units > 0) {
-      in.n = n;
-      in.tu = tu_h[A];
-      in.tup = tu_c[B];
-      in.un = at<float>(ws, L.u[B]);
-      launch_ac_in_fwd(in, st);
-    }
-    fr.n = n;
-    fr.tu = fu_h[A];
-    fr.tup = fu_c[B];
-    fr.tpx = fpx[A];
-    fr.tpz = fpz[A];
-    fr.u = at<float>(ws, L.u[A]);
-    fr.un = at<float>(ws, L.u[B]);
-    fr.psx_in = at<float>(ws, L.psx[A]);
-    fr.psx_out = at<float>(ws, L.psx[B]);
-    fr.psz_in = at<float>(ws, L.psz[A]);
-    fr.psz_out = at<float>(ws, L.psz[B]);
-    fr.save = save ? save + (size_t)(n + 1) * g.nshot * g.nring : nullptr;
-    launch_ac_fr_fwd(fr, st);
+    in.n = n;
+    in.tu = tu_h[A];
+    in.tup = tu_c[B];
+    in.un = at<float>(ws, L.u[B]);
+    launch_ac_in_fwd(in, st);
+    cz.u = cx.u = at<float>(ws, L.u[A]);
+    cz.un = cx.un = at<float>(ws, L.u[B]);
+    cz.pin = at<float>(ws, L.psz[A]);
+    cz.pout = at<float>(ws, L.psz[B]);
+    cx.pin = at<float>(ws, L.psx[A]);
+    cx.pout = at<float>(ws, L.psx[B]);
+    cz.save = cx.save = save ? save + (size_t)(n + 1) * g.nshot * g.nring : nullptr;
+    launch_ac_corr_fwd(cz, cx, st);
     profile_end(tok, st);
   }
   return SWEEP_OK;
@@ -354,7 +320,8 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
 
 // Backward loop: adjoint propagation from the residual `res`; optionally the
 // imaging condition with wavefield reconstruction (gradient) and/or the
-// adjoint source gather (wgrad).
+// adjoint source gather (wgrad).  Per step the plain kernel over the whole
+// grid, then the z and x CPML corrections of mu^n.
 int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
                            const float* wavelet, const int32_t* src, const int32_t* rec,
                            const float* res, float* wgrad, bool imaging, bool illum,
@@ -367,118 +334,73 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
     if (illum) cudaMemsetAsync(at<float>(ws, L.iraw), 0, F, st);
   }
   int* status = at<int>(ws, L.status);
-  const int32_t* rbox = at<int32_t>(ws, L.rbox);
   float* save = imaging ? at<float>(ws, L.save) : nullptr;
 
   AcInBwdArgs in{};
   in.g = g;
   in.units = region_units(g.bin, g.nshot, IN_BZ_B, &in.ntx);
   CUtensorMap tu_h[2], tu_c[2], tm_h[2], tm_c[2];
-  if (in.units > 0) {
-    for (int b = 0; b < 2; ++b) {
-      if (imaging && !field_maps(g, at<float>(ws, L.u[b]), &tu_h[b], &tu_c[b], IN_BZ_B))
-        return SWEEP_ECUDA;
-      if (!field_maps(g, at<float>(ws, L.m[b]), &tm_h[b], &tm_c[b], IN_BZ_B)) return SWEEP_ECUDA;
-    }
-    if (!map2(&in.tK, g, at<float>(ws, L.K), IN_BX, IN_BZ_B)) return SWEEP_ECUDA;
-    if (imaging && !field_maps(g, at<float>(ws, L.graw), nullptr, &in.tG, IN_BZ_B))
+  for (int b = 0; b < 2; ++b) {
+    if (imaging && !field_maps(g, at<float>(ws, L.u[b]), &tu_h[b], &tu_c[b], IN_BZ_B))
       return SWEEP_ECUDA;
+    if (!field_maps(g, at<float>(ws, L.m[b]), &tm_h[b], &tm_c[b], IN_BZ_B)) return SWEEP_ECUDA;
   }
+  if (!map2(&in.tK, g, at<float>(ws, L.K), IN_BX, IN_BZ_B)) return SWEEP_ECUDA;
+  if (imaging && !field_maps(g, at<float>(ws, L.graw), nullptr, &in.tG, IN_BZ_B))
+    return SWEEP_ECUDA;
   in.graw = imaging ? at<float>(ws, L.graw) : nullptr;
   in.illum = (imaging && illum) ? at<float>(ws, L.iraw) : nullptr;
   in.K = at<float>(ws, L.K);
   in.wavelet = wavelet;
   in.src = src;
   in.rec = rec;
-  in.rbox = rbox;
+  in.rbox = at<int32_t>(ws, L.rbox);
   in.res = res;
   in.wgrad = wgrad;
   in.status = status;
 
-  AcFrBwdArgs fr{};
-  fr.g = g;
-  fr.fr = frame_rects(g, g.bin);
-  fr.units = fr.fr.first[fr.fr.n] * g.nshot;
-  CUtensorMap fm_h[2], fm_c[2], fu_h[2], fu_c[2], fzbx[2], fpbx[2], fzbz[2], fpbz[2];
-  for (int b = 0; b < 2; ++b) {
-    if (!map3(&fm_h[b], g, at<float>(ws, L.m[b]), FR_HW, FR_HH) ||
-        !map3(&fm_c[b], g, at<float>(ws, L.m[b]), FR_TX, FR_TZ) ||
-        !map3(&fzbx[b], g, at<float>(ws, L.zbx[b]), FR_HW, FR_TZ) ||
-        !map3(&fpbx[b], g, at<float>(ws, L.pbx[b]), FR_HW, FR_TZ) ||
-        !map3(&fzbz[b], g, at<float>(ws, L.zbz[b]), FR_TX, FR_HH) ||
-        !map3(&fpbz[b], g, at<float>(ws, L.pbz[b]), FR_TX, FR_HH))
-      return SWEEP_ECUDA;
-    if (imaging && (!map3(&fu_h[b], g, at<float>(ws, L.u[b]), FR_HW, FR_HH) ||
-                    !map3(&fu_c[b], g, at<float>(ws, L.u[b]), FR_TX, FR_TZ)))
-      return SWEEP_ECUDA;
-  }
-  if (!map2(&fr.tK, g, at<float>(ws, L.K), FR_TX, FR_TZ)) return SWEEP_ECUDA;
-  if (imaging && !map3(&fr.tG, g, at<float>(ws, L.graw), FR_TX, FR_TZ)) return SWEEP_ECUDA;
-  if (imaging && illum && !map3(&fr.tI, g, at<float>(ws, L.iraw), FR_TX, FR_TZ))
-    return SWEEP_ECUDA;
-  fr.K = at<float>(ws, L.K);
-  fr.ax = at<float>(ws, L.ax);
-  fr.bx = at<float>(ws, L.bx);
-  fr.az = at<float>(ws, L.az);
-  fr.bz = at<float>(ws, L.bz);
-  fr.wavelet = wavelet;
-  fr.src = src;
-  fr.rec = rec;
-  fr.rbox = rbox;
-  fr.res = res;
-  fr.graw = in.graw;
-  fr.illum = in.illum;
-  fr.wgrad = wgrad;
-  fr.status = status;
+  AcCorrArgs cz{}, cx{};
+  cz.g = cx.g = g;
+  cz.K = cx.K = at<float>(ws, L.K);
+  cz.ax = cx.ax = at<float>(ws, L.ax);
+  cz.bx = cx.bx = at<float>(ws, L.bx);
+  cz.az = cx.az = at<float>(ws, L.az);
+  cz.bz = cx.bz = at<float>(ws, L.bz);
+  cz.status = cx.status = status;
   for (int n = g.nt; n >= 0; --n) {
     const int A = n & 1, B = (n + 1) & 1;  // u^n in u[A]; mu^{n+1} in m[B]
     const int do_adj = n >= 1;
     const int do_img = imaging && n <= g.nt - 1;
     const int do_rec = imaging && n >= 1 && n <= g.nt - 1;
+    if (!(do_adj || do_img || wgrad)) continue;
     void* tok = profile_begin(SWEEP_K_AC_BWD, st);
-    if (in.units > 0 && (do_adj || do_img || wgrad)) {
-      in.n = n;
-      in.do_adj = do_adj;
-      in.do_img = do_img;
-      in.do_rec = do_rec;
-      if (imaging) {
-        in.tuA = tu_h[A];
-        in.tuB = tu_c[B];
-      }
-      in.tmA = tm_h[B];
-      in.tmB = tm_c[A];
-      in.uB = imaging ? at<float>(ws, L.u[B]) : nullptr;
-      in.mB = at<float>(ws, L.m[A]);
-      launch_ac_in_bwd(in, st);
-    }
-    fr.n = n;
-    fr.do_adj = do_adj;
-    fr.do_img = do_img;
-    fr.do_rec = do_rec;
-    fr.tmA = fm_h[B];
-    fr.tmB = fm_c[A];
+    in.n = n;
+    in.do_adj = do_adj;
+    in.do_img = do_img;
+    in.do_rec = do_rec;
     if (imaging) {
-      fr.tuA = fu_h[A];
-      fr.tuB = fu_c[B];
+      in.tuA = tu_h[A];
+      in.tuB = tu_c[B];
     }
-    fr.tzbx = fzbx[A];
-    fr.tpbx = fpbx[A];
-    fr.tzbz = fzbz[A];
-    fr.tpbz = fpbz[A];
-    fr.uA = imaging ? at<float>(ws, L.u[A]) : nullptr;
-    fr.uB = imaging ? at<float>(ws, L.u[B]) : nullptr;
-    fr.mA = at<float>(ws, L.m[B]);
-    fr.mB = at<float>(ws, L.m[A]);
-    fr.pbx_in = at<float>(ws, L.pbx[A]);
-    fr.pbx_out = at<float>(ws, L.pbx[B]);
-    fr.pbz_in = at<float>(ws, L.pbz[A]);
-    fr.pbz_out = at<float>(ws, L.pbz[B]);
-    fr.zbx_in = at<float>(ws, L.zbx[A]);
-    fr.zbx_out = at<float>(ws, L.zbx[B]);
-    fr.zbz_in = at<float>(ws, L.zbz[A]);
-    fr.zbz_out = at<float>(ws, L.zbz[B]);
-    fr.save = (save && n >= 1) ? save + (size_t)(n - 1) * g.nshot * g.nring : nullptr;
-    launch_ac_fr_bwd(fr, st);
+    in.tmA = tm_h[B];
+    in.tmB = tm_c[A];
+    in.uB = imaging ? at<float>(ws, L.u[B]) : nullptr;
+    in.mB = at<float>(ws, L.m[A]);
+    in.save = (save && n >= 1) ? save + (size_t)(n - 1) * g.nshot * g.nring : nullptr;
+    launch_ac_in_bwd(in, st);
+    if (do_adj) {
+      cz.u = cx.u = at<float>(ws, L.m[B]);
+      cz.un = cx.un = at<float>(ws, L.m[A]);
+      cz.pin = at<float>(ws, L.pbz[A]);
+      cz.pout = at<float>(ws, L.pbz[B]);
+      cz.zeta = at<float>(ws, L.zbz[A]);
+      cz.zout = at<float>(ws, L.zbz[B]);
+      cx.pin = at<float>(ws, L.pbx[A]);
+      cx.pout = at<float>(ws, L.pbx[B]);
+      cx.zeta = at<float>(ws, L.zbx[A]);
+      cx.zout = at<float>(ws, L.zbx[B]);
+      launch_ac_corr_bwd(cz, cx, st);
+    }
     profile_end(tok, st);
   }
   return SWEEP_OK;

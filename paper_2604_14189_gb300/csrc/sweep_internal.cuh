@@ -27,9 +27,8 @@ struct Geom {
   int ringw;          // width of the saved ring, min(P, 4)
   int nring;          // cells in the ring
   long long fstride;  // floats per shot per field = NZ * NXp
-  // Cells whose update is the plain stencil: forward = interior cells
-  // (columns aligned to 4); backward = interior cells at least 4 away from
-  // the border.  The frame kernels update every other cell.
+  // Cells covered by the plain-stencil kernels (forward, backward): the
+  // whole padded grid; the CPML correction kernels then add the border terms.
   Region fin, bin;
 };
 
@@ -71,6 +70,7 @@ struct AcInBwdArgs {
   float* mB;         // out mu^n
   float* graw;       // [S][NZ][NXp]
   float* illum;      // [S][NZ][NXp] or null
+  const float* save; // ring slot of u^{n-1} [S][nring] or null
   const float* K;
   const float* wavelet;
   const int32_t* src;
@@ -84,104 +84,29 @@ struct AcInBwdArgs {
   int units, ntx;
 };
 
-// --------------------------------------------------------------------- frame
-// Tiles of FR_TZ x FR_TX cells; each thread owns one column of FR_TZ /
-// (FR_THREADS / FR_TX) rows.
-constexpr int FR_TZ = 16;
-constexpr int FR_TX = 64;
-constexpr int FR_THREADS = 512;
-constexpr int FR_HW = FR_TX + 8;  // halo tile width
-constexpr int FR_HH = FR_TZ + 8;  // halo tile height
-
-struct FrameRects {
-  int n;               // rectangles (<= 4)
-  int z0[4], z1[4], x0[4], x1[4];
-  int ntx[4];          // tiles along x per rectangle
-  int first[5];        // prefix sum of tiles
-};
-
-// The frame kernels are persistent TMA pipelines over (frame tile, shot)
-// units, like the interior kernels; boxes: halo (FR_HW, FR_HH), centre
-// (FR_TX, FR_TZ), x halo (FR_HW, FR_TZ), z halo (FR_TX, FR_HH).
-struct AcFrFwdArgs {
+// CPML correction kernels (acoustic_cpml.cu), one axis per argument set.
+// Forward: u = u^n, un = u^{n+1} (updated), pin/pout = psi^{n-1}/psi^n,
+// zeta updated in place, save = ring slot of u^{n+1} or null.
+// Backward: u = mu^{n+1}, un = mu^n (updated), pin/pout = psibar^n/^{n-1},
+// zeta/zout = zetabar^n/^{n-1}.
+struct AcCorrArgs {
   Geom g;
-  FrameRects fr;
-  CUtensorMap tu;     // u^n, halo box
-  CUtensorMap tup;    // u^{n-1}, centre box
-  CUtensorMap tK;     // K, centre box (2D)
-  CUtensorMap tpx;    // psi_x^{n-1}, x-halo box
-  CUtensorMap tpz;    // psi_z^{n-1}, z-halo box
-  CUtensorMap tzx;    // zeta_x, centre box
-  CUtensorMap tzz;    // zeta_z, centre box
-  int units;
-  const float* u;     // u^n
-  float* un;          // in u^{n-1}, out u^{n+1}
+  const float* u;
+  float* un;
   const float* K;
-  const float* psx_in;
-  float* psx_out;
-  const float* psz_in;
-  float* psz_out;
-  float* zex;
-  float* zez;
+  const float* pin;
+  float* pout;
+  float* zeta;
+  float* zout;
   const float* ax;
   const float* bx;
   const float* az;
   const float* bz;
-  const float* wavelet;
-  const int32_t* src;
-  const int32_t* rec;
-  const int32_t* rbox;
-  float* data;
-  float* save;        // ring slot of u^{n+1} [S][nring] or null
-  int* status;
-  int n;
+  float* save;
+  const int* status;
 };
-
-struct AcFrBwdArgs {
-  Geom g;
-  FrameRects fr;
-  CUtensorMap tmA;    // mu^{n+1}, halo box
-  CUtensorMap tuA;    // u^n, halo box
-  CUtensorMap tK;     // K, centre box (2D)
-  CUtensorMap tmB;    // mu^{n+2}, centre box
-  CUtensorMap tuB;    // u^{n+1}, centre box
-  CUtensorMap tG;     // graw, centre box
-  CUtensorMap tI;     // illumination, centre box
-  CUtensorMap tzbx;   // zetabar_x^n, x-halo box
-  CUtensorMap tpbx;   // psibar_x^n, x-halo box
-  CUtensorMap tzbz;   // zetabar_z^n, z-halo box
-  CUtensorMap tpbz;   // psibar_z^n, z-halo box
-  int units;
-  const float* uA;    // u^n
-  float* uB;          // in u^{n+1}, out u^{n-1}
-  const float* mA;    // mu^{n+1}
-  float* mB;          // in mu^{n+2}, out mu^n
-  const float* pbx_in;
-  float* pbx_out;
-  const float* pbz_in;
-  float* pbz_out;
-  const float* zbx_in;
-  float* zbx_out;
-  const float* zbz_in;
-  float* zbz_out;
-  const float* K;
-  const float* ax;
-  const float* bx;
-  const float* az;
-  const float* bz;
-  const float* wavelet;
-  const int32_t* src;
-  const int32_t* rec;
-  const int32_t* rbox;
-  const float* res;
-  const float* save;  // ring slot of u^{n-1} or null
-  float* graw;        // [S][NZ][NXp]
-  float* illum;
-  float* wgrad;
-  int* status;
-  int n;
-  int do_adj, do_img, do_rec;
-};
+void launch_ac_corr_fwd(const AcCorrArgs& z, const AcCorrArgs& x, cudaStream_t st);
+void launch_ac_corr_bwd(const AcCorrArgs& z, const AcCorrArgs& x, cudaStream_t st);
 
 // ------------------------------------------------------------------- elastic
 // Coefficients on the padded grid [NZ][NXp], pre-scaled by dt / dx:
@@ -219,12 +144,9 @@ struct ElStepArgs {
 void launch_el_params(const ElParamArgs& a, cudaStream_t st);
 void launch_el_step(const ElStepArgs& a, cudaStream_t st);
 
-// Kernel launchers (acoustic_interior.cu, acoustic_frame.cu)
+// Kernel launchers (acoustic_interior.cu)
 void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st);
 void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st);
-void launch_ac_fr_fwd(const AcFrFwdArgs& a, cudaStream_t st);
-void launch_ac_fr_bwd(const AcFrBwdArgs& a, cudaStream_t st);
-FrameRects frame_rects(const Geom& g, const Region& inner);
 int device_sms();
 
 // Setup (setup.cu)
