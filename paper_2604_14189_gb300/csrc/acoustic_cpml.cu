@@ -6,7 +6,7 @@
 // kernel that visits only the cells its terms reach (see
 // acoustic_common.cuh for the full update):
 //
-// forward, axis strip cells (σ ≠ 0 along that axis):
+// forward, axis strip cells (sigma != 0 along that axis):
 //   W = D2 u^n + D1 psi^{n-1};  zeta^n = a zeta^{n-1} + b W;
 //   psi^n = a psi^{n-1} + b D1 u^n;  u^{n+1} += K (D1 psi^{n-1} + zeta^n)
 // backward, strip cells and the 4 cells next to them:
@@ -14,107 +14,197 @@
 //   mu^n += K (D2 C - D1 B)
 //   strip cells: psibar^{n-1} = a psibar^n - D1 (m (mu^{n+1} + C)),
 //                zetabar^{n-1} = a (mu^{n+1} + zetabar^n)
-// The z kernels walk down a column per thread with register windows
-// (coalesced across the warp); the x kernels stage row segments of the
-// strips in shared memory.  The forward kernels also save the ring cells of
-// their strips after the final update (z kernel: ring cells outside the x
-// strips; x kernel: ring cells inside them, the x kernel runs last).
+//
+// The profiles a, b are zero off the border, and so are psi, zeta and their
+// adjoints (never written there), which removes most masks.
+//
+// z kernels: a thread owns 2 adjacent columns (8-byte accesses, coalesced
+// across the warp) and a chunk of ZCH rows; x kernels: a thread owns 4
+// consecutive cells of a row (16-byte accesses) and reads its 4 + 4
+// x-neighbours as two more 16-byte loads.  Every load of a thread is issued
+// before its arithmetic, so the memory latency is paid once per thread.
+// The forward kernels also save the ring cells of their strips after the
+// final update (z kernel: ring cells outside the x strips; x kernel: ring
+// cells inside them, the x kernel runs last).
 #include "acoustic_common.cuh"
 
 namespace sweep {
 namespace {
 
-constexpr int CZ_T = 128;   // threads (columns) per block, z kernels
-constexpr int CX_TZ = 16;   // rows per block, x kernels
-constexpr int CX_TX = 64;   // strip columns per block, x kernels
-constexpr int CX_T = 256;
-constexpr int CX_W = CX_TX + 16;  // staged width (halo + alignment)
+constexpr int ZT = 128;  // threads per block, z kernels (256 columns)
+constexpr int ZCH = 8;   // rows per thread, z kernels
+constexpr int ZW = ZCH + 8;
+constexpr int XT = 256;  // threads per block, x kernels
 
-__device__ __forceinline__ float ldz(const float* f, const Geom& g, int z, int x) {
-  return (z >= 0 && z < g.NZ) ? f[(long long)z * g.NXp + x] : 0.f;
+__device__ __forceinline__ float2 ld2(const float* p) {
+  return *reinterpret_cast<const float2*>(p);
+}
+__device__ __forceinline__ float2 ldg2(const float* p) {
+  return __ldg(reinterpret_cast<const float2*>(p));
+}
+__device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+__device__ __forceinline__ float4 ld4(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+__device__ __forceinline__ float4 ldg4(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ void st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// D2 and D1 on column pairs with the packed FP32 pipe (same rounding
+// sequence as the scalar forms: one multiply, then a chain of fused adds).
+__device__ __forceinline__ float2 d2p(const float2* w) {
+  float2 r = __fmul2_rn(f2(kC0), w[4]);
+  r = __ffma2_rn(f2(kC1), __fadd2_rn(w[5], w[3]), r);
+  r = __ffma2_rn(f2(kC2), __fadd2_rn(w[6], w[2]), r);
+  r = __ffma2_rn(f2(kC3), __fadd2_rn(w[7], w[1]), r);
+  r = __ffma2_rn(f2(kC4), __fadd2_rn(w[8], w[0]), r);
+  return r;
+}
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ float2 d1p(const float2* w) {
+  float2 r = __fmul2_rn(f2(kD1), __fadd2_rn(w[5], neg2(w[3])));
+  r = __ffma2_rn(f2(kD2), __fadd2_rn(w[6], neg2(w[2])), r);
+  r = __ffma2_rn(f2(kD3), __fadd2_rn(w[7], neg2(w[1])), r);
+  r = __ffma2_rn(f2(kD4), __fadd2_rn(w[8], neg2(w[0])), r);
+  return r;
 }
 
 // ------------------------------------------------------------- forward, z
-// A thread owns one column and a chunk of CH rows of one strip; every load
-// of the chunk is issued before any arithmetic so that the memory latency is
-// paid once per chunk.  blockIdx.y: strip (top [0, P), bottom [P+nz, NZ))
-// times chunk; blockIdx.z: shot.
-constexpr int CH = 8;
-constexpr int CW = CH + 8;
-
-__global__ void __launch_bounds__(CZ_T) ac_cz_fwd_kernel(const AcCorrArgs a) {
+// blockIdx.y: strip (top [0, P), bottom [P+nz, NZ)) times chunk of ZCH rows;
+// blockIdx.z: shot.
+__global__ void __launch_bounds__(ZT) ac_cz_fwd_kernel(const AcCorrArgs a) {
+  grid_dep_wait();
+  grid_dep_trigger();
   if (*a.status) return;
   const Geom& g = a.g;
-  const int x = blockIdx.x * CZ_T + threadIdx.x;
+  const int x = 2 * (blockIdx.x * ZT + threadIdx.x);
   if (x >= g.NX) return;
-  const int s = blockIdx.z;
-  const long long so = (long long)s * g.fstride;
-  const int nch = (g.P + CH - 1) / CH;
-  const int strip = blockIdx.y / nch, ch = blockIdx.y - strip * nch;
-  const int base = strip == 0 ? 0 : g.P + g.nz;
-  const int zs = base + ch * CH;
-  const int ze = min(zs + CH, base + g.P);
+  const int nch = (g.P + ZCH - 1) / ZCH;
+  const int strip = (int)blockIdx.y >= nch ? 1 : 0;
+  const int base = strip ? g.P + g.nz : 0;
+  const int zs = base + ((int)blockIdx.y - strip * nch) * ZCH;
+  const int ze = min(zs + ZCH, base + g.P);
+  const size_t so = (size_t)blockIdx.z * g.fstride + x;
   const float* u = a.u + so;
   const float* pin = a.pin + so;
-  float wu[CW], wp[CW], zt[CH], kk[CH], un[CH];
+  float2 wu[ZW], wp[ZW], zt[ZCH], kk[ZCH], un[ZCH];
 #pragma unroll
-  for (int k = 0; k < CW; ++k) {
-    wu[k] = ldz(u, g, zs - 4 + k, x);
-    wp[k] = ldz(pin, g, zs - 4 + k, x);
+  for (int k = 0; k < ZW; ++k) {
+    const int zz = zs - 4 + k;
+    const bool ok = zz >= 0 && zz < g.NZ;
+    const size_t o = (size_t)zz * g.NXp;
+    wu[k] = ok ? ldg2(u + o) : f2(0.f);
+    wp[k] = ok ? ldg2(pin + o) : f2(0.f);
   }
 #pragma unroll
-  for (int q = 0; q < CH; ++q) {
-    const int z = zs + q;
-    const long long c = (long long)z * g.NXp + x;
-    const bool ok = z < ze;
-    zt[q] = ok ? a.zeta[so + c] : 0.f;
-    kk[q] = ok ? a.K[c] : 0.f;
-    un[q] = ok ? a.un[so + c] : 0.f;
+  for (int q = 0; q < ZCH; ++q) {
+    const bool ok = zs + q < ze;
+    const size_t o = (size_t)(zs + q) * g.NXp;
+    zt[q] = ok ? ld2(a.zeta + so + o) : f2(0.f);
+    kk[q] = ok ? ldg2(a.K + x + o) : f2(0.f);
+    un[q] = ok ? ld2(a.un + so + o) : f2(0.f);
   }
-  const bool xin = x >= g.P && x < g.P + g.nx;
+  // ring cells of these rows that lie outside the x strips
+  const bool sv0 = x >= g.P && x < g.P + g.nx, sv1 = x + 1 >= g.P && x + 1 < g.P + g.nx;
 #pragma unroll
-  for (int q = 0; q < CH; ++q) {
+  for (int q = 0; q < ZCH; ++q) {
     const int z = zs + q;
     if (z >= ze) break;
-    const float* w = wu + q;
-    const float* p = wp + q;
-    const long long c = (long long)z * g.NXp + x;
-    const float A = __ldg(a.az + z), B = __ldg(a.bz + z);
-    const float d2u = d2(w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7], w[8]);
-    const float d1u = d1(w[0], w[1], w[2], w[3], w[5], w[6], w[7], w[8]);
-    const float d1p = d1(p[0], p[1], p[2], p[3], p[5], p[6], p[7], p[8]);
-    const float zn = A * zt[q] + B * (d2u + d1p);
-    a.pout[so + c] = A * p[4] + B * d1u;
-    a.zeta[so + c] = zn;
-    const float v = un[q] + kk[q] * (d1p + zn);
-    a.un[so + c] = v;
-    if (a.save && xin) {
-      const int ri = ring_index(g, z, x);
-      if (ri >= 0) a.save[(long long)s * g.nring + ri] = v;
+    const float2 A = f2(__ldg(a.az + z)), B = f2(__ldg(a.bz + z));
+    const float2 d2u = d2p(wu + q), d1u = d1p(wu + q), dp = d1p(wp + q);
+    const float2 zn = __ffma2_rn(A, zt[q], __fmul2_rn(B, __fadd2_rn(d2u, dp)));
+    const float2 po = __ffma2_rn(A, wp[q + 4], __fmul2_rn(B, d1u));
+    const float2 v = __ffma2_rn(kk[q], __fadd2_rn(dp, zn), un[q]);
+    const size_t o = so + (size_t)z * g.NXp;
+    st2(a.pout + o, po);
+    st2(a.zeta + o, zn);
+    st2(a.un + o, v);
+    if (a.save) {
+      const int r0 = sv0 ? ring_index(g, z, x) : -1;
+      const int r1 = sv1 ? ring_index(g, z, x + 1) : -1;
+      float* sb = a.save + (size_t)blockIdx.z * g.nring;
+      if (r0 >= 0) sb[r0] = v.x;
+      if (r1 >= 0) sb[r1] = v.y;
     }
   }
 }
 
-// ------------------------------------------------------------- forward, x
-// Two column bands, left [0, lw) and right [r0, NX), tiled by CX_TZ x CX_TX.
-// blockIdx.x: tile index over both bands; blockIdx.z: shot.
-__host__ __device__ __forceinline__ int x_band_tiles(const Geom& g, int w) {
-  return ((w + CX_TX - 1) / CX_TX) * ((g.NZ + CX_TZ - 1) / CX_TZ);
+// ---------------------------------------------------------------- x groups
+// The x kernels cover a left and a right band of columns in 4-cell groups:
+// left groups [0, gl), right groups [gr0, ceil(NX/4)).  Thread -> (row, group)
+struct XBands {
+  int gl, gr0, ngr;
+};
+__host__ __device__ __forceinline__ XBands x_bands(int lo_end, int hi_start, int NX) {
+  XBands b;
+  b.gl = (lo_end + 3) / 4;
+  b.gr0 = hi_start / 4;
+  if (b.gr0 < b.gl) b.gr0 = b.gl;
+  b.ngr = b.gl + (NX + 3) / 4 - b.gr0;
+  return b;
 }
 
-__device__ __forceinline__ void x_tile(const Geom& g, int t, int lw, int r0, int& z0, int& xa,
-                                       int& xb) {
-  const int ntz = (g.NZ + CX_TZ - 1) / CX_TZ;
-  const int nl = x_band_tiles(g, lw);
-  const bool right = t >= nl;
-  const int w = right ? g.NX - r0 : lw;
-  const int ntx = (w + CX_TX - 1) / CX_TX;
-  const int r = right ? t - nl : t;
-  const int tz = r / ntx, tx = r - tz * ntx;
-  (void)ntz;
-  z0 = tz * CX_TZ;
-  xa = (right ? r0 : 0) + tx * CX_TX;
-  xb = min(xa + CX_TX, right ? g.NX : lw);
+// 12 cells x-4 .. x+7 of a row (zero outside [0, NXp))
+__device__ __forceinline__ void ldrow12(const float* row, int x, int NXp, float* e) {
+  const float4 l = x >= 4 ? ldg4(row + x - 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 c = ldg4(row + x);
+  const float4 r = x + 4 < NXp ? ldg4(row + x + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+  f4a(l, e);
+  f4a(c, e + 4);
+  f4a(r, e + 8);
+}
+
+// ------------------------------------------------------------- forward, x
+// Strip columns [0, P) and [P+nx, NX), all rows.
+__global__ void __launch_bounds__(XT) ac_cx_fwd_kernel(const AcCorrArgs a, const XBands xb) {
+  grid_dep_wait();
+  grid_dep_trigger();
+  if (*a.status) return;
+  const Geom& g = a.g;
+  const int idx = blockIdx.x * XT + threadIdx.x;
+  const int z = idx / xb.ngr;
+  if (z >= g.NZ) return;
+  const int j = idx - z * xb.ngr;
+  const int x = 4 * (j < xb.gl ? j : xb.gr0 + (j - xb.gl));
+  const size_t ro = (size_t)blockIdx.y * g.fstride + (size_t)z * g.NXp;
+  float e[12], f[12], zt[4], kk[4], un[4], A[4], B[4];
+  ldrow12(a.u + ro, x, g.NXp, e);
+  ldrow12(a.pin + ro, x, g.NXp, f);
+  f4a(ld4(a.zeta + ro + x), zt);
+  f4a(ldg4(a.K + (size_t)z * g.NXp + x), kk);
+  f4a(ld4(a.un + ro + x), un);
+  f4a(ldg4(a.ax + x), A);
+  f4a(ldg4(a.bx + x), B);
+  float po[4], zo[4], uo[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float* w = e + c;
+    const float* p = f + c;
+    const float d2u = d2(w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7], w[8]);
+    const float d1u = d1(w[0], w[1], w[2], w[3], w[5], w[6], w[7], w[8]);
+    const float dp = d1(p[0], p[1], p[2], p[3], p[5], p[6], p[7], p[8]);
+    const float zn = A[c] * zt[c] + B[c] * (d2u + dp);
+    const bool m = x_border(g, x + c) && x + c < g.NX;
+    po[c] = A[c] * p[4] + B[c] * d1u;  // zero off the strip (a = b = psi = 0)
+    zo[c] = zn;
+    uo[c] = m ? un[c] + kk[c] * (dp + zn) : un[c];
+  }
+  st4(a.pout + ro + x, po);
+  st4(a.zeta + ro + x, zo);
+  st4(a.un + ro + x, uo);
+  if (a.save) {
+    float* sb = a.save + (size_t)blockIdx.y * g.nring;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (!(x_border(g, x + c) && x + c < g.NX)) continue;
+      const int ri = ring_index(g, z, x + c);
+      if (ri >= 0) sb[ri] = uo[c];
+    }
+  }
 }
 
 // Row bands of the backward z kernel and column bands of the backward x
@@ -124,168 +214,117 @@ __host__ __device__ __forceinline__ int band_hi_start(int P, int n, int N) {
   return max(P + n - 4, band_lo_end(P, N));
 }
 
-__global__ void __launch_bounds__(CX_T) ac_cx_fwd_kernel(const AcCorrArgs a) {
-  __shared__ __align__(16) float su[CX_TZ * CX_W];
-  __shared__ __align__(16) float sp[CX_TZ * CX_W];
-  if (*a.status) return;
-  const Geom& g = a.g;
-  const int s = blockIdx.z;
-  const long long so = (long long)s * g.fstride;
-  int z0, x0, x1;
-  x_tile(g, blockIdx.x, g.P, g.P + g.nx, z0, x0, x1);
-  const int xs = (x0 - 4) & ~3;  // aligned staging origin (covers x0-4 .. x0+CX_TX+4)
-  for (int idx = threadIdx.x; idx < CX_TZ * (CX_W / 4); idx += CX_T) {
-    const int r = idx / (CX_W / 4), c4 = idx - r * (CX_W / 4);
-    const int z = z0 + r, x = xs + 4 * c4;
-    float4 vu = make_float4(0.f, 0.f, 0.f, 0.f), vp = vu;
-    if (z < g.NZ && x >= 0 && x < g.NXp) {
-      vu = *reinterpret_cast<const float4*>(a.u + so + (long long)z * g.NXp + x);
-      vp = *reinterpret_cast<const float4*>(a.pin + so + (long long)z * g.NXp + x);
-    }
-    *reinterpret_cast<float4*>(su + r * CX_W + 4 * c4) = vu;
-    *reinterpret_cast<float4*>(sp + r * CX_W + 4 * c4) = vp;
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < CX_TZ * CX_TX; idx += CX_T) {
-    const int r = idx / CX_TX, cc = idx - r * CX_TX;
-    const int z = z0 + r, x = x0 + cc;
-    if (z >= g.NZ || x >= x1) continue;
-    const float* ur = su + r * CX_W + (x - xs);
-    const float* pr = sp + r * CX_W + (x - xs);
-    const float d2u = d2(ur[-4], ur[-3], ur[-2], ur[-1], ur[0], ur[1], ur[2], ur[3], ur[4]);
-    const float d1u = d1(ur[-4], ur[-3], ur[-2], ur[-1], ur[1], ur[2], ur[3], ur[4]);
-    const float d1p = d1(pr[-4], pr[-3], pr[-2], pr[-1], pr[1], pr[2], pr[3], pr[4]);
-    const long long c = (long long)z * g.NXp + x;
-    const float A = __ldg(a.ax + x), B = __ldg(a.bx + x);
-    const float zn = A * a.zeta[so + c] + B * (d2u + d1p);
-    a.pout[so + c] = A * pr[0] + B * d1u;
-    a.zeta[so + c] = zn;
-    const float v = a.un[so + c] + a.K[c] * (d1p + zn);
-    a.un[so + c] = v;
-    if (a.save) {
-      const int ri = ring_index(g, z, x);
-      if (ri >= 0) a.save[(long long)s * g.nring + ri] = v;
-    }
-  }
-}
-
 // ------------------------------------------------------------ backward, z
-// Bands [0, P+4) and [P+nz-4, NZ) (without overlap), chunks of CH rows per
-// thread, all loads of a chunk issued first.  blockIdx.y: band times chunk.
-__global__ void __launch_bounds__(CZ_T) ac_cz_bwd_kernel(const AcCorrArgs a) {
+// Bands [0, P+4) and [P+nz-4, NZ) in chunks of ZCH rows; blockIdx.y: band
+// times chunk.
+__global__ void __launch_bounds__(ZT) ac_cz_bwd_kernel(const AcCorrArgs a) {
+  grid_dep_wait();
+  grid_dep_trigger();
   if (*a.status) return;
   const Geom& g = a.g;
-  const int x = blockIdx.x * CZ_T + threadIdx.x;
+  const int x = 2 * (blockIdx.x * ZT + threadIdx.x);
   if (x >= g.NX) return;
-  const int s = blockIdx.z;
-  const long long so = (long long)s * g.fstride;
   const int lo_end = band_lo_end(g.P, g.NZ), hi_start = band_hi_start(g.P, g.nz, g.NZ);
-  const int nlo = (lo_end + CH - 1) / CH;
+  const int nlo = (lo_end + ZCH - 1) / ZCH;
   const int band = (int)blockIdx.y >= nlo ? 1 : 0;
-  const int ch = band ? blockIdx.y - nlo : blockIdx.y;
-  const int zs = (band ? hi_start : 0) + ch * CH;
-  const int ze = min(zs + CH, band ? g.NZ : lo_end);
+  const int zs = (band ? hi_start : 0) + ((int)blockIdx.y - band * nlo) * ZCH;
+  const int ze = min(zs + ZCH, band ? g.NZ : lo_end);
   if (zs >= ze) return;
+  const size_t so = (size_t)blockIdx.z * g.fstride + x;
   const float* m1 = a.u + so;  // mu^{n+1}
   const float* zb = a.zeta + so;
   const float* pb = a.pin + so;
-  // rows zs-4 .. zs+CH+3: C = b (mu + zetabar), B = b psibar, m G
-  float wm[CW], wz[CW], wp[CW];
+  float2 wm[ZW], wz[ZW], wp[ZW], mo[ZCH], kk[ZCH];
+  float bb[ZW];
 #pragma unroll
-  for (int k = 0; k < CW; ++k) {
+  for (int k = 0; k < ZW; ++k) {
     const int zz = zs - 4 + k;
-    const bool inb = zz >= 0 && zz < g.NZ;
-    const bool bord = inb && z_border(g, zz);
-    const long long c = (long long)zz * g.NXp + x;
-    wm[k] = bord ? m1[c] : 0.f;
-    wz[k] = bord ? zb[c] : 0.f;
-    wp[k] = bord ? pb[c] : 0.f;
+    const bool ok = zz >= 0 && zz < g.NZ;
+    const size_t o = (size_t)zz * g.NXp;
+    wm[k] = ok ? ldg2(m1 + o) : f2(0.f);
+    wz[k] = ok ? ldg2(zb + o) : f2(0.f);
+    wp[k] = ok ? ldg2(pb + o) : f2(0.f);
+    bb[k] = ok ? __ldg(a.bz + zz) : 0.f;
   }
-  float mo[CH], kk[CH];
 #pragma unroll
-  for (int q = 0; q < CH; ++q) {
-    const int z = zs + q;
-    const long long c = (long long)z * g.NXp + x;
-    mo[q] = z < ze ? a.un[so + c] : 0.f;
-    kk[q] = z < ze ? a.K[c] : 0.f;
+  for (int q = 0; q < ZCH; ++q) {
+    const bool ok = zs + q < ze;
+    const size_t o = (size_t)(zs + q) * g.NXp;
+    mo[q] = ok ? ld2(a.un + so + o) : f2(0.f);
+    kk[q] = ok ? ldg2(a.K + x + o) : f2(0.f);
   }
-  float wc[CW], wb[CW], wg[CW];
+  float2 wc[ZW], wb[ZW], wg[ZW];
 #pragma unroll
-  for (int k = 0; k < CW; ++k) {
+  for (int k = 0; k < ZW; ++k) {
     const int zz = zs - 4 + k;
-    const float b = (zz >= 0 && zz < g.NZ && z_border(g, zz)) ? __ldg(a.bz + zz) : 0.f;
-    wc[k] = b * (wm[k] + wz[k]);
-    wb[k] = b * wp[k];
-    wg[k] = wm[k] + wc[k];  // zero off the border rows (m G)
+    const float2 b = f2(bb[k]);
+    wc[k] = __fmul2_rn(b, __fadd2_rn(wm[k], wz[k]));
+    wb[k] = __fmul2_rn(b, wp[k]);
+    // m G: zero off the strip rows
+    wg[k] = (zz >= 0 && zz < g.NZ && z_border(g, zz)) ? __fadd2_rn(wm[k], wc[k]) : f2(0.f);
   }
 #pragma unroll
-  for (int q = 0; q < CH; ++q) {
+  for (int q = 0; q < ZCH; ++q) {
     const int z = zs + q;
     if (z >= ze) break;
-    const long long c = (long long)z * g.NXp + x;
-    const float* C = wc + q;
-    const float* B = wb + q;
-    const float* G = wg + q;
-    const float corr = d2(C[0], C[1], C[2], C[3], C[4], C[5], C[6], C[7], C[8]) -
-                       d1(B[0], B[1], B[2], B[3], B[5], B[6], B[7], B[8]);
-    a.un[so + c] = mo[q] + kk[q] * corr;  // mu^n
+    const size_t o = so + (size_t)z * g.NXp;
+    const float2 corr = __fadd2_rn(d2p(wc + q), neg2(d1p(wb + q)));
+    st2(a.un + o, __ffma2_rn(kk[q], corr, mo[q]));  // mu^n
     if (z_border(g, z)) {
-      const float A = __ldg(a.az + z);
-      a.pout[so + c] = A * wp[q + 4] - d1(G[0], G[1], G[2], G[3], G[5], G[6], G[7], G[8]);
-      a.zout[so + c] = A * (wm[q + 4] + wz[q + 4]);
+      const float2 A = f2(__ldg(a.az + z));
+      st2(a.pout + o, __fadd2_rn(__fmul2_rn(A, wp[q + 4]), neg2(d1p(wg + q))));
+      st2(a.zout + o, __fmul2_rn(A, __fadd2_rn(wm[q + 4], wz[q + 4])));
     }
   }
 }
 
 // ------------------------------------------------------------ backward, x
-// bands [0, P+4) and [P+nx-4, NX) over all rows
-__global__ void __launch_bounds__(CX_T) ac_cx_bwd_kernel(const AcCorrArgs a) {
-  __shared__ __align__(16) float sc[CX_TZ * CX_W];  // C
-  __shared__ __align__(16) float sb[CX_TZ * CX_W];  // B
-  __shared__ __align__(16) float sg[CX_TZ * CX_W];  // m G
+// Bands [0, P+4) and [P+nx-4, NX), all rows.
+__global__ void __launch_bounds__(XT) ac_cx_bwd_kernel(const AcCorrArgs a, const XBands xb) {
+  grid_dep_wait();
+  grid_dep_trigger();
   if (*a.status) return;
   const Geom& g = a.g;
-  const int s = blockIdx.z;
-  const long long so = (long long)s * g.fstride;
-  int z0, x0, x1;
-  x_tile(g, blockIdx.x, band_lo_end(g.P, g.NX), band_hi_start(g.P, g.nx, g.NX), z0, x0, x1);
-  const int xs = (x0 - 4) & ~3;
-  for (int idx = threadIdx.x; idx < CX_TZ * CX_W; idx += CX_T) {
-    const int r = idx / CX_W, j = idx - r * CX_W;
-    const int z = z0 + r, x = xs + j;
-    float C = 0.f, Bv = 0.f, G = 0.f;
-    if (z < g.NZ && x >= 0 && x < g.NX && x_border(g, x)) {
-      const long long c = so + (long long)z * g.NXp + x;
-      const float b = __ldg(a.bx + x);
-      const float m = a.u[c];
-      C = b * (m + a.zeta[c]);
-      Bv = b * a.pin[c];
-      G = m + C;
-    }
-    sc[idx] = C;
-    sb[idx] = Bv;
-    sg[idx] = G;
+  const int idx = blockIdx.x * XT + threadIdx.x;
+  const int z = idx / xb.ngr;
+  if (z >= g.NZ) return;
+  const int j = idx - z * xb.ngr;
+  const int x = 4 * (j < xb.gl ? j : xb.gr0 + (j - xb.gl));
+  const size_t ro = (size_t)blockIdx.y * g.fstride + (size_t)z * g.NXp;
+  float em[12], ez[12], ep[12], bb[12], kk[4], mo[4], A[4];
+  ldrow12(a.u + ro, x, g.NXp, em);
+  ldrow12(a.zeta + ro, x, g.NXp, ez);
+  ldrow12(a.pin + ro, x, g.NXp, ep);
+  ldrow12(a.bx, x, g.NXp, bb);
+  f4a(ldg4(a.K + (size_t)z * g.NXp + x), kk);
+  f4a(ld4(a.un + ro + x), mo);
+  f4a(ldg4(a.ax + x), A);
+  float C[12], Bv[12], G[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int xx = x - 4 + k;
+    C[k] = bb[k] * (em[k] + ez[k]);
+    Bv[k] = bb[k] * ep[k];
+    G[k] = (xx >= 0 && xx < g.NX && x_border(g, xx)) ? em[k] + C[k] : 0.f;
   }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < CX_TZ * CX_TX; idx += CX_T) {
-    const int r = idx / CX_TX, cc = idx - r * CX_TX;
-    const int z = z0 + r, x = x0 + cc;
-    if (z >= g.NZ || x >= x1) continue;
-    const int o = r * CX_W + (x - xs);
-    const float* C = sc + o;
-    const float* Bv = sb + o;
-    const float* G = sg + o;
-    const float corr = d2(C[-4], C[-3], C[-2], C[-1], C[0], C[1], C[2], C[3], C[4]) -
-                       d1(Bv[-4], Bv[-3], Bv[-2], Bv[-1], Bv[1], Bv[2], Bv[3], Bv[4]);
-    const long long c = (long long)z * g.NXp + x;
-    a.un[so + c] += a.K[c] * corr;
-    if (x_border(g, x)) {
-      const float A = __ldg(a.ax + x);
-      const float m = a.u[so + c];
-      a.pout[so + c] = A * a.pin[so + c] - d1(G[-4], G[-3], G[-2], G[-1], G[1], G[2], G[3], G[4]);
-      a.zout[so + c] = A * (m + a.zeta[so + c]);
-    }
+  float uo[4], po[4], zo[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float* Cc = C + c;
+    const float* Bc = Bv + c;
+    const float* Gc = G + c;
+    const float corr = d2(Cc[0], Cc[1], Cc[2], Cc[3], Cc[4], Cc[5], Cc[6], Cc[7], Cc[8]) -
+                       d1(Bc[0], Bc[1], Bc[2], Bc[3], Bc[5], Bc[6], Bc[7], Bc[8]);
+    const bool in = x + c < g.NX;
+    const bool m = in && x_border(g, x + c);
+    uo[c] = in ? mo[c] + kk[c] * corr : mo[c];
+    po[c] = m ? A[c] * ep[c + 4] - d1(Gc[0], Gc[1], Gc[2], Gc[3], Gc[5], Gc[6], Gc[7], Gc[8])
+              : 0.f;
+    zo[c] = m ? A[c] * (em[c + 4] + ez[c + 4]) : 0.f;
   }
+  st4(a.un + ro + x, uo);
+  st4(a.pout + ro + x, po);
+  st4(a.zout + ro + x, zo);
 }
 
 }  // namespace
@@ -294,10 +333,11 @@ void launch_ac_corr_fwd(const AcCorrArgs& z, const AcCorrArgs& x, cudaStream_t s
   const Geom& g = z.g;
   if (g.P <= 0 || g.nshot <= 0) return;
   void* tok = profile_begin(SWEEP_K_AC_FWD_FR, st);
-  dim3 gz((g.NX + CZ_T - 1) / CZ_T, 2 * ((g.P + CH - 1) / CH), g.nshot);
-  ac_cz_fwd_kernel<<<gz, CZ_T, 0, st>>>(z);
-  dim3 gx(x_band_tiles(g, g.P) + x_band_tiles(g, g.NX - (g.P + g.nx)), 1, g.nshot);
-  ac_cx_fwd_kernel<<<gx, CX_T, 0, st>>>(x);
+  const dim3 gz((g.NX + 2 * ZT - 1) / (2 * ZT), 2 * ((g.P + ZCH - 1) / ZCH), g.nshot);
+  launch_dependent(ac_cz_fwd_kernel, gz, dim3(ZT), 0, st, z);
+  const XBands xb = x_bands(g.P, g.P + g.nx, g.NX);
+  const dim3 gx((unsigned)(((long long)g.NZ * xb.ngr + XT - 1) / XT), g.nshot, 1);
+  launch_dependent(ac_cx_fwd_kernel, gx, dim3(XT), 0, st, x, xb);
   profile_end(tok, st);
   note_launches(2);
 }
@@ -307,12 +347,13 @@ void launch_ac_corr_bwd(const AcCorrArgs& z, const AcCorrArgs& x, cudaStream_t s
   if (g.P <= 0 || g.nshot <= 0) return;
   void* tok = profile_begin(SWEEP_K_AC_BWD_FR, st);
   const int lo_end = band_lo_end(g.P, g.NZ), hi_start = band_hi_start(g.P, g.nz, g.NZ);
-  dim3 gz((g.NX + CZ_T - 1) / CZ_T, (lo_end + CH - 1) / CH + (g.NZ - hi_start + CH - 1) / CH,
-          g.nshot);
-  ac_cz_bwd_kernel<<<gz, CZ_T, 0, st>>>(z);
-  const int lw = band_lo_end(g.P, g.NX), r0 = band_hi_start(g.P, g.nx, g.NX);
-  dim3 gx(x_band_tiles(g, lw) + x_band_tiles(g, g.NX - r0), 1, g.nshot);
-  ac_cx_bwd_kernel<<<gx, CX_T, 0, st>>>(x);
+  const dim3 gz((g.NX + 2 * ZT - 1) / (2 * ZT),
+                (lo_end + ZCH - 1) / ZCH + (g.NZ - hi_start + ZCH - 1) / ZCH, g.nshot);
+  launch_dependent(ac_cz_bwd_kernel, gz, dim3(ZT), 0, st, z);
+  const XBands xb =
+      x_bands(band_lo_end(g.P, g.NX), band_hi_start(g.P, g.nx, g.NX), g.NX);
+  const dim3 gx((unsigned)(((long long)g.NZ * xb.ngr + XT - 1) / XT), g.nshot, 1);
+  launch_dependent(ac_cx_bwd_kernel, gx, dim3(XT), 0, st, x, xb);
   profile_end(tok, st);
   note_launches(2);
 }

@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
   constexpr int D = FWD_STAGES;
   FwdStage* stg = reinterpret_cast<FwdStage*>(smem_raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(FwdStage));
+  grid_dep_wait();
   if (*a.status) return;
   const Geom& g = a.g;
   const Region& R = g.fin;
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
   const int lx = 4 * lane, r0 = warp * RPW_F;
   int k = 0;
   for (; k < count; ++k) {
+    if (k == count - 1) grid_dep_trigger();  // the next kernel may start
     const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
     if (__syncthreads_or(!got)) break;
     const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_F, blockIdx.x + k * G);
@@ -192,6 +194,7 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
   constexpr int D = BWD_STAGES;
   BwdStage* stg = reinterpret_cast<BwdStage*>(smem_raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(BwdStage));
+  grid_dep_wait();
   if (*a.status) return;
   const Geom& g = a.g;
   const Region& R = g.bin;
@@ -228,6 +231,7 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
   const int lx = 4 * lane, r0 = warp * RPW_B;
   int k = 0;
   for (; k < count; ++k) {
+    if (k == count - 1) grid_dep_trigger();  // the next kernel may start
     const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_B, blockIdx.x + k * G);
     const BwdFlags f = bwd_flags(g, img, rec, a.save != nullptr, p);
     // saved ring values of u^{n-1} of this thread's cells, fetched before the
@@ -396,7 +400,7 @@ void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st) {
   int grid = device_sms();
   if (grid > a.units) grid = a.units;
   void* tok = profile_begin(SWEEP_K_AC_FWD_IN, st);
-  ac_in_fwd_kernel<<<grid, IN_THREADS, kFwdSmem, st>>>(a);
+  launch_dependent(ac_in_fwd_kernel, dim3(grid), dim3(IN_THREADS), kFwdSmem, st, a);
   profile_end(tok, st);
   note_launches(1);
 }
@@ -412,7 +416,7 @@ void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st) {
   int grid = device_sms();
   if (grid > a.units) grid = a.units;
   void* tok = profile_begin(SWEEP_K_AC_BWD_IN, st);
-  ac_in_bwd_kernel<<<grid, IN_THREADS, kBwdSmem, st>>>(a);
+  launch_dependent(ac_in_bwd_kernel, dim3(grid), dim3(IN_THREADS), kBwdSmem, st, a);
   profile_end(tok, st);
   note_launches(1);
 }

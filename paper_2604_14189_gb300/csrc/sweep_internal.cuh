@@ -197,4 +197,33 @@ __device__ __forceinline__ void latch(int* status, int code) {
   atomicCAS(status, 0, code);
 }
 
+// Programmatic dependent launch.  A kernel started by launch_dependent may be
+// scheduled while the kernel before it in the stream is still draining; it
+// must call grid_dep_wait() before its first access to memory that an
+// earlier kernel writes (every such kernel here calls it first thing, so the
+// stream order stays transitive).  grid_dep_trigger() lets the next kernel
+// be scheduled once every CTA of this one has called it or exited.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t st, const Args&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace sweep
