@@ -18,8 +18,10 @@
 namespace sweep {
 namespace {
 
-constexpr int RPW_F = IN_BZ_F / (IN_THREADS / 32);  // rows per warp, forward
-constexpr int RPW_B = IN_BZ_B / (IN_THREADS / 32);  // rows per warp, backward
+constexpr int FWD_THREADS = 256;
+constexpr int BWD_THREADS = 256;
+constexpr int RPW_F = IN_BZ_F / (FWD_THREADS / 32);  // rows per warp, forward
+constexpr int RPW_B = IN_BZ_B / (BWD_THREADS / 32);  // rows per warp, backward
 constexpr int HF_F = IN_HW * (IN_BZ_F + 8);          // floats, forward halo tile
 constexpr int CF_F = IN_BX * IN_BZ_F;                // floats, forward centre tile
 constexpr int HF_B = IN_HW * (IN_BZ_B + 8);
@@ -84,11 +86,59 @@ __device__ __forceinline__ UnitPos unit_pos(const Region& R, int S, int ntx, int
   return p;
 }
 
+// Per-unit facts, computed once by the thread that issues the unit's
+// transfers and read by every thread from shared memory.
+enum : int {
+  U_IMG = 1,   // meets the interior: imaging (backward)
+  U_RING = 2,  // meets the saved ring: restore from the forward save (backward)
+  U_U1 = 4,    // needs u^{n+1} (reconstruction or restore, backward)
+  U_SRC = 8,   // holds the source cell
+  U_REC = 16,  // meets the receiver box
+};
+struct UnitDesc {
+  int s, z0, x0, flags;
+  int sz, sx;  // source cell (padded coordinates)
+  float fn;    // wavelet sample of this step (0 where not needed)
+  int pad;
+};
+
+__device__ __forceinline__ UnitDesc make_desc(const Region& R, const Geom& g, const ShotTable& T,
+                                              const AcInFwdArgs* af, const AcInBwdArgs* ab,
+                                              int bz, int unit) {
+  const int S = g.nshot;
+  const int ntx = af ? af->ntx : ab->ntx;
+  const UnitPos p = unit_pos(R, S, ntx, bz, unit);
+  const bool img = ab && ab->do_img;
+  const ShotInfo si =
+      af ? shot_info(T, g, af->src, af->wavelet, af->rbox, af->n, p.s)
+         : shot_info(T, g, ab->src, img ? ab->wavelet : nullptr, ab->rbox, ab->n, p.s);
+  UnitDesc d;
+  d.s = p.s;
+  d.z0 = p.z0;
+  d.x0 = p.x0;
+  d.sz = si.sz;
+  d.sx = si.sx;
+  d.fn = si.fn;
+  d.pad = 0;
+  int f = 0;
+  if (si.sz >= p.z0 && si.sz < p.z0 + bz && si.sx >= p.x0 && si.sx < p.x0 + IN_BX &&
+      in_region(R, si.sz, si.sx))
+    f |= U_SRC;
+  if (tile_meets(si.box, p.z0, bz, p.x0, IN_BX)) f |= U_REC;
+  if (ab) {
+    const BwdFlags b = bwd_flags(g, img, ab->do_rec != 0, ab->save != nullptr, p);
+    f |= (b.imgt ? U_IMG : 0) | (b.ringt ? U_RING : 0) | (b.needu1 ? U_U1 : 0);
+  }
+  d.flags = f;
+  return d;
+}
+
 // -------------------------------------------------------------- forward
-__global__ void __launch_bounds__(IN_THREADS, 1)
+__global__ void __launch_bounds__(FWD_THREADS, 1)
     ac_in_fwd_kernel(const __grid_constant__ AcInFwdArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ ShotTable T;
+  __shared__ UnitDesc desc[FWD_STAGES];
   constexpr int D = FWD_STAGES;
   FwdStage* stg = reinterpret_cast<FwdStage*>(smem_raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(FwdStage));
@@ -96,7 +146,6 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
   if (*a.status) return;
   const Geom& g = a.g;
   const Region& R = g.fin;
-  const int S = g.nshot;
   const int G = gridDim.x;
   const int count = (a.units - (int)blockIdx.x + G - 1) / G;  // units b, b+G, ...
   if (count <= 0) return;
@@ -106,14 +155,17 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
     fence_barrier_init();
   }
   __syncthreads();
+  // the unit's descriptor is stored before the arrive on its barrier, so a
+  // thread that has waited on the barrier sees it
   auto issue = [&](int k) {
-    const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_F, blockIdx.x + k * G);
+    const UnitDesc d = make_desc(R, g, T, &a, nullptr, IN_BZ_F, blockIdx.x + k * G);
+    desc[k % D] = d;
     FwdStage& sg = stg[k % D];
     uint64_t* b = &bar[k % D];
     mbar_arrive_expect_tx(b, kFwdBytes);
-    tma_load_3d(sg.u, &a.tu, b, p.x0 - 4, p.z0 - 4, p.s);
-    tma_load_3d(sg.up, &a.tup, b, p.x0, p.z0, p.s);
-    tma_load_2d(sg.k, &a.tK, b, p.x0, p.z0);
+    tma_load_3d(sg.u, &a.tu, b, d.x0 - 4, d.z0 - 4, d.s);
+    tma_load_3d(sg.up, &a.tup, b, d.x0, d.z0, d.s);
+    tma_load_2d(sg.k, &a.tK, b, d.x0, d.z0);
   };
   if (threadIdx.x == 0)
     for (int k = 0; k < D && k < count; ++k) issue(k);
@@ -124,18 +176,17 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
     if (k == count - 1) grid_dep_trigger();  // the next kernel may start
     const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
     if (__syncthreads_or(!got)) break;
-    const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_F, blockIdx.x + k * G);
-    const ShotInfo si = shot_info(T, g, a.src, a.wavelet, a.rbox, a.n, p.s);
+    const UnitDesc d = desc[k % D];
     const FwdStage& sg = stg[k % D];
-    const long long so = (long long)p.s * g.fstride;
-    const int gx = p.x0 + lx;
+    const long long so = (long long)d.s * g.fstride;
+    const int gx = d.x0 + lx;
     float w[9][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) f4a(lds4(sg.u, IN_HW, r0 + j, lx + 4), w[j]);
 #pragma unroll
     for (int q = 0; q < RPW_F; ++q) {
       f4a(lds4(sg.u, IN_HW, r0 + q + 8, lx + 4), w[8]);
-      const int gz = p.z0 + r0 + q;
+      const int gz = d.z0 + r0 + q;
       if (gz < R.z1 && gx < R.x1) {
         float e[12], up[4], kk[4], out[4];
         f4a(lds4(sg.u, IN_HW, r0 + q + 4, lx), e);
@@ -151,7 +202,11 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
                  e[c + 8]) +
               d2(w[0][c], w[1][c], w[2][c], w[3][c], w[4][c], w[5][c], w[6][c], w[7][c], w[8][c]);
           out[c] = 2.f * w[4][c] - up[c] + kk[c] * lap;
-          if (gz == si.sz && gx + c == si.sx) out[c] += kk[c] * si.fn;
+        }
+        if ((d.flags & U_SRC) && gz == d.sz) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (gx + c == d.sx) out[c] += kk[c] * d.fn;
         }
         *reinterpret_cast<float4*>(a.un + so + (long long)gz * g.NXp + gx) =
             make_float4(out[0], out[1], out[2], out[3]);
@@ -168,13 +223,13 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
       issue(k + D);
     }
     // receivers of this shot inside this tile (read back this CTA's stores)
-    if (a.data && tile_meets(si.box, p.z0, IN_BZ_F, p.x0, IN_BX)) {
-      for (int r = threadIdx.x; r < g.nrec; r += IN_THREADS) {
-        const int32_t* q = a.rec + 2 * ((long long)p.s * g.nrec + r);
+    if (a.data && (d.flags & U_REC)) {
+      for (int r = threadIdx.x; r < g.nrec; r += FWD_THREADS) {
+        const int32_t* q = a.rec + 2 * ((long long)d.s * g.nrec + r);
         const int rz = q[0] + g.P, rx = q[1] + g.P;
-        if (rz >= p.z0 && rz < p.z0 + IN_BZ_F && rx >= p.x0 && rx < p.x0 + IN_BX &&
+        if (rz >= d.z0 && rz < d.z0 + IN_BZ_F && rx >= d.x0 && rx < d.x0 + IN_BX &&
             in_region(R, rz, rx))
-          a.data[((long long)p.s * g.nrec + r) * g.nt + a.n] =
+          a.data[((long long)d.s * g.nrec + r) * g.nt + a.n] =
               a.un[so + (long long)rz * g.NXp + rx];
       }
     }
@@ -187,22 +242,23 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
 }
 
 // -------------------------------------------------------------- backward
-__global__ void __launch_bounds__(IN_THREADS, 1)
+__global__ void __launch_bounds__(BWD_THREADS, 1)
     ac_in_bwd_kernel(const __grid_constant__ AcInBwdArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ ShotTable T;
+  __shared__ UnitDesc desc[BWD_STAGES];
   constexpr int D = BWD_STAGES;
+  static_assert(D >= 2, "the ring prefetch reads a descriptor written two barriers earlier");
   BwdStage* stg = reinterpret_cast<BwdStage*>(smem_raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(BwdStage));
   grid_dep_wait();
   if (*a.status) return;
   const Geom& g = a.g;
   const Region& R = g.bin;
-  const int S = g.nshot;
   const int G = gridDim.x;
   const int count = (a.units - (int)blockIdx.x + G - 1) / G;
   if (count <= 0) return;
-  const bool img = a.do_img != 0, adj = a.do_adj != 0, rec = a.do_rec != 0;
+  const bool img = a.do_img != 0, adj = a.do_adj != 0;
   load_shot_table(T, g, a.src, img ? a.wavelet : nullptr, a.rbox, a.n);
   if (threadIdx.x == 0) {
     for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
@@ -210,64 +266,69 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
   }
   __syncthreads();
   auto issue = [&](int k) {
-    const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_B, blockIdx.x + k * G);
-    const BwdFlags f = bwd_flags(g, img, rec, a.save != nullptr, p);
+    const UnitDesc d = make_desc(R, g, T, nullptr, &a, IN_BZ_B, blockIdx.x + k * G);
+    desc[k % D] = d;
     BwdStage& sg = stg[k % D];
     uint64_t* b = &bar[k % D];
-    mbar_arrive_expect_tx(b, (HF_B + CF_B) * 4 + (f.imgt ? (HF_B + CF_B) * 4 : 0) +
-                                 (f.needu1 ? CF_B * 4 : 0) + (adj ? CF_B * 4 : 0));
-    tma_load_3d(sg.ma, &a.tmA, b, p.x0 - 4, p.z0 - 4, p.s);
-    tma_load_2d(sg.k, &a.tK, b, p.x0, p.z0);
-    if (f.imgt) {
-      tma_load_3d(sg.ua, &a.tuA, b, p.x0 - 4, p.z0 - 4, p.s);
-      tma_load_3d(sg.gr, &a.tG, b, p.x0, p.z0, p.s);
+    const bool imgt = d.flags & U_IMG;
+    mbar_arrive_expect_tx(b, (HF_B + CF_B) * 4 + (imgt ? (HF_B + CF_B) * 4 : 0) +
+                                 ((d.flags & U_U1) ? CF_B * 4 : 0) + (adj ? CF_B * 4 : 0));
+    tma_load_3d(sg.ma, &a.tmA, b, d.x0 - 4, d.z0 - 4, d.s);
+    tma_load_2d(sg.k, &a.tK, b, d.x0, d.z0);
+    if (imgt) {
+      tma_load_3d(sg.ua, &a.tuA, b, d.x0 - 4, d.z0 - 4, d.s);
+      tma_load_3d(sg.gr, &a.tG, b, d.x0, d.z0, d.s);
     }
-    if (f.needu1) tma_load_3d(sg.ub, &a.tuB, b, p.x0, p.z0, p.s);
-    if (adj) tma_load_3d(sg.mb, &a.tmB, b, p.x0, p.z0, p.s);
+    if (d.flags & U_U1) tma_load_3d(sg.ub, &a.tuB, b, d.x0, d.z0, d.s);
+    if (adj) tma_load_3d(sg.mb, &a.tmB, b, d.x0, d.z0, d.s);
   };
   if (threadIdx.x == 0)
     for (int k = 0; k < D && k < count; ++k) issue(k);
+  __syncthreads();  // first descriptors visible before the ring prefetch below
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = 4 * lane, r0 = warp * RPW_B;
   int k = 0;
   for (; k < count; ++k) {
     if (k == count - 1) grid_dep_trigger();  // the next kernel may start
-    const UnitPos p = unit_pos(R, S, a.ntx, IN_BZ_B, blockIdx.x + k * G);
-    const BwdFlags f = bwd_flags(g, img, rec, a.save != nullptr, p);
+    const UnitDesc d = desc[k % D];
+    const bool imgt = d.flags & U_IMG, needu1 = d.flags & U_U1;
+    const int gx = d.x0 + lx;
     // saved ring values of u^{n-1} of this thread's cells, fetched before the
     // wait so that their latency overlaps the stage's transfer
     float rv[RPW_B][4];
     unsigned rmask = 0;
-    if (f.ringt) {
-      const int gx0 = p.x0 + lx;
+    if (d.flags & U_RING) {
 #pragma unroll
       for (int q = 0; q < RPW_B; ++q) {
-        const int gz = p.z0 + r0 + q;
+        const int gz = d.z0 + r0 + q;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const int ri = (gz < R.z1 && gx0 + c < R.x1) ? ring_index(g, gz, gx0 + c) : -1;
-          rv[q][c] = ri >= 0 ? a.save[(long long)p.s * g.nring + ri] : 0.f;
+          const int ri = (gz < R.z1 && gx + c < R.x1) ? ring_index(g, gz, gx + c) : -1;
+          rv[q][c] = ri >= 0 ? a.save[(long long)d.s * g.nring + ri] : 0.f;
           if (ri >= 0) rmask |= 1u << (4 * q + c);
         }
       }
     }
     const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
     if (__syncthreads_or(!got)) break;
-    const ShotInfo si = shot_info(T, g, a.src, img ? a.wavelet : nullptr, a.rbox, a.n, p.s);
     const BwdStage& sg = stg[k % D];
-    const long long so = (long long)p.s * g.fstride;
-    const int gx = p.x0 + lx;
+    const long long so = (long long)d.s * g.fstride;
+    // interior columns among this lane's 4 cells
+    unsigned cmask = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (gx + c >= g.P && gx + c < g.P + g.nx) cmask |= 1u << c;
     float wm[9][4], wu[9][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       f4a(lds4(sg.ma, IN_HW, r0 + j, lx + 4), wm[j]);
-      if (f.imgt) f4a(lds4(sg.ua, IN_HW, r0 + j, lx + 4), wu[j]);
+      if (imgt) f4a(lds4(sg.ua, IN_HW, r0 + j, lx + 4), wu[j]);
     }
 #pragma unroll
     for (int q = 0; q < RPW_B; ++q) {
       f4a(lds4(sg.ma, IN_HW, r0 + q + 8, lx + 4), wm[8]);
-      if (f.imgt) f4a(lds4(sg.ua, IN_HW, r0 + q + 8, lx + 4), wu[8]);
-      const int gz = p.z0 + r0 + q;
+      if (imgt) f4a(lds4(sg.ua, IN_HW, r0 + q + 8, lx + 4), wu[8]);
+      const int gz = d.z0 + r0 + q;
       if (gz < R.z1 && gx < R.x1) {
         const long long ci = so + (long long)gz * g.NXp + gx;
         float kk[4];
@@ -290,49 +351,54 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
           }
           *reinterpret_cast<float4*>(a.mB + ci) = make_float4(out[0], out[1], out[2], out[3]);
         }
+        // interior cells of this lane in this row
+        const unsigned im = (imgt && gz >= g.P && gz < g.P + g.nz) ? cmask : 0u;
         float lap[4] = {0.f, 0.f, 0.f, 0.f};
-        bool ins[4] = {false, false, false, false};
-        if (f.imgt) {
-          // imaging on interior cells: graw += mu^{n+1} (Lap u^n + f^n delta_s)
+        if (im) {
+          // imaging: graw += mu^{n+1} (Lap u^n + f^n delta_s)
           float e[12];
           f4a(lds4(sg.ua, IN_HW, r0 + q + 4, lx), e);
           f4a(lds4(sg.ua, IN_HW, r0 + q + 4, lx + 8), e + 8);
 #pragma unroll
           for (int c = 0; c < 4; ++c) e[4 + c] = wu[4][c];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            ins[c] = interior(g, gz, gx + c);
+          for (int c = 0; c < 4; ++c)
             lap[c] = d2(e[c], e[c + 1], e[c + 2], e[c + 3], e[c + 4], e[c + 5], e[c + 6],
                         e[c + 7], e[c + 8]) +
                      d2(wu[0][c], wu[1][c], wu[2][c], wu[3][c], wu[4][c], wu[5][c], wu[6][c],
                         wu[7][c], wu[8][c]);
-            if (gz == si.sz && gx + c == si.sx) lap[c] += si.fn;
+          if ((d.flags & U_SRC) && gz == d.sz) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (gx + c == d.sx) lap[c] += d.fn;
           }
           float gvv[4];
           f4a(lds4(sg.gr, IN_BX, r0 + q, lx), gvv);
 #pragma unroll
           for (int c = 0; c < 4; ++c)
-            if (ins[c]) gvv[c] += wm[4][c] * lap[c];
+            if ((im >> c) & 1u) gvv[c] += wm[4][c] * lap[c];
           *reinterpret_cast<float4*>(a.graw + ci) = make_float4(gvv[0], gvv[1], gvv[2], gvv[3]);
           if (a.illum) {
             float iv[4];
             f4a(*reinterpret_cast<const float4*>(a.illum + ci), iv);
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-              if (ins[c]) iv[c] += wu[4][c] * wu[4][c];
+              if ((im >> c) & 1u) iv[c] += wu[4][c] * wu[4][c];
             *reinterpret_cast<float4*>(a.illum + ci) = make_float4(iv[0], iv[1], iv[2], iv[3]);
           }
         }
-        if (f.needu1) {
-          // u^{n-1}: reconstructed on interior cells, restored on the ring
+        const unsigned rm = (rmask >> (4 * q)) & 0xFu;
+        if (needu1 && (im | rm)) {
+          // u^{n-1}: reconstructed on interior cells, restored on the ring;
+          // cells beyond the ring are never read again and keep u^{n+1}
           float u1[4], out[4];
           f4a(lds4(sg.ub, IN_BX, r0 + q, lx), u1);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            if (ins[c])
+            if ((im >> c) & 1u)
               out[c] = 2.f * wu[4][c] - u1[c] + kk[c] * lap[c];
             else
-              out[c] = (rmask >> (4 * q + c)) & 1u ? rv[q][c] : u1[c];
+              out[c] = ((rm >> c) & 1u) ? rv[q][c] : u1[c];
           }
           *reinterpret_cast<float4*>(a.uB + ci) = make_float4(out[0], out[1], out[2], out[3]);
         }
@@ -347,23 +413,22 @@ __global__ void __launch_bounds__(IN_THREADS, 1)
       }
     }
     // adjoint source gather: f-bar^n = mu^{n+1}(s)
-    if (a.wgrad && threadIdx.x == 0 && a.n < g.nt && si.sz >= p.z0 && si.sz < p.z0 + IN_BZ_B &&
-        si.sx >= p.x0 && si.sx < p.x0 + IN_BX && in_region(R, si.sz, si.sx))
-      a.wgrad[(long long)p.s * g.nt + a.n] =
-          sg.ma[(si.sz - p.z0 + 4) * IN_HW + (si.sx - p.x0 + 4)];
+    if (a.wgrad && threadIdx.x == 0 && a.n < g.nt && (d.flags & U_SRC))
+      a.wgrad[(long long)d.s * g.nt + a.n] =
+          sg.ma[(d.sz - d.z0 + 4) * IN_HW + (d.sx - d.x0 + 4)];
     __syncthreads();  // stage released; mu^n stores visible to this CTA
     if (threadIdx.x == 0 && k + D < count) {
       fence_proxy_async_smem();
       issue(k + D);
     }
     // residual injection mu^n(r) += K(r) r^{n-1} for receivers in this tile
-    if (adj && a.n >= 1 && tile_meets(si.box, p.z0, IN_BZ_B, p.x0, IN_BX)) {
-      for (int r = threadIdx.x; r < g.nrec; r += IN_THREADS) {
-        const int32_t* q = a.rec + 2 * ((long long)p.s * g.nrec + r);
+    if (adj && a.n >= 1 && (d.flags & U_REC)) {
+      for (int r = threadIdx.x; r < g.nrec; r += BWD_THREADS) {
+        const int32_t* q = a.rec + 2 * ((long long)d.s * g.nrec + r);
         const int rz = q[0] + g.P, rx = q[1] + g.P;
-        if (rz >= p.z0 && rz < p.z0 + IN_BZ_B && rx >= p.x0 && rx < p.x0 + IN_BX &&
+        if (rz >= d.z0 && rz < d.z0 + IN_BZ_B && rx >= d.x0 && rx < d.x0 + IN_BX &&
             in_region(R, rz, rx)) {
-          const float rv = a.res[((long long)p.s * g.nrec + r) * g.nt + (a.n - 1)];
+          const float rv = a.res[((long long)d.s * g.nrec + r) * g.nt + (a.n - 1)];
           atomicAdd(a.mB + so + (long long)rz * g.NXp + rx,
                     a.K[(long long)rz * g.NXp + rx] * rv);
         }
@@ -400,7 +465,7 @@ void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st) {
   int grid = device_sms();
   if (grid > a.units) grid = a.units;
   void* tok = profile_begin(SWEEP_K_AC_FWD_IN, st);
-  launch_dependent(ac_in_fwd_kernel, dim3(grid), dim3(IN_THREADS), kFwdSmem, st, a);
+  launch_dependent(ac_in_fwd_kernel, dim3(grid), dim3(FWD_THREADS), kFwdSmem, st, a);
   profile_end(tok, st);
   note_launches(1);
 }
@@ -416,7 +481,7 @@ void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st) {
   int grid = device_sms();
   if (grid > a.units) grid = a.units;
   void* tok = profile_begin(SWEEP_K_AC_BWD_IN, st);
-  launch_dependent(ac_in_bwd_kernel, dim3(grid), dim3(IN_THREADS), kBwdSmem, st, a);
+  launch_dependent(ac_in_bwd_kernel, dim3(grid), dim3(BWD_THREADS), kBwdSmem, st, a);
   profile_end(tok, st);
   note_launches(1);
 }

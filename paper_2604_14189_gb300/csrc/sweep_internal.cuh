@@ -34,12 +34,11 @@ struct Geom {
 
 // ------------------------------------------------------------------ interior
 // Tiles of IN_BZ_F (forward) or IN_BZ_B (backward) rows x IN_BX cells;
-// IN_THREADS threads: each warp owns a band of rows, each lane 4 consecutive
+// each warp owns a band of rows, each lane 4 consecutive
 // cells of a row.  Halo tiles are IN_HW wide and 8 rows taller.
 constexpr int IN_BX = 128;
 constexpr int IN_BZ_F = 32;
 constexpr int IN_BZ_B = 16;
-constexpr int IN_THREADS = 256;
 constexpr int IN_HW = IN_BX + 8;  // halo tile width
 
 struct AcInFwdArgs {
