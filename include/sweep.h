@@ -172,23 +172,26 @@ const char* sweep_strerror(int code);
 unsigned long long sweep_kernel_launches(void);
 
 /* Kernel timing for benchmarks.  While enabled, every launch of a time-step
- * kernel is bracketed by two CUDA events recorded on the launching stream.
- * sweep_profile_enable(1) clears earlier records; (0) stops recording.
+ * kernel class selected by the mask is bracketed by two CUDA events recorded
+ * on the launching stream.  sweep_profile_enable(mask) clears earlier records
+ * and records the classes k with bit (1 << k) set in `mask` (-1: all
+ * classes); sweep_profile_enable(0) stops recording.
  * sweep_profile_read() synchronises on the recorded events and returns, for
  * kernel class `kernel` (SWEEP_K_*), the summed device time in ms and the
- * number of launches.  Host-side cost: two event records per launch. */
+ * number of launches.  Cost: two event records per recorded launch, and an
+ * event between two kernels ends their programmatic overlap. */
 enum {
   SWEEP_K_AC_FWD = 0,     /* acoustic forward step (all its kernels)   */
   SWEEP_K_AC_BWD = 1,     /* acoustic backward step (all its kernels)  */
   SWEEP_K_EL_VEL = 2,     /* elastic velocity half step                */
   SWEEP_K_EL_STR = 3,     /* elastic stress step                       */
-  SWEEP_K_AC_FWD_IN = 4,  /* acoustic forward, interior kernel         */
-  SWEEP_K_AC_FWD_FR = 5,  /* acoustic forward, border-frame kernel     */
-  SWEEP_K_AC_BWD_IN = 6,  /* acoustic backward, interior kernel        */
-  SWEEP_K_AC_BWD_FR = 7,  /* acoustic backward, border-frame kernel    */
+  SWEEP_K_AC_FWD_IN = 4,  /* acoustic forward, stencil kernel          */
+  SWEEP_K_AC_FWD_FR = 5,  /* acoustic forward, CPML correction kernels */
+  SWEEP_K_AC_BWD_IN = 6,  /* acoustic backward, stencil kernel         */
+  SWEEP_K_AC_BWD_FR = 7,  /* acoustic backward, CPML correction kernels*/
   SWEEP_K_COUNT = 8
 };
-int sweep_profile_enable(int on);
+int sweep_profile_enable(int mask);
 int sweep_profile_read(int kernel, double* ms, long long* launches);
 
 #ifdef __cplusplus

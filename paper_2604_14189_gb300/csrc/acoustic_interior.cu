@@ -1,7 +1,8 @@
-// Interior acoustic step kernels: the plain 8th-order update on the cells
-// away from the absorbing border (forward), and the fused adjoint +
-// reconstruction + imaging update on interior cells at least 4 cells from
-// the border (backward).  See acoustic_common.cuh for the equations.
+// Stencil kernels of the acoustic step: the plain 8th-order update of every
+// cell of the padded grid (forward), and the fused adjoint + reconstruction
+// + imaging update (backward).  The CPML terms are added afterwards by the
+// per-axis correction kernels (acoustic_cpml.cu).  See acoustic_common.cuh
+// for the equations.
 //
 // Work is a list of (tile, shot) units taken round-robin by persistent CTAs
 // (one per SM).  Each CTA runs a multi-stage TMA pipeline: while it computes

@@ -13,7 +13,7 @@ struct Rec {
 };
 
 std::mutex g_mu;
-bool g_on = false;
+int g_mask = 0;  // bit k: record kernel class k
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 
@@ -38,14 +38,10 @@ void release_all() {
 
 }  // namespace
 
-bool profiling() {
-  std::lock_guard<std::mutex> lk(g_mu);
-  return g_on;
-}
 
 void* profile_begin(int kernel, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_on) return nullptr;
+  if (kernel < 0 || kernel >= 31 || !((g_mask >> kernel) & 1)) return nullptr;
   Rec r{kernel, take_event(), take_event()};
   if (!r.a || !r.b) return nullptr;
   cudaEventRecord(r.a, st);
@@ -62,10 +58,10 @@ void profile_end(void* token, cudaStream_t st) {
 
 }  // namespace sweep
 
-extern "C" int sweep_profile_enable(int on) {
+extern "C" int sweep_profile_enable(int mask) {
   std::lock_guard<std::mutex> lk(sweep::g_mu);
   sweep::release_all();
-  sweep::g_on = on != 0;
+  sweep::g_mask = mask;
   return SWEEP_OK;
 }
 

@@ -119,8 +119,11 @@ def kernel_launches() -> int:
     return int(_lib.sweep_kernel_launches())
 
 
-def profile_enable(on: bool) -> None:
-    _lib.sweep_profile_enable(1 if on else 0)
+def profile_enable(on) -> None:
+    """True: record every kernel class; an int: bit mask of classes (1 << K_*);
+    False / 0: stop recording."""
+    mask = -1 if on is True else (0 if on is False else int(on))
+    _lib.sweep_profile_enable(mask)
 
 
 def profile_read(kernel: int) -> tuple[float, int]:
