@@ -102,6 +102,10 @@ struct UnitDesc {
   float fn;    // wavelet sample of this step (0 where not needed)
   int pad;
 };
+// Descriptors of a CTA's first kUnitTable units are computed by all its
+// threads in the prologue; later units (large batches) are described by the
+// issuing thread into a ring beside the stages.
+constexpr int kUnitTable = 256;
 
 __device__ __forceinline__ UnitDesc make_desc(const Region& R, const Geom& g, const ShotTable& T,
                                               const AcInFwdArgs* af, const AcInBwdArgs* ab,
@@ -140,6 +144,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ ShotTable T;
   __shared__ UnitDesc desc[FWD_STAGES];
+  __shared__ UnitDesc utab[kUnitTable];
   constexpr int D = FWD_STAGES;
   FwdStage* stg = reinterpret_cast<FwdStage*>(smem_raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(FwdStage));
@@ -151,6 +156,9 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
   const int count = (a.units - (int)blockIdx.x + G - 1) / G;  // units b, b+G, ...
   if (count <= 0) return;
   load_shot_table(T, g, a.src, a.wavelet, a.rbox, a.n);
+  __syncthreads();  // shot table visible
+  for (int i = threadIdx.x; i < count && i < kUnitTable; i += FWD_THREADS)
+    utab[i] = make_desc(R, g, T, &a, nullptr, IN_BZ_F, blockIdx.x + i * G);
   if (threadIdx.x == 0) {
     for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
     fence_barrier_init();
@@ -159,8 +167,13 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
   // the unit's descriptor is stored before the arrive on its barrier, so a
   // thread that has waited on the barrier sees it
   auto issue = [&](int k) {
-    const UnitDesc d = make_desc(R, g, T, &a, nullptr, IN_BZ_F, blockIdx.x + k * G);
-    desc[k % D] = d;
+    UnitDesc d;
+    if (k < kUnitTable) {
+      d = utab[k];
+    } else {
+      d = make_desc(R, g, T, &a, nullptr, IN_BZ_F, blockIdx.x + k * G);
+      desc[k % D] = d;
+    }
     FwdStage& sg = stg[k % D];
     uint64_t* b = &bar[k % D];
     mbar_arrive_expect_tx(b, kFwdBytes);
@@ -177,7 +190,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
     if (k == count - 1) grid_dep_trigger();  // the next kernel may start
     const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
     if (__syncthreads_or(!got)) break;
-    const UnitDesc d = desc[k % D];
+    const UnitDesc d = k < kUnitTable ? utab[k] : desc[k % D];
     const FwdStage& sg = stg[k % D];
     const long long so = (long long)d.s * g.fstride;
     const int gx = d.x0 + lx;
@@ -248,6 +261,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ ShotTable T;
   __shared__ UnitDesc desc[BWD_STAGES];
+  __shared__ UnitDesc utab[kUnitTable];
   constexpr int D = BWD_STAGES;
   static_assert(D >= 2, "the ring prefetch reads a descriptor written two barriers earlier");
   BwdStage* stg = reinterpret_cast<BwdStage*>(smem_raw);
@@ -261,14 +275,22 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
   if (count <= 0) return;
   const bool img = a.do_img != 0, adj = a.do_adj != 0;
   load_shot_table(T, g, a.src, img ? a.wavelet : nullptr, a.rbox, a.n);
+  __syncthreads();  // shot table visible
+  for (int i = threadIdx.x; i < count && i < kUnitTable; i += BWD_THREADS)
+    utab[i] = make_desc(R, g, T, nullptr, &a, IN_BZ_B, blockIdx.x + i * G);
   if (threadIdx.x == 0) {
     for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
     fence_barrier_init();
   }
   __syncthreads();
   auto issue = [&](int k) {
-    const UnitDesc d = make_desc(R, g, T, nullptr, &a, IN_BZ_B, blockIdx.x + k * G);
-    desc[k % D] = d;
+    UnitDesc d;
+    if (k < kUnitTable) {
+      d = utab[k];
+    } else {
+      d = make_desc(R, g, T, nullptr, &a, IN_BZ_B, blockIdx.x + k * G);
+      desc[k % D] = d;
+    }
     BwdStage& sg = stg[k % D];
     uint64_t* b = &bar[k % D];
     const bool imgt = d.flags & U_IMG;
@@ -291,7 +313,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
   int k = 0;
   for (; k < count; ++k) {
     if (k == count - 1) grid_dep_trigger();  // the next kernel may start
-    const UnitDesc d = desc[k % D];
+    const UnitDesc d = k < kUnitTable ? utab[k] : desc[k % D];
     const bool imgt = d.flags & U_IMG, needu1 = d.flags & U_U1;
     const int gx = d.x0 + lx;
     // saved ring values of u^{n-1} of this thread's cells, fetched before the
