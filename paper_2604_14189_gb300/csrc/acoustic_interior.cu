@@ -20,9 +20,10 @@ namespace sweep {
 namespace {
 
 constexpr int FWD_THREADS = 256;
-constexpr int BWD_THREADS = 256;
+constexpr int BWD_ROLE_WARPS = 8;  // backward: 8 adjoint + 8 imaging warps
+constexpr int BWD_THREADS = 64 * BWD_ROLE_WARPS;
 constexpr int RPW_F = IN_BZ_F / (FWD_THREADS / 32);  // rows per warp, forward
-constexpr int RPW_B = IN_BZ_B / (BWD_THREADS / 32);  // rows per warp, backward
+constexpr int RPW_B = IN_BZ_B / BWD_ROLE_WARPS;      // rows per warp, backward
 constexpr int HF_F = IN_HW * (IN_BZ_F + 8);          // floats, forward halo tile
 constexpr int CF_F = IN_BX * IN_BZ_F;                // floats, forward centre tile
 constexpr int HF_B = IN_HW * (IN_BZ_B + 8);
@@ -309,7 +310,10 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
     for (int k = 0; k < D && k < count; ++k) issue(k);
   __syncthreads();  // first descriptors visible before the ring prefetch below
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int lx = 4 * lane, r0 = warp * RPW_B;
+  // warps 0..7: adjoint update of mu; warps 8..15: imaging and the
+  // reconstruction of u.  Each owns RPW_B rows of the tile.
+  const bool adj_warp = warp < BWD_ROLE_WARPS;
+  const int lx = 4 * lane, r0 = (warp % BWD_ROLE_WARPS) * RPW_B;
   int k = 0;
   for (; k < count; ++k) {
     if (k == count - 1) grid_dep_trigger();  // the next kernel may start
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
     // wait so that their latency overlaps the stage's transfer
     float rv[RPW_B][4];
     unsigned rmask = 0;
-    if (d.flags & U_RING) {
+    if (!adj_warp && (d.flags & U_RING)) {
 #pragma unroll
       for (int q = 0; q < RPW_B; ++q) {
         const int gz = d.z0 + r0 + q;
@@ -336,103 +340,119 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
     if (__syncthreads_or(!got)) break;
     const BwdStage& sg = stg[k % D];
     const long long so = (long long)d.s * g.fstride;
-    // interior columns among this lane's 4 cells
-    unsigned cmask = 0;
+    if (adj_warp) {
+      if (adj) {
+        // mu^n = 2 mu^{n+1} - mu^{n+2} + K Lap mu^{n+1}
+        float wm[9][4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-      if (gx + c >= g.P && gx + c < g.P + g.nx) cmask |= 1u << c;
-    float wm[9][4], wu[9][4];
+        for (int j = 0; j < 8; ++j) f4a(lds4(sg.ma, IN_HW, r0 + j, lx + 4), wm[j]);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      f4a(lds4(sg.ma, IN_HW, r0 + j, lx + 4), wm[j]);
-      if (imgt) f4a(lds4(sg.ua, IN_HW, r0 + j, lx + 4), wu[j]);
-    }
+        for (int q = 0; q < RPW_B; ++q) {
+          f4a(lds4(sg.ma, IN_HW, r0 + q + 8, lx + 4), wm[8]);
+          const int gz = d.z0 + r0 + q;
+          if (gz < R.z1 && gx < R.x1) {
+            float e[12], m2[4], kk[4], out[4];
+            f4a(lds4(sg.ma, IN_HW, r0 + q + 4, lx), e);
+            f4a(lds4(sg.ma, IN_HW, r0 + q + 4, lx + 8), e + 8);
 #pragma unroll
-    for (int q = 0; q < RPW_B; ++q) {
-      f4a(lds4(sg.ma, IN_HW, r0 + q + 8, lx + 4), wm[8]);
-      if (imgt) f4a(lds4(sg.ua, IN_HW, r0 + q + 8, lx + 4), wu[8]);
-      const int gz = d.z0 + r0 + q;
-      if (gz < R.z1 && gx < R.x1) {
-        const long long ci = so + (long long)gz * g.NXp + gx;
-        float kk[4];
-        f4a(lds4(sg.k, IN_BX, r0 + q, lx), kk);
-        if (adj) {
-          float e[12], m2[4], out[4];
-          f4a(lds4(sg.ma, IN_HW, r0 + q + 4, lx), e);
-          f4a(lds4(sg.ma, IN_HW, r0 + q + 4, lx + 8), e + 8);
+            for (int c = 0; c < 4; ++c) e[4 + c] = wm[4][c];
+            f4a(lds4(sg.mb, IN_BX, r0 + q, lx), m2);
+            f4a(lds4(sg.k, IN_BX, r0 + q, lx), kk);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) e[4 + c] = wm[4][c];
-          f4a(lds4(sg.mb, IN_BX, r0 + q, lx), m2);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float lap =
-                d2(e[c], e[c + 1], e[c + 2], e[c + 3], e[c + 4], e[c + 5], e[c + 6], e[c + 7],
-                   e[c + 8]) +
-                d2(wm[0][c], wm[1][c], wm[2][c], wm[3][c], wm[4][c], wm[5][c], wm[6][c],
-                   wm[7][c], wm[8][c]);
-            out[c] = 2.f * wm[4][c] - m2[c] + kk[c] * lap;
+            for (int c = 0; c < 4; ++c) {
+              const float lap =
+                  d2(e[c], e[c + 1], e[c + 2], e[c + 3], e[c + 4], e[c + 5], e[c + 6],
+                     e[c + 7], e[c + 8]) +
+                  d2(wm[0][c], wm[1][c], wm[2][c], wm[3][c], wm[4][c], wm[5][c], wm[6][c],
+                     wm[7][c], wm[8][c]);
+              out[c] = 2.f * wm[4][c] - m2[c] + kk[c] * lap;
+            }
+            *reinterpret_cast<float4*>(a.mB + so + (long long)gz * g.NXp + gx) =
+                make_float4(out[0], out[1], out[2], out[3]);
           }
-          *reinterpret_cast<float4*>(a.mB + ci) = make_float4(out[0], out[1], out[2], out[3]);
-        }
-        // interior cells of this lane in this row
-        const unsigned im = (imgt && gz >= g.P && gz < g.P + g.nz) ? cmask : 0u;
-        float lap[4] = {0.f, 0.f, 0.f, 0.f};
-        if (im) {
-          // imaging: graw += mu^{n+1} (Lap u^n + f^n delta_s)
-          float e[12];
-          f4a(lds4(sg.ua, IN_HW, r0 + q + 4, lx), e);
-          f4a(lds4(sg.ua, IN_HW, r0 + q + 4, lx + 8), e + 8);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) e[4 + c] = wu[4][c];
+          for (int j = 0; j < 8; ++j)
 #pragma unroll
-          for (int c = 0; c < 4; ++c)
-            lap[c] = d2(e[c], e[c + 1], e[c + 2], e[c + 3], e[c + 4], e[c + 5], e[c + 6],
-                        e[c + 7], e[c + 8]) +
-                     d2(wu[0][c], wu[1][c], wu[2][c], wu[3][c], wu[4][c], wu[5][c], wu[6][c],
-                        wu[7][c], wu[8][c]);
-          if ((d.flags & U_SRC) && gz == d.sz) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-              if (gx + c == d.sx) lap[c] += d.fn;
-          }
-          float gvv[4];
-          f4a(lds4(sg.gr, IN_BX, r0 + q, lx), gvv);
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if ((im >> c) & 1u) gvv[c] += wm[4][c] * lap[c];
-          *reinterpret_cast<float4*>(a.graw + ci) = make_float4(gvv[0], gvv[1], gvv[2], gvv[3]);
-          if (a.illum) {
-            float iv[4];
-            f4a(*reinterpret_cast<const float4*>(a.illum + ci), iv);
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-              if ((im >> c) & 1u) iv[c] += wu[4][c] * wu[4][c];
-            *reinterpret_cast<float4*>(a.illum + ci) = make_float4(iv[0], iv[1], iv[2], iv[3]);
-          }
-        }
-        const unsigned rm = (rmask >> (4 * q)) & 0xFu;
-        if (needu1 && (im | rm)) {
-          // u^{n-1}: reconstructed on interior cells, restored on the ring;
-          // cells beyond the ring are never read again and keep u^{n+1}
-          float u1[4], out[4];
-          f4a(lds4(sg.ub, IN_BX, r0 + q, lx), u1);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            if ((im >> c) & 1u)
-              out[c] = 2.f * wu[4][c] - u1[c] + kk[c] * lap[c];
-            else
-              out[c] = ((rm >> c) & 1u) ? rv[q][c] : u1[c];
-          }
-          *reinterpret_cast<float4*>(a.uB + ci) = make_float4(out[0], out[1], out[2], out[3]);
+            for (int c = 0; c < 4; ++c) wm[j][c] = wm[j + 1][c];
         }
       }
+    } else if (imgt || rmask) {
+      // interior columns among this lane's 4 cells
+      unsigned cmask = 0;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int c = 0; c < 4; ++c)
+        if (gx + c >= g.P && gx + c < g.P + g.nx) cmask |= 1u << c;
+      float wu[9][4];
+      if (imgt) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          wm[j][c] = wm[j + 1][c];
-          wu[j][c] = wu[j + 1][c];
+        for (int j = 0; j < 8; ++j) f4a(lds4(sg.ua, IN_HW, r0 + j, lx + 4), wu[j]);
+      }
+#pragma unroll
+      for (int q = 0; q < RPW_B; ++q) {
+        if (imgt) f4a(lds4(sg.ua, IN_HW, r0 + q + 8, lx + 4), wu[8]);
+        const int gz = d.z0 + r0 + q;
+        if (gz < R.z1 && gx < R.x1) {
+          const long long ci = so + (long long)gz * g.NXp + gx;
+          // interior cells of this lane in this row
+          const unsigned im = (imgt && gz >= g.P && gz < g.P + g.nz) ? cmask : 0u;
+          float lap[4] = {0.f, 0.f, 0.f, 0.f};
+          if (im) {
+            // imaging: graw += mu^{n+1} (Lap u^n + f^n delta_s)
+            float e[12], m1[4], gvv[4];
+            f4a(lds4(sg.ua, IN_HW, r0 + q + 4, lx), e);
+            f4a(lds4(sg.ua, IN_HW, r0 + q + 4, lx + 8), e + 8);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) e[4 + c] = wu[4][c];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              lap[c] = d2(e[c], e[c + 1], e[c + 2], e[c + 3], e[c + 4], e[c + 5], e[c + 6],
+                          e[c + 7], e[c + 8]) +
+                       d2(wu[0][c], wu[1][c], wu[2][c], wu[3][c], wu[4][c], wu[5][c],
+                          wu[6][c], wu[7][c], wu[8][c]);
+            if ((d.flags & U_SRC) && gz == d.sz) {
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                if (gx + c == d.sx) lap[c] += d.fn;
+            }
+            f4a(lds4(sg.ma, IN_HW, r0 + q + 4, lx + 4), m1);
+            f4a(lds4(sg.gr, IN_BX, r0 + q, lx), gvv);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if ((im >> c) & 1u) gvv[c] += m1[c] * lap[c];
+            *reinterpret_cast<float4*>(a.graw + ci) =
+                make_float4(gvv[0], gvv[1], gvv[2], gvv[3]);
+            if (a.illum) {
+              float iv[4];
+              f4a(*reinterpret_cast<const float4*>(a.illum + ci), iv);
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                if ((im >> c) & 1u) iv[c] += wu[4][c] * wu[4][c];
+              *reinterpret_cast<float4*>(a.illum + ci) =
+                  make_float4(iv[0], iv[1], iv[2], iv[3]);
+            }
+          }
+          const unsigned rm = (rmask >> (4 * q)) & 0xFu;
+          if (needu1 && (im | rm)) {
+            // u^{n-1}: reconstructed on interior cells, restored on the
+            // ring; cells beyond the ring are never read again and keep
+            // u^{n+1}
+            float u1[4], kk[4], out[4];
+            f4a(lds4(sg.ub, IN_BX, r0 + q, lx), u1);
+            f4a(lds4(sg.k, IN_BX, r0 + q, lx), kk);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              if ((im >> c) & 1u)
+                out[c] = 2.f * wu[4][c] - u1[c] + kk[c] * lap[c];
+              else
+                out[c] = ((rm >> c) & 1u) ? rv[q][c] : u1[c];
+            }
+            *reinterpret_cast<float4*>(a.uB + ci) = make_float4(out[0], out[1], out[2], out[3]);
+          }
         }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) wu[j][c] = wu[j + 1][c];
       }
     }
     // adjoint source gather: f-bar^n = mu^{n+1}(s)
