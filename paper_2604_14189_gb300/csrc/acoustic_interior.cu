@@ -95,7 +95,6 @@ enum : int {
   U_RING = 2,  // meets the saved ring: restore from the forward save (backward)
   U_U1 = 4,    // needs u^{n+1} (reconstruction or restore, backward)
   U_SRC = 8,   // holds the source cell
-  U_REC = 16,  // meets the receiver box
 };
 struct UnitDesc {
   int s, z0, x0, flags;
@@ -130,7 +129,6 @@ __device__ __forceinline__ UnitDesc make_desc(const Region& R, const Geom& g, co
   if (si.sz >= p.z0 && si.sz < p.z0 + bz && si.sx >= p.x0 && si.sx < p.x0 + IN_BX &&
       in_region(R, si.sz, si.sx))
     f |= U_SRC;
-  if (tile_meets(si.box, p.z0, bz, p.x0, IN_BX)) f |= U_REC;
   if (ab) {
     const BwdFlags b = bwd_flags(g, img, ab->do_rec != 0, ab->save != nullptr, p);
     f |= (b.imgt ? U_IMG : 0) | (b.ringt ? U_RING : 0) | (b.needu1 ? U_U1 : 0);
@@ -236,17 +234,6 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
     if (threadIdx.x == 0 && k + D < count) {
       fence_proxy_async_smem();
       issue(k + D);
-    }
-    // receivers of this shot inside this tile (read back this CTA's stores)
-    if (a.data && (d.flags & U_REC)) {
-      for (int r = threadIdx.x; r < g.nrec; r += FWD_THREADS) {
-        const int32_t* q = a.rec + 2 * ((long long)d.s * g.nrec + r);
-        const int rz = q[0] + g.P, rx = q[1] + g.P;
-        if (rz >= d.z0 && rz < d.z0 + IN_BZ_F && rx >= d.x0 && rx < d.x0 + IN_BX &&
-            in_region(R, rz, rx))
-          a.data[((long long)d.s * g.nrec + r) * g.nt + a.n] =
-              a.un[so + (long long)rz * g.NXp + rx];
-      }
     }
   }
   if (k < count && threadIdx.x == 0) {
@@ -463,19 +450,6 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
     if (threadIdx.x == 0 && k + D < count) {
       fence_proxy_async_smem();
       issue(k + D);
-    }
-    // residual injection mu^n(r) += K(r) r^{n-1} for receivers in this tile
-    if (adj && a.n >= 1 && (d.flags & U_REC)) {
-      for (int r = threadIdx.x; r < g.nrec; r += BWD_THREADS) {
-        const int32_t* q = a.rec + 2 * ((long long)d.s * g.nrec + r);
-        const int rz = q[0] + g.P, rx = q[1] + g.P;
-        if (rz >= d.z0 && rz < d.z0 + IN_BZ_B && rx >= d.x0 && rx < d.x0 + IN_BX &&
-            in_region(R, rz, rx)) {
-          const float rv = a.res[((long long)d.s * g.nrec + r) * g.nt + (a.n - 1)];
-          atomicAdd(a.mB + so + (long long)rz * g.NXp + rx,
-                    a.K[(long long)rz * g.NXp + rx] * rv);
-        }
-      }
     }
   }
   if (k < count && threadIdx.x == 0) {

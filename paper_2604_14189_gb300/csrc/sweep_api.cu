@@ -261,7 +261,8 @@ int region_units(const Region& R, int nshot, int bz, int* ntx) {
 }
 
 // Forward time loop of the acoustic engine: per step the plain-stencil
-// kernel over the whole padded grid, then the z and x CPML corrections.  On
+// kernel over the whole padded grid, then one kernel adding both axes' CPML
+// terms, recording the receivers and saving the ring of u^n.  On
 // return the workspace holds u^{nt} in u[nt % 2] and u^{nt-1} in
 // u[(nt + 1) % 2].
 int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
@@ -282,21 +283,21 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
   if (!map2(&in.tK, g, at<float>(ws, L.K), IN_BX, IN_BZ_F)) return SWEEP_ECUDA;
   in.wavelet = wavelet;
   in.src = src;
-  in.rec = rec;
   in.rbox = at<int32_t>(ws, L.rbox);
-  in.data = data;
   in.status = status;
 
-  AcCorrArgs cz{}, cx{};
-  cz.g = cx.g = g;
-  cz.K = cx.K = at<float>(ws, L.K);
-  cz.ax = cx.ax = at<float>(ws, L.ax);
-  cz.bx = cx.bx = at<float>(ws, L.bx);
-  cz.az = cx.az = at<float>(ws, L.az);
-  cz.bz = cx.bz = at<float>(ws, L.bz);
-  cz.zeta = at<float>(ws, L.zez);
-  cx.zeta = at<float>(ws, L.zex);
-  cz.status = cx.status = status;
+  AcFixArgs fx{};
+  fx.g = g;
+  fx.K = at<float>(ws, L.K);
+  fx.ax = at<float>(ws, L.ax);
+  fx.bx = at<float>(ws, L.bx);
+  fx.az = at<float>(ws, L.az);
+  fx.bz = at<float>(ws, L.bz);
+  fx.zzin = fx.zzout = at<float>(ws, L.zez);
+  fx.zxin = fx.zxout = at<float>(ws, L.zex);
+  fx.rec = rec;
+  fx.data = data;
+  fx.status = status;
   for (int n = 0; n < g.nt; ++n) {
     const int A = n & 1, B = (n + 1) & 1;
     void* tok = profile_begin(SWEEP_K_AC_FWD, st);
@@ -305,14 +306,15 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
     in.tup = tu_c[B];
     in.un = at<float>(ws, L.u[B]);
     launch_ac_in_fwd(in, st);
-    cz.u = cx.u = at<float>(ws, L.u[A]);
-    cz.un = cx.un = at<float>(ws, L.u[B]);
-    cz.pin = at<float>(ws, L.psz[A]);
-    cz.pout = at<float>(ws, L.psz[B]);
-    cx.pin = at<float>(ws, L.psx[A]);
-    cx.pout = at<float>(ws, L.psx[B]);
-    cz.save = cx.save = save ? save + (size_t)(n + 1) * g.nshot * g.nring : nullptr;
-    launch_ac_corr_fwd(cz, cx, st);
+    fx.n = n;
+    fx.u = at<float>(ws, L.u[A]);
+    fx.un = at<float>(ws, L.u[B]);
+    fx.pzin = at<float>(ws, L.psz[A]);
+    fx.pzout = at<float>(ws, L.psz[B]);
+    fx.pxin = at<float>(ws, L.psx[A]);
+    fx.pxout = at<float>(ws, L.psx[B]);
+    fx.save = save ? save + (size_t)n * g.nshot * g.nring : nullptr;  // ring of u^n
+    launch_ac_fix_fwd(fx, st);
     profile_end(tok, st);
   }
   return SWEEP_OK;
@@ -321,7 +323,8 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
 // Backward loop: adjoint propagation from the residual `res`; optionally the
 // imaging condition with wavefield reconstruction (gradient) and/or the
 // adjoint source gather (wgrad).  Per step the plain kernel over the whole
-// grid, then the z and x CPML corrections of mu^n.
+// grid, then one kernel adding both axes' CPML terms of mu^n and the
+// residual injection.
 int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
                            const float* wavelet, const int32_t* src, const int32_t* rec,
                            const float* res, float* wgrad, bool imaging, bool illum,
@@ -350,23 +353,22 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
     return SWEEP_ECUDA;
   in.graw = imaging ? at<float>(ws, L.graw) : nullptr;
   in.illum = (imaging && illum) ? at<float>(ws, L.iraw) : nullptr;
-  in.K = at<float>(ws, L.K);
   in.wavelet = wavelet;
   in.src = src;
-  in.rec = rec;
   in.rbox = at<int32_t>(ws, L.rbox);
-  in.res = res;
   in.wgrad = wgrad;
   in.status = status;
 
-  AcCorrArgs cz{}, cx{};
-  cz.g = cx.g = g;
-  cz.K = cx.K = at<float>(ws, L.K);
-  cz.ax = cx.ax = at<float>(ws, L.ax);
-  cz.bx = cx.bx = at<float>(ws, L.bx);
-  cz.az = cx.az = at<float>(ws, L.az);
-  cz.bz = cx.bz = at<float>(ws, L.bz);
-  cz.status = cx.status = status;
+  AcFixArgs fx{};
+  fx.g = g;
+  fx.K = at<float>(ws, L.K);
+  fx.ax = at<float>(ws, L.ax);
+  fx.bx = at<float>(ws, L.bx);
+  fx.az = at<float>(ws, L.az);
+  fx.bz = at<float>(ws, L.bz);
+  fx.rec = rec;
+  fx.res = g.nrec > 0 ? res : nullptr;
+  fx.status = status;
   for (int n = g.nt; n >= 0; --n) {
     const int A = n & 1, B = (n + 1) & 1;  // u^n in u[A]; mu^{n+1} in m[B]
     const int do_adj = n >= 1;
@@ -389,17 +391,19 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
     in.save = (save && n >= 1) ? save + (size_t)(n - 1) * g.nshot * g.nring : nullptr;
     launch_ac_in_bwd(in, st);
     if (do_adj) {
-      cz.u = cx.u = at<float>(ws, L.m[B]);
-      cz.un = cx.un = at<float>(ws, L.m[A]);
-      cz.pin = at<float>(ws, L.pbz[A]);
-      cz.pout = at<float>(ws, L.pbz[B]);
-      cz.zeta = at<float>(ws, L.zbz[A]);
-      cz.zout = at<float>(ws, L.zbz[B]);
-      cx.pin = at<float>(ws, L.pbx[A]);
-      cx.pout = at<float>(ws, L.pbx[B]);
-      cx.zeta = at<float>(ws, L.zbx[A]);
-      cx.zout = at<float>(ws, L.zbx[B]);
-      launch_ac_corr_bwd(cz, cx, st);
+      // CPML terms of mu^n and the residual injection mu^n(r) += K r^{n-1}
+      fx.n = n;
+      fx.u = at<float>(ws, L.m[B]);
+      fx.un = at<float>(ws, L.m[A]);
+      fx.pzin = at<float>(ws, L.pbz[A]);
+      fx.pzout = at<float>(ws, L.pbz[B]);
+      fx.zzin = at<float>(ws, L.zbz[A]);
+      fx.zzout = at<float>(ws, L.zbz[B]);
+      fx.pxin = at<float>(ws, L.pbx[A]);
+      fx.pxout = at<float>(ws, L.pbx[B]);
+      fx.zxin = at<float>(ws, L.zbx[A]);
+      fx.zxout = at<float>(ws, L.zbx[B]);
+      launch_ac_fix_bwd(fx, st);
     }
     profile_end(tok, st);
   }

@@ -49,9 +49,7 @@ struct AcInFwdArgs {
   float* un;         // out u^{n+1} (the u^{n-1} buffer)
   const float* wavelet;
   const int32_t* src;
-  const int32_t* rec;
   const int32_t* rbox;  // [S][4] receiver bounding box (z0, z1, x0, x1) padded
-  float* data;          // [S][R][nt] or null
   int* status;
   int n;
   int units, ntx;       // (tile, shot) units; tiles along x
@@ -70,12 +68,9 @@ struct AcInBwdArgs {
   float* graw;       // [S][NZ][NXp]
   float* illum;      // [S][NZ][NXp] or null
   const float* save; // ring slot of u^{n-1} [S][nring] or null
-  const float* K;
   const float* wavelet;
   const int32_t* src;
-  const int32_t* rec;
   const int32_t* rbox;
-  const float* res;  // [S][R][nt]
   float* wgrad;      // [S][nt] or null
   int* status;
   int n;
@@ -83,29 +78,49 @@ struct AcInBwdArgs {
   int units, ntx;
 };
 
-// CPML correction kernels (acoustic_cpml.cu), one axis per argument set.
-// Forward: u = u^n, un = u^{n+1} (updated), pin/pout = psi^{n-1}/psi^n,
-// zeta updated in place, save = ring slot of u^{n+1} or null.
-// Backward: u = mu^{n+1}, un = mu^n (updated), pin/pout = psibar^n/^{n-1},
-// zeta/zout = zetabar^n/^{n-1}.
-struct AcCorrArgs {
+// Second kernel of an acoustic time step (acoustic_cpml.cu): the CPML terms
+// of both axes and the receiver work, all added to the step's output field
+// with vector reductions (red.global.add), so the parts run concurrently.
+// Forward: u = u^n, un = u^{n+1}, p*in/p*out = psi^{n-1}/psi^n, zeta updated
+// in place (z*out == z*in), data = recorded traces (d[n] = u^{n+1}(r)),
+// save = ring slot that receives the ring cells of u^n (gradient mode).
+// Backward: u = mu^{n+1}, un = mu^n, p*in/p*out = psibar^n/^{n-1},
+// z*in/z*out = zetabar^n/^{n-1}, res = residual injected at the receivers
+// (mu^n(r) += K(r) res[n-1]).
+struct XBands {  // 4-cell column groups: left [0, gl), right [gr0, ceil(NX/4))
+  int gl, gr0, ngr;
+};
+struct AcFixArgs {
   Geom g;
   const float* u;
   float* un;
   const float* K;
-  const float* pin;
-  float* pout;
-  float* zeta;
-  float* zout;
+  const float* pzin;
+  float* pzout;
+  float* zzin;
+  float* zzout;
+  const float* pxin;
+  float* pxout;
+  float* zxin;
+  float* zxout;
   const float* ax;
   const float* bx;
   const float* az;
   const float* bz;
+  const int32_t* rec;
+  float* data;
+  const float* res;
   float* save;
   const int* status;
+  int n;
+  // work split, set by the launcher: blocks of the z, x, receiver and ring
+  // parts
+  int nbz, nbx, nbr, nbs;
+  int ncp, nchz;  // column pairs; row chunks per shot (z part)
+  XBands xb;
 };
-void launch_ac_corr_fwd(const AcCorrArgs& z, const AcCorrArgs& x, cudaStream_t st);
-void launch_ac_corr_bwd(const AcCorrArgs& z, const AcCorrArgs& x, cudaStream_t st);
+void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st);
+void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st);
 
 // ------------------------------------------------------------------- elastic
 // Coefficients on the padded grid [NZ][NXp], pre-scaled by dt / dx:
