@@ -20,6 +20,7 @@
 //   strip cells: psibar^{n-1} = a psibar^n - D1 (m (mu^{n+1} + C)),
 //                zetabar^{n-1} = a (mu^{n+1} + zetabar^n)
 //   receivers: mu^n(r) += K(r) res^{n-1}(r)
+//   ring restore: u^{n-1} on the ring from the forward save (gradient mode)
 //
 // The profiles a, b are zero off the border, and so are psi, zeta and their
 // adjoints (never written there), which removes most masks.
@@ -208,6 +209,25 @@ __device__ __forceinline__ void fwd_rec(const AcFixArgs& a, long long t) {
   a.data[i * g.nt + a.n] = a.un[(size_t)s * g.fstride + (size_t)rz * g.NXp + rx];
 }
 
+// Interior coordinates (zi, xi) of ring cell ri: the inverse of ring_index
+// (rows above, rows below, then the left and right side columns).
+__device__ __forceinline__ void ring_cell(const Geom& g, int ri, int& zi, int& xi) {
+  const int w = g.ringw, W = g.nx + 2 * w;
+  if (ri < 2 * w * W) {
+    const int r = ri < w * W ? ri : ri - w * W;
+    zi = ri < w * W ? r / W - w : g.nz + r / W;
+    xi = r % W - w;
+  } else if (ri < 2 * w * W + g.nz * w) {
+    const int r = ri - 2 * w * W;
+    zi = r / w;
+    xi = r % w - w;
+  } else {
+    const int r = ri - 2 * w * W - g.nz * w;
+    zi = r / w;
+    xi = g.nx + r % w;
+  }
+}
+
 // boundary save: ring cells 4q .. 4q+3 of u^n (final: the previous step's
 // kernels have completed) into the ring slot, in ring order
 __device__ __forceinline__ void fwd_ring(const AcFixArgs& a, long long t) {
@@ -215,27 +235,14 @@ __device__ __forceinline__ void fwd_ring(const AcFixArgs& a, long long t) {
   const int nq = (g.nring + 3) / 4;
   const int q = (int)(t % nq), s = (int)(t / nq);
   if (s >= g.nshot) return;
-  const int w = g.ringw, W = g.nx + 2 * w;
   const float* u = a.u + (size_t)s * g.fstride;
   float* sv = a.save + (size_t)s * g.nring;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int ri = 4 * q + j;
     if (ri >= g.nring) break;
-    int zi, xi;  // interior coordinates of ring cell ri (inverse of ring_index)
-    if (ri < 2 * w * W) {
-      const int r = ri < w * W ? ri : ri - w * W;
-      zi = ri < w * W ? r / W - w : g.nz + r / W;
-      xi = r % W - w;
-    } else if (ri < 2 * w * W + g.nz * w) {
-      const int r = ri - 2 * w * W;
-      zi = r / w;
-      xi = r % w - w;
-    } else {
-      const int r = ri - 2 * w * W - g.nz * w;
-      zi = r / w;
-      xi = g.nx + r % w;
-    }
+    int zi, xi;
+    ring_cell(g, ri, zi, xi);
     sv[ri] = u[(size_t)(zi + g.P) * g.NXp + (xi + g.P)];
   }
 }
@@ -367,6 +374,25 @@ __device__ __forceinline__ void bwd_rec(const AcFixArgs& a, long long t) {
   atomicAdd(a.un + (size_t)s * g.fstride + c, a.K[c] * a.res[i * g.nt + (a.n - 1)]);
 }
 
+// ring restore: u^{n-1} on the ring cells 4q .. 4q+3 from the forward save
+// (the stencil kernel reconstructs the interior and leaves the ring alone)
+__device__ __forceinline__ void bwd_ring(const AcFixArgs& a, long long t) {
+  const Geom& g = a.g;
+  const int nq = (g.nring + 3) / 4;
+  const int q = (int)(t % nq), s = (int)(t / nq);
+  if (s >= g.nshot) return;
+  float* u = a.uring + (size_t)s * g.fstride;
+  const float* sv = a.save + (size_t)s * g.nring;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int ri = 4 * q + j;
+    if (ri >= g.nring) break;
+    int zi, xi;
+    ring_cell(g, ri, zi, xi);
+    u[(size_t)(zi + g.P) * g.NXp + (xi + g.P)] = sv[ri];
+  }
+}
+
 __global__ void __launch_bounds__(FT) ac_fix_bwd_kernel(const AcFixArgs a) {
   grid_dep_wait();
   grid_dep_trigger();
@@ -382,7 +408,12 @@ __global__ void __launch_bounds__(FT) ac_fix_bwd_kernel(const AcFixArgs a) {
     return;
   }
   b -= a.nbx;
-  bwd_rec(a, (long long)b * FT + threadIdx.x);
+  if (b < a.nbr) {
+    bwd_rec(a, (long long)b * FT + threadIdx.x);
+    return;
+  }
+  b -= a.nbr;
+  bwd_ring(a, (long long)b * FT + threadIdx.x);
 }
 
 int blocks(long long threads) { return (int)((threads + FT - 1) / FT); }
@@ -417,9 +448,13 @@ void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st) {
   a.nbz = g.P > 0 ? blocks((long long)a.ncp * a.nchz * g.nshot) : 0;
   a.nbx = g.P > 0 ? blocks((long long)g.NZ * a.xb.ngr * g.nshot) : 0;
   a.nbr = (a.res && g.nrec > 0 && a.n >= 1) ? blocks((long long)g.nrec * g.nshot) : 0;
-  if (a.nbz + a.nbx + a.nbr == 0) return;
+  a.nbs = (a.save && a.uring && g.nring > 0)
+              ? blocks((long long)((g.nring + 3) / 4) * g.nshot)
+              : 0;
+  const int nb = a.nbz + a.nbx + a.nbr + a.nbs;
+  if (nb == 0) return;
   void* tok = profile_begin(SWEEP_K_AC_BWD_FR, st);
-  launch_dependent(ac_fix_bwd_kernel, dim3(a.nbz + a.nbx + a.nbr), dim3(FT), 0, st, a);
+  launch_dependent(ac_fix_bwd_kernel, dim3(nb), dim3(FT), 0, st, a);
   profile_end(tok, st);
   note_launches(1);
 }

@@ -58,23 +58,17 @@ struct UnitPos {
   int s, z0, x0;
 };
 
-// What a backward unit touches: interior cells (imaging, reconstruction) and
-// ring cells (restore from the forward save).
+// What a backward unit touches: interior cells (imaging, reconstruction).
 struct BwdFlags {
-  bool imgt, ringt, needu1;
+  bool imgt, needu1;
 };
-__device__ __forceinline__ BwdFlags bwd_flags(const Geom& g, bool img, bool rec, bool has_save,
+__device__ __forceinline__ BwdFlags bwd_flags(const Geom& g, bool img, bool rec,
                                               const UnitPos& p) {
   const int z1 = p.z0 + IN_BZ_B, x1 = p.x0 + IN_BX;
-  const int w = g.ringw;
   const bool touch_int = z1 > g.P && p.z0 < g.P + g.nz && x1 > g.P && p.x0 < g.P + g.nx;
-  const bool inside = p.z0 >= g.P && z1 <= g.P + g.nz && p.x0 >= g.P && x1 <= g.P + g.nx;
-  const bool touch_ring = w > 0 && !inside && z1 > g.P - w && p.z0 < g.P + g.nz + w &&
-                          x1 > g.P - w && p.x0 < g.P + g.nx + w;
   BwdFlags f;
   f.imgt = img && touch_int;
-  f.ringt = rec && has_save && touch_ring;
-  f.needu1 = rec && (f.imgt || f.ringt);
+  f.needu1 = rec && f.imgt;
   return f;
 }
 
@@ -92,8 +86,7 @@ __device__ __forceinline__ UnitPos unit_pos(const Region& R, int S, int ntx, int
 // transfers and read by every thread from shared memory.
 enum : int {
   U_IMG = 1,   // meets the interior: imaging (backward)
-  U_RING = 2,  // meets the saved ring: restore from the forward save (backward)
-  U_U1 = 4,    // needs u^{n+1} (reconstruction or restore, backward)
+  U_U1 = 4,    // needs u^{n+1} (reconstruction, backward)
   U_SRC = 8,   // holds the source cell
 };
 struct UnitDesc {
@@ -130,8 +123,8 @@ __device__ __forceinline__ UnitDesc make_desc(const Region& R, const Geom& g, co
       in_region(R, si.sz, si.sx))
     f |= U_SRC;
   if (ab) {
-    const BwdFlags b = bwd_flags(g, img, ab->do_rec != 0, ab->save != nullptr, p);
-    f |= (b.imgt ? U_IMG : 0) | (b.ringt ? U_RING : 0) | (b.needu1 ? U_U1 : 0);
+    const BwdFlags b = bwd_flags(g, img, ab->do_rec != 0, p);
+    f |= (b.imgt ? U_IMG : 0) | (b.needu1 ? U_U1 : 0);
   }
   d.flags = f;
   return d;
@@ -307,22 +300,6 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
     const UnitDesc d = k < kUnitTable ? utab[k] : desc[k % D];
     const bool imgt = d.flags & U_IMG, needu1 = d.flags & U_U1;
     const int gx = d.x0 + lx;
-    // saved ring values of u^{n-1} of this thread's cells, fetched before the
-    // wait so that their latency overlaps the stage's transfer
-    float rv[RPW_B][4];
-    unsigned rmask = 0;
-    if (!adj_warp && (d.flags & U_RING)) {
-#pragma unroll
-      for (int q = 0; q < RPW_B; ++q) {
-        const int gz = d.z0 + r0 + q;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int ri = (gz < R.z1 && gx + c < R.x1) ? ring_index(g, gz, gx + c) : -1;
-          rv[q][c] = ri >= 0 ? a.save[(long long)d.s * g.nring + ri] : 0.f;
-          if (ri >= 0) rmask |= 1u << (4 * q + c);
-        }
-      }
-    }
     const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
     if (__syncthreads_or(!got)) break;
     const BwdStage& sg = stg[k % D];
@@ -363,7 +340,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
             for (int c = 0; c < 4; ++c) wm[j][c] = wm[j + 1][c];
         }
       }
-    } else if (imgt || rmask) {
+    } else if (imgt) {
       // interior columns among this lane's 4 cells
       unsigned cmask = 0;
 #pragma unroll
@@ -418,21 +395,16 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
                   make_float4(iv[0], iv[1], iv[2], iv[3]);
             }
           }
-          const unsigned rm = (rmask >> (4 * q)) & 0xFu;
-          if (needu1 && (im | rm)) {
-            // u^{n-1}: reconstructed on interior cells, restored on the
-            // ring; cells beyond the ring are never read again and keep
-            // u^{n+1}
+          if (needu1 && im) {
+            // u^{n-1} on interior cells; the ring is restored from the
+            // forward save by the step's second kernel, and cells beyond it
+            // are never read again (they keep u^{n+1})
             float u1[4], kk[4], out[4];
             f4a(lds4(sg.ub, IN_BX, r0 + q, lx), u1);
             f4a(lds4(sg.k, IN_BX, r0 + q, lx), kk);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              if ((im >> c) & 1u)
-                out[c] = 2.f * wu[4][c] - u1[c] + kk[c] * lap[c];
-              else
-                out[c] = ((rm >> c) & 1u) ? rv[q][c] : u1[c];
-            }
+            for (int c = 0; c < 4; ++c)
+              out[c] = ((im >> c) & 1u) ? 2.f * wu[4][c] - u1[c] + kk[c] * lap[c] : u1[c];
             *reinterpret_cast<float4*>(a.uB + ci) = make_float4(out[0], out[1], out[2], out[3]);
           }
         }

@@ -324,7 +324,7 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
 // imaging condition with wavefield reconstruction (gradient) and/or the
 // adjoint source gather (wgrad).  Per step the plain kernel over the whole
 // grid, then one kernel adding both axes' CPML terms of mu^n and the
-// residual injection.
+// residual injection, and restoring the ring of u^{n-1}.
 int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
                            const float* wavelet, const int32_t* src, const int32_t* rec,
                            const float* res, float* wgrad, bool imaging, bool illum,
@@ -388,7 +388,6 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
     in.tmB = tm_c[A];
     in.uB = imaging ? at<float>(ws, L.u[B]) : nullptr;
     in.mB = at<float>(ws, L.m[A]);
-    in.save = (save && n >= 1) ? save + (size_t)(n - 1) * g.nshot * g.nring : nullptr;
     launch_ac_in_bwd(in, st);
     if (do_adj) {
       // CPML terms of mu^n and the residual injection mu^n(r) += K r^{n-1}
@@ -403,6 +402,8 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
       fx.pxout = at<float>(ws, L.pbx[B]);
       fx.zxin = at<float>(ws, L.zbx[A]);
       fx.zxout = at<float>(ws, L.zbx[B]);
+      fx.save = do_rec && save ? save + (size_t)(n - 1) * g.nshot * g.nring : nullptr;
+      fx.uring = do_rec ? at<float>(ws, L.u[B]) : nullptr;  // u^{n-1}
       launch_ac_fix_bwd(fx, st);
     }
     profile_end(tok, st);

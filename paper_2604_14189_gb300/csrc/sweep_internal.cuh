@@ -67,7 +67,6 @@ struct AcInBwdArgs {
   float* mB;         // out mu^n
   float* graw;       // [S][NZ][NXp]
   float* illum;      // [S][NZ][NXp] or null
-  const float* save; // ring slot of u^{n-1} [S][nring] or null
   const float* wavelet;
   const int32_t* src;
   const int32_t* rbox;
@@ -86,7 +85,7 @@ struct AcInBwdArgs {
 // save = ring slot that receives the ring cells of u^n (gradient mode).
 // Backward: u = mu^{n+1}, un = mu^n, p*in/p*out = psibar^n/^{n-1},
 // z*in/z*out = zetabar^n/^{n-1}, res = residual injected at the receivers
-// (mu^n(r) += K(r) res[n-1]).
+// (mu^n(r) += K(r) res[n-1]), save/uring = ring restore of u^{n-1}.
 struct XBands {  // 4-cell column groups: left [0, gl), right [gr0, ceil(NX/4))
   int gl, gr0, ngr;
 };
@@ -110,7 +109,8 @@ struct AcFixArgs {
   const int32_t* rec;
   float* data;
   const float* res;
-  float* save;
+  float* save;       // forward: ring slot of u^n; backward: ring slot of u^{n-1}
+  float* uring;      // backward: the u^{n-1} field whose ring is restored
   const int* status;
   int n;
   // work split, set by the launcher: blocks of the z, x, receiver and ring
