@@ -349,7 +349,7 @@ def run_sweep(args, w, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "acoustic backward time step: stencil kernel (adjoint, "
-                               "reconstruction, imaging) + z and x CPML correction kernels",
+                               "reconstruction, imaging) + CPML / receiver / ring kernel",
                      "peak_source": peak_src,
                      "frac_of_8000": achieved / 8000.0,
                      "alg_bytes_per_launch": alg_bytes_bwd(c) * nshot,

@@ -25,8 +25,8 @@
 // The profiles a, b are zero off the border, and so are psi, zeta and their
 // adjoints (never written there), which removes most masks.
 //
-// z part: a thread owns 2 adjacent columns (8-byte accesses, coalesced across
-// the warp) and a chunk of ZCH rows; x part: a thread owns 4 consecutive
+// z part: a thread owns a column (coalesced across the warp) and a chunk of
+// ZCH rows; x part: a thread owns 4 consecutive
 // cells of a row (16-byte accesses) and reads its 4 + 4 x-neighbours as two
 // more 16-byte loads.  Every load of a thread is issued before its
 // arithmetic, so the memory latency is paid once per thread.
@@ -36,13 +36,9 @@ namespace sweep {
 namespace {
 
 constexpr int FT = 256;  // threads per block
-constexpr int ZCH = 4;   // rows per thread, z part
+constexpr int ZCH = 8;   // rows per thread, z part
 constexpr int ZW = ZCH + 8;
 
-__device__ __forceinline__ float2 ldg2(const float* p) {
-  return __ldg(reinterpret_cast<const float2*>(p));
-}
-__device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
 __device__ __forceinline__ float4 ldg4(const float* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
 }
@@ -52,33 +48,9 @@ __device__ __forceinline__ float4 ld4(const float* p) {
 __device__ __forceinline__ void st4(float* p, const float* v) {
   *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
-__device__ __forceinline__ void red2(float* p, float2 v) {
-  atomicAdd(reinterpret_cast<float2*>(p), v);
-}
 __device__ __forceinline__ void red4(float* p, const float* v) {
   atomicAdd(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
 }
-__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
-
-// D2 and D1 on column pairs with the packed FP32 pipe (same rounding
-// sequence as the scalar forms: one multiply, then a chain of fused adds).
-__device__ __forceinline__ float2 d2p(const float2* w) {
-  float2 r = __fmul2_rn(f2(kC0), w[4]);
-  r = __ffma2_rn(f2(kC1), __fadd2_rn(w[5], w[3]), r);
-  r = __ffma2_rn(f2(kC2), __fadd2_rn(w[6], w[2]), r);
-  r = __ffma2_rn(f2(kC3), __fadd2_rn(w[7], w[1]), r);
-  r = __ffma2_rn(f2(kC4), __fadd2_rn(w[8], w[0]), r);
-  return r;
-}
-__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
-__device__ __forceinline__ float2 d1p(const float2* w) {
-  float2 r = __fmul2_rn(f2(kD1), __fadd2_rn(w[5], neg2(w[3])));
-  r = __ffma2_rn(f2(kD2), __fadd2_rn(w[6], neg2(w[2])), r);
-  r = __ffma2_rn(f2(kD3), __fadd2_rn(w[7], neg2(w[1])), r);
-  r = __ffma2_rn(f2(kD4), __fadd2_rn(w[8], neg2(w[0])), r);
-  return r;
-}
-
 // 12 cells x-4 .. x+7 of a row (zero outside [0, NXp))
 __device__ __forceinline__ void ldrow12(const float* row, int x, int NXp, float* e) {
   const float4 l = x >= 4 ? ldg4(row + x - 4) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -105,80 +77,67 @@ __host__ __device__ __forceinline__ XBands x_bands(int lo_end, int hi_start, int
   return b;
 }
 
-// (column pair, row chunk, shot) of z-part thread t; false past the end
-__device__ __forceinline__ bool z_item(const AcFixArgs& a, long long t, int& x, int& ch,
-                                       int& s) {
-  const int cp = (int)(t % a.ncp);
-  const long long r = t / a.ncp;
-  ch = (int)(r % a.nchz);
-  s = (int)(r / a.nchz);
-  x = 2 * cp;
-  return s < a.g.nshot && x < a.g.NX;
-}
-
-// (row, column group origin, shot) of x-part thread t
-__device__ __forceinline__ bool x_item(const AcFixArgs& a, long long t, int& z, int& x,
-                                       int& s) {
-  const int j = (int)(t % a.xb.ngr);
-  const long long r = t / a.xb.ngr;
-  z = (int)(r % a.g.NZ);
-  s = (int)(r / a.g.NZ);
-  x = 4 * (j < a.xb.gl ? j : a.xb.gr0 + (j - a.xb.gl));
-  return s < a.g.nshot;
-}
+// Work split: block b of the grid belongs to shot b / bps (bps = blocks per
+// shot, one division per block); within a shot the blocks are, in order,
+// nbz z-part blocks (row chunk = block / zbx, columns (block % zbx) * FT +
+// thread), nbx x-part blocks (8 rows each, a warp per row, a lane per 4-cell
+// column group), nbr receiver blocks and nbs ring blocks.
+constexpr int XROWS = FT / 32;
 
 // ------------------------------------------------------------------ forward
-__device__ __forceinline__ void fwd_z(const AcFixArgs& a, long long t) {
+__device__ __forceinline__ void fwd_z(const AcFixArgs& a, int s, int bl) {
   const Geom& g = a.g;
-  int x, ch, s;
-  if (!z_item(a, t, x, ch, s)) return;
+  const int ch = bl / a.zbx;
+  const int x = (bl - ch * a.zbx) * FT + threadIdx.x;
+  if (x >= g.NX) return;
   const int nch = (g.P + ZCH - 1) / ZCH;  // chunks per strip
   const int strip = ch >= nch ? 1 : 0;
   const int base = strip ? g.P + g.nz : 0;
   const int zs = base + (ch - strip * nch) * ZCH;
   const int ze = min(zs + ZCH, base + g.P);
-  const size_t so = (size_t)s * g.fstride + x;
-  float2 wu[ZW], wp[ZW], zt[ZCH], kk[ZCH];
+  const size_t so = (size_t)s * g.fstride + x;  // this column of this shot
+  float wu[ZW], wp[ZW], zt[ZCH], kk[ZCH];
 #pragma unroll
   for (int k = 0; k < ZW; ++k) {
     const int zz = zs - 4 + k;
     const bool ok = zz >= 0 && zz < g.NZ;
-    const size_t o = (size_t)zz * g.NXp;
-    wu[k] = ok ? ldg2(a.u + so + o) : f2(0.f);
-    wp[k] = ok ? ldg2(a.pzin + so + o) : f2(0.f);
+    const int o = zz * g.NXp;
+    wu[k] = ok ? __ldg(a.u + so + o) : 0.f;
+    wp[k] = ok ? __ldg(a.pzin + so + o) : 0.f;
   }
 #pragma unroll
   for (int q = 0; q < ZCH; ++q) {
     const bool ok = zs + q < ze;
-    const size_t o = (size_t)(zs + q) * g.NXp;
-    zt[q] = ok ? *reinterpret_cast<const float2*>(a.zzin + so + o) : f2(0.f);
-    kk[q] = ok ? ldg2(a.K + x + o) : f2(0.f);
+    const int o = (zs + q) * g.NXp;
+    zt[q] = ok ? a.zzin[so + o] : 0.f;
+    kk[q] = ok ? __ldg(a.K + x + o) : 0.f;
   }
 #pragma unroll
   for (int q = 0; q < ZCH; ++q) {
     const int z = zs + q;
     if (z >= ze) break;
-    const float2 A = f2(__ldg(a.az + z)), B = f2(__ldg(a.bz + z));
-    const float2 d2u = d2p(wu + q), d1u = d1p(wu + q), dp = d1p(wp + q);
-    const float2 zn = __ffma2_rn(A, zt[q], __fmul2_rn(B, __fadd2_rn(d2u, dp)));
-    const float2 po = __ffma2_rn(A, wp[q + 4], __fmul2_rn(B, d1u));
-    const size_t o = so + (size_t)z * g.NXp;
-    st2(a.pzout + o, po);
-    st2(a.zzout + o, zn);
-    red2(a.un + o, __fmul2_rn(kk[q], __fadd2_rn(dp, zn)));
+    const float A = __ldg(a.az + z), B = __ldg(a.bz + z);
+    const float* w = wu + q;
+    const float* p = wp + q;
+    const float d2u = d2(w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7], w[8]);
+    const float d1u = d1(w[0], w[1], w[2], w[3], w[5], w[6], w[7], w[8]);
+    const float dp = d1(p[0], p[1], p[2], p[3], p[5], p[6], p[7], p[8]);
+    const float zn = A * zt[q] + B * (d2u + dp);
+    const size_t o = so + z * g.NXp;
+    a.pzout[o] = A * p[4] + B * d1u;
+    a.zzout[o] = zn;
+    atomicAdd(a.un + o, kk[q] * (dp + zn));
   }
 }
 
-__device__ __forceinline__ void fwd_x(const AcFixArgs& a, long long t) {
+__device__ __forceinline__ void fwd_x_group(const AcFixArgs& a, int s, int z, int x) {
   const Geom& g = a.g;
-  int z, x, s;
-  if (!x_item(a, t, z, x, s)) return;
-  const size_t ro = (size_t)s * g.fstride + (size_t)z * g.NXp;
+  const size_t ro = (size_t)s * g.fstride + z * g.NXp;
   float e[12], f[12], zt[4], kk[4], A[4], B[4];
   ldrow12(a.u + ro, x, g.NXp, e);
   ldrow12(a.pxin + ro, x, g.NXp, f);
   f4a(ld4(a.zxin + ro + x), zt);
-  f4a(ldg4(a.K + (size_t)z * g.NXp + x), kk);
+  f4a(ldg4(a.K + z * g.NXp + x), kk);
   f4a(ldg4(a.ax + x), A);
   f4a(ldg4(a.bx + x), B);
   float po[4], zo[4], du[4];
@@ -200,10 +159,18 @@ __device__ __forceinline__ void fwd_x(const AcFixArgs& a, long long t) {
   red4(a.un + ro + x, du);
 }
 
-__device__ __forceinline__ void fwd_rec(const AcFixArgs& a, long long t) {
+__device__ __forceinline__ void fwd_x(const AcFixArgs& a, int s, int bl) {
   const Geom& g = a.g;
-  const int r = (int)(t % g.nrec), s = (int)(t / g.nrec);
-  if (s >= g.nshot) return;
+  const int z = bl * XROWS + (threadIdx.x >> 5);
+  if (z >= g.NZ) return;
+  for (int j = threadIdx.x & 31; j < a.xb.ngr; j += 32)
+    fwd_x_group(a, s, z, 4 * (j < a.xb.gl ? j : a.xb.gr0 + (j - a.xb.gl)));
+}
+
+__device__ __forceinline__ void fwd_rec(const AcFixArgs& a, int s, int bl) {
+  const Geom& g = a.g;
+  const int r = bl * FT + threadIdx.x;
+  if (r >= g.nrec) return;
   const long long i = (long long)s * g.nrec + r;
   const int rz = a.rec[2 * i] + g.P, rx = a.rec[2 * i + 1] + g.P;
   a.data[i * g.nt + a.n] = a.un[(size_t)s * g.fstride + (size_t)rz * g.NXp + rx];
@@ -230,11 +197,10 @@ __device__ __forceinline__ void ring_cell(const Geom& g, int ri, int& zi, int& x
 
 // boundary save: ring cells 4q .. 4q+3 of u^n (final: the previous step's
 // kernels have completed) into the ring slot, in ring order
-__device__ __forceinline__ void fwd_ring(const AcFixArgs& a, long long t) {
+__device__ __forceinline__ void fwd_ring(const AcFixArgs& a, int s, int bl) {
   const Geom& g = a.g;
-  const int nq = (g.nring + 3) / 4;
-  const int q = (int)(t % nq), s = (int)(t / nq);
-  if (s >= g.nshot) return;
+  const int q = bl * FT + threadIdx.x;
+  if (4 * q >= g.nring) return;
   const float* u = a.u + (size_t)s * g.fstride;
   float* sv = a.save + (size_t)s * g.nring;
 #pragma unroll
@@ -251,90 +217,92 @@ __global__ void __launch_bounds__(FT) ac_fix_fwd_kernel(const AcFixArgs a) {
   grid_dep_wait();
   grid_dep_trigger();
   if (*a.status) return;
-  int b = blockIdx.x;
+  const int bps = a.nbz + a.nbx + a.nbr + a.nbs;
+  const int s = blockIdx.x / bps;
+  int b = blockIdx.x - s * bps;
   if (b < a.nbz) {
-    fwd_z(a, (long long)b * FT + threadIdx.x);
+    fwd_z(a, s, b);
     return;
   }
   b -= a.nbz;
   if (b < a.nbx) {
-    fwd_x(a, (long long)b * FT + threadIdx.x);
+    fwd_x(a, s, b);
     return;
   }
   b -= a.nbx;
   if (b < a.nbr) {
-    fwd_rec(a, (long long)b * FT + threadIdx.x);
+    fwd_rec(a, s, b);
     return;
   }
-  b -= a.nbr;
-  fwd_ring(a, (long long)b * FT + threadIdx.x);
+  fwd_ring(a, s, b - a.nbr);
 }
 
 // ----------------------------------------------------------------- backward
-__device__ __forceinline__ void bwd_z(const AcFixArgs& a, long long t) {
+__device__ __forceinline__ void bwd_z(const AcFixArgs& a, int s, int bl) {
   const Geom& g = a.g;
-  int x, ch, s;
-  if (!z_item(a, t, x, ch, s)) return;
+  const int ch = bl / a.zbx;
+  const int x = (bl - ch * a.zbx) * FT + threadIdx.x;
+  if (x >= g.NX) return;
   const int lo_end = band_lo_end(g.P, g.NZ), hi_start = band_hi_start(g.P, g.nz, g.NZ);
   const int nlo = (lo_end + ZCH - 1) / ZCH;
   const int band = ch >= nlo ? 1 : 0;
   const int zs = (band ? hi_start : 0) + (ch - band * nlo) * ZCH;
   const int ze = min(zs + ZCH, band ? g.NZ : lo_end);
   if (zs >= ze) return;
-  const size_t so = (size_t)s * g.fstride + x;
-  float2 wm[ZW], wz[ZW], wp[ZW], kk[ZCH];
-  float bb[ZW];
+  const size_t so = (size_t)s * g.fstride + x;  // this column of this shot
+  float wm[ZW], wz[ZW], wp[ZW], kk[ZCH], bb[ZW];
 #pragma unroll
   for (int k = 0; k < ZW; ++k) {
     const int zz = zs - 4 + k;
     const bool ok = zz >= 0 && zz < g.NZ;
-    const size_t o = (size_t)zz * g.NXp;
-    wm[k] = ok ? ldg2(a.u + so + o) : f2(0.f);
-    wz[k] = ok ? ldg2(a.zzin + so + o) : f2(0.f);
-    wp[k] = ok ? ldg2(a.pzin + so + o) : f2(0.f);
+    const int o = zz * g.NXp;
+    wm[k] = ok ? __ldg(a.u + so + o) : 0.f;
+    wz[k] = ok ? __ldg(a.zzin + so + o) : 0.f;
+    wp[k] = ok ? __ldg(a.pzin + so + o) : 0.f;
     bb[k] = ok ? __ldg(a.bz + zz) : 0.f;
   }
 #pragma unroll
   for (int q = 0; q < ZCH; ++q) {
     const bool ok = zs + q < ze;
-    kk[q] = ok ? ldg2(a.K + x + (size_t)(zs + q) * g.NXp) : f2(0.f);
+    kk[q] = ok ? __ldg(a.K + x + (zs + q) * g.NXp) : 0.f;
   }
-  float2 wc[ZW], wb[ZW], wg[ZW];
+  float wc[ZW], wb[ZW], wg[ZW];
 #pragma unroll
   for (int k = 0; k < ZW; ++k) {
     const int zz = zs - 4 + k;
-    const float2 b = f2(bb[k]);
-    wc[k] = __fmul2_rn(b, __fadd2_rn(wm[k], wz[k]));
-    wb[k] = __fmul2_rn(b, wp[k]);
+    wc[k] = bb[k] * (wm[k] + wz[k]);
+    wb[k] = bb[k] * wp[k];
     // m G: zero off the strip rows
-    wg[k] = (zz >= 0 && zz < g.NZ && z_border(g, zz)) ? __fadd2_rn(wm[k], wc[k]) : f2(0.f);
+    wg[k] = (zz >= 0 && zz < g.NZ && z_border(g, zz)) ? wm[k] + wc[k] : 0.f;
   }
 #pragma unroll
   for (int q = 0; q < ZCH; ++q) {
     const int z = zs + q;
     if (z >= ze) break;
-    const size_t o = so + (size_t)z * g.NXp;
-    const float2 corr = __fadd2_rn(d2p(wc + q), neg2(d1p(wb + q)));
-    red2(a.un + o, __fmul2_rn(kk[q], corr));  // mu^n
+    const size_t o = so + z * g.NXp;
+    const float* C = wc + q;
+    const float* B = wb + q;
+    const float* G = wg + q;
+    const float corr = d2(C[0], C[1], C[2], C[3], C[4], C[5], C[6], C[7], C[8]) -
+                       d1(B[0], B[1], B[2], B[3], B[5], B[6], B[7], B[8]);
+    atomicAdd(a.un + o, kk[q] * corr);  // mu^n
     if (z_border(g, z)) {
-      const float2 A = f2(__ldg(a.az + z));
-      st2(a.pzout + o, __fadd2_rn(__fmul2_rn(A, wp[q + 4]), neg2(d1p(wg + q))));
-      st2(a.zzout + o, __fmul2_rn(A, __fadd2_rn(wm[q + 4], wz[q + 4])));
+      const float A = __ldg(a.az + z);
+      a.pzout[o] = A * wp[q + 4] - d1(G[0], G[1], G[2], G[3], G[5], G[6], G[7], G[8]);
+      a.zzout[o] = A * (wm[q + 4] + wz[q + 4]);
     }
   }
 }
 
-__device__ __forceinline__ void bwd_x(const AcFixArgs& a, long long t) {
+__device__ __forceinline__ void bwd_x_group(const AcFixArgs& a, int s, int z, int x) {
   const Geom& g = a.g;
-  int z, x, s;
-  if (!x_item(a, t, z, x, s)) return;
-  const size_t ro = (size_t)s * g.fstride + (size_t)z * g.NXp;
+  const size_t ro = (size_t)s * g.fstride + z * g.NXp;
   float em[12], ez[12], ep[12], bb[12], kk[4], A[4];
   ldrow12(a.u + ro, x, g.NXp, em);
   ldrow12(a.zxin + ro, x, g.NXp, ez);
   ldrow12(a.pxin + ro, x, g.NXp, ep);
   ldrow12(a.bx, x, g.NXp, bb);
-  f4a(ldg4(a.K + (size_t)z * g.NXp + x), kk);
+  f4a(ldg4(a.K + z * g.NXp + x), kk);
   f4a(ldg4(a.ax + x), A);
   float C[12], Bv[12], G[12];
 #pragma unroll
@@ -364,10 +332,18 @@ __device__ __forceinline__ void bwd_x(const AcFixArgs& a, long long t) {
   st4(a.zxout + ro + x, zo);
 }
 
-__device__ __forceinline__ void bwd_rec(const AcFixArgs& a, long long t) {
+__device__ __forceinline__ void bwd_x(const AcFixArgs& a, int s, int bl) {
   const Geom& g = a.g;
-  const int r = (int)(t % g.nrec), s = (int)(t / g.nrec);
-  if (s >= g.nshot) return;
+  const int z = bl * XROWS + (threadIdx.x >> 5);
+  if (z >= g.NZ) return;
+  for (int j = threadIdx.x & 31; j < a.xb.ngr; j += 32)
+    bwd_x_group(a, s, z, 4 * (j < a.xb.gl ? j : a.xb.gr0 + (j - a.xb.gl)));
+}
+
+__device__ __forceinline__ void bwd_rec(const AcFixArgs& a, int s, int bl) {
+  const Geom& g = a.g;
+  const int r = bl * FT + threadIdx.x;
+  if (r >= g.nrec) return;
   const long long i = (long long)s * g.nrec + r;
   const int rz = a.rec[2 * i] + g.P, rx = a.rec[2 * i + 1] + g.P;
   const size_t c = (size_t)rz * g.NXp + rx;
@@ -376,11 +352,10 @@ __device__ __forceinline__ void bwd_rec(const AcFixArgs& a, long long t) {
 
 // ring restore: u^{n-1} on the ring cells 4q .. 4q+3 from the forward save
 // (the stencil kernel reconstructs the interior and leaves the ring alone)
-__device__ __forceinline__ void bwd_ring(const AcFixArgs& a, long long t) {
+__device__ __forceinline__ void bwd_ring(const AcFixArgs& a, int s, int bl) {
   const Geom& g = a.g;
-  const int nq = (g.nring + 3) / 4;
-  const int q = (int)(t % nq), s = (int)(t / nq);
-  if (s >= g.nshot) return;
+  const int q = bl * FT + threadIdx.x;
+  if (4 * q >= g.nring) return;
   float* u = a.uring + (size_t)s * g.fstride;
   const float* sv = a.save + (size_t)s * g.nring;
 #pragma unroll
@@ -397,43 +372,44 @@ __global__ void __launch_bounds__(FT) ac_fix_bwd_kernel(const AcFixArgs a) {
   grid_dep_wait();
   grid_dep_trigger();
   if (*a.status) return;
-  int b = blockIdx.x;
+  const int bps = a.nbz + a.nbx + a.nbr + a.nbs;
+  const int s = blockIdx.x / bps;
+  int b = blockIdx.x - s * bps;
   if (b < a.nbz) {
-    bwd_z(a, (long long)b * FT + threadIdx.x);
+    bwd_z(a, s, b);
     return;
   }
   b -= a.nbz;
   if (b < a.nbx) {
-    bwd_x(a, (long long)b * FT + threadIdx.x);
+    bwd_x(a, s, b);
     return;
   }
   b -= a.nbx;
   if (b < a.nbr) {
-    bwd_rec(a, (long long)b * FT + threadIdx.x);
+    bwd_rec(a, s, b);
     return;
   }
-  b -= a.nbr;
-  bwd_ring(a, (long long)b * FT + threadIdx.x);
+  bwd_ring(a, s, b - a.nbr);
 }
 
-int blocks(long long threads) { return (int)((threads + FT - 1) / FT); }
+int cdiv(int a, int b) { return (a + b - 1) / b; }
 
 }  // namespace
 
 void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st) {
   const Geom& g = a.g;
   if (g.nshot <= 0) return;
-  a.ncp = (g.NX + 1) / 2;
-  a.nchz = g.P > 0 ? 2 * ((g.P + ZCH - 1) / ZCH) : 0;
+  a.zbx = cdiv(g.NX, FT);
+  a.nchz = g.P > 0 ? 2 * cdiv(g.P, ZCH) : 0;
   a.xb = x_bands(g.P, g.P + g.nx, g.NX);
-  a.nbz = g.P > 0 ? blocks((long long)a.ncp * a.nchz * g.nshot) : 0;
-  a.nbx = g.P > 0 ? blocks((long long)g.NZ * a.xb.ngr * g.nshot) : 0;
-  a.nbr = (a.data && g.nrec > 0) ? blocks((long long)g.nrec * g.nshot) : 0;
-  a.nbs = (a.save && g.nring > 0) ? blocks((long long)((g.nring + 3) / 4) * g.nshot) : 0;
-  const int nb = a.nbz + a.nbx + a.nbr + a.nbs;
-  if (nb == 0) return;
+  a.nbz = a.zbx * a.nchz;
+  a.nbx = g.P > 0 ? cdiv(g.NZ, XROWS) : 0;
+  a.nbr = (a.data && g.nrec > 0) ? cdiv(g.nrec, FT) : 0;
+  a.nbs = (a.save && g.nring > 0) ? cdiv(cdiv(g.nring, 4), FT) : 0;
+  const int bps = a.nbz + a.nbx + a.nbr + a.nbs;
+  if (bps == 0) return;
   void* tok = profile_begin(SWEEP_K_AC_FWD_FR, st);
-  launch_dependent(ac_fix_fwd_kernel, dim3(nb), dim3(FT), 0, st, a);
+  launch_dependent(ac_fix_fwd_kernel, dim3(bps * g.nshot), dim3(FT), 0, st, a);
   profile_end(tok, st);
   note_launches(1);
 }
@@ -442,19 +418,17 @@ void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st) {
   const Geom& g = a.g;
   if (g.nshot <= 0) return;
   const int lo_end = band_lo_end(g.P, g.NZ), hi_start = band_hi_start(g.P, g.nz, g.NZ);
-  a.ncp = (g.NX + 1) / 2;
-  a.nchz = g.P > 0 ? (lo_end + ZCH - 1) / ZCH + (g.NZ - hi_start + ZCH - 1) / ZCH : 0;
+  a.zbx = cdiv(g.NX, FT);
+  a.nchz = g.P > 0 ? cdiv(lo_end, ZCH) + cdiv(g.NZ - hi_start, ZCH) : 0;
   a.xb = x_bands(band_lo_end(g.P, g.NX), band_hi_start(g.P, g.nx, g.NX), g.NX);
-  a.nbz = g.P > 0 ? blocks((long long)a.ncp * a.nchz * g.nshot) : 0;
-  a.nbx = g.P > 0 ? blocks((long long)g.NZ * a.xb.ngr * g.nshot) : 0;
-  a.nbr = (a.res && g.nrec > 0 && a.n >= 1) ? blocks((long long)g.nrec * g.nshot) : 0;
-  a.nbs = (a.save && a.uring && g.nring > 0)
-              ? blocks((long long)((g.nring + 3) / 4) * g.nshot)
-              : 0;
-  const int nb = a.nbz + a.nbx + a.nbr + a.nbs;
-  if (nb == 0) return;
+  a.nbz = a.zbx * a.nchz;
+  a.nbx = g.P > 0 ? cdiv(g.NZ, XROWS) : 0;
+  a.nbr = (a.res && g.nrec > 0 && a.n >= 1) ? cdiv(g.nrec, FT) : 0;
+  a.nbs = (a.save && a.uring && g.nring > 0) ? cdiv(cdiv(g.nring, 4), FT) : 0;
+  const int bps = a.nbz + a.nbx + a.nbr + a.nbs;
+  if (bps == 0) return;
   void* tok = profile_begin(SWEEP_K_AC_BWD_FR, st);
-  launch_dependent(ac_fix_bwd_kernel, dim3(nb), dim3(FT), 0, st, a);
+  launch_dependent(ac_fix_bwd_kernel, dim3(bps * g.nshot), dim3(FT), 0, st, a);
   profile_end(tok, st);
   note_launches(1);
 }

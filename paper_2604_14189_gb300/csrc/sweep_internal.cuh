@@ -113,10 +113,10 @@ struct AcFixArgs {
   float* uring;      // backward: the u^{n-1} field whose ring is restored
   const int* status;
   int n;
-  // work split, set by the launcher: blocks of the z, x, receiver and ring
-  // parts
+  // work split, set by the launcher: blocks per shot of the z, x, receiver
+  // and ring parts; z part: blocks per row chunk, row chunks
   int nbz, nbx, nbr, nbs;
-  int ncp, nchz;  // column pairs; row chunks per shot (z part)
+  int zbx, nchz;
   XBands xb;
 };
 void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st);
