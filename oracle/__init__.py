@@ -86,6 +86,8 @@ def _load():
             lib.oracle_acoustic_adjoint.argtypes = [P, dp, dp, ip, ip, dp]
             lib.oracle_acoustic_adjoint.restype = ctypes.c_int
             lib.oracle_acoustic_gradient.argtypes = [P, dp, dp, ip, ip, dp, dp, dp]
+            lib.oracle_elastic_adjoint.argtypes = [P, dp, dp, ip, ip, dp]
+            lib.oracle_elastic_gradient.argtypes = [P, dp, dp, ip, ip, dp, dp, dp]
             lib.oracle_acoustic_gradient.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -197,3 +199,30 @@ def elastic_forward(p: Problem, model, wavelet, src, rec, wavefield=False):
         _ptr(wf, ctypes.c_double) if wf is not None else None)
     _check(rc)
     return (data, wf) if wavefield else data
+
+
+def elastic_adjoint(p: Problem, model, adj_data, src, rec):
+    """Wavelet adjoint [nshot][nt] of the elastic data map for adj_data
+    [nshot][2][nrec][nt]."""
+    lib = _load()
+    model, adj_data, src, rec = _d(model), _d(adj_data), _i(src), _i(rec)
+    wg = np.zeros((p.nshot, p.nt))
+    rc = lib.oracle_elastic_adjoint(
+        ctypes.byref(p), _ptr(model, ctypes.c_double), _ptr(adj_data, ctypes.c_double),
+        _ptr(src, ctypes.c_int32), _ptr(rec, ctypes.c_int32), _ptr(wg, ctypes.c_double))
+    _check(rc)
+    return wg
+
+
+def elastic_gradient(p: Problem, model, wavelet, src, rec, d_obs):
+    """(grad [3][nz][nx] of the misfit w.r.t. (vp, vs, rho), misfit J)."""
+    lib = _load()
+    model, wavelet, src, rec, d_obs = _d(model), _d(wavelet), _i(src), _i(rec), _d(d_obs)
+    grad = np.zeros((3, p.nz, p.nx))
+    J = ctypes.c_double(0.0)
+    rc = lib.oracle_elastic_gradient(
+        ctypes.byref(p), _ptr(model, ctypes.c_double), _ptr(wavelet, ctypes.c_double),
+        _ptr(src, ctypes.c_int32), _ptr(rec, ctypes.c_int32), _ptr(d_obs, ctypes.c_double),
+        _ptr(grad, ctypes.c_double), ctypes.byref(J))
+    _check(rc)
+    return grad, J.value

@@ -104,6 +104,22 @@ int oracle_elastic_forward(const oracle_problem* p, const double* model,
                            const double* wavelet, const int32_t* src,
                            const int32_t* rec, double* data, double* wavefield);
 
+/* Elastic adjoint of the map wavelet -> data (model fixed): adj_data
+ * [nshot][2][nrec][nt] in the layout of the data, wavelet_grad [nshot][nt].
+ * The exact transpose of the recurrence, run backwards in time.            */
+int oracle_elastic_adjoint(const oracle_problem* p, const double* model,
+                           const double* adj_data, const int32_t* src,
+                           const int32_t* rec, double* wavelet_grad);
+
+/* Elastic L2 misfit J = 1/2 sum (d - d_obs)^2 over both components and its
+ * gradient with respect to the interior (vp, vs, rho), grad [3][nz][nx]
+ * (sum over shots); padding and CPML profiles held fixed (set v_pml).
+ * Keeps every forward state in memory: small problems only.                */
+int oracle_elastic_gradient(const oracle_problem* p, const double* model,
+                            const double* wavelet, const int32_t* src,
+                            const int32_t* rec, const double* d_obs, double* grad,
+                            double* misfit);
+
 #ifdef __cplusplus
 }
 #endif

@@ -131,3 +131,79 @@ def test_elastic_cpml_absorbs():
     assert np.all(np.isfinite(e))
     assert e[-1] < 1e-4 * e.max()
     assert e[-1] < e[nt // 2]
+
+
+# ---------------------------------------------------------------- reverse mode
+def _small_elastic(seed=5, nt=160):
+    rng = np.random.default_rng(seed)
+    nz, nx, pml, dx, dt = 18, 22, 6, 5.0, 4e-4
+    vp = 2500 + 100 * rng.standard_normal((nz, nx))
+    vs = vp / 1.8
+    rho = 2000 + 100 * rng.random((nz, nx))
+    src = np.array([[3, 8], [4, 14]])
+    rec = np.array([[[2, j] for j in range(2, 20, 3)]] * 2)
+    p = oracle.make_problem(1, nz, nx, pml, dx, dt, nt, 2, rec.shape[1], 30.0, v_pml=3200.0)
+    w = np.stack([inputs.ricker(40.0, dt, nt)] * 2) * 1e6
+    return p, np.stack([vp, vs, rho]), w, src, rec, rng
+
+
+def test_elastic_adjoint_dot_product():
+    """<F w, d> = <w, F^T d> for the linear map wavelet -> traces (the
+    adjoint is the exact transpose of the discrete recurrence)."""
+    p, m, w, src, rec, rng = _small_elastic()
+    d = oracle.elastic_forward(p, m, w, src, rec)
+    db = rng.standard_normal(d.shape)
+    wg = oracle.elastic_adjoint(p, m, db, src, rec)
+    lhs, rhs = np.sum(d * db), np.sum(w * wg)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_elastic_adjoint_of_a_single_trace_sample():
+    """Brute force on one entry: the adjoint of a unit impulse in one trace
+    sample equals the column of the forward map (the response of that sample
+    to a unit wavelet sample), checked for a few wavelet samples."""
+    p, m, w, src, rec, rng = _small_elastic(nt=40)
+    db = np.zeros((p.nshot, 2, p.nrec, p.nt))
+    db[1, 1, 3, 30] = 1.0
+    wg = oracle.elastic_adjoint(p, m, db, src, rec)
+    for n in (0, 7, 19):
+        e = np.zeros_like(w)
+        e[1, n] = 1.0
+        d = oracle.elastic_forward(p, m, e, src, rec)
+        assert abs(d[1, 1, 3, 30] - wg[1, n]) <= 1e-12 * max(abs(d[1, 1, 3, 30]), 1e-30)
+
+
+def _taper(a):
+    a = a.copy()
+    a[:2] = 0
+    a[-2:] = 0
+    a[:, :2] = 0
+    a[:, -2:] = 0
+    return a
+
+
+def test_elastic_gradient_matches_finite_differences():
+    """Central differences of the misfit along smooth perturbations of vp,
+    vs and rho (zero on the interior edge, so the edge-replicated padding is
+    unchanged) against <grad, dm>; fixes the chain rule through Hooke's
+    parameters, the buoyancy averages and the harmonic shear average."""
+    from scipy.ndimage import gaussian_filter
+
+    p, m, w, src, rec, rng = _small_elastic()
+    mt = m.copy()
+    mt[0, 8:12, 8:14] *= 1.05
+    mt[1, 5:9, 10:16] *= 0.95
+    mt[2, 10:14, 4:9] *= 1.04
+    dobs = oracle.elastic_forward(p, mt, w, src, rec)
+    g, J = oracle.elastic_gradient(p, m, w, src, rec, dobs)
+    d = oracle.elastic_forward(p, m, w, src, rec)
+    assert abs(J - 0.5 * np.sum((d - dobs) ** 2)) <= 1e-12 * J
+    for k in range(3):
+        dm = np.zeros_like(m)
+        dm[k] = _taper(gaussian_filter(rng.standard_normal(m[k].shape), 2.0)) * m[k].mean() * 1e-3
+        h = 0.5
+        Jp = 0.5 * np.sum((oracle.elastic_forward(p, m + h * dm, w, src, rec) - dobs) ** 2)
+        Jm = 0.5 * np.sum((oracle.elastic_forward(p, m - h * dm, w, src, rec) - dobs) ** 2)
+        fd = (Jp - Jm) / (2 * h)
+        an = np.sum(g[k] * dm[k])
+        assert abs(fd - an) <= 2e-5 * abs(fd), (k, fd, an)
