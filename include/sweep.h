@@ -118,21 +118,29 @@ int sweep_forward(const sweep_problem* prob, const float* model,
                   const float* wavelet, const int32_t* src, const int32_t* rec,
                   float* data, void* ws, size_t ws_bytes, void* stream);
 
-/* Adjoint of the linear map wavelet -> data at fixed model (acoustic only):
- * wavelet_grad[s][n] = sum_{r,m} adj_data[s][r][m] d data[s][r][m]/d f_s^n.
- * The dot-product test <F f, d> = <f, F^T d> holds to rounding.            */
+/* Adjoint of the linear map wavelet -> data at fixed model:
+ * wavelet_grad[s][n] = sum_{c,r,m} adj_data[s][c][r][m] d data[s][c][r][m]/d f_s^n
+ * (adj_data in the layout of data).  The exact transpose of the discrete
+ * recurrence, run backwards in time; the dot-product test
+ * <F f, d> = <f, F^T d> holds to rounding.                                 */
 int sweep_adjoint(const sweep_problem* prob, const float* model,
                   const float* adj_data, const int32_t* src,
                   const int32_t* rec, float* wavelet_grad, void* ws,
                   size_t ws_bytes, void* stream);
 
-/* FWI velocity gradient (acoustic only): forward with boundary saving, L2
- * residual, adjoint propagation with wavefield reconstruction and the imaging
- * condition g = (2/v) sum_n mu^{n+1} (Lap u^n + f^n delta_s), mu = K lambda.
- *   d_obs    [nshot][1][nrec][nt] observed data (or residual, see flags)
- *   grad     out [nz][nx] dJ/dv, summed over shots (FP64 sum, FP32 result)
- *   misfit   out device double, J = 1/2 sum r^2 (may be NULL)
- *   illum    out [nz][nx] sum over shots and steps of u^2 (may be NULL)   */
+/* FWI gradient of the L2 misfit J = 1/2 sum r^2, r = data - d_obs, with the
+ * padding and the CPML profiles held fixed (set v_pml to fix the profiles).
+ * Acoustic: forward with boundary saving, adjoint propagation with wavefield
+ * reconstruction and the imaging condition
+ * g = (2/v) sum_n mu^{n+1} (Lap u^n + f^n delta_s), mu = K lambda.
+ * Elastic: forward with sqrt(nt) checkpoints, the transposed steps with each
+ * checkpoint segment replayed, d J / d (vp, vs, rho) through Hooke's
+ * parameters, the buoyancy averages and the harmonic shear average.
+ *   d_obs    [nshot][ncomp][nrec][nt] observed data (or residual, see flags)
+ *   grad     out [npar][nz][nx], summed over shots (FP64 sum, FP32 result)
+ *   misfit   out device double, J (may be NULL)
+ *   illum    out [nz][nx] sum over shots and steps of u^2 (may be NULL;
+ *            acoustic only, SWEEP_EUNSUPPORTED for elastic)               */
 int sweep_gradient(const sweep_problem* prob, const float* model,
                    const float* wavelet, const int32_t* src, const int32_t* rec,
                    const float* d_obs, float* grad, double* misfit, float* illum,

@@ -1,0 +1,299 @@
+// Elastic adjoint: the exact transpose of one velocity-stress step
+// (elastic.cu, Sec. 3.5, Eq. 12), and the chain rule from the step
+// coefficients to (vp, vs, rho).
+//
+// Forward step n (unit-spacing staggered differences D, 1/dx folded into
+// the coefficients c* = (dt/dx) x physical coefficient):
+//   vx += cbx (Dpx txx + p1' + Dmz txz + p2'),  p1' = axh p1 + bxh Dpx txx ...
+//   vz += cbz (Dmx txz + p3' + Dpz tzz + p4')
+//   record v^{n+1/2};  Ex = Dmx vx + p5',  Ez = Dmz vz + p6'
+//   txx += cl2m Ex + clam Ez;  tzz += clam Ex + cl2m Ez
+//   txz += cmu (Dpz vx + p7' + Dpx vz + p8');  txx(s), tzz(s) += (dt/dx^2) f^n
+// Its transpose, in reverse order, with T = adjoint of a quantity:
+//   wavelet: f^n-bar = (dt/dx^2) (txx-bar + tzz-bar)(s)
+//   stress:  Ex-bar = cl2m txx-bar + clam tzz-bar (Ez-bar likewise);
+//            P = p5-bar + Ex-bar;  exx-bar = Ex-bar + bx P;  p5-bar = ax P
+//            (p6..p8 alike); vx-bar += -Dpx(exx-bar) - Dmz(ezx-bar),
+//            vz-bar += -Dpz(ezz-bar) - Dmx(exz-bar)      (Dp^T = -Dm)
+//   receivers: v-bar(r) += residual^n(r)
+//   velocity: Q = cbx vx-bar;  P = p1-bar + Q;  dxt-bar = Q + bxh P;
+//            p1-bar = axh P (p2..p4 alike); txx-bar += -Dmx(dxt-bar), ...
+//   coefficients: d J / d cl2m += txx-bar Ex + tzz-bar Ez, d J / d clam +=
+//            txx-bar Ez + tzz-bar Ex, d J / d cmu += txz-bar (shear bracket),
+//            d J / d cbx += vx-bar (vx bracket), d J / d cbz likewise.
+// Each half is a pointwise kernel (the adjoint derivative terms into four
+// scratch fields, memory variables, coefficient adjoints) and a gather
+// kernel (the transposed differences of those terms).
+#include "sweep_internal.cuh"
+
+namespace sweep {
+namespace {
+
+constexpr float kS1 = 9.0f / 8.0f;
+constexpr float kS2 = -1.0f / 24.0f;
+constexpr int AT = 128;  // threads per block (a row segment of one shot)
+
+struct Fld {
+  const float* f;
+  int NZ, NX, NXp;
+  __device__ __forceinline__ float operator()(int z, int x) const {
+    return (z >= 0 && z < NZ && x >= 0 && x < NX) ? f[z * NXp + x] : 0.f;
+  }
+};
+__device__ __forceinline__ Fld fld(const float* f, const Geom& g, int s) {
+  return Fld{f + (size_t)s * g.fstride, g.NZ, g.NX, g.NXp};
+}
+// staggered differences, as in the forward kernels
+__device__ __forceinline__ float dpx(const Fld& f, int z, int x) {
+  return kS1 * (f(z, x + 1) - f(z, x)) + kS2 * (f(z, x + 2) - f(z, x - 1));
+}
+__device__ __forceinline__ float dmx(const Fld& f, int z, int x) {
+  return kS1 * (f(z, x) - f(z, x - 1)) + kS2 * (f(z, x + 1) - f(z, x - 2));
+}
+__device__ __forceinline__ float dpz(const Fld& f, int z, int x) {
+  return kS1 * (f(z + 1, x) - f(z, x)) + kS2 * (f(z + 2, x) - f(z - 1, x));
+}
+__device__ __forceinline__ float dmz(const Fld& f, int z, int x) {
+  return kS1 * (f(z, x) - f(z - 1, x)) + kS2 * (f(z + 1, x) - f(z - 2, x));
+}
+
+enum { G_L2M = 0, G_LAM = 1, G_MU = 2, G_BX = 3, G_BZ = 4 };
+
+// ------------------------------------------------------------- wavelet
+__global__ void el_adj_src_kernel(const ElAdjArgs a) {
+  if (*a.status) return;
+  const Geom& g = a.g;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.nshot) return;
+  const size_t c = (size_t)s * g.fstride + (size_t)(a.src[2 * s] + g.P) * g.NXp +
+                   (a.src[2 * s + 1] + g.P);
+  a.wgrad[(size_t)s * g.nt + a.n] = a.src_scale * (a.atxx[c] + a.atzz[c]);
+}
+
+// ------------------------------------------------------- stress, pointwise
+__global__ void __launch_bounds__(AT) el_adj_str_pt_kernel(const ElAdjArgs a) {
+  if (*a.status) return;
+  const Geom& g = a.g;
+  const int x = blockIdx.x * AT + threadIdx.x, z = blockIdx.y, s = blockIdx.z;
+  if (x >= g.NXp) return;
+  const size_t c = (size_t)s * g.fstride + (size_t)z * g.NXp + x;
+  if (x >= g.NX) {  // zero terms beyond the grid for the gather kernel
+    a.e0[c] = a.e1[c] = a.e2[c] = a.e3[c] = 0.f;
+    return;
+  }
+  const size_t pc = (size_t)z * g.NXp + x;
+  const float txx = a.atxx[c], tzz = a.atzz[c], txz = a.atxz[c];
+  const float l2m = a.cl2m[pc], lam = a.clam[pc], mu = a.cmu[pc];
+  if (a.gacc) {
+    const Fld vx = fld(a.fvx, g, s), vz = fld(a.fvz, g, s);
+    const float ex = dmx(vx, z, x) + a.fp[4][c];
+    const float ez = dmz(vz, z, x) + a.fp[5][c];
+    const float sxz = dpz(vx, z, x) + a.fp[6][c] + dpx(vz, z, x) + a.fp[7][c];
+    float* ga = a.gacc + (size_t)s * 5 * g.fstride + pc;
+    ga[G_L2M * g.fstride] += txx * ex + tzz * ez;
+    ga[G_LAM * g.fstride] += txx * ez + tzz * ex;
+    ga[G_MU * g.fstride] += txz * sxz;
+  }
+  // txz += cmu (ezx + p7' + exz + p8')
+  const float T = mu * txz;
+  const float P7 = a.ap[6][c] + T, P8 = a.ap[7][c] + T;
+  a.e2[c] = T + a.bzh[z] * P7;  // ezx-bar
+  a.e3[c] = T + a.bxh[x] * P8;  // exz-bar
+  a.ap[6][c] = a.azh[z] * P7;
+  a.ap[7][c] = a.axh[x] * P8;
+  // txx += cl2m Ex + clam Ez, tzz += clam Ex + cl2m Ez
+  const float Ex = l2m * txx + lam * tzz, Ez = lam * txx + l2m * tzz;
+  const float P5 = a.ap[4][c] + Ex, P6 = a.ap[5][c] + Ez;
+  a.e0[c] = Ex + a.bx[x] * P5;  // exx-bar
+  a.e1[c] = Ez + a.bz[z] * P6;  // ezz-bar
+  a.ap[4][c] = a.ax[x] * P5;
+  a.ap[5][c] = a.az[z] * P6;
+}
+
+// ----------------------------------------------------------- stress, gather
+__global__ void __launch_bounds__(AT) el_adj_str_sc_kernel(const ElAdjArgs a) {
+  if (*a.status) return;
+  const Geom& g = a.g;
+  const int x = blockIdx.x * AT + threadIdx.x, z = blockIdx.y, s = blockIdx.z;
+  if (x >= g.NX) return;
+  const size_t c = (size_t)s * g.fstride + (size_t)z * g.NXp + x;
+  const Fld exx = fld(a.e0, g, s), ezz = fld(a.e1, g, s), ezx = fld(a.e2, g, s),
+            exz = fld(a.e3, g, s);
+  a.avx[c] -= dpx(exx, z, x) + dmz(ezx, z, x);
+  a.avz[c] -= dpz(ezz, z, x) + dmx(exz, z, x);
+}
+
+// ---------------------------------------------------------------- receivers
+__global__ void el_adj_rec_kernel(const ElAdjArgs a) {
+  if (*a.status) return;
+  const Geom& g = a.g;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x, s = blockIdx.y;
+  if (r >= g.nrec) return;
+  const int32_t* q = a.rec + 2 * ((size_t)s * g.nrec + r);
+  const size_t c = (size_t)s * g.fstride + (size_t)(q[0] + g.P) * g.NXp + (q[1] + g.P);
+  a.avx[c] += a.res[(((size_t)s * 2 + 0) * g.nrec + r) * g.nt + a.n];
+  a.avz[c] += a.res[(((size_t)s * 2 + 1) * g.nrec + r) * g.nt + a.n];
+}
+
+// ----------------------------------------------------- velocity, pointwise
+__global__ void __launch_bounds__(AT) el_adj_vel_pt_kernel(const ElAdjArgs a) {
+  if (*a.status) return;
+  const Geom& g = a.g;
+  const int x = blockIdx.x * AT + threadIdx.x, z = blockIdx.y, s = blockIdx.z;
+  if (x >= g.NXp) return;
+  const size_t c = (size_t)s * g.fstride + (size_t)z * g.NXp + x;
+  if (x >= g.NX) {
+    a.e0[c] = a.e1[c] = a.e2[c] = a.e3[c] = 0.f;
+    return;
+  }
+  const size_t pc = (size_t)z * g.NXp + x;
+  const float vx = a.avx[c], vz = a.avz[c];
+  if (a.gacc) {
+    const Fld txx = fld(a.ftxx, g, s), tzz = fld(a.ftzz, g, s), txz = fld(a.ftxz, g, s);
+    const float sx = dpx(txx, z, x) + a.fp[0][c] + dmz(txz, z, x) + a.fp[1][c];
+    const float sz = dmx(txz, z, x) + a.fp[2][c] + dpz(tzz, z, x) + a.fp[3][c];
+    float* ga = a.gacc + (size_t)s * 5 * g.fstride + pc;
+    ga[G_BX * g.fstride] += vx * sx;
+    ga[G_BZ * g.fstride] += vz * sz;
+  }
+  // vx += cbx (dxt + p1' + dzt + p2')
+  const float Q = a.cbx[pc] * vx;
+  const float P1 = a.ap[0][c] + Q, P2 = a.ap[1][c] + Q;
+  a.e0[c] = Q + a.bxh[x] * P1;  // dxt-bar (Dpx txx)
+  a.e1[c] = Q + a.bz[z] * P2;   // dzt-bar (Dmz txz)
+  a.ap[0][c] = a.axh[x] * P1;
+  a.ap[1][c] = a.az[z] * P2;
+  // vz += cbz (dxt + p3' + dzt + p4')
+  const float Qz = a.cbz[pc] * vz;
+  const float P3 = a.ap[2][c] + Qz, P4 = a.ap[3][c] + Qz;
+  a.e2[c] = Qz + a.bx[x] * P3;   // dxt-bar (Dmx txz)
+  a.e3[c] = Qz + a.bzh[z] * P4;  // dzt-bar (Dpz tzz)
+  a.ap[2][c] = a.ax[x] * P3;
+  a.ap[3][c] = a.azh[z] * P4;
+}
+
+// --------------------------------------------------------- velocity, gather
+__global__ void __launch_bounds__(AT) el_adj_vel_sc_kernel(const ElAdjArgs a) {
+  if (*a.status) return;
+  const Geom& g = a.g;
+  const int x = blockIdx.x * AT + threadIdx.x, z = blockIdx.y, s = blockIdx.z;
+  if (x >= g.NX) return;
+  const size_t c = (size_t)s * g.fstride + (size_t)z * g.NXp + x;
+  const Fld d0 = fld(a.e0, g, s), d1 = fld(a.e1, g, s), d2 = fld(a.e2, g, s),
+            d3 = fld(a.e3, g, s);
+  a.atxx[c] -= dmx(d0, z, x);
+  a.atxz[c] -= dpz(d1, z, x) + dpx(d2, z, x);
+  a.atzz[c] -= dmz(d3, z, x);
+}
+
+// ------------------------------------------------------------ chain rule
+__device__ __forceinline__ double mval(const float* model, const Geom& g, int padded, int par,
+                                       int z, int x) {
+  z = min(max(z, 0), g.NZ - 1);
+  x = min(max(x, 0), g.NX - 1);
+  if (padded) return model[((size_t)par * g.NZ + z) * g.NX + x];
+  const int zi = min(max(z - g.P, 0), g.nz - 1), xi = min(max(x - g.P, 0), g.nx - 1);
+  return model[((size_t)par * g.nz + zi) * g.nx + xi];
+}
+__device__ __forceinline__ double mu_at(const float* model, const Geom& g, int padded, int z,
+                                        int x) {
+  const double vs = mval(model, g, padded, 1, z, x);
+  return mval(model, g, padded, 2, z, x) * vs * vs;
+}
+// coefficient adjoint k at padded point (z, x), summed over shots in FP64
+__device__ __forceinline__ double gsum(const float* gacc, const Geom& g, int k, int z, int x) {
+  double t = 0.0;
+  for (int s = 0; s < g.nshot; ++s)
+    t += gacc[((size_t)s * 5 + k) * g.fstride + (size_t)z * g.NXp + x];
+  return t;
+}
+
+__global__ void el_grad_kernel(const Geom g, const float* gacc, const float* model, int padded,
+                               double sc, float* grad, const int* status) {
+  if (*status) return;
+  const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= g.nx) return;
+  const int Z = i + g.P, X = j + g.P;
+  const double vp = mval(model, g, padded, 0, Z, X), vs = mval(model, g, padded, 1, Z, X);
+  const double rho = mval(model, g, padded, 2, Z, X), mu = rho * vs * vs;
+  // lam = rho (vp^2 - 2 vs^2): cl2m = sc (lam + 2 mu), clam = sc lam
+  const double gl2m = gsum(gacc, g, G_L2M, Z, X);
+  const double glam = sc * (gl2m + gsum(gacc, g, G_LAM, Z, X));
+  double gmu = 2.0 * sc * gl2m;
+  double grho = 0.0;
+  // cmu at (pz, px) = sc 4 / sum 1/mu over (pz|pz+1) x (px|px+1), clamped
+  for (int dz = -1; dz <= 0; ++dz)
+    for (int dx = -1; dx <= 0; ++dx) {
+      const int pz = Z + dz, px = X + dx;
+      if (pz < 0 || px < 0) continue;
+      const int pz1 = min(pz + 1, g.NZ - 1), px1 = min(px + 1, g.NX - 1);
+      const int cz[4] = {pz, pz, pz1, pz1}, cx[4] = {px, px1, px, px1};
+      int mult = 0;
+      double inv = 0.0;
+      bool zero = false;
+      for (int k = 0; k < 4; ++k) {
+        const double m = mu_at(model, g, padded, cz[k], cx[k]);
+        if (m == 0.0) zero = true;
+        else inv += 1.0 / m;
+        if (cz[k] == Z && cx[k] == X) ++mult;
+      }
+      if (mult == 0 || zero) continue;
+      const double mxz = 4.0 / inv;
+      gmu += mult * sc * gsum(gacc, g, G_MU, pz, px) * mxz * mxz / (4.0 * mu * mu);
+    }
+  // cbx at (Z, px) = sc 2 / (rho(Z, px) + rho(Z, px+1)), cbz likewise in z
+  for (int dx = -1; dx <= 0; ++dx) {
+    const int px = X + dx;
+    if (px < 0) continue;
+    const int px1 = min(px + 1, g.NX - 1);
+    const int mult = (px == X) + (px1 == X);
+    if (!mult) continue;
+    const double r2 = mval(model, g, padded, 2, Z, px) + mval(model, g, padded, 2, Z, px1);
+    grho += mult * sc * gsum(gacc, g, G_BX, Z, px) * (-2.0 / (r2 * r2));
+  }
+  for (int dz = -1; dz <= 0; ++dz) {
+    const int pz = Z + dz;
+    if (pz < 0) continue;
+    const int pz1 = min(pz + 1, g.NZ - 1);
+    const int mult = (pz == Z) + (pz1 == Z);
+    if (!mult) continue;
+    const double r2 = mval(model, g, padded, 2, pz, X) + mval(model, g, padded, 2, pz1, X);
+    grho += mult * sc * gsum(gacc, g, G_BZ, pz, X) * (-2.0 / (r2 * r2));
+  }
+  const size_t M = (size_t)g.nz * g.nx, o = (size_t)i * g.nx + j;
+  grad[o] = (float)(glam * 2.0 * rho * vp);
+  grad[M + o] = (float)(glam * (-4.0 * rho * vs) + gmu * 2.0 * rho * vs);
+  grad[2 * M + o] = (float)(grho + glam * (vp * vp - 2.0 * vs * vs) + gmu * vs * vs);
+}
+
+}  // namespace
+
+void launch_el_adj_step(const ElAdjArgs& a, cudaStream_t st) {
+  const Geom& g = a.g;
+  const dim3 grid((g.NXp + AT - 1) / AT, g.NZ, g.nshot);
+  int k = 0;
+  if (a.wgrad) {
+    el_adj_src_kernel<<<(g.nshot + 127) / 128, 128, 0, st>>>(a);
+    ++k;
+  }
+  el_adj_str_pt_kernel<<<grid, AT, 0, st>>>(a);
+  el_adj_str_sc_kernel<<<grid, AT, 0, st>>>(a);
+  k += 2;
+  if (a.res && g.nrec > 0) {
+    el_adj_rec_kernel<<<dim3((g.nrec + 127) / 128, g.nshot), 128, 0, st>>>(a);
+    ++k;
+  }
+  el_adj_vel_pt_kernel<<<grid, AT, 0, st>>>(a);
+  el_adj_vel_sc_kernel<<<grid, AT, 0, st>>>(a);
+  note_launches(k + 2);
+}
+
+void launch_el_grad(const Geom& g, const float* gacc, const float* model, int padded, float dx,
+                    float dt, float* grad, const int* status, cudaStream_t st) {
+  const double sc = (double)dt / (double)dx;
+  el_grad_kernel<<<dim3((g.nx + 127) / 128, g.nz), 128, 0, st>>>(g, gacc, model, padded, sc,
+                                                                 grad, status);
+  note_launches(1);
+}
+
+}  // namespace sweep

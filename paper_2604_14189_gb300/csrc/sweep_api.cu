@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 
 #include <atomic>
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -71,6 +72,11 @@ struct Layout {
   size_t el_par[5] = {0, 0, 0, 0, 0};  // elastic coefficients
   size_t el_f[5] = {0, 0, 0, 0, 0};    // vx, vz, txx, tzz, txz
   size_t el_p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // elastic adjoint state (same 13 fields in the same order), scratch, the
+  // per-shot coefficient adjoints, and the checkpoints / segment states of
+  // the forward replay (each a copy of the range [fwd_lo, fwd_hi))
+  size_t el_a = 0, el_e[4] = {0, 0, 0, 0}, el_g = 0, el_ck = 0, el_seg = 0;
+  int el_C = 0, el_ncp = 0;
   size_t fwd_lo = 0, fwd_hi = 0;  // contiguous range of forward fields
   size_t adj_lo = 0, adj_hi = 0;  // contiguous range of adjoint fields
   size_t total = 0;
@@ -147,6 +153,24 @@ Layout layout(const sweep_problem* p, int mode) {
     for (int i = 0; i < 5; ++i) L.el_f[i] = b.take(F);
     for (int i = 0; i < 8; ++i) L.el_p[i] = b.take(F);
     L.fwd_hi = b.off;
+    if (mode == SWEEP_MODE_ADJOINT || mode == SWEEP_MODE_GRADIENT) {
+      L.adj_lo = b.off;
+      L.el_a = b.take(L.fwd_hi - L.fwd_lo);
+      L.adj_hi = b.off;
+      for (int i = 0; i < 4; ++i) L.el_e[i] = b.take(F);
+    }
+    if (mode == SWEEP_MODE_GRADIENT) {
+      // sqrt(nt) checkpoints of the forward state, and one segment of
+      // states replayed from a checkpoint
+      int C = 1;
+      while ((long long)C * C < g.nt) ++C;
+      L.el_C = C;
+      L.el_ncp = (g.nt + C - 1) / C;
+      L.el_g = b.take(5 * F);
+      L.data = b.take(sizeof(float) * (size_t)g.nshot * 2 * g.nrec * g.nt);
+      L.el_ck = b.take((L.fwd_hi - L.fwd_lo) * (size_t)L.el_ncp);
+      L.el_seg = b.take((L.fwd_hi - L.fwd_lo) * (size_t)C);
+    }
     L.total = b.off;
     return L;
   }
@@ -411,14 +435,12 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
   return SWEEP_OK;
 }
 
-// Elastic forward time loop: velocity then stress kernel per step.
-int elastic_forward_loop(const sweep_problem* p, const Layout& L, void* ws, const float* model,
-                         const float* wavelet, const int32_t* src, const int32_t* rec,
-                         float* data, cudaStream_t st) {
-  const Geom g = make_geom(p);
-  cudaMemsetAsync(at<char>(ws, L.fwd_lo), 0, L.fwd_hi - L.fwd_lo, st);
+// Elastic coefficients (once per call) and the step arguments on the
+// forward state starting at `state` (a copy of the range [fwd_lo, fwd_hi)).
+void elastic_params(const sweep_problem* p, const Layout& L, void* ws, const float* model,
+                    cudaStream_t st) {
   ElParamArgs pa{};
-  pa.g = g;
+  pa.g = make_geom(p);
   pa.model = model;
   pa.padded = (p->flags & SWEEP_F_PADDED_MODEL) ? 1 : 0;
   pa.dx = p->dx;
@@ -429,20 +451,30 @@ int elastic_forward_loop(const sweep_problem* p, const Layout& L, void* ws, cons
   pa.clam = at<float>(ws, L.el_par[3]);
   pa.cmu = at<float>(ws, L.el_par[4]);
   launch_el_params(pa, st);
+}
+
+float* state_field(const Layout& L, char* state, int k) {  // k: 0..4 fields, 5..12 p1..p8
+  const size_t off = k < 5 ? L.el_f[k] : L.el_p[k - 5];
+  return reinterpret_cast<float*>(state + (off - L.fwd_lo));
+}
+
+ElStepArgs elastic_step_args(const sweep_problem* p, const Layout& L, void* ws, char* state,
+                             const float* wavelet, const int32_t* src, const int32_t* rec,
+                             float* data) {
   ElStepArgs a{};
-  a.g = g;
-  a.vx = at<float>(ws, L.el_f[0]);
-  a.vz = at<float>(ws, L.el_f[1]);
-  a.txx = at<float>(ws, L.el_f[2]);
-  a.tzz = at<float>(ws, L.el_f[3]);
-  a.txz = at<float>(ws, L.el_f[4]);
+  a.g = make_geom(p);
+  a.vx = state_field(L, state, 0);
+  a.vz = state_field(L, state, 1);
+  a.txx = state_field(L, state, 2);
+  a.tzz = state_field(L, state, 3);
+  a.txz = state_field(L, state, 4);
   float** ps[8] = {&a.p1, &a.p2, &a.p3, &a.p4, &a.p5, &a.p6, &a.p7, &a.p8};
-  for (int i = 0; i < 8; ++i) *ps[i] = at<float>(ws, L.el_p[i]);
-  a.cbx = pa.cbx;
-  a.cbz = pa.cbz;
-  a.cl2m = pa.cl2m;
-  a.clam = pa.clam;
-  a.cmu = pa.cmu;
+  for (int i = 0; i < 8; ++i) *ps[i] = state_field(L, state, 5 + i);
+  a.cbx = at<float>(ws, L.el_par[0]);
+  a.cbz = at<float>(ws, L.el_par[1]);
+  a.cl2m = at<float>(ws, L.el_par[2]);
+  a.clam = at<float>(ws, L.el_par[3]);
+  a.cmu = at<float>(ws, L.el_par[4]);
   a.ax = at<float>(ws, L.ax);
   a.bx = at<float>(ws, L.bx);
   a.axh = at<float>(ws, L.axh);
@@ -458,9 +490,107 @@ int elastic_forward_loop(const sweep_problem* p, const Layout& L, void* ws, cons
   a.data = data;
   a.src_scale = (float)((double)p->dt / ((double)p->dx * p->dx));
   a.status = at<int>(ws, L.status);
+  return a;
+}
+
+// Elastic forward time loop: velocity then stress kernel per step.  With
+// checkpoints (gradient mode) the state before step k C is copied to
+// checkpoint k.
+int elastic_forward_loop(const sweep_problem* p, const Layout& L, void* ws, const float* model,
+                         const float* wavelet, const int32_t* src, const int32_t* rec,
+                         float* data, bool checkpoints, cudaStream_t st) {
+  const Geom g = make_geom(p);
+  char* state = at<char>(ws, L.fwd_lo);
+  const size_t sb = L.fwd_hi - L.fwd_lo;
+  cudaMemsetAsync(state, 0, sb, st);
+  elastic_params(p, L, ws, model, st);
+  ElStepArgs a = elastic_step_args(p, L, ws, state, wavelet, src, rec, data);
   for (int n = 0; n < g.nt; ++n) {
+    if (checkpoints && n % L.el_C == 0)
+      cudaMemcpyAsync(at<char>(ws, L.el_ck) + (size_t)(n / L.el_C) * sb, state, sb,
+                      cudaMemcpyDeviceToDevice, st);
     a.n = n;
     launch_el_step(a, st);
+  }
+  return SWEEP_OK;
+}
+
+// Elastic reverse loop: the transposed steps n = nt-1 .. 0 from the residual
+// (or adjoint data) `res`.  gradient: replays each checkpoint segment of the
+// forward, keeping the state after every step, and accumulates the
+// coefficient adjoints; wgrad: wavelet adjoint.
+int elastic_reverse_loop(const sweep_problem* p, const Layout& L, void* ws, const float* wavelet,
+                         const int32_t* src, const int32_t* rec, const float* res, float* wgrad,
+                         bool gradient, cudaStream_t st) {
+  const Geom g = make_geom(p);
+  const size_t F = sizeof(float) * (size_t)g.fstride * (size_t)g.nshot;
+  char* adj = at<char>(ws, L.el_a);
+  const size_t sb = L.fwd_hi - L.fwd_lo;
+  cudaMemsetAsync(adj, 0, sb, st);
+  ElAdjArgs a{};
+  a.g = g;
+  a.avx = state_field(L, adj, 0);
+  a.avz = state_field(L, adj, 1);
+  a.atxx = state_field(L, adj, 2);
+  a.atzz = state_field(L, adj, 3);
+  a.atxz = state_field(L, adj, 4);
+  for (int i = 0; i < 8; ++i) a.ap[i] = state_field(L, adj, 5 + i);
+  a.e0 = at<float>(ws, L.el_e[0]);
+  a.e1 = at<float>(ws, L.el_e[1]);
+  a.e2 = at<float>(ws, L.el_e[2]);
+  a.e3 = at<float>(ws, L.el_e[3]);
+  a.cbx = at<float>(ws, L.el_par[0]);
+  a.cbz = at<float>(ws, L.el_par[1]);
+  a.cl2m = at<float>(ws, L.el_par[2]);
+  a.clam = at<float>(ws, L.el_par[3]);
+  a.cmu = at<float>(ws, L.el_par[4]);
+  a.ax = at<float>(ws, L.ax);
+  a.bx = at<float>(ws, L.bx);
+  a.axh = at<float>(ws, L.axh);
+  a.bxh = at<float>(ws, L.bxh);
+  a.az = at<float>(ws, L.az);
+  a.bz = at<float>(ws, L.bz);
+  a.azh = at<float>(ws, L.azh);
+  a.bzh = at<float>(ws, L.bzh);
+  a.res = g.nrec > 0 ? res : nullptr;
+  a.src = src;
+  a.rec = rec;
+  a.wgrad = wgrad;
+  a.src_scale = (float)((double)p->dt / ((double)p->dx * p->dx));
+  a.status = at<int>(ws, L.status);
+  if (!gradient) {
+    for (int n = g.nt - 1; n >= 0; --n) {
+      a.n = n;
+      launch_el_adj_step(a, st);
+    }
+    return SWEEP_OK;
+  }
+  a.gacc = at<float>(ws, L.el_g);
+  cudaMemsetAsync(a.gacc, 0, 5 * F, st);
+  char* state = at<char>(ws, L.fwd_lo);
+  char* ck = at<char>(ws, L.el_ck);
+  char* seg = at<char>(ws, L.el_seg);
+  ElStepArgs fs = elastic_step_args(p, L, ws, state, wavelet, src, rec, nullptr);
+  for (int k = L.el_ncp - 1; k >= 0; --k) {
+    const int n0 = k * L.el_C, n1 = std::min(n0 + L.el_C, g.nt);
+    cudaMemcpyAsync(state, ck + (size_t)k * sb, sb, cudaMemcpyDeviceToDevice, st);
+    for (int n = n0; n < n1; ++n) {
+      fs.n = n;
+      launch_el_step(fs, st);
+      cudaMemcpyAsync(seg + (size_t)(n - n0) * sb, state, sb, cudaMemcpyDeviceToDevice, st);
+    }
+    for (int n = n1 - 1; n >= n0; --n) {
+      char* after = seg + (size_t)(n - n0) * sb;
+      char* before = n > n0 ? seg + (size_t)(n - n0 - 1) * sb : ck + (size_t)k * sb;
+      a.fvx = state_field(L, after, 0);
+      a.fvz = state_field(L, after, 1);
+      for (int i = 0; i < 8; ++i) a.fp[i] = state_field(L, after, 5 + i);
+      a.ftxx = state_field(L, before, 2);
+      a.ftzz = state_field(L, before, 3);
+      a.ftxz = state_field(L, before, 4);
+      a.n = n;
+      launch_el_adj_step(a, st);
+    }
   }
   return SWEEP_OK;
 }
@@ -503,7 +633,7 @@ int sweep_forward(const sweep_problem* p, const float* model, const float* wavel
     sa.K = nullptr;  // no acoustic K for the elastic engine
     launch_setup(sa, st);
     rc = elastic_forward_loop(p, L, ws, model, wavelet, src, rec, p->nrec > 0 ? data : nullptr,
-                              st);
+                              false, st);
     if (rc) return rc;
     return cuda_rc(cudaGetLastError());
   }
@@ -523,9 +653,17 @@ int sweep_adjoint(const sweep_problem* p, const float* model, const float* adj_d
   if (!model) return SWEEP_EINVAL;
   if (p->nshot > 0 && (!src || !wavelet_grad)) return SWEEP_EINVAL;
   if (p->nshot > 0 && p->nrec > 0 && (!rec || !adj_data)) return SWEEP_EINVAL;
-  if (p->physics != SWEEP_ACOUSTIC) return SWEEP_EUNSUPPORTED;
   if (p->nshot == 0) return SWEEP_OK;
   const Layout L = layout(p, SWEEP_MODE_ADJOINT);
+  if (p->physics == SWEEP_ELASTIC) {
+    SetupArgs sa = setup_args(p, L, ws, model, src, rec);
+    sa.K = nullptr;
+    launch_setup(sa, st);
+    elastic_params(p, L, ws, model, st);
+    rc = elastic_reverse_loop(p, L, ws, nullptr, src, rec, adj_data, wavelet_grad, false, st);
+    if (rc) return rc;
+    return cuda_rc(cudaGetLastError());
+  }
   launch_setup(setup_args(p, L, ws, model, src, rec), st);
   // no imaging: the backward kernels never read the wavelet
   rc = acoustic_backward_loop(p, L, ws, nullptr, src, rec, adj_data, wavelet_grad, false, false,
@@ -543,15 +681,35 @@ int sweep_gradient(const sweep_problem* p, const float* model, const float* wave
   if (!model || !grad) return SWEEP_EINVAL;
   if (p->nshot > 0 && (!wavelet || !src)) return SWEEP_EINVAL;
   if (p->nshot > 0 && p->nrec > 0 && (!rec || !d_obs)) return SWEEP_EINVAL;
-  if (p->physics != SWEEP_ACOUSTIC) return SWEEP_EUNSUPPORTED;
+  if (p->physics == SWEEP_ELASTIC && illum) return SWEEP_EUNSUPPORTED;
   const Geom g = make_geom(p);
+  const int npar = p->physics == SWEEP_ELASTIC ? 3 : 1;
   if (p->nshot == 0) {
-    cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)g.nz * g.nx, st);
+    cudaMemsetAsync(grad, 0, sizeof(float) * npar * (size_t)g.nz * g.nx, st);
     if (illum) cudaMemsetAsync(illum, 0, sizeof(float) * (size_t)g.nz * g.nx, st);
     if (misfit) cudaMemsetAsync(misfit, 0, sizeof(double), st);
     return cuda_rc(cudaGetLastError());
   }
   const Layout L = layout(p, SWEEP_MODE_GRADIENT);
+  if (p->physics == SWEEP_ELASTIC) {
+    SetupArgs sa = setup_args(p, L, ws, model, src, rec);
+    sa.K = nullptr;
+    launch_setup(sa, st);
+    float* d = at<float>(ws, L.data);
+    rc = elastic_forward_loop(p, L, ws, model, wavelet, src, rec, p->nrec > 0 ? d : nullptr,
+                              true, st);
+    if (rc) return rc;
+    const long long nd = (long long)g.nshot * 2 * g.nrec * g.nt;
+    launch_residual_misfit(d, d_obs, d, nd, (p->flags & SWEEP_F_RESIDUAL_IN) ? 1 : 0,
+                           at<double>(ws, L.partial), RED_BLOCKS, misfit, at<int>(ws, L.status),
+                           st);
+    note_launches(2);
+    rc = elastic_reverse_loop(p, L, ws, wavelet, src, rec, d, nullptr, true, st);
+    if (rc) return rc;
+    launch_el_grad(g, at<float>(ws, L.el_g), model, (p->flags & SWEEP_F_PADDED_MODEL) ? 1 : 0,
+                   p->dx, p->dt, grad, at<int>(ws, L.status), st);
+    return cuda_rc(cudaGetLastError());
+  }
   launch_setup(setup_args(p, L, ws, model, src, rec), st);
   float* d = at<float>(ws, L.data);
   rc = acoustic_forward_loop(p, L, ws, wavelet, src, rec, p->nrec > 0 ? d : nullptr, true, st);

@@ -225,12 +225,14 @@ def sweep_adjoint(p: Problem, model, adj_data, src, rec, wavelet_grad=None, ws=N
 
 def sweep_gradient(p: Problem, model, wavelet, src, rec, d_obs, grad=None, misfit=None,
                    illum=None, want_illum=False, ws=None, stream=None, sync=True):
-    """Returns (grad [nz][nx], misfit (device float64 scalar), illum or None)."""
+    """Returns (grad, misfit (device float64 scalar), illum or None); grad is
+    [nz][nx] (acoustic: d J / d vp) or [3][nz][nx] (elastic: vp, vs, rho)."""
     _check_dtype(model, torch.float32, "model")
     _check_dtype(d_obs, torch.float32, "d_obs")
     dev = model.device
     if grad is None:
-        grad = torch.empty((p.nz, p.nx), dtype=torch.float32, device=dev)
+        shape = (3, p.nz, p.nx) if p.physics == ELASTIC else (p.nz, p.nx)
+        grad = torch.empty(shape, dtype=torch.float32, device=dev)
     if misfit is None:
         misfit = torch.empty((), dtype=torch.float64, device=dev)
     if illum is None and want_illum:
