@@ -371,6 +371,173 @@ def run_sweep(args, w, rank, world, local_rank):
     print(json.dumps(out), flush=True)
 
 
+# -------------------------------------------------------------------- elastic
+def alg_bytes_elastic_fwd(c):
+    """Algorithmic bytes of one fused elastic step per shot: 5 fields read and
+    written, 5 coefficients read, 4 memory variables read and written per
+    strip cell per axis."""
+    return 60 * c["N_pad"] + 32 * (c["N_x"] + c["N_z"])
+
+
+def run_elastic(args, rank, world, local_rank):
+    """Elastic forward (isotropic velocity-stress, 500 x 1500 + 40, 64 shots,
+    nt 4000, 750 receivers) or elastic gradient (same grid, 8 shots,
+    nt = --nt or 1000: the checkpointed replay keeps sqrt(nt) forward
+    states per shot in HBM)."""
+    import torch
+
+    from paper_2604_14189_gb300 import sweep
+
+    grad_mode = args.workload == "elastic-gradient"
+    nshot = 8 if grad_mode else 64
+    nt = args.nt if args.nt != 3000 else (1000 if grad_mode else 4000)
+    w = inputs.workload_elastic(nshot=nshot, nt=nt)
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    nrec = w["rec"].shape[1]
+    p = sweep.problem(sweep.ELASTIC, nz=w["nz"], nx=w["nx"], pml=w["pml"], dx=w["dx"],
+                      dt=w["dt"], nt=nt, nshot=nshot, nrec=nrec, f_ref=w["f0"])
+    wav_h = np.stack([inputs.ricker(w["f0"], w["dt"], nt)] * nshot).astype(np.float32)
+    model = torch.tensor(w["model"], dtype=torch.float32, device=dev)
+    wav = torch.tensor(wav_h, device=dev)
+    src = torch.tensor(w["src"], device=dev)
+    rec = torch.tensor(w["rec"], device=dev)
+    stream = torch.cuda.current_stream(dev)
+    c = counts(w["nz"], w["nx"], w["pml"])
+    if grad_mode:
+        m_true = w["model"].copy()
+        m_true[:, 150:250, 500:900] *= 1.03
+        d_obs = sweep.sweep_forward(p, torch.tensor(m_true, dtype=torch.float32, device=dev),
+                                    wav, src, rec)
+        ws = sweep.alloc_workspace(p, sweep.MODE_GRADIENT, dev)
+        grad = torch.empty((3, w["nz"], w["nx"]), dtype=torch.float32, device=dev)
+        mis = torch.empty((), dtype=torch.float64, device=dev)
+
+        def step():
+            sweep.sweep_gradient(p, model, wav, src, rec, d_obs, grad=grad, misfit=mis, ws=ws,
+                                 sync=False)
+    else:
+        ws = sweep.alloc_workspace(p, sweep.MODE_FORWARD, dev)
+        data = torch.empty((nshot, 2, nrec, nt), dtype=torch.float32, device=dev)
+
+        def step():
+            sweep.sweep_forward(p, model, wav, src, rec, data=data, ws=ws, sync=False)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    st = sweep.status(ws)
+    if st != sweep.OK:
+        raise sweep.SweepError(st, "warm-up")
+    sampler = ClockSampler(local_rank)
+    l0 = sweep.kernel_launches()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()  # inputs (4.6 GB of fields per step) exceed L2
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = sweep.kernel_launches() - l0
+    ms_step = e0.elapsed_time(e1) / args.steps
+    if sweep.status(ws) != sweep.OK:
+        raise sweep.SweepError(sweep.status(ws), "timed region")
+    value = c["N_pad"] * nt * nshot / (ms_step * 1e-3) / 1e9
+    # per-step kernel time of the forward (velocity + stress kernels)
+    sweep.profile_enable((1 << sweep.K_EL_VEL) | (1 << sweep.K_EL_STR))
+    if not grad_mode:
+        step()
+    else:
+        sweep.sweep_forward(p, model, wav, src, rec)
+    torch.cuda.synchronize()
+    vms, vn = sweep.profile_read(sweep.K_EL_VEL)
+    sms, sn = sweep.profile_read(sweep.K_EL_STR)
+    sweep.profile_enable(False)
+    step_ms = vms / max(vn, 1) + sms / max(sn, 1)
+    peak, peak_src = peaks()
+    achieved = alg_bytes_elastic_fwd(c) * nshot / (step_ms * 1e-3) / 1e9
+    # end to end with host buffers
+    model_h = torch.tensor(w["model"], dtype=torch.float32).pin_memory()
+    wav_hh = torch.tensor(wav_h).pin_memory()
+    if grad_mode:
+        dob_h = d_obs.cpu().pin_memory()
+        grad_h = torch.empty_like(grad, device="cpu").pin_memory()
+        bufs = [torch.empty_like(t, device=dev) for t in (model_h, wav_hh, dob_h)]
+        h2d = sum(t.numel() * t.element_size() for t in (model_h, wav_hh, dob_h))
+        d2h = grad_h.numel() * 4 + 8
+
+        def e2e():
+            for dst, sb in zip(bufs, (model_h, wav_hh, dob_h)):
+                dst.copy_(sb, non_blocking=True)
+            sweep.sweep_gradient(p, bufs[0], bufs[1], src, rec, bufs[2], grad=grad, misfit=mis,
+                                 ws=ws, sync=False)
+            grad_h.copy_(grad, non_blocking=True)
+    else:
+        data_h = torch.empty_like(data, device="cpu").pin_memory()
+        bufs = [torch.empty_like(t, device=dev) for t in (model_h, wav_hh)]
+        h2d = sum(t.numel() * t.element_size() for t in (model_h, wav_hh))
+        d2h = data_h.numel() * 4
+
+        def e2e():
+            for dst, sb in zip(bufs, (model_h, wav_hh)):
+                dst.copy_(sb, non_blocking=True)
+            sweep.sweep_forward(p, bufs[0], bufs[1], src, rec, data=data, ws=ws, sync=False)
+            data_h.copy_(data, non_blocking=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    e2e()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = c["N_pad"] * nt * nshot / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        cores = os.cpu_count() or 1
+        oracle.set_threads(cores)
+        ns_s, nt_s = (2, 30) if grad_mode else (4, 30)
+        q = oracle.make_problem(1, w["nz"], w["nx"], w["pml"], w["dx"], w["dt"], nt_s, ns_s,
+                                nrec, w["f0"], v_pml=5000.0)
+        wv = np.stack([inputs.ricker(w["f0"], w["dt"], nt_s)] * ns_s)
+        t = time.perf_counter()
+        if grad_mode:
+            oracle.elastic_gradient(q, w["model"], wv, w["src"][:ns_s], w["rec"][:ns_s],
+                                    np.zeros((ns_s, 2, nrec, nt_s)))
+        else:
+            oracle.elastic_forward(q, w["model"], wv, w["src"][:ns_s], w["rec"][:ns_s])
+        el = time.perf_counter() - t
+        cpu = {"value": c["N_pad"] * nt_s * ns_s / el / 1e9, "unit": "Gpts/s",
+               "cores": min(cores, ns_s), "kind": "oracle",
+               "sample": f"oracle elastic {'gradient' if grad_mode else 'forward'}, "
+                         f"{ns_s} shots x {nt_s} steps of the same grid ({el:.1f} s)"}
+    metric = "Gpts/s elastic fwd+adj" if grad_mode else "Gpts/s elastic fwd"
+    out = {
+        "metric": metric, "value": value, "unit": "Gpts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"elastic {'gradient' if grad_mode else 'forward'} "
+                               f"{w['nz']}x{w['nx']} + {w['pml']}-cell CPML, dx 5 m, dt 0.5 ms, "
+                               f"nt {nt}, {nshot} shots, {nrec} receivers (vx, vz), 15 Hz "
+                               f"explosive Ricker",
+                   "l2": "fields of all shots (%.1f GB) exceed L2" % (ws.numel() / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "elastic forward step (velocity + stress kernels)",
+                     "peak_source": peak_src,
+                     "alg_bytes_per_launch": alg_bytes_elastic_fwd(c) * nshot,
+                     "avg_launch_ms": step_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "Gpts/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -379,6 +546,10 @@ def main():
     ap.add_argument("--impl", choices=["sweep", "reference"], default="sweep")
     ap.add_argument("--nt", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="acoustic-gradient",
+                    choices=["acoustic-gradient", "elastic-forward", "elastic-gradient"],
+                    help="acoustic-gradient is the headline; the elastic workloads are "
+                         "measured on request")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -386,6 +557,11 @@ def main():
     w = inputs.workload_marmousi(nshot=20, nt=args.nt)
     if args.impl == "reference":
         run_reference(args, w, rank)
+        return
+    if args.workload != "acoustic-gradient":
+        if world > 1 and rank != 0:
+            return  # one GPU per box: the elastic workloads run as rank 0 only
+        run_elastic(args, rank, 1, local_rank)
         return
     if world > 1:
         import torch
