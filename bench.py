@@ -538,6 +538,80 @@ def run_elastic(args, rank, world, local_rank):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------------ fwi
+def run_fwi(args, local_rank):
+    """Plain (illumination-preconditioned) FWI: 20 iterations on the seeded
+    256 x 256 layered + anomaly model, 16 shots, nt 1500.  The relative model
+    error after 20 plain iterations is the target error of the comparison
+    with a learned preconditioner; value = seconds to reach it."""
+    import torch
+
+    from paper_2604_14189_gb300 import fwi, sweep
+
+    w = inputs.workload_fwi()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    nshot, nt, nrec = w["src"].shape[0], w["nt"], w["rec"].shape[1]
+    p = sweep.problem(nz=w["nz"], nx=w["nx"], pml=w["pml"], dx=w["dx"], dt=w["dt"], nt=nt,
+                      nshot=nshot, nrec=nrec, f_ref=w["f0"], v_pml=4500.0)
+    wav = torch.tensor(np.stack([inputs.ricker(w["f0"], w["dt"], nt)] * nshot),
+                       dtype=torch.float32, device=dev)
+    src = torch.tensor(w["src"], device=dev)
+    rec = torch.tensor(w["rec"], device=dev)
+    vt = torch.tensor(w["v_true"], dtype=torch.float32, device=dev)
+    d_obs = sweep.sweep_forward(p, vt, wav, src, rec)
+    inv = fwi.Fwi(p, wav, src, rec, d_obs)
+    m0 = torch.tensor(w["model"], dtype=torch.float32, device=dev)
+    cfg = fwi.FwiConfig(iterations=20, step=50.0, vmin=1400.0, vmax=4700.0)
+    for _ in range(max(args.warmup, 0)):
+        inv.gradient(m0)
+    sampler = ClockSampler(local_rank)
+    l0 = sweep.kernel_launches()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = time.perf_counter()
+    model, hist = inv.run(m0, cfg)
+    torch.cuda.synchronize()
+    seconds = time.perf_counter() - t0
+    clocks = sampler.stop()
+    launches = sweep.kernel_launches() - l0
+    e0 = float((m0 - vt).norm() / vt.norm())
+    e1 = float((model - vt).norm() / vt.norm())
+    c = counts(w["nz"], w["nx"], w["pml"])
+    sweep.profile_enable(1 << sweep.K_AC_BWD)
+    inv.gradient(model)
+    torch.cuda.synchronize()
+    bms, bn = sweep.profile_read(sweep.K_AC_BWD)
+    sweep.profile_enable(False)
+    peak, peak_src = peaks()
+    achieved = alg_bytes_bwd(c) * nshot / (bms / max(bn, 1) * 1e-3) / 1e9
+    grads = len(hist)
+    trials = sum(h["trials"] for h in hist)
+    out = {
+        "metric": "FWI s to target model error (plain)", "value": seconds, "unit": "s",
+        "n_gpus": 1, "steps": grads, "warmup": args.warmup,
+        "ms_per_step": seconds * 1e3 / max(grads, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "plain illumination-preconditioned FWI, 20 iterations, "
+                               f"{w['nz']}x{w['nx']} + {w['pml']}-cell CPML, dx 10 m, nt {nt}, "
+                               f"{nshot} shots, {nrec} receivers, 10 Hz",
+                   "model_error_initial": e0, "model_error_final": e1,
+                   "misfit_initial": hist[0]["misfit"], "misfit_final": hist[-1]["misfit_after"],
+                   "gradients": grads, "line_search_forwards": trials,
+                   "step": "a gradient (step) plus its line-search forwards"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "acoustic backward time step (as in the headline workload)",
+                     "peak_source": peak_src, "avg_launch_ms": bms / max(bn, 1)},
+        "cpu_baseline": None,
+        "e2e": {"value": seconds, "unit": "s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -547,7 +621,7 @@ def main():
     ap.add_argument("--nt", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="acoustic-gradient",
-                    choices=["acoustic-gradient", "elastic-forward", "elastic-gradient"],
+                    choices=["acoustic-gradient", "elastic-forward", "elastic-gradient", "fwi"],
                     help="acoustic-gradient is the headline; the elastic workloads are "
                          "measured on request")
     args = ap.parse_args()
@@ -560,8 +634,11 @@ def main():
         return
     if args.workload != "acoustic-gradient":
         if world > 1 and rank != 0:
-            return  # one GPU per box: the elastic workloads run as rank 0 only
-        run_elastic(args, rank, 1, local_rank)
+            return  # one GPU per box: these workloads run as rank 0 only
+        if args.workload == "fwi":
+            run_fwi(args, local_rank)
+        else:
+            run_elastic(args, rank, 1, local_rank)
         return
     if world > 1:
         import torch

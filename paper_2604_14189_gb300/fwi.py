@@ -1,0 +1,113 @@
+"""Full-waveform inversion loop over the C ABI.
+
+FWI is the inversion use of the solver (Sec. 1; the FWI examples of Sec. 3):
+update the velocity model along the negative misfit gradient until the
+modelled data fit the observed data.  This module runs that loop with
+
+* the gradient and the illumination I = sum over shots and steps of u^2
+  from one ``sweep_gradient`` call (the illumination is accumulated inside
+  the backward stencil kernel);
+* the illumination-preconditioned direction d = -g / (I + eps max I),
+  scaled so that max |d| = 1 (a step is then a velocity change in m/s);
+* a backtracking line search with misfit confirmation: a trial model is
+  accepted only if the solver's misfit of that model is lower than the
+  current one; otherwise the step is halved (at most ``max_halvings`` times)
+  and the model is kept if no trial improves;
+* a bound constraint vmin <= v <= vmax on every trial.
+
+The misfit of a trial model is J = 1/2 |d - d_obs|^2 from ``sweep_forward``
+and three FP64 dot products of the library (no host round trip of the data).
+The line search and the preconditioner are host logic, testable without a
+GPU (``line_search`` takes any misfit function).
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from typing import Callable
+
+import torch
+
+from . import sweep
+
+
+@dataclasses.dataclass
+class FwiConfig:
+    iterations: int = 20
+    step: float = 50.0       # first trial: largest velocity change, m/s
+    eps: float = 1e-2        # illumination stabiliser, relative to max I
+    vmin: float = 1000.0
+    vmax: float = 6000.0
+    max_halvings: int = 5
+    grow: float = 1.5        # step growth after a first-trial acceptance
+
+
+def precondition(grad: torch.Tensor, illum: torch.Tensor, eps: float) -> torch.Tensor:
+    """Descent direction -g / (I + eps max I), scaled to max |d| = 1."""
+    d = -grad / (illum + eps * illum.max())
+    m = d.abs().max()
+    return d / m if float(m) > 0 else d
+
+
+def line_search(misfit: Callable[[torch.Tensor], float], model: torch.Tensor,
+                direction: torch.Tensor, j0: float, step: float, max_halvings: int,
+                vmin: float, vmax: float):
+    """Backtracking with misfit confirmation.  Returns (model, misfit, step
+    of the accepted trial (or the last tried), trials, accepted)."""
+    for k in range(max_halvings + 1):
+        trial = (model + step * direction).clamp_(vmin, vmax)
+        j = misfit(trial)
+        if j < j0:
+            return trial, j, step, k + 1, True
+        step *= 0.5
+    return model, j0, step, max_halvings + 1, False
+
+
+class Fwi:
+    """FWI of one acoustic problem: fixed geometry, wavelets and observed data."""
+
+    def __init__(self, problem: sweep.Problem, wavelet, src, rec, d_obs):
+        self.p = problem
+        self.wavelet, self.src, self.rec, self.d_obs = wavelet, src, rec, d_obs
+        dev = d_obs.device
+        self.ws_g = sweep.alloc_workspace(problem, sweep.MODE_GRADIENT, dev)
+        self.ws_f = sweep.alloc_workspace(problem, sweep.MODE_FORWARD, dev)
+        self.data = torch.empty_like(d_obs)
+        self.dd_obs = float(sweep.sweep_dot(d_obs.reshape(-1), d_obs.reshape(-1)))
+
+    def misfit(self, model: torch.Tensor) -> float:
+        """J = 1/2 (<d, d> - 2 <d, d_obs> + <d_obs, d_obs>), FP64 sums."""
+        d = sweep.sweep_forward(self.p, model, self.wavelet, self.src, self.rec, data=self.data,
+                                ws=self.ws_f)
+        dd = float(sweep.sweep_dot(d.reshape(-1), d.reshape(-1)))
+        do = float(sweep.sweep_dot(d.reshape(-1), self.d_obs.reshape(-1)))
+        return 0.5 * (dd - 2.0 * do + self.dd_obs)
+
+    def gradient(self, model: torch.Tensor):
+        g, j, illum = sweep.sweep_gradient(self.p, model, self.wavelet, self.src, self.rec,
+                                           self.d_obs, want_illum=True, ws=self.ws_g)
+        return g, float(j), illum
+
+    def run(self, model0: torch.Tensor, cfg: FwiConfig,
+            callback: Callable[[int, torch.Tensor, dict], None] | None = None):
+        """Returns (model, history); history[i] = dict(misfit, step, trials,
+        accepted, seconds) of iteration i (misfit before the update)."""
+        model = model0.clone().contiguous()
+        step = cfg.step
+        history = []
+        t0 = time.perf_counter()
+        for it in range(cfg.iterations):
+            g, j, illum = self.gradient(model)
+            d = precondition(g, illum, cfg.eps)
+            model, jn, used, trials, ok = line_search(self.misfit, model, d, j, step,
+                                                     cfg.max_halvings, cfg.vmin, cfg.vmax)
+            model = model.contiguous()
+            step = used * (cfg.grow if ok and trials == 1 else 1.0)
+            rec = dict(misfit=j, misfit_after=jn, step=used, trials=trials, accepted=ok,
+                       seconds=time.perf_counter() - t0)
+            history.append(rec)
+            if callback is not None:
+                callback(it, model, rec)
+            if not ok:
+                break
+        return model, history

@@ -133,3 +133,16 @@ def workload_elastic(nshot: int = 64, nt: int = 4000, seed: int = 1002,
     rec = surface_line(nshot, 2, np.arange(0, nx, 2))
     return dict(nz=nz, nx=nx, pml=40, dx=5.0, dt=5e-4, nt=nt, f0=15.0,
                 model=m, src=src, rec=rec)
+
+
+def workload_fwi(seed: int = 1004, n: int = 256, nshot: int = 16, nt: int = 1500):
+    """FWI on a seeded n x n layered + Gaussian-anomaly model (the generator
+    of the 301 x 901 workload), dx = 10 m, nt = 1500, 16 surface shots,
+    receivers at every surface cell, 10 Hz; starting model = the true model
+    blurred with a 40-cell Gaussian."""
+    v_true, v0 = marmousi_like(n, n, seed)
+    sx = np.round(np.linspace(0, n - 1, nshot)).astype(np.int32)
+    src = np.stack([np.full_like(sx, 2), sx], axis=-1).astype(np.int32)
+    rec = surface_line(nshot, 2, np.arange(0, n))
+    return dict(nz=n, nx=n, pml=40, dx=10.0, dt=1e-3, nt=nt, f0=10.0,
+                v_true=v_true, model=v0, src=src, rec=rec)
