@@ -490,6 +490,7 @@ ElStepArgs elastic_step_args(const sweep_problem* p, const Layout& L, void* ws, 
   a.data = data;
   a.src_scale = (float)((double)p->dt / ((double)p->dx * p->dx));
   a.status = at<int>(ws, L.status);
+  if (!el_step_maps(a)) a.units = -1;  // reported by the callers
   return a;
 }
 
@@ -505,6 +506,7 @@ int elastic_forward_loop(const sweep_problem* p, const Layout& L, void* ws, cons
   cudaMemsetAsync(state, 0, sb, st);
   elastic_params(p, L, ws, model, st);
   ElStepArgs a = elastic_step_args(p, L, ws, state, wavelet, src, rec, data);
+  if (a.units < 0) return SWEEP_ECUDA;
   for (int n = 0; n < g.nt; ++n) {
     if (checkpoints && n % L.el_C == 0)
       cudaMemcpyAsync(at<char>(ws, L.el_ck) + (size_t)(n / L.el_C) * sb, state, sb,
@@ -571,6 +573,7 @@ int elastic_reverse_loop(const sweep_problem* p, const Layout& L, void* ws, cons
   char* ck = at<char>(ws, L.el_ck);
   char* seg = at<char>(ws, L.el_seg);
   ElStepArgs fs = elastic_step_args(p, L, ws, state, wavelet, src, rec, nullptr);
+  if (fs.units < 0) return SWEEP_ECUDA;
   for (int k = L.el_ncp - 1; k >= 0; --k) {
     const int n0 = k * L.el_C, n1 = std::min(n0 + L.el_C, g.nt);
     cudaMemcpyAsync(state, ck + (size_t)k * sb, sb, cudaMemcpyDeviceToDevice, st);

@@ -152,10 +152,17 @@ struct ElStepArgs {
   const int32_t* rbox;
   float* data;                             // [S][2][R][nt] or null
   float src_scale;                         // dt / dx^2
-  const int* status;
+  int* status;
   int n;
+  // TMA descriptors (built by el_step_maps): stress fields with the halos
+  // the velocity kernel needs, velocities with both halos, coefficients
+  CUtensorMap m_txx, m_txz, m_tzz, m_vx, m_vz;
+  CUtensorMap m_cbx, m_cbz, m_l2m, m_lam, m_mu;
+  int units, ntx;  // (tile, shot) units of the persistent kernels
 };
 void launch_el_params(const ElParamArgs& a, cudaStream_t st);
+// Fills the descriptors and the unit count of `a` (false on a driver error).
+bool el_step_maps(ElStepArgs& a);
 void launch_el_step(const ElStepArgs& a, cudaStream_t st);
 
 // Elastic adjoint step (elastic_adjoint.cu): the transpose of one
