@@ -253,9 +253,11 @@ def test_edge_cases(sw):
     d = sw.sweep_forward(p, v, w, src, rec).cpu().numpy()[:, 0]
     ref = oracle.acoustic_forward(q, f32(c["v"]), f32(c["w"]), c["src"], c["rec"])
     assert rel(d, ref) <= 1e-4
-    # elastic adjoint is not provided
+    # the illumination output is acoustic only
     pe = sw.problem(sw.ELASTIC, nz=30, nx=40, pml=5, dx=10.0, dt=1e-3, nt=100, nshot=2, nrec=4)
+    me = torch.stack([torch.full((30, 40), 2000.0), torch.full((30, 40), 1000.0),
+                      torch.full((30, 40), 2000.0)]).cuda()
     with pytest.raises(sw.SweepError) as e:
-        sw.sweep_adjoint(pe, torch.ones((3, 30, 40), device="cuda"), torch.zeros((2, 2, 4, 100),
-                         device="cuda"), src, rec)
+        sw.sweep_gradient(pe, me, torch.zeros((2, 100), device="cuda"), src, rec,
+                          torch.zeros((2, 2, 4, 100), device="cuda"), want_illum=True)
     assert e.value.code == sw.EUNSUPPORTED
