@@ -612,6 +612,69 @@ def run_fwi(args, local_rank):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------- batch
+def run_batch(args, local_rank):
+    """Heterogeneous batch: 256 seeded layered models of uneven size, border,
+    record length and shot count, forward + adjoint gradient of 1/2 |d|^2
+    each, run concurrently (batch.run); value = padded cell-steps of the
+    whole batch / wall time."""
+    import torch
+
+    from paper_2604_14189_gb300 import batch, sweep
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    items = []
+    cells = 0
+    for w in inputs.workload_batch():
+        ns, nrec, nt = w["src"].shape[0], w["rec"].shape[1], w["nt"]
+        p = sweep.problem(nz=w["nz"], nx=w["nx"], pml=w["pml"], dx=w["dx"], dt=w["dt"], nt=nt,
+                          nshot=ns, nrec=nrec, f_ref=w["f0"])
+        items.append(batch.Item(
+            p, torch.tensor(w["model"], dtype=torch.float32, device=dev),
+            torch.tensor(np.stack([inputs.ricker(w["f0"], w["dt"], nt)] * ns),
+                         dtype=torch.float32, device=dev),
+            torch.tensor(w["src"], device=dev), torch.tensor(w["rec"], device=dev),
+            d_obs=torch.zeros((ns, 1, nrec, nt), dtype=torch.float32, device=dev)))
+        cells += batch.cost(p)
+    # schedule autotuning on a sample of the batch
+    best, times = batch.autotune_streams(items[:48], candidates=(4, 8, 16))
+    for _ in range(max(args.warmup, 0)):
+        batch.run(items, streams=best)
+    sampler = ClockSampler(local_rank)
+    l0 = sweep.kernel_launches()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        codes = batch.run(items, streams=best)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / args.steps
+    clocks = sampler.stop()
+    launches = sweep.kernel_launches() - l0
+    if any(codes):
+        raise RuntimeError(f"batch errors: {sorted(set(codes))}")
+    value = cells / sec / 1e9
+    out = {
+        "metric": "Gpts/s fwd+adj (heterogeneous batch)", "value": value, "unit": "Gpts/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "256 seeded layered models, interior 128..512 squared (uneven), "
+                               "20..40-cell CPML, nt 800..3000, 1..8 shots, gradient of "
+                               "1/2 |d|^2 each", "padded_cell_steps": cells,
+                   "streams": best, "autotune_seconds": times,
+                   "step": "one pass over the whole batch"},
+        "roofline": None,
+        "cpu_baseline": None,
+        "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 4 * len(items)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -621,7 +684,8 @@ def main():
     ap.add_argument("--nt", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="acoustic-gradient",
-                    choices=["acoustic-gradient", "elastic-forward", "elastic-gradient", "fwi"],
+                    choices=["acoustic-gradient", "elastic-forward", "elastic-gradient", "fwi",
+                             "batch"],
                     help="acoustic-gradient is the headline; the elastic workloads are "
                          "measured on request")
     args = ap.parse_args()
@@ -637,6 +701,8 @@ def main():
             return  # one GPU per box: these workloads run as rank 0 only
         if args.workload == "fwi":
             run_fwi(args, local_rank)
+        elif args.workload == "batch":
+            run_batch(args, local_rank)
         else:
             run_elastic(args, rank, 1, local_rank)
         return

@@ -1,0 +1,139 @@
+"""Heterogeneous batches: many independent acoustic problems of uneven grid
+size, border width, record length and shot count in one call.
+
+Batch modelling is the shot / model dimension of Sec. 2.2; the paper also
+runs several velocity models at once.  Here every problem keeps its own
+geometry and time loop, and the batch is made to fill the GPU by running
+problems concurrently:
+
+* each problem's stencil kernels are persistent with a grid of
+  min(#SMs, work units), so a small problem occupies only some SMs and the
+  others are free for concurrent problems;
+* problems are dealt to ``streams`` CUDA streams, longest first, each to the
+  stream with the least work queued so far (LPT list scheduling, within 4/3
+  of the optimal makespan); the cost of a problem is its padded cell-steps
+  (padded cells x nt x shots);
+* every stream is fed by its own host thread: the C ABI releases the GIL,
+  so the launches of the streams are issued in parallel and the host does
+  not become the bottleneck of thousands of short time steps;
+* a stream reuses one workspace (sized for its largest problem), and after
+  every problem the library's status word is copied to a per-problem slot,
+  so an error is attributed to its problem without synchronising.
+
+``autotune_streams`` times the batch (or a sample of it) for a few stream
+counts and returns the fastest: the schedule, not the kernels, is what
+varies between batches.
+"""
+from __future__ import annotations
+
+import dataclasses
+import threading
+import time
+
+import torch
+
+from . import sweep
+
+
+@dataclasses.dataclass
+class Item:
+    """One problem: inputs on the GPU; outputs filled by ``run``."""
+    problem: sweep.Problem
+    model: torch.Tensor
+    wavelet: torch.Tensor
+    src: torch.Tensor
+    rec: torch.Tensor
+    d_obs: torch.Tensor | None = None   # gradient mode
+    grad: torch.Tensor | None = None    # out (gradient mode)
+    misfit: torch.Tensor | None = None  # out (gradient mode)
+    data: torch.Tensor | None = None    # out (forward mode)
+
+
+def cost(p: sweep.Problem) -> int:
+    """Padded cell-steps of a problem (the unit of work of the solver)."""
+    return (p.nz + 2 * p.pml) * (p.nx + 2 * p.pml) * p.nt * p.nshot
+
+
+def schedule(costs, nstreams: int) -> list[list[int]]:
+    """Longest-processing-time-first list scheduling of jobs on nstreams
+    identical machines; returns the job indices of each stream, in order."""
+    if nstreams < 1:
+        raise ValueError("nstreams >= 1")
+    queues: list[list[int]] = [[] for _ in range(nstreams)]
+    load = [0] * nstreams
+    for j in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        k = min(range(nstreams), key=lambda s: (load[s], s))
+        queues[k].append(j)
+        load[k] += costs[j]
+    return queues
+
+
+def run(items: list[Item], mode: int = sweep.MODE_GRADIENT, streams: int = 8,
+        device=None) -> list[int]:
+    """Runs every item; returns the status code of each (0 = ok).  Outputs
+    are allocated on first use and written in place."""
+    device = torch.device(device or "cuda")
+    if not items:
+        return []
+    for it in items:
+        if mode == sweep.MODE_GRADIENT:
+            if it.grad is None:
+                it.grad = torch.empty((it.problem.nz, it.problem.nx), dtype=torch.float32,
+                                      device=device)
+            if it.misfit is None:
+                it.misfit = torch.empty((), dtype=torch.float64, device=device)
+        elif mode == sweep.MODE_FORWARD and it.data is None:
+            it.data = torch.empty((it.problem.nshot, 1, it.problem.nrec, it.problem.nt),
+                                  dtype=torch.float32, device=device)
+    queues = [q for q in schedule([cost(it.problem) for it in items], streams) if q]
+    codes = torch.zeros(len(items), dtype=torch.int32, device=device)
+    errors: list[BaseException] = []
+
+    def worker(queue, stream):
+        try:
+            nbytes = max(sweep.workspace_bytes(items[i].problem, mode) for i in queue)
+            with torch.cuda.stream(stream):
+                ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+                off = (-ws.data_ptr()) % 256
+                ws = ws[off:off + nbytes]
+                for i in queue:
+                    it = items[i]
+                    if mode == sweep.MODE_GRADIENT:
+                        sweep.sweep_gradient(it.problem, it.model, it.wavelet, it.src, it.rec,
+                                             it.d_obs, grad=it.grad, misfit=it.misfit, ws=ws,
+                                             stream=stream, sync=False)
+                    else:
+                        sweep.sweep_forward(it.problem, it.model, it.wavelet, it.src, it.rec,
+                                            data=it.data, ws=ws, stream=stream, sync=False)
+                    # the status word leads the workspace
+                    codes[i:i + 1].copy_(ws[:4].view(torch.int32), non_blocking=True)
+        except BaseException as e:  # reported after the join
+            errors.append(e)
+
+    pool = [torch.cuda.Stream(device=device) for _ in queues]
+    for s in pool:  # inputs made on the current stream are ready first
+        s.wait_stream(torch.cuda.current_stream(device))
+    threads = [threading.Thread(target=worker, args=(q, s)) for q, s in zip(queues, pool)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for s in pool:
+        s.synchronize()
+    if errors:
+        raise errors[0]
+    return [int(c) for c in codes.cpu()]
+
+
+def autotune_streams(items: list[Item], candidates=(2, 4, 8, 16),
+                     mode: int = sweep.MODE_GRADIENT, device=None):
+    """Times ``run`` for each stream count; returns (best, {count: seconds})."""
+    times = {}
+    for n in candidates:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run(items, mode, n, device)
+        torch.cuda.synchronize()
+        times[n] = time.perf_counter() - t0
+    best = min(times, key=lambda n: (times[n], n))
+    return best, times

@@ -433,24 +433,23 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
 }  // namespace
 
 int device_sms() {
-  static int n = 0;
-  if (n == 0) {
+  static const int n = [] {  // thread-safe one-time initialisation
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    n = v > 0 ? v : 1;
-  }
+    return v > 0 ? v : 1;
+  }();
   return n;
 }
 
 void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st) {
   if (a.units <= 0) return;
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {  // thread-safe one-time initialisation
     cudaFuncSetAttribute(ac_in_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kFwdSmem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   int grid = device_sms();
   if (grid > a.units) grid = a.units;
   void* tok = profile_begin(SWEEP_K_AC_FWD_IN, st);
@@ -461,12 +460,12 @@ void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st) {
 
 void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st) {
   if (a.units <= 0) return;
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {  // thread-safe one-time initialisation
     cudaFuncSetAttribute(ac_in_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kBwdSmem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   int grid = device_sms();
   if (grid > a.units) grid = a.units;
   void* tok = profile_begin(SWEEP_K_AC_BWD_IN, st);

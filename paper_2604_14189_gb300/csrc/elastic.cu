@@ -495,14 +495,14 @@ bool el_step_maps(ElStepArgs& a) {
 void launch_el_step(const ElStepArgs& a, cudaStream_t st) {
   const Geom& g = a.g;
   if (a.units <= 0) return;
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {  // thread-safe one-time initialisation
     cudaFuncSetAttribute(el_vel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kVelSmem);
     cudaFuncSetAttribute(el_str_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kStrSmem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const int grid = std::min(device_sms(), a.units);
   void* t1 = profile_begin(SWEEP_K_EL_VEL, st);
   launch_dependent(el_vel_kernel, dim3(grid), dim3(E_THREADS), kVelSmem, st, a);

@@ -1,4 +1,5 @@
 // Optional per-launch event timing of the time-step kernels (benchmarks).
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -13,7 +14,7 @@ struct Rec {
 };
 
 std::mutex g_mu;
-int g_mask = 0;  // bit k: record kernel class k
+std::atomic<int> g_mask{0};  // bit k: record kernel class k
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 
@@ -40,8 +41,11 @@ void release_all() {
 
 
 void* profile_begin(int kernel, cudaStream_t st) {
+  // checked before taking the lock: launches from several host threads do
+  // not serialise on it while profiling is off
+  if (kernel < 0 || kernel >= 31 || !((g_mask.load(std::memory_order_relaxed) >> kernel) & 1))
+    return nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (kernel < 0 || kernel >= 31 || !((g_mask >> kernel) & 1)) return nullptr;
   Rec r{kernel, take_event(), take_event()};
   if (!r.a || !r.b) return nullptr;
   cudaEventRecord(r.a, st);
@@ -61,7 +65,7 @@ void profile_end(void* token, cudaStream_t st) {
 extern "C" int sweep_profile_enable(int mask) {
   std::lock_guard<std::mutex> lk(sweep::g_mu);
   sweep::release_all();
-  sweep::g_mask = mask;
+  sweep::g_mask.store(mask);
   return SWEEP_OK;
 }
 

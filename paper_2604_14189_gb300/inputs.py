@@ -146,3 +146,30 @@ def workload_fwi(seed: int = 1004, n: int = 256, nshot: int = 16, nt: int = 1500
     rec = surface_line(nshot, 2, np.arange(0, n))
     return dict(nz=n, nx=n, pml=40, dx=10.0, dt=1e-3, nt=nt, f0=10.0,
                 v_true=v_true, model=v0, src=src, rec=rec)
+
+
+def workload_batch(seed: int = 1003, count: int = 256):
+    """Heterogeneous batch: `count` seeded random layered models, interior
+    nz, nx ~ U[128, 512], border 20..40 cells, nt ~ U[800, 3000], 1..8 shots,
+    3..8 flat layers in [1500, 4500] m/s, dx = 10 m, dt = 1 ms, 10 Hz;
+    sources at z = 2 evenly spaced, receivers at z = 2 in every cell."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        nz, nx = int(rng.integers(128, 513)), int(rng.integers(128, 513))
+        pml = int(rng.integers(20, 41))
+        nt = int(rng.integers(800, 3001))
+        ns = int(rng.integers(1, 9))
+        nl = int(rng.integers(3, 9))
+        tops = np.sort(rng.integers(1, nz, nl - 1))
+        vel = np.sort(rng.uniform(1500.0, 4500.0, nl))
+        z = np.arange(nz)[:, None] + np.zeros((1, nx))
+        v = np.full((nz, nx), vel[0])
+        for t, vv in zip(tops, vel[1:]):
+            v[z >= t] = vv
+        sx = np.round(np.linspace(0, nx - 1, ns)).astype(np.int32)
+        src = np.stack([np.full_like(sx, 2), sx], axis=-1).astype(np.int32)
+        rec = surface_line(ns, 2, np.arange(nx))
+        out.append(dict(nz=nz, nx=nx, pml=pml, dx=10.0, dt=1e-3, nt=nt, f0=10.0, model=v,
+                        src=src, rec=rec))
+    return out

@@ -1,0 +1,73 @@
+"""Heterogeneous batches: the LPT schedule (CPU) and batch runs equal to
+one-by-one runs (GPU)."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2604_14189_gb300 import batch
+
+
+def _optimal_makespan(costs, m):
+    best = float("inf")
+    for assign in itertools.product(range(m), repeat=len(costs)):
+        load = [0] * m
+        for c, k in zip(costs, assign):
+            load[k] += c
+        best = min(best, max(load))
+    return best
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_schedule_covers_every_job_once_within_lpt_bound(seed):
+    rng = np.random.default_rng(seed)
+    costs = [int(c) for c in rng.integers(1, 100, 7)]
+    m = int(rng.integers(1, 4))
+    q = batch.schedule(costs, m)
+    assert sorted(j for s in q for j in s) == list(range(len(costs)))
+    makespan = max(sum(costs[j] for j in s) for s in q)
+    opt = _optimal_makespan(costs, m)
+    assert makespan <= (4.0 / 3.0 - 1.0 / (3 * m)) * opt + 1e-9
+
+
+def test_schedule_deals_longest_first():
+    q = batch.schedule([5, 9, 1, 7], 2)
+    # 9 -> s0, 7 -> s1, 5 -> s1 (7 < 9), 1 -> s0 (9 < 12)
+    assert q == [[1, 2], [3, 0]]
+    with pytest.raises(ValueError):
+        batch.schedule([1], 0)
+
+
+@pytest.mark.gpu
+def test_batch_matches_individual_runs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_14189_gb300 import inputs, sweep
+
+    rng = np.random.default_rng(7)
+    items, refs = [], []
+    for k in range(6):
+        nz, nx = int(rng.integers(40, 90)), int(rng.integers(40, 120))
+        pml, nt, ns = int(rng.integers(8, 20)), int(rng.integers(150, 400)), int(rng.integers(1, 4))
+        z = np.arange(nz)[:, None] + np.zeros((1, nx))
+        v = np.where(z < nz // 3, 1800.0, np.where(z < 2 * nz // 3, 2300.0, 2900.0))
+        sx = np.round(np.linspace(1, nx - 2, ns)).astype(np.int32)
+        src = np.stack([np.full(ns, 2), sx], -1).astype(np.int32)
+        rec = inputs.surface_line(ns, 2, np.arange(0, nx, 2))
+        p = sweep.problem(nz=nz, nx=nx, pml=pml, dx=10.0, dt=1e-3, nt=nt, nshot=ns,
+                          nrec=rec.shape[1], f_ref=10.0)
+        dev = "cuda"
+        w = torch.tensor(np.stack([inputs.ricker(10.0, 1e-3, nt)] * ns), dtype=torch.float32,
+                         device=dev)
+        vt = torch.tensor(v, dtype=torch.float32, device=dev)
+        st, rt = torch.tensor(src, device=dev), torch.tensor(rec, device=dev)
+        d_obs = sweep.sweep_forward(p, vt * 1.02, w, st, rt)
+        items.append(batch.Item(p, vt, w, st, rt, d_obs=d_obs))
+        g, J, _ = sweep.sweep_gradient(p, vt, w, st, rt, d_obs)
+        refs.append((g.clone(), float(J)))
+    codes = batch.run(items, streams=3)
+    assert codes == [0] * len(items)
+    for it, (g, J) in zip(items, refs):
+        assert torch.linalg.norm(it.grad - g) <= 1e-5 * torch.linalg.norm(g)
+        assert abs(float(it.misfit) - J) <= 1e-5 * J  # corner additions in either order
