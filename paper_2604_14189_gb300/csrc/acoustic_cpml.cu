@@ -26,7 +26,7 @@
 // adjoints (never written there), which removes most masks.
 //
 // z part: a thread owns a column (coalesced across the warp) and a chunk of
-// ZCH rows; x part: a thread owns 4 consecutive
+// ZCH_F / ZCH_B rows; x part: a thread owns 4 consecutive
 // cells of a row (16-byte accesses) and reads its 4 + 4 x-neighbours as two
 // more 16-byte loads.  Every load of a thread is issued before its
 // arithmetic, so the memory latency is paid once per thread.
@@ -35,9 +35,12 @@
 namespace sweep {
 namespace {
 
-constexpr int FT = 256;  // threads per block
-constexpr int ZCH = 8;   // rows per thread, z part
-constexpr int ZW = ZCH + 8;
+// Block size and rows per z-part thread: chosen by a sweep on GB300 (ZCH 4,
+// 8, 12 x 128, 256 threads; 301x901+40, 20 shots): forward 8 rows, backward
+// 4 rows (its thread keeps three windows), 128 threads.
+constexpr int FT = 128;     // threads per block
+constexpr int ZCH_F = 8;    // rows per thread, forward z part
+constexpr int ZCH_B = 4;    // rows per thread, backward z part
 
 __device__ __forceinline__ float4 ldg4(const float* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
@@ -90,6 +93,7 @@ __device__ __forceinline__ void fwd_z(const AcFixArgs& a, int s, int bl) {
   const int ch = bl / a.zbx;
   const int x = (bl - ch * a.zbx) * FT + threadIdx.x;
   if (x >= g.NX) return;
+  constexpr int ZCH = ZCH_F, ZW = ZCH + 8;
   const int nch = (g.P + ZCH - 1) / ZCH;  // chunks per strip
   const int strip = ch >= nch ? 1 : 0;
   const int base = strip ? g.P + g.nz : 0;
@@ -244,6 +248,7 @@ __device__ __forceinline__ void bwd_z(const AcFixArgs& a, int s, int bl) {
   const int x = (bl - ch * a.zbx) * FT + threadIdx.x;
   if (x >= g.NX) return;
   const int lo_end = band_lo_end(g.P, g.NZ), hi_start = band_hi_start(g.P, g.nz, g.NZ);
+  constexpr int ZCH = ZCH_B, ZW = ZCH + 8;
   const int nlo = (lo_end + ZCH - 1) / ZCH;
   const int band = ch >= nlo ? 1 : 0;
   const int zs = (band ? hi_start : 0) + (ch - band * nlo) * ZCH;
@@ -400,7 +405,7 @@ void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st) {
   const Geom& g = a.g;
   if (g.nshot <= 0) return;
   a.zbx = cdiv(g.NX, FT);
-  a.nchz = g.P > 0 ? 2 * cdiv(g.P, ZCH) : 0;
+  a.nchz = g.P > 0 ? 2 * cdiv(g.P, ZCH_F) : 0;
   a.xb = x_bands(g.P, g.P + g.nx, g.NX);
   a.nbz = a.zbx * a.nchz;
   a.nbx = g.P > 0 ? cdiv(g.NZ, XROWS) : 0;
@@ -419,7 +424,7 @@ void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st) {
   if (g.nshot <= 0) return;
   const int lo_end = band_lo_end(g.P, g.NZ), hi_start = band_hi_start(g.P, g.nz, g.NZ);
   a.zbx = cdiv(g.NX, FT);
-  a.nchz = g.P > 0 ? cdiv(lo_end, ZCH) + cdiv(g.NZ - hi_start, ZCH) : 0;
+  a.nchz = g.P > 0 ? cdiv(lo_end, ZCH_B) + cdiv(g.NZ - hi_start, ZCH_B) : 0;
   a.xb = x_bands(band_lo_end(g.P, g.NX), band_hi_start(g.P, g.nx, g.NX), g.NX);
   a.nbz = a.zbx * a.nchz;
   a.nbx = g.P > 0 ? cdiv(g.NZ, XROWS) : 0;
