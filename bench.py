@@ -108,18 +108,27 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock / throttle sampling.  Started before the warm-up so
+    that the tool's own start-up (driver initialisation on the host) does not
+    overlap the timed region; mark() brackets the timed region, and only the
+    samples taken inside it are summarised."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.t0 = self.t1 = None
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
 
     def start(self):
         try:
+            # one synchronous query first, so that the sampling loop's
+            # first sample is not delayed by the tool's own start-up
+            subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm",
+                            "--format=csv,noheader"], stdout=subprocess.DEVNULL,
+                           stderr=subprocess.DEVNULL, timeout=30)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
@@ -127,7 +136,17 @@ class ClockSampler:
         except OSError:
             self.proc = None
 
+    def mark(self):
+        """First call: the timed region starts; second call: it ends."""
+        import datetime
+        now = datetime.datetime.now()
+        if self.t0 is None:
+            self.t0 = now
+        else:
+            self.t1 = now
+
     def stop(self):
+        import datetime
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -139,9 +158,21 @@ class ClockSampler:
         rows = []
         for line in open(self.f.name):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
+            if len(parts) >= 10:
                 rows.append(parts)
         os.unlink(self.f.name)
+
+        def when(r):
+            try:
+                return datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                return None
+        if self.t0 is not None and self.t1 is not None:
+            lo = self.t0 - datetime.timedelta(seconds=0.25)
+            hi = self.t1 + datetime.timedelta(seconds=0.25)
+            inside = [r for r in rows if when(r) is not None and lo <= when(r) <= hi]
+            rows = inside or rows
+        rows = [r[1:] for r in rows]
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -238,17 +269,22 @@ def run_sweep(args, w, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
+    sampler = ClockSampler(local_rank)
+    sampler.start()  # its start-up overlaps the warm-up, not the timed region
+    # The warm-up runs the timed loop's body, L2 flush included: the first
+    # launch of torch's fill kernel in a process loads its module (lazy
+    # loading), which on a cold page cache stalls the host for ~0.2 s.
     for _ in range(max(args.warmup, 0)):
+        flush.zero_()
         step()
     st = sweep.status(ws)
     if st != sweep.OK:
         raise sweep.SweepError(st, "warm-up")
 
-    sampler = ClockSampler(local_rank)
     l0 = sweep.kernel_launches()
     barrier()
     torch.cuda.synchronize()
-    sampler.start()
+    sampler.mark()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -258,6 +294,7 @@ def run_sweep(args, w, rank, world, local_rank):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    sampler.mark()
     barrier()
     clocks = sampler.stop()
     launches = sweep.kernel_launches() - l0
@@ -335,7 +372,7 @@ def run_sweep(args, w, rank, world, local_rank):
     path_gbs = (alg_bytes_fwd(c) + alg_bytes_bwd(c)) * nshot * nt / (ms_step * 1e-3) / 1e9
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        g, el, cores, sample = oracle_sample(w, nshot, 200)
+        g, el, cores, sample = oracle_sample(w, nshot, 600)
         cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -423,15 +460,16 @@ def run_elastic(args, rank, world, local_rank):
         def step():
             sweep.sweep_forward(p, model, wav, src, rec, data=data, ws=ws, sync=False)
 
+    sampler = ClockSampler(local_rank)
+    sampler.start()  # its start-up overlaps the warm-up, not the timed region
     for _ in range(max(args.warmup, 0)):
         step()
     st = sweep.status(ws)
     if st != sweep.OK:
         raise sweep.SweepError(st, "warm-up")
-    sampler = ClockSampler(local_rank)
     l0 = sweep.kernel_launches()
     torch.cuda.synchronize()
-    sampler.start()
+    sampler.mark()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -439,6 +477,7 @@ def run_elastic(args, rank, world, local_rank):
         step()  # inputs (4.6 GB of fields per step) exceed L2
     e1.record(stream)
     torch.cuda.synchronize()
+    sampler.mark()
     clocks = sampler.stop()
     launches = sweep.kernel_launches() - l0
     ms_step = e0.elapsed_time(e1) / args.steps
@@ -569,10 +608,12 @@ def run_fwi(args, local_rank):
     l0 = sweep.kernel_launches()
     torch.cuda.synchronize()
     sampler.start()
+    sampler.mark()
     t0 = time.perf_counter()
     model, hist = inv.run(m0, cfg)
     torch.cuda.synchronize()
     seconds = time.perf_counter() - t0
+    sampler.mark()
     clocks = sampler.stop()
     launches = sweep.kernel_launches() - l0
     e0 = float((m0 - vt).norm() / vt.norm())
@@ -645,11 +686,13 @@ def run_batch(args, local_rank):
     l0 = sweep.kernel_launches()
     torch.cuda.synchronize()
     sampler.start()
+    sampler.mark()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         codes = batch.run(items, streams=best)
     torch.cuda.synchronize()
     sec = (time.perf_counter() - t0) / args.steps
+    sampler.mark()
     clocks = sampler.stop()
     launches = sweep.kernel_launches() - l0
     if any(codes):
