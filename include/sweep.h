@@ -179,6 +179,33 @@ const char* sweep_strerror(int code);
  * (monotone counter, for accounting launches per step). */
 unsigned long long sweep_kernel_launches(void);
 
+/* CUDA-graph capture.  A job that repeats the same calls with the same
+ * buffers (an FWI loop, a batch of equal problems) can record them once and
+ * replay every kernel of them with one host call; the kernels keep their
+ * programmatic-launch overlap inside the graph.  Library extension: the paper
+ * has no counterpart; it names kernel launches as the cost of its time loop
+ * (Sec. 2.2).
+ *
+ * sweep_capture_begin(stream) starts a thread-local capture on `stream` (not
+ * the legacy default stream 0: SWEEP_EINVAL); the library calls that this
+ * thread then makes on `stream` are recorded, not run, and may not allocate,
+ * synchronise or call sweep_status.  sweep_capture_end(stream, &graph) ends
+ * the capture and returns an instantiated graph in *graph (SWEEP_EINVAL
+ * without an active capture on this thread, SWEEP_ECUDA if the capture was
+ * invalidated, e.g. by a synchronising call, in which case *graph = NULL).
+ * sweep_graph_launch(graph, stream) replays it on any stream (asynchronous;
+ * the recorded calls' pointers are reused, so their buffers must stay
+ * alive and their contents are read at replay time); sweep_graph_kernels
+ * returns the number of kernel nodes (each launch adds it to
+ * sweep_kernel_launches; recorded calls add nothing); sweep_graph_destroy
+ * frees the graph (the caller makes sure no replay of it is pending or
+ * running).  Graphs hold no device memory of the caller's. */
+int sweep_capture_begin(void* stream);
+int sweep_capture_end(void* stream, void** graph);
+int sweep_graph_launch(void* graph, void* stream);
+int sweep_graph_kernels(void* graph);
+void sweep_graph_destroy(void* graph);
+
 /* Kernel timing for benchmarks.  While enabled, every launch of a time-step
  * kernel class selected by the mask is bracketed by two CUDA events recorded
  * on the launching stream.  sweep_profile_enable(mask) clears earlier records

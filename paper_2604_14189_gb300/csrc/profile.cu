@@ -45,6 +45,7 @@ void* profile_begin(int kernel, cudaStream_t st) {
   // not serialise on it while profiling is off
   if (kernel < 0 || kernel >= 31 || !((g_mask.load(std::memory_order_relaxed) >> kernel) & 1))
     return nullptr;
+  if (t_capturing) return nullptr;  // calls recorded into a graph are not timed
   std::lock_guard<std::mutex> lk(g_mu);
   Rec r{kernel, take_event(), take_event()};
   if (!r.a || !r.b) return nullptr;

@@ -16,7 +16,9 @@
 namespace sweep {
 
 std::atomic<unsigned long long> g_launches{0};
-void note_launches(int k) { g_launches.fetch_add((unsigned long long)k); }
+void note_launches(int k) {
+  if (!t_capturing) g_launches.fetch_add((unsigned long long)k);
+}
 
 // ------------------------------------------------------------- tensor maps
 namespace {

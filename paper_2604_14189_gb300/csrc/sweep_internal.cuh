@@ -239,7 +239,9 @@ void launch_dot(const float* a, const float* b, long long n, double* partial,
 constexpr int RED_BLOCKS = 1024;  // partial sums of the FP64 reductions
 
 // Launch accounting and optional per-launch event timing (profile.cu,
-// sweep_api.cu).
+// sweep_api.cu).  While this thread records a graph (graph.cu) neither
+// counts nor times anything.
+extern thread_local bool t_capturing;
 void note_launches(int k);
 void* profile_begin(int kernel, cudaStream_t st);
 void profile_end(void* token, cudaStream_t st);

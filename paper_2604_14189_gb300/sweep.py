@@ -7,8 +7,10 @@ fallback: importing this module fails if the library cannot be loaded.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
+import threading
 
 import torch
 
@@ -32,7 +34,8 @@ DOT_NOALLOC_MAX_N = 33554432
 EXPORTS = ("sweep_workspace_bytes", "sweep_forward", "sweep_adjoint", "sweep_gradient",
            "sweep_dot_workspace_bytes", "sweep_dot", "sweep_status", "sweep_strerror",
            "sweep_kernel_launches", "sweep_profile_enable", "sweep_profile_read",
-           "sweep_dot_noalloc")
+           "sweep_dot_noalloc", "sweep_capture_begin", "sweep_capture_end",
+           "sweep_graph_launch", "sweep_graph_kernels", "sweep_graph_destroy")
 K_AC_FWD, K_AC_BWD, K_EL_VEL, K_EL_STR = 0, 1, 2, 3
 
 
@@ -101,6 +104,16 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.sweep_profile_read.argtypes = [i32, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_longlong)]
     lib.sweep_profile_read.restype = i32
+    lib.sweep_capture_begin.argtypes = [vp]
+    lib.sweep_capture_begin.restype = i32
+    lib.sweep_capture_end.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p)]
+    lib.sweep_capture_end.restype = i32
+    lib.sweep_graph_launch.argtypes = [vp, vp]
+    lib.sweep_graph_launch.restype = i32
+    lib.sweep_graph_kernels.argtypes = [vp]
+    lib.sweep_graph_kernels.restype = i32
+    lib.sweep_graph_destroy.argtypes = [vp]
+    lib.sweep_graph_destroy.restype = None
     return lib
 
 
@@ -181,7 +194,7 @@ def status(ws: torch.Tensor, stream=None) -> int:
 def _finish(rc, ws, where, stream, sync):
     if rc != OK:
         raise SweepError(rc, where)
-    if sync:
+    if sync and not getattr(_capture_state, "on", False):
         st = status(ws, stream)
         if st != OK:
             raise SweepError(st, where)
@@ -245,6 +258,71 @@ def sweep_gradient(p: Problem, model, wavelet, src, rec, d_obs, grad=None, misfi
                              _stream(stream))
     _finish(rc, ws, "sweep_gradient", stream, sync)
     return grad, misfit, illum
+
+
+_capture_state = threading.local()
+
+
+class Graph:
+    """A recorded sequence of library calls (``capture``), replayed with
+    ``launch``.  The recorded calls' tensors are reused at every replay:
+    keep them alive and write new inputs into them in place."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @property
+    def kernels(self) -> int:
+        return int(_lib.sweep_graph_kernels(self._h))
+
+    def launch(self, stream=None) -> None:
+        if not self._h:
+            raise ValueError("sweep.Graph: closed")
+        rc = _lib.sweep_graph_launch(self._h, _stream(stream))
+        if rc != OK:
+            raise SweepError(rc, "sweep_graph_launch")
+
+    def close(self) -> None:
+        """Frees the graph; no replay of it may be pending."""
+        if self._h:
+            _lib.sweep_graph_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+
+class _Capture:
+    graph: Graph | None = None
+
+
+@contextlib.contextmanager
+def capture(stream: torch.cuda.Stream):
+    """Records the library calls made on ``stream`` by this thread inside the
+    block into a ``Graph`` (``with capture(s) as c: ...; c.graph.launch(s)``).
+    Inside the block, pass every output and workspace tensor explicitly (no
+    allocation may happen during a capture) and ``stream=stream``; the
+    status check of the calls is skipped (read it after a replay with
+    ``status``).  ``stream`` must not be the legacy default stream."""
+    if stream is None or stream.cuda_stream == 0:
+        raise ValueError("sweep.capture: needs a non-default torch.cuda.Stream")
+    stream.wait_stream(torch.cuda.current_stream(stream.device))
+    rc = _lib.sweep_capture_begin(ctypes.c_void_p(stream.cuda_stream))
+    if rc != OK:
+        raise SweepError(rc, "sweep_capture_begin")
+    cap = _Capture()
+    _capture_state.on = True
+    ok = False
+    try:
+        yield cap
+        ok = True
+    finally:
+        _capture_state.on = False
+        h = ctypes.c_void_p(None)
+        rc = _lib.sweep_capture_end(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if ok:
+            if rc != OK:
+                raise SweepError(rc, "sweep_capture_end")
+            cap.graph = Graph(h.value)
+        elif h.value:
+            _lib.sweep_graph_destroy(h)
 
 
 _dot_ws = {}

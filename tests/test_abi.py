@@ -73,3 +73,18 @@ def test_host_errors_before_launch():
                            ctypes.c_void_p(257), 1 << 30, None) == sweep.EWORKSPACE
     assert L.sweep_dot(None, None, -1, None, None, 0, None) == sweep.EINVAL
     assert sweep.strerror(sweep.ECFL).startswith("time step")
+
+
+def test_capture_rejects_bad_arguments(lib):
+    """Host-side checks of the graph calls, before any CUDA call: the legacy
+    default stream cannot be captured, and ending or launching needs a
+    capture or a graph."""
+    from paper_2604_14189_gb300 import sweep
+    L = sweep.lib()
+    assert L.sweep_capture_begin(None) == sweep.EINVAL
+    h = ctypes.c_void_p(None)
+    assert L.sweep_capture_end(None, ctypes.byref(h)) == sweep.EINVAL
+    assert L.sweep_capture_end(ctypes.c_void_p(1), None) == sweep.EINVAL
+    assert L.sweep_graph_launch(None, None) == sweep.EINVAL
+    assert L.sweep_graph_kernels(None) == sweep.EINVAL
+    L.sweep_graph_destroy(None)  # no-op
