@@ -6,7 +6,9 @@ surface, 301 receivers every 3 cells, 10 Hz Ricker; the model is the seeded
 layered + Gaussian-anomaly starting model, d_obs the forward data of the true
 model (synthetic).  One step = one sweep_gradient call: forward with ring
 saving, residual + FP64 misfit, backward with reconstruction + imaging, FP64
-shot sum.  value = padded cells x nt x shots x ranks / step time (Gpts/s).
+shot sum; the timed steps replay it from a CUDA graph recorded once
+(--no-graph: direct calls).  value = padded cells x nt x shots x ranks / step
+time (Gpts/s).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sweep|reference]
 
@@ -68,14 +70,20 @@ def alg_bytes_fwd(c):
     return 16 * c["N_pad"] + 16 * (c["N_x"] + c["N_z"]) + 4 * c["N_ring"]
 
 
+# the sources the acoustic time-step kernels are compiled from
+KERNEL_SOURCES = ("acoustic_common.cuh", "acoustic_cpml.cu", "acoustic_interior.cu",
+                  "sweep_internal.cuh", "tma.cuh")
+
+
 def kernel_source_hash():
-    """Hash of the CUDA sources with comments and blank space removed, so that
-    a profile stays valid across edits that do not change the code."""
+    """Hash of the time-step kernels' sources with comments and blank space
+    removed, so that a profile stays valid across edits that do not change
+    the kernels' code."""
     import re
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2604_14189_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
+        if f in KERNEL_SOURCES:
             src = open(os.path.join(d, f), encoding="utf-8").read()
             src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
             src = re.sub(r"//[^\n]*", " ", src)
@@ -260,9 +268,25 @@ def run_sweep(args, w, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    def call(st=None):
         sweep.sweep_gradient(p, v0, wav, src, rec, d_obs, grad=grad, misfit=mis, ws=ws,
-                             sync=False)
+                             stream=st, sync=False)
+
+    graph = None
+    if not args.no_graph:
+        # the timed steps replay one recorded sweep_gradient call (same
+        # buffers every step); captured on a side stream, replayed on this one
+        side = torch.cuda.Stream(dev)
+        with sweep.capture(side) as cap:
+            call(side)
+        graph = cap.graph
+        torch.cuda.current_stream(dev).wait_stream(side)
+
+    def step():
+        if graph is not None:
+            graph.launch(stream)
+        else:
+            call()
         shots.reduce_gradient(grad, mis)
 
     def barrier():
@@ -318,7 +342,7 @@ def run_sweep(args, w, rank, world, local_rank):
     prof_steps = max(1, min(args.steps, 2))
     sweep.profile_enable((1 << sweep.K_AC_BWD) | (1 << sweep.K_AC_FWD))
     for _ in range(prof_steps):
-        step()
+        call()  # direct calls: a graph replay records no events
     torch.cuda.synchronize()
     bwd_ms, bwd_n = sweep.profile_read(sweep.K_AC_BWD)
     fwd_ms, fwd_n = sweep.profile_read(sweep.K_AC_FWD)
@@ -362,6 +386,9 @@ def run_sweep(args, w, rank, world, local_rank):
     e2e_value = pts_step / (ms_e2e / args.steps * 1e-3) / 1e9
     if not np.isfinite(float(mis_h)):
         raise RuntimeError("non-finite misfit in the end-to-end run")
+    if graph is not None:
+        torch.cuda.synchronize()
+        graph.close()
 
     if rank != 0:
         return
@@ -382,7 +409,9 @@ def run_sweep(args, w, rank, world, local_rank):
                    "pml": w["pml"], "nt": nt, "shots_per_gpu": nshot, "nrec": nrec,
                    "l2": "inputs larger than L2 (workspace %.2f GB per step); 256 MB L2 flush "
                          "between timed steps" % (ws.numel() / 1e9),
-                   "reductions": "f64"},
+                   "reductions": "f64",
+                   "launch": ("CUDA-graph replay of one recorded sweep_gradient call per step"
+                              if graph is not None else "direct sweep_gradient call per step")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "acoustic backward time step: stencil kernel (adjoint, "
@@ -620,8 +649,10 @@ def run_fwi(args, local_rank):
     e1 = float((model - vt).norm() / vt.norm())
     c = counts(w["nz"], w["nx"], w["pml"])
     sweep.profile_enable(1 << sweep.K_AC_BWD)
-    inv.gradient(model)
+    sweep.sweep_gradient(p, model.contiguous(), wav, src, rec, d_obs, want_illum=True,
+                         ws=inv.ws_g)  # a direct call: graph replays record no events
     torch.cuda.synchronize()
+    inv.close()
     bms, bn = sweep.profile_read(sweep.K_AC_BWD)
     sweep.profile_enable(False)
     peak, peak_src = peaks()
@@ -639,7 +670,9 @@ def run_fwi(args, local_rank):
                    "model_error_initial": e0, "model_error_final": e1,
                    "misfit_initial": hist[0]["misfit"], "misfit_final": hist[-1]["misfit_after"],
                    "gradients": grads, "line_search_forwards": trials,
-                   "step": "a gradient (step) plus its line-search forwards"},
+                   "step": "a gradient (step) plus its line-search forwards",
+                   "launch": "recorded CUDA graphs replayed per evaluation (gradient; "
+                             "forward + two FP64 dot products)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "acoustic backward time step (as in the headline workload)",
@@ -726,6 +759,8 @@ def main():
     ap.add_argument("--impl", choices=["sweep", "reference"], default="sweep")
     ap.add_argument("--nt", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time direct sweep_gradient calls instead of a graph replay")
     ap.add_argument("--workload", default="acoustic-gradient",
                     choices=["acoustic-gradient", "elastic-forward", "elastic-gradient", "fwi",
                              "batch"],

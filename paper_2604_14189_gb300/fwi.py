@@ -19,6 +19,12 @@ The misfit of a trial model is J = 1/2 |d - d_obs|^2 from ``sweep_forward``
 and three FP64 dot products of the library (no host round trip of the data).
 The line search and the preconditioner are host logic, testable without a
 GPU (``line_search`` takes any misfit function).
+
+With ``graphs=True`` (the default) the gradient call and the trial-misfit
+calls (forward + two dot products) are recorded once as CUDA graphs over
+fixed buffers; each evaluation copies the model into its buffer and replays
+the graph, so an iteration costs a few host calls instead of tens of
+thousands of launches.
 """
 from __future__ import annotations
 
@@ -66,7 +72,7 @@ def line_search(misfit: Callable[[torch.Tensor], float], model: torch.Tensor,
 class Fwi:
     """FWI of one acoustic problem: fixed geometry, wavelets and observed data."""
 
-    def __init__(self, problem: sweep.Problem, wavelet, src, rec, d_obs):
+    def __init__(self, problem: sweep.Problem, wavelet, src, rec, d_obs, graphs: bool = True):
         self.p = problem
         self.wavelet, self.src, self.rec, self.d_obs = wavelet, src, rec, d_obs
         dev = d_obs.device
@@ -74,9 +80,57 @@ class Fwi:
         self.ws_f = sweep.alloc_workspace(problem, sweep.MODE_FORWARD, dev)
         self.data = torch.empty_like(d_obs)
         self.dd_obs = float(sweep.sweep_dot(d_obs.reshape(-1), d_obs.reshape(-1)))
+        self._gg = self._gf = None
+        if graphs:
+            self._record(dev)
+
+    def _record(self, dev):
+        """Records the gradient call and the trial-misfit calls over fixed
+        buffers (model in, results out)."""
+        p = self.p
+        shape = (p.nz, p.nx)
+        self._mg = torch.empty(shape, dtype=torch.float32, device=dev)  # gradient model
+        self._mt = torch.empty(shape, dtype=torch.float32, device=dev)  # trial model
+        self._g = torch.empty(shape, dtype=torch.float32, device=dev)
+        self._il = torch.empty(shape, dtype=torch.float32, device=dev)
+        self._j = torch.empty((), dtype=torch.float64, device=dev)
+        self._dd = torch.empty((), dtype=torch.float64, device=dev)
+        self._do = torch.empty((), dtype=torch.float64, device=dev)
+        d, do = self.data.reshape(-1), self.d_obs.reshape(-1)
+        side = torch.cuda.Stream(dev)
+        with sweep.capture(side) as c:
+            sweep.sweep_gradient(p, self._mg, self.wavelet, self.src, self.rec, self.d_obs,
+                                 grad=self._g, misfit=self._j, illum=self._il, ws=self.ws_g,
+                                 stream=side)
+        self._gg = c.graph
+        with sweep.capture(side) as c:
+            sweep.sweep_forward(p, self._mt, self.wavelet, self.src, self.rec, data=self.data,
+                                ws=self.ws_f, stream=side)
+            sweep.sweep_dot(d, d, out=self._dd, stream=side)
+            sweep.sweep_dot(d, do, out=self._do, stream=side)
+        self._gf = c.graph
+        torch.cuda.current_stream(dev).wait_stream(side)
+
+    def close(self) -> None:
+        """Frees the recorded graphs (none of their replays may be pending)."""
+        for g in (self._gg, self._gf):
+            if g is not None:
+                g.close()
+        self._gg = self._gf = None
+
+    @staticmethod
+    def _checked(ws):
+        st = sweep.status(ws)
+        if st != sweep.OK:
+            raise sweep.SweepError(st, "fwi")
 
     def misfit(self, model: torch.Tensor) -> float:
         """J = 1/2 (<d, d> - 2 <d, d_obs> + <d_obs, d_obs>), FP64 sums."""
+        if self._gf is not None:
+            self._mt.copy_(model)
+            self._gf.launch()
+            self._checked(self.ws_f)
+            return 0.5 * (float(self._dd) - 2.0 * float(self._do) + self.dd_obs)
         d = sweep.sweep_forward(self.p, model, self.wavelet, self.src, self.rec, data=self.data,
                                 ws=self.ws_f)
         dd = float(sweep.sweep_dot(d.reshape(-1), d.reshape(-1)))
@@ -84,6 +138,12 @@ class Fwi:
         return 0.5 * (dd - 2.0 * do + self.dd_obs)
 
     def gradient(self, model: torch.Tensor):
+        """(gradient, misfit, illumination) of `model`; new tensors."""
+        if self._gg is not None:
+            self._mg.copy_(model)
+            self._gg.launch()
+            self._checked(self.ws_g)
+            return self._g.clone(), float(self._j), self._il.clone()
         g, j, illum = sweep.sweep_gradient(self.p, model, self.wavelet, self.src, self.rec,
                                            self.d_obs, want_illum=True, ws=self.ws_g)
         return g, float(j), illum

@@ -53,10 +53,7 @@ def test_precondition_divides_by_stabilised_illumination():
     assert float(d.abs().max()) == 1.0
 
 
-@pytest.mark.gpu
-def test_small_acoustic_fwi_reduces_misfit_and_model_error():
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
+def _small_case():
     from paper_2604_14189_gb300 import sweep
     from scipy.ndimage import gaussian_filter
 
@@ -78,6 +75,15 @@ def test_small_acoustic_fwi_reduces_misfit_and_model_error():
     rec_t = torch.tensor(rec, device=dev)
     d_obs = sweep.sweep_forward(p, torch.tensor(vt, dtype=torch.float32, device=dev), wav,
                                 src_t, rec_t)
+    return p, wav, src_t, rec_t, d_obs, vt, v0
+
+
+@pytest.mark.gpu
+def test_small_acoustic_fwi_reduces_misfit_and_model_error():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p, wav, src_t, rec_t, d_obs, vt, v0 = _small_case()
+    dev = "cuda"
     inv = fwi.Fwi(p, wav, src_t, rec_t, d_obs)
     m0 = torch.tensor(v0, dtype=torch.float32, device=dev)
     cfg = fwi.FwiConfig(iterations=8, step=60.0, vmin=1500.0, vmax=3500.0)
@@ -94,3 +100,32 @@ def test_small_acoustic_fwi_reduces_misfit_and_model_error():
     # (to rounding: the two CPML axes add into corner cells in either order,
     # and the misfit is a difference of FP64 sums of the traces)
     assert abs(inv.misfit(model) - hist[-1]["misfit_after"]) <= 1e-4 * hist[-1]["misfit_after"]
+
+
+@pytest.mark.gpu
+def test_graph_replay_fwi_matches_direct_calls():
+    """The recorded-graph evaluations give the direct calls' iterations:
+    same accepted steps, misfits and models to rounding (corner cells of
+    the border take their two CPML additions in either order)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p, wav, src_t, rec_t, d_obs, vt, v0 = _small_case()
+    m0 = torch.tensor(v0, dtype=torch.float32, device="cuda")
+    cfg = fwi.FwiConfig(iterations=3, step=60.0, vmin=1500.0, vmax=3500.0)
+    direct = fwi.Fwi(p, wav, src_t, rec_t, d_obs, graphs=False)
+    graph = fwi.Fwi(p, wav, src_t, rec_t, d_obs, graphs=True)
+    try:
+        m_d, h_d = direct.run(m0, cfg)
+        m_g, h_g = graph.run(m0, cfg)
+        assert len(h_d) == len(h_g)
+        for a, b in zip(h_d, h_g):
+            assert a["trials"] == b["trials"] and a["step"] == b["step"]
+            assert abs(a["misfit"] - b["misfit"]) <= 1e-4 * a["misfit"]
+            assert abs(a["misfit_after"] - b["misfit_after"]) <= 1e-4 * a["misfit_after"]
+        assert float((m_d - m_g).abs().max()) <= 1e-5 * float(m_d.abs().max())
+        # evaluations return new tensors, not the recorded buffers
+        g1, _, _ = graph.gradient(m0)
+        g2, _, _ = graph.gradient(m_g)
+        assert g1.data_ptr() != g2.data_ptr()
+    finally:
+        graph.close()
