@@ -24,6 +24,11 @@
 // Each half is a pointwise kernel (the adjoint derivative terms into four
 // scratch fields, memory variables, coefficient adjoints) and a gather
 // kernel (the transposed differences of those terms).
+//
+// A memory variable and its adjoint stay zero wherever its profile pair
+// (a, b) is zero, i.e. off its border strip (both start at zero and are
+// only ever replaced by a x (...)); the pointwise kernels neither read nor
+// write them there, which is most of the grid.
 #include "sweep_internal.cuh"
 
 namespace sweep {
@@ -84,11 +89,17 @@ __global__ void __launch_bounds__(AT) el_adj_str_pt_kernel(const ElAdjArgs a) {
   const size_t pc = (size_t)z * g.NXp + x;
   const float txx = a.atxx[c], tzz = a.atzz[c], txz = a.atxz[c];
   const float l2m = a.cl2m[pc], lam = a.clam[pc], mu = a.cmu[pc];
+  // profile pairs of p5 (x), p6 (z), p7 (z, half points), p8 (x, half points)
+  const float A5 = a.ax[x], B5 = a.bx[x], A6 = a.az[z], B6 = a.bz[z];
+  const float A7 = a.azh[z], B7 = a.bzh[z], A8 = a.axh[x], B8 = a.bxh[x];
+  const bool o5 = A5 != 0.f || B5 != 0.f, o6 = A6 != 0.f || B6 != 0.f;
+  const bool o7 = A7 != 0.f || B7 != 0.f, o8 = A8 != 0.f || B8 != 0.f;
   if (a.gacc) {
     const Fld vx = fld(a.fvx, g, s), vz = fld(a.fvz, g, s);
-    const float ex = dmx(vx, z, x) + a.fp[4][c];
-    const float ez = dmz(vz, z, x) + a.fp[5][c];
-    const float sxz = dpz(vx, z, x) + a.fp[6][c] + dpx(vz, z, x) + a.fp[7][c];
+    const float ex = dmx(vx, z, x) + (o5 ? a.fp[4][c] : 0.f);
+    const float ez = dmz(vz, z, x) + (o6 ? a.fp[5][c] : 0.f);
+    const float sxz = dpz(vx, z, x) + (o7 ? a.fp[6][c] : 0.f) + dpx(vz, z, x) +
+                      (o8 ? a.fp[7][c] : 0.f);
     float* ga = a.gacc + (size_t)s * 5 * g.fstride + pc;
     ga[G_L2M * g.fstride] += txx * ex + tzz * ez;
     ga[G_LAM * g.fstride] += txx * ez + tzz * ex;
@@ -96,18 +107,18 @@ __global__ void __launch_bounds__(AT) el_adj_str_pt_kernel(const ElAdjArgs a) {
   }
   // txz += cmu (ezx + p7' + exz + p8')
   const float T = mu * txz;
-  const float P7 = a.ap[6][c] + T, P8 = a.ap[7][c] + T;
-  a.e2[c] = T + a.bzh[z] * P7;  // ezx-bar
-  a.e3[c] = T + a.bxh[x] * P8;  // exz-bar
-  a.ap[6][c] = a.azh[z] * P7;
-  a.ap[7][c] = a.axh[x] * P8;
+  const float P7 = (o7 ? a.ap[6][c] : 0.f) + T, P8 = (o8 ? a.ap[7][c] : 0.f) + T;
+  a.e2[c] = T + B7 * P7;  // ezx-bar
+  a.e3[c] = T + B8 * P8;  // exz-bar
+  if (o7) a.ap[6][c] = A7 * P7;
+  if (o8) a.ap[7][c] = A8 * P8;
   // txx += cl2m Ex + clam Ez, tzz += clam Ex + cl2m Ez
   const float Ex = l2m * txx + lam * tzz, Ez = lam * txx + l2m * tzz;
-  const float P5 = a.ap[4][c] + Ex, P6 = a.ap[5][c] + Ez;
-  a.e0[c] = Ex + a.bx[x] * P5;  // exx-bar
-  a.e1[c] = Ez + a.bz[z] * P6;  // ezz-bar
-  a.ap[4][c] = a.ax[x] * P5;
-  a.ap[5][c] = a.az[z] * P6;
+  const float P5 = (o5 ? a.ap[4][c] : 0.f) + Ex, P6 = (o6 ? a.ap[5][c] : 0.f) + Ez;
+  a.e0[c] = Ex + B5 * P5;  // exx-bar
+  a.e1[c] = Ez + B6 * P6;  // ezz-bar
+  if (o5) a.ap[4][c] = A5 * P5;
+  if (o6) a.ap[5][c] = A6 * P6;
 }
 
 // ----------------------------------------------------------- stress, gather
@@ -148,28 +159,35 @@ __global__ void __launch_bounds__(AT) el_adj_vel_pt_kernel(const ElAdjArgs a) {
   }
   const size_t pc = (size_t)z * g.NXp + x;
   const float vx = a.avx[c], vz = a.avz[c];
+  // profile pairs of p1 (x, half points), p2 (z), p3 (x), p4 (z, half points)
+  const float A1 = a.axh[x], B1 = a.bxh[x], A2 = a.az[z], B2 = a.bz[z];
+  const float A3 = a.ax[x], B3 = a.bx[x], A4 = a.azh[z], B4 = a.bzh[z];
+  const bool o1 = A1 != 0.f || B1 != 0.f, o2 = A2 != 0.f || B2 != 0.f;
+  const bool o3 = A3 != 0.f || B3 != 0.f, o4 = A4 != 0.f || B4 != 0.f;
   if (a.gacc) {
     const Fld txx = fld(a.ftxx, g, s), tzz = fld(a.ftzz, g, s), txz = fld(a.ftxz, g, s);
-    const float sx = dpx(txx, z, x) + a.fp[0][c] + dmz(txz, z, x) + a.fp[1][c];
-    const float sz = dmx(txz, z, x) + a.fp[2][c] + dpz(tzz, z, x) + a.fp[3][c];
+    const float sx = dpx(txx, z, x) + (o1 ? a.fp[0][c] : 0.f) + dmz(txz, z, x) +
+                     (o2 ? a.fp[1][c] : 0.f);
+    const float sz = dmx(txz, z, x) + (o3 ? a.fp[2][c] : 0.f) + dpz(tzz, z, x) +
+                     (o4 ? a.fp[3][c] : 0.f);
     float* ga = a.gacc + (size_t)s * 5 * g.fstride + pc;
     ga[G_BX * g.fstride] += vx * sx;
     ga[G_BZ * g.fstride] += vz * sz;
   }
   // vx += cbx (dxt + p1' + dzt + p2')
   const float Q = a.cbx[pc] * vx;
-  const float P1 = a.ap[0][c] + Q, P2 = a.ap[1][c] + Q;
-  a.e0[c] = Q + a.bxh[x] * P1;  // dxt-bar (Dpx txx)
-  a.e1[c] = Q + a.bz[z] * P2;   // dzt-bar (Dmz txz)
-  a.ap[0][c] = a.axh[x] * P1;
-  a.ap[1][c] = a.az[z] * P2;
+  const float P1 = (o1 ? a.ap[0][c] : 0.f) + Q, P2 = (o2 ? a.ap[1][c] : 0.f) + Q;
+  a.e0[c] = Q + B1 * P1;  // dxt-bar (Dpx txx)
+  a.e1[c] = Q + B2 * P2;  // dzt-bar (Dmz txz)
+  if (o1) a.ap[0][c] = A1 * P1;
+  if (o2) a.ap[1][c] = A2 * P2;
   // vz += cbz (dxt + p3' + dzt + p4')
   const float Qz = a.cbz[pc] * vz;
-  const float P3 = a.ap[2][c] + Qz, P4 = a.ap[3][c] + Qz;
-  a.e2[c] = Qz + a.bx[x] * P3;   // dxt-bar (Dmx txz)
-  a.e3[c] = Qz + a.bzh[z] * P4;  // dzt-bar (Dpz tzz)
-  a.ap[2][c] = a.ax[x] * P3;
-  a.ap[3][c] = a.azh[z] * P4;
+  const float P3 = (o3 ? a.ap[2][c] : 0.f) + Qz, P4 = (o4 ? a.ap[3][c] : 0.f) + Qz;
+  a.e2[c] = Qz + B3 * P3;  // dxt-bar (Dmx txz)
+  a.e3[c] = Qz + B4 * P4;  // dzt-bar (Dpz tzz)
+  if (o3) a.ap[2][c] = A3 * P3;
+  if (o4) a.ap[3][c] = A4 * P4;
 }
 
 // --------------------------------------------------------- velocity, gather
@@ -267,6 +285,56 @@ __global__ void el_grad_kernel(const Geom g, const float* gacc, const float* mod
 }
 
 }  // namespace
+
+namespace {
+
+// profile pair of memory variable k (p1..p8): x axis?, half points?
+__device__ __forceinline__ bool snap_on(const ElSnapArgs& a, int k, int z, int x) {
+  const Geom& g = a.g;
+  const bool xaxis = k == 0 || k == 2 || k == 4 || k == 7;
+  const bool half = k == 0 || k == 3 || k == 6 || k == 7;
+  if (!xaxis) {
+    const float A = half ? a.azh[z] : a.az[z], B = half ? a.bzh[z] : a.bz[z];
+    return A != 0.f || B != 0.f;
+  }
+  bool on = false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (x + i < g.NX) {
+      const float A = half ? a.axh[x + i] : a.ax[x + i];
+      const float B = half ? a.bxh[x + i] : a.bx[x + i];
+      on = on || A != 0.f || B != 0.f;
+    }
+  }
+  return on;
+}
+
+// one thread per 4-cell group of a row of one shot
+__global__ void __launch_bounds__(128) el_snapshot_kernel(const ElSnapArgs a) {
+  const Geom& g = a.g;
+  const int x = 4 * (blockIdx.x * 128 + threadIdx.x), z = blockIdx.y, s = blockIdx.z;
+  if (x >= g.NXp) return;
+  const size_t c = (size_t)s * g.fstride + (size_t)z * g.NXp + x;
+#pragma unroll
+  for (int f = 0; f < 5; ++f)
+    *reinterpret_cast<float4*>(a.dst[f] + c) = *reinterpret_cast<const float4*>(a.src[f] + c);
+  if (x >= g.NX) return;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (snap_on(a, k, z, x))
+      *reinterpret_cast<float4*>(a.dst[5 + k] + c) =
+          *reinterpret_cast<const float4*>(a.src[5 + k] + c);
+}
+
+}  // namespace
+
+void launch_el_snapshot(const ElSnapArgs& a, cudaStream_t st) {
+  const Geom& g = a.g;
+  if (g.nshot <= 0) return;
+  const dim3 grid((g.NXp / 4 + 127) / 128, g.NZ, g.nshot);
+  el_snapshot_kernel<<<grid, 128, 0, st>>>(a);
+  note_launches(1);
+}
 
 void launch_el_adj_step(const ElAdjArgs& a, cudaStream_t st) {
   const Geom& g = a.g;

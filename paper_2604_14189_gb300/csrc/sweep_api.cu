@@ -576,13 +576,26 @@ int elastic_reverse_loop(const sweep_problem* p, const Layout& L, void* ws, cons
   char* seg = at<char>(ws, L.el_seg);
   ElStepArgs fs = elastic_step_args(p, L, ws, state, wavelet, src, rec, nullptr);
   if (fs.units < 0) return SWEEP_ECUDA;
+  ElSnapArgs sn{};
+  sn.g = g;
+  for (int i = 0; i < 13; ++i) sn.src[i] = state_field(L, state, i);
+  sn.ax = a.ax;
+  sn.bx = a.bx;
+  sn.axh = a.axh;
+  sn.bxh = a.bxh;
+  sn.az = a.az;
+  sn.bz = a.bz;
+  sn.azh = a.azh;
+  sn.bzh = a.bzh;
   for (int k = L.el_ncp - 1; k >= 0; --k) {
     const int n0 = k * L.el_C, n1 = std::min(n0 + L.el_C, g.nt);
     cudaMemcpyAsync(state, ck + (size_t)k * sb, sb, cudaMemcpyDeviceToDevice, st);
     for (int n = n0; n < n1; ++n) {
       fs.n = n;
       launch_el_step(fs, st);
-      cudaMemcpyAsync(seg + (size_t)(n - n0) * sb, state, sb, cudaMemcpyDeviceToDevice, st);
+      // keep the state after step n (memory variables on their strips only)
+      for (int i = 0; i < 13; ++i) sn.dst[i] = state_field(L, seg + (size_t)(n - n0) * sb, i);
+      launch_el_snapshot(sn, st);
     }
     for (int n = n1 - 1; n >= n0; --n) {
       char* after = seg + (size_t)(n - n0) * sb;

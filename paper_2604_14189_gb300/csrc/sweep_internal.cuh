@@ -190,6 +190,18 @@ struct ElAdjArgs {
   int n;
 };
 void launch_el_adj_step(const ElAdjArgs& a, cudaStream_t st);
+// Copy of a forward state for the adjoint (elastic_adjoint.cu): the five
+// wavefields everywhere, each memory variable only where its profile pair
+// (a, b) is nonzero (float4 groups meeting that set); elsewhere the
+// variable is zero and the adjoint kernels never read it.  src/dst: fields
+// 0..4 (vx, vz, txx, tzz, txz), 5..12 (p1..p8), each [S][NZ][NXp].
+struct ElSnapArgs {
+  Geom g;
+  const float* src[13];
+  float* dst[13];
+  const float *ax, *bx, *axh, *bxh, *az, *bz, *azh, *bzh;
+};
+void launch_el_snapshot(const ElSnapArgs& a, cudaStream_t st);
 // d J / d (vp, vs, rho) on interior cells, [3][nz][nx], from the per-shot
 // coefficient adjoints (FP64 sum over shots); padding held fixed.
 void launch_el_grad(const Geom& g, const float* gacc, const float* model, int padded, float dx,
