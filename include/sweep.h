@@ -172,6 +172,16 @@ int sweep_dot_noalloc(const float* a, const float* b, int64_t n, double* out,
  * last call that used it (SWEEP_OK or a negative code). */
 int sweep_status(void* ws, void* stream);
 
+/* Diagnostic of the device-side timeout path.  Every pipeline wait in the
+ * kernels is bounded (0.5 s); a wait that runs out latches SWEEP_ETIMEOUT in
+ * the workspace status word and its kernel returns, leaving the context
+ * usable.  This call launches one kernel whose bounded wait on a barrier
+ * that nothing completes runs out: afterwards sweep_status(ws) returns
+ * SWEEP_ETIMEOUT (the next solver call on ws clears it).  ws: any workspace
+ * of this library (256-byte aligned, >= 4 bytes); only its status word is
+ * written.  Takes ~0.5 s of one SM.  Asynchronous on `stream`. */
+int sweep_check_wait_timeout(void* ws, size_t ws_bytes, void* stream);
+
 /* Static description of a code. */
 const char* sweep_strerror(int code);
 

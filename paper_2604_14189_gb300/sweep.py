@@ -35,7 +35,8 @@ EXPORTS = ("sweep_workspace_bytes", "sweep_forward", "sweep_adjoint", "sweep_gra
            "sweep_dot_workspace_bytes", "sweep_dot", "sweep_status", "sweep_strerror",
            "sweep_kernel_launches", "sweep_profile_enable", "sweep_profile_read",
            "sweep_dot_noalloc", "sweep_capture_begin", "sweep_capture_end",
-           "sweep_graph_launch", "sweep_graph_kernels", "sweep_graph_destroy")
+           "sweep_graph_launch", "sweep_graph_kernels", "sweep_graph_destroy",
+           "sweep_check_wait_timeout")
 K_AC_FWD, K_AC_BWD, K_EL_VEL, K_EL_STR = 0, 1, 2, 3
 
 
@@ -114,6 +115,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.sweep_graph_kernels.restype = i32
     lib.sweep_graph_destroy.argtypes = [vp]
     lib.sweep_graph_destroy.restype = None
+    lib.sweep_check_wait_timeout.argtypes = [vp, sz, vp]
+    lib.sweep_check_wait_timeout.restype = i32
     return lib
 
 
@@ -185,6 +188,14 @@ def alloc_workspace(p: Problem, mode: int, device=None) -> torch.Tensor:
 
 def _ws_args(ws):
     return ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel())
+
+
+def check_wait_timeout(ws: torch.Tensor, stream=None) -> None:
+    """Runs the timeout diagnostic on `ws` (see sweep_check_wait_timeout)."""
+    w, wn = _ws_args(ws)
+    rc = _lib.sweep_check_wait_timeout(w, wn, _stream(stream))
+    if rc != OK:
+        raise SweepError(rc, "sweep_check_wait_timeout")
 
 
 def status(ws: torch.Tensor, stream=None) -> int:

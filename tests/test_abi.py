@@ -88,3 +88,11 @@ def test_capture_rejects_bad_arguments(lib):
     assert L.sweep_graph_launch(None, None) == sweep.EINVAL
     assert L.sweep_graph_kernels(None) == sweep.EINVAL
     L.sweep_graph_destroy(None)  # no-op
+
+
+def test_wait_timeout_diagnostic_checks_workspace(lib):
+    from paper_2604_14189_gb300 import sweep
+    L = sweep.lib()
+    assert L.sweep_check_wait_timeout(None, 1024, None) == sweep.EWORKSPACE
+    assert L.sweep_check_wait_timeout(ctypes.c_void_p(256), 2, None) == sweep.EWORKSPACE
+    assert L.sweep_check_wait_timeout(ctypes.c_void_p(257), 1024, None) == sweep.EWORKSPACE

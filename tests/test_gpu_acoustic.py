@@ -261,3 +261,18 @@ def test_edge_cases(sw):
         sw.sweep_gradient(pe, me, torch.zeros((2, 100), device="cuda"), src, rec,
                           torch.zeros((2, 2, 4, 100), device="cuda"), want_illum=True)
     assert e.value.code == sw.EUNSUPPORTED
+
+
+def test_bounded_wait_runs_out_and_context_survives(sw):
+    """A device-side wait that nothing completes gives up after its bound,
+    latches ETIMEOUT in the status word, and leaves the context usable: the
+    next call on the same workspace clears the word and matches the oracle."""
+    c = case(30, 40, 5, 80, 1, 3, seed=61)
+    p, q = probs(sw, c)
+    ws = sw.alloc_workspace(p, sw.MODE_FORWARD)
+    sw.check_wait_timeout(ws)
+    assert sw.status(ws) == sw.ETIMEOUT
+    d = sw.sweep_forward(p, cuda(c["v"]), cuda(c["w"]), cuda(c["src"], torch.int32),
+                         cuda(c["rec"], torch.int32), ws=ws)
+    ref = oracle.acoustic_forward(q, f32(c["v"]), f32(c["w"]), c["src"], c["rec"])
+    assert rel(d.cpu().numpy()[:, 0], ref) <= 1e-4
