@@ -1,8 +1,8 @@
 // Stencil kernels of the acoustic step: the plain 8th-order update of every
 // cell of the padded grid (forward), and the fused adjoint + reconstruction
-// + imaging update (backward).  The CPML terms are added afterwards by the
-// per-axis correction kernels (acoustic_cpml.cu).  See acoustic_common.cuh
-// for the equations.
+// + imaging update (backward).  The CPML terms of both axes, the receivers
+// and the boundary ring are handled afterwards by the step's second kernel
+// (acoustic_cpml.cu).  See acoustic_common.cuh for the equations.
 //
 // Work is a list of (tile, shot) units taken round-robin by persistent CTAs
 // (one per SM).  Each CTA runs a multi-stage TMA pipeline: while it computes

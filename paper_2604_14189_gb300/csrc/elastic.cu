@@ -18,7 +18,7 @@
 // zero-fills outside the padded grid (the Dirichlet condition).
 #include <algorithm>
 
-#include "sweep_internal.cuh"
+#include "elastic_internal.cuh"
 #include "tma.cuh"
 
 namespace sweep {

@@ -29,7 +29,7 @@
 // (a, b) is zero, i.e. off its border strip (both start at zero and are
 // only ever replaced by a x (...)); the pointwise kernels neither read nor
 // write them there, which is most of the grid.
-#include "sweep_internal.cuh"
+#include "elastic_internal.cuh"
 
 namespace sweep {
 namespace {

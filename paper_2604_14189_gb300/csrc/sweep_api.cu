@@ -10,7 +10,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "sweep_internal.cuh"
+#include "elastic_internal.cuh"
 #include "tma.cuh"
 
 namespace sweep {

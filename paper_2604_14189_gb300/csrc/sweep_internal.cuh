@@ -122,91 +122,6 @@ struct AcFixArgs {
 void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st);
 void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st);
 
-// ------------------------------------------------------------------- elastic
-// Coefficients on the padded grid [NZ][NXp], pre-scaled by dt / dx:
-// cbx, cbz = buoyancy at vx / vz points; cl2m = lambda + 2 mu, clam = lambda
-// at normal-stress points; cmu = mu at txz points.
-struct ElParamArgs {
-  Geom g;
-  const float* model;  // [3][nz][nx] (vp, vs, rho) or padded
-  int padded;
-  float dx, dt;
-  float* cbx;
-  float* cbz;
-  float* cl2m;
-  float* clam;
-  float* cmu;
-};
-
-struct ElStepArgs {
-  Geom g;
-  float *vx, *vz, *txx, *tzz, *txz;        // [S][NZ][NXp]
-  float *p1, *p2, *p3, *p4;                // velocity CPML memory variables
-  float *p5, *p6, *p7, *p8;                // stress CPML memory variables
-  const float *cbx, *cbz, *cl2m, *clam, *cmu;
-  const float *ax, *bx, *axh, *bxh;        // x profiles (integer, half points)
-  const float *az, *bz, *azh, *bzh;        // z profiles
-  const float* wavelet;
-  const int32_t* src;
-  const int32_t* rec;
-  const int32_t* rbox;
-  float* data;                             // [S][2][R][nt] or null
-  float src_scale;                         // dt / dx^2
-  int* status;
-  int n;
-  // TMA descriptors (built by el_step_maps): stress fields with the halos
-  // the velocity kernel needs, velocities with both halos, coefficients
-  CUtensorMap m_txx, m_txz, m_tzz, m_vx, m_vz;
-  CUtensorMap m_cbx, m_cbz, m_l2m, m_lam, m_mu;
-  int units, ntx;  // (tile, shot) units of the persistent kernels
-};
-void launch_el_params(const ElParamArgs& a, cudaStream_t st);
-// Fills the descriptors and the unit count of `a` (false on a driver error).
-bool el_step_maps(ElStepArgs& a);
-void launch_el_step(const ElStepArgs& a, cudaStream_t st);
-
-// Elastic adjoint step (elastic_adjoint.cu): the transpose of one
-// ElStepArgs step, run backwards in time.  Adjoint state (vx, vz, txx, tzz,
-// txz, p1..p8) in av*, at*, ap; e0..e3 scratch fields [S][NZ][NXp].  With
-// gacc non-null the step also accumulates d J / d (cl2m, clam, cmu, cbx, cbz)
-// per shot ([S][5][NZ][NXp]) from the forward state: fvx, fvz = v^{n+1/2}
-// and fp = p1..p8 after step n, ft* = tau^n (before the step).
-struct ElAdjArgs {
-  Geom g;
-  float *avx, *avz, *atxx, *atzz, *atxz;
-  float* ap[8];
-  float *e0, *e1, *e2, *e3;
-  const float *fvx, *fvz, *ftxx, *ftzz, *ftxz;
-  const float* fp[8];
-  float* gacc;
-  const float *cbx, *cbz, *cl2m, *clam, *cmu;
-  const float *ax, *bx, *axh, *bxh, *az, *bz, *azh, *bzh;
-  const float* res;     // [S][2][R][nt] injected at the receivers, or null
-  const int32_t* src;
-  const int32_t* rec;
-  float* wgrad;         // [S][nt] wavelet adjoint, or null
-  float src_scale;      // dt / dx^2
-  const int* status;
-  int n;
-};
-void launch_el_adj_step(const ElAdjArgs& a, cudaStream_t st);
-// Copy of a forward state for the adjoint (elastic_adjoint.cu): the five
-// wavefields everywhere, each memory variable only where its profile pair
-// (a, b) is nonzero (float4 groups meeting that set); elsewhere the
-// variable is zero and the adjoint kernels never read it.  src/dst: fields
-// 0..4 (vx, vz, txx, tzz, txz), 5..12 (p1..p8), each [S][NZ][NXp].
-struct ElSnapArgs {
-  Geom g;
-  const float* src[13];
-  float* dst[13];
-  const float *ax, *bx, *axh, *bxh, *az, *bz, *azh, *bzh;
-};
-void launch_el_snapshot(const ElSnapArgs& a, cudaStream_t st);
-// d J / d (vp, vs, rho) on interior cells, [3][nz][nx], from the per-shot
-// coefficient adjoints (FP64 sum over shots); padding held fixed.
-void launch_el_grad(const Geom& g, const float* gacc, const float* model, int padded, float dx,
-                    float dt, float* grad, const int* status, cudaStream_t st);
-
 // Kernel launchers (acoustic_interior.cu)
 void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st);
 void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st);
