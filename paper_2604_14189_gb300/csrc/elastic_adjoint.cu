@@ -18,7 +18,8 @@
 //   receivers: v-bar(r) += residual^n(r)
 //   velocity: Q = cbx vx-bar;  P = p1-bar + Q;  dxt-bar = Q + bxh P;
 //            p1-bar = axh P (p2..p4 alike); txx-bar += -Dmx(dxt-bar), ...
-//   coefficients: d J / d cl2m += txx-bar Ex + tzz-bar Ez, d J / d clam +=
+//   coefficients (summed over shots and steps in FP64):
+//            d J / d cl2m += txx-bar Ex + tzz-bar Ez, d J / d clam +=
 //            txx-bar Ez + tzz-bar Ex, d J / d cmu += txz-bar (shear bracket),
 //            d J / d cbx += vx-bar (vx bracket), d J / d cbz likewise.
 // Each half is a pointwise kernel (the adjoint derivative terms into four
@@ -76,49 +77,63 @@ __global__ void el_adj_src_kernel(const ElAdjArgs a) {
 }
 
 // ------------------------------------------------------- stress, pointwise
+// One thread per cell for all shots: the coefficient adjoints are summed
+// over the shots in FP64 registers and added once per step to the FP64
+// accumulators [5][NZ][NXp] (shot sum and time sum in FP64).
 __global__ void __launch_bounds__(AT) el_adj_str_pt_kernel(const ElAdjArgs a) {
   if (*a.status) return;
   const Geom& g = a.g;
-  const int x = blockIdx.x * AT + threadIdx.x, z = blockIdx.y, s = blockIdx.z;
+  const int x = blockIdx.x * AT + threadIdx.x, z = blockIdx.y;
   if (x >= g.NXp) return;
-  const size_t c = (size_t)s * g.fstride + (size_t)z * g.NXp + x;
+  const size_t pc = (size_t)z * g.NXp + x;
   if (x >= g.NX) {  // zero terms beyond the grid for the gather kernel
-    a.e0[c] = a.e1[c] = a.e2[c] = a.e3[c] = 0.f;
+    for (int s = 0; s < g.nshot; ++s) {
+      const size_t c = (size_t)s * g.fstride + pc;
+      a.e0[c] = a.e1[c] = a.e2[c] = a.e3[c] = 0.f;
+    }
     return;
   }
-  const size_t pc = (size_t)z * g.NXp + x;
-  const float txx = a.atxx[c], tzz = a.atzz[c], txz = a.atxz[c];
   const float l2m = a.cl2m[pc], lam = a.clam[pc], mu = a.cmu[pc];
   // profile pairs of p5 (x), p6 (z), p7 (z, half points), p8 (x, half points)
   const float A5 = a.ax[x], B5 = a.bx[x], A6 = a.az[z], B6 = a.bz[z];
   const float A7 = a.azh[z], B7 = a.bzh[z], A8 = a.axh[x], B8 = a.bxh[x];
   const bool o5 = A5 != 0.f || B5 != 0.f, o6 = A6 != 0.f || B6 != 0.f;
   const bool o7 = A7 != 0.f || B7 != 0.f, o8 = A8 != 0.f || B8 != 0.f;
-  if (a.gacc) {
-    const Fld vx = fld(a.fvx, g, s), vz = fld(a.fvz, g, s);
-    const float ex = dmx(vx, z, x) + (o5 ? a.fp[4][c] : 0.f);
-    const float ez = dmz(vz, z, x) + (o6 ? a.fp[5][c] : 0.f);
-    const float sxz = dpz(vx, z, x) + (o7 ? a.fp[6][c] : 0.f) + dpx(vz, z, x) +
-                      (o8 ? a.fp[7][c] : 0.f);
-    float* ga = a.gacc + (size_t)s * 5 * g.fstride + pc;
-    ga[G_L2M * g.fstride] += txx * ex + tzz * ez;
-    ga[G_LAM * g.fstride] += txx * ez + tzz * ex;
-    ga[G_MU * g.fstride] += txz * sxz;
+  double sl2m = 0.0, slam = 0.0, smu = 0.0;
+  for (int s = 0; s < g.nshot; ++s) {
+    const size_t c = (size_t)s * g.fstride + pc;
+    const float txx = a.atxx[c], tzz = a.atzz[c], txz = a.atxz[c];
+    if (a.gacc) {
+      const Fld vx = fld(a.fvx, g, s), vz = fld(a.fvz, g, s);
+      const float ex = dmx(vx, z, x) + (o5 ? a.fp[4][c] : 0.f);
+      const float ez = dmz(vz, z, x) + (o6 ? a.fp[5][c] : 0.f);
+      const float sxz = dpz(vx, z, x) + (o7 ? a.fp[6][c] : 0.f) + dpx(vz, z, x) +
+                        (o8 ? a.fp[7][c] : 0.f);
+      sl2m += (double)(txx * ex + tzz * ez);
+      slam += (double)(txx * ez + tzz * ex);
+      smu += (double)(txz * sxz);
+    }
+    // txz += cmu (ezx + p7' + exz + p8')
+    const float T = mu * txz;
+    const float P7 = (o7 ? a.ap[6][c] : 0.f) + T, P8 = (o8 ? a.ap[7][c] : 0.f) + T;
+    a.e2[c] = T + B7 * P7;  // ezx-bar
+    a.e3[c] = T + B8 * P8;  // exz-bar
+    if (o7) a.ap[6][c] = A7 * P7;
+    if (o8) a.ap[7][c] = A8 * P8;
+    // txx += cl2m Ex + clam Ez, tzz += clam Ex + cl2m Ez
+    const float Ex = l2m * txx + lam * tzz, Ez = lam * txx + l2m * tzz;
+    const float P5 = (o5 ? a.ap[4][c] : 0.f) + Ex, P6 = (o6 ? a.ap[5][c] : 0.f) + Ez;
+    a.e0[c] = Ex + B5 * P5;  // exx-bar
+    a.e1[c] = Ez + B6 * P6;  // ezz-bar
+    if (o5) a.ap[4][c] = A5 * P5;
+    if (o6) a.ap[5][c] = A6 * P6;
   }
-  // txz += cmu (ezx + p7' + exz + p8')
-  const float T = mu * txz;
-  const float P7 = (o7 ? a.ap[6][c] : 0.f) + T, P8 = (o8 ? a.ap[7][c] : 0.f) + T;
-  a.e2[c] = T + B7 * P7;  // ezx-bar
-  a.e3[c] = T + B8 * P8;  // exz-bar
-  if (o7) a.ap[6][c] = A7 * P7;
-  if (o8) a.ap[7][c] = A8 * P8;
-  // txx += cl2m Ex + clam Ez, tzz += clam Ex + cl2m Ez
-  const float Ex = l2m * txx + lam * tzz, Ez = lam * txx + l2m * tzz;
-  const float P5 = (o5 ? a.ap[4][c] : 0.f) + Ex, P6 = (o6 ? a.ap[5][c] : 0.f) + Ez;
-  a.e0[c] = Ex + B5 * P5;  // exx-bar
-  a.e1[c] = Ez + B6 * P6;  // ezz-bar
-  if (o5) a.ap[4][c] = A5 * P5;
-  if (o6) a.ap[5][c] = A6 * P6;
+  if (a.gacc) {
+    double* ga = a.gacc + pc;
+    ga[G_L2M * g.fstride] += sl2m;
+    ga[G_LAM * g.fstride] += slam;
+    ga[G_MU * g.fstride] += smu;
+  }
 }
 
 // ----------------------------------------------------------- stress, gather
@@ -150,44 +165,55 @@ __global__ void el_adj_rec_kernel(const ElAdjArgs a) {
 __global__ void __launch_bounds__(AT) el_adj_vel_pt_kernel(const ElAdjArgs a) {
   if (*a.status) return;
   const Geom& g = a.g;
-  const int x = blockIdx.x * AT + threadIdx.x, z = blockIdx.y, s = blockIdx.z;
+  const int x = blockIdx.x * AT + threadIdx.x, z = blockIdx.y;
   if (x >= g.NXp) return;
-  const size_t c = (size_t)s * g.fstride + (size_t)z * g.NXp + x;
+  const size_t pc = (size_t)z * g.NXp + x;
   if (x >= g.NX) {
-    a.e0[c] = a.e1[c] = a.e2[c] = a.e3[c] = 0.f;
+    for (int s = 0; s < g.nshot; ++s) {
+      const size_t c = (size_t)s * g.fstride + pc;
+      a.e0[c] = a.e1[c] = a.e2[c] = a.e3[c] = 0.f;
+    }
     return;
   }
-  const size_t pc = (size_t)z * g.NXp + x;
-  const float vx = a.avx[c], vz = a.avz[c];
+  const float cbx = a.cbx[pc], cbz = a.cbz[pc];
   // profile pairs of p1 (x, half points), p2 (z), p3 (x), p4 (z, half points)
   const float A1 = a.axh[x], B1 = a.bxh[x], A2 = a.az[z], B2 = a.bz[z];
   const float A3 = a.ax[x], B3 = a.bx[x], A4 = a.azh[z], B4 = a.bzh[z];
   const bool o1 = A1 != 0.f || B1 != 0.f, o2 = A2 != 0.f || B2 != 0.f;
   const bool o3 = A3 != 0.f || B3 != 0.f, o4 = A4 != 0.f || B4 != 0.f;
-  if (a.gacc) {
-    const Fld txx = fld(a.ftxx, g, s), tzz = fld(a.ftzz, g, s), txz = fld(a.ftxz, g, s);
-    const float sx = dpx(txx, z, x) + (o1 ? a.fp[0][c] : 0.f) + dmz(txz, z, x) +
-                     (o2 ? a.fp[1][c] : 0.f);
-    const float sz = dmx(txz, z, x) + (o3 ? a.fp[2][c] : 0.f) + dpz(tzz, z, x) +
-                     (o4 ? a.fp[3][c] : 0.f);
-    float* ga = a.gacc + (size_t)s * 5 * g.fstride + pc;
-    ga[G_BX * g.fstride] += vx * sx;
-    ga[G_BZ * g.fstride] += vz * sz;
+  double sbx = 0.0, sbz = 0.0;
+  for (int s = 0; s < g.nshot; ++s) {
+    const size_t c = (size_t)s * g.fstride + pc;
+    const float vx = a.avx[c], vz = a.avz[c];
+    if (a.gacc) {
+      const Fld txx = fld(a.ftxx, g, s), tzz = fld(a.ftzz, g, s), txz = fld(a.ftxz, g, s);
+      const float sx = dpx(txx, z, x) + (o1 ? a.fp[0][c] : 0.f) + dmz(txz, z, x) +
+                       (o2 ? a.fp[1][c] : 0.f);
+      const float sz = dmx(txz, z, x) + (o3 ? a.fp[2][c] : 0.f) + dpz(tzz, z, x) +
+                       (o4 ? a.fp[3][c] : 0.f);
+      sbx += (double)(vx * sx);
+      sbz += (double)(vz * sz);
+    }
+    // vx += cbx (dxt + p1' + dzt + p2')
+    const float Q = cbx * vx;
+    const float P1 = (o1 ? a.ap[0][c] : 0.f) + Q, P2 = (o2 ? a.ap[1][c] : 0.f) + Q;
+    a.e0[c] = Q + B1 * P1;  // dxt-bar (Dpx txx)
+    a.e1[c] = Q + B2 * P2;  // dzt-bar (Dmz txz)
+    if (o1) a.ap[0][c] = A1 * P1;
+    if (o2) a.ap[1][c] = A2 * P2;
+    // vz += cbz (dxt + p3' + dzt + p4')
+    const float Qz = cbz * vz;
+    const float P3 = (o3 ? a.ap[2][c] : 0.f) + Qz, P4 = (o4 ? a.ap[3][c] : 0.f) + Qz;
+    a.e2[c] = Qz + B3 * P3;  // dxt-bar (Dmx txz)
+    a.e3[c] = Qz + B4 * P4;  // dzt-bar (Dpz tzz)
+    if (o3) a.ap[2][c] = A3 * P3;
+    if (o4) a.ap[3][c] = A4 * P4;
   }
-  // vx += cbx (dxt + p1' + dzt + p2')
-  const float Q = a.cbx[pc] * vx;
-  const float P1 = (o1 ? a.ap[0][c] : 0.f) + Q, P2 = (o2 ? a.ap[1][c] : 0.f) + Q;
-  a.e0[c] = Q + B1 * P1;  // dxt-bar (Dpx txx)
-  a.e1[c] = Q + B2 * P2;  // dzt-bar (Dmz txz)
-  if (o1) a.ap[0][c] = A1 * P1;
-  if (o2) a.ap[1][c] = A2 * P2;
-  // vz += cbz (dxt + p3' + dzt + p4')
-  const float Qz = a.cbz[pc] * vz;
-  const float P3 = (o3 ? a.ap[2][c] : 0.f) + Qz, P4 = (o4 ? a.ap[3][c] : 0.f) + Qz;
-  a.e2[c] = Qz + B3 * P3;  // dxt-bar (Dmx txz)
-  a.e3[c] = Qz + B4 * P4;  // dzt-bar (Dpz tzz)
-  if (o3) a.ap[2][c] = A3 * P3;
-  if (o4) a.ap[3][c] = A4 * P4;
+  if (a.gacc) {
+    double* ga = a.gacc + pc;
+    ga[G_BX * g.fstride] += sbx;
+    ga[G_BZ * g.fstride] += sbz;
+  }
 }
 
 // --------------------------------------------------------- velocity, gather
@@ -218,15 +244,12 @@ __device__ __forceinline__ double mu_at(const float* model, const Geom& g, int p
   const double vs = mval(model, g, padded, 1, z, x);
   return mval(model, g, padded, 2, z, x) * vs * vs;
 }
-// coefficient adjoint k at padded point (z, x), summed over shots in FP64
-__device__ __forceinline__ double gsum(const float* gacc, const Geom& g, int k, int z, int x) {
-  double t = 0.0;
-  for (int s = 0; s < g.nshot; ++s)
-    t += gacc[((size_t)s * 5 + k) * g.fstride + (size_t)z * g.NXp + x];
-  return t;
+// coefficient adjoint k at padded point (z, x), summed over shots and steps
+__device__ __forceinline__ double gsum(const double* gacc, const Geom& g, int k, int z, int x) {
+  return gacc[(size_t)k * g.fstride + (size_t)z * g.NXp + x];
 }
 
-__global__ void el_grad_kernel(const Geom g, const float* gacc, const float* model, int padded,
+__global__ void el_grad_kernel(const Geom g, const double* gacc, const float* model, int padded,
                                double sc, float* grad, const int* status) {
   if (*status) return;
   const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -339,24 +362,25 @@ void launch_el_snapshot(const ElSnapArgs& a, cudaStream_t st) {
 void launch_el_adj_step(const ElAdjArgs& a, cudaStream_t st) {
   const Geom& g = a.g;
   const dim3 grid((g.NXp + AT - 1) / AT, g.NZ, g.nshot);
+  const dim3 cells((g.NXp + AT - 1) / AT, g.NZ);  // pointwise kernels: all shots per thread
   int k = 0;
   if (a.wgrad) {
     el_adj_src_kernel<<<(g.nshot + 127) / 128, 128, 0, st>>>(a);
     ++k;
   }
-  el_adj_str_pt_kernel<<<grid, AT, 0, st>>>(a);
+  el_adj_str_pt_kernel<<<cells, AT, 0, st>>>(a);
   el_adj_str_sc_kernel<<<grid, AT, 0, st>>>(a);
   k += 2;
   if (a.res && g.nrec > 0) {
     el_adj_rec_kernel<<<dim3((g.nrec + 127) / 128, g.nshot), 128, 0, st>>>(a);
     ++k;
   }
-  el_adj_vel_pt_kernel<<<grid, AT, 0, st>>>(a);
+  el_adj_vel_pt_kernel<<<cells, AT, 0, st>>>(a);
   el_adj_vel_sc_kernel<<<grid, AT, 0, st>>>(a);
   note_launches(k + 2);
 }
 
-void launch_el_grad(const Geom& g, const float* gacc, const float* model, int padded, float dx,
+void launch_el_grad(const Geom& g, const double* gacc, const float* model, int padded, float dx,
                     float dt, float* grad, const int* status, cudaStream_t st) {
   const double sc = (double)dt / (double)dx;
   el_grad_kernel<<<dim3((g.nx + 127) / 128, g.nz), 128, 0, st>>>(g, gacc, model, padded, sc,

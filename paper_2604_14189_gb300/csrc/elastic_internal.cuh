@@ -52,9 +52,10 @@ void launch_el_step(const ElStepArgs& a, cudaStream_t st);
 // Elastic adjoint step (elastic_adjoint.cu): the transpose of one
 // ElStepArgs step, run backwards in time.  Adjoint state (vx, vz, txx, tzz,
 // txz, p1..p8) in av*, at*, ap; e0..e3 scratch fields [S][NZ][NXp].  With
-// gacc non-null the step also accumulates d J / d (cl2m, clam, cmu, cbx, cbz)
-// per shot ([S][5][NZ][NXp]) from the forward state: fvx, fvz = v^{n+1/2}
-// and fp = p1..p8 after step n, ft* = tau^n (before the step).
+// gacc non-null the step also adds d J / d (cl2m, clam, cmu, cbx, cbz),
+// summed over the shots, to the FP64 accumulators gacc [5][NZ][NXp], from
+// the forward state: fvx, fvz = v^{n+1/2} and fp = p1..p8 after step n,
+// ft* = tau^n (before the step).
 struct ElAdjArgs {
   Geom g;
   float *avx, *avz, *atxx, *atzz, *atxz;
@@ -62,7 +63,7 @@ struct ElAdjArgs {
   float *e0, *e1, *e2, *e3;
   const float *fvx, *fvz, *ftxx, *ftzz, *ftxz;
   const float* fp[8];
-  float* gacc;
+  double* gacc;
   const float *cbx, *cbz, *cl2m, *clam, *cmu;
   const float *ax, *bx, *axh, *bxh, *az, *bz, *azh, *bzh;
   const float* res;     // [S][2][R][nt] injected at the receivers, or null
@@ -86,9 +87,9 @@ struct ElSnapArgs {
   const float *ax, *bx, *axh, *bxh, *az, *bz, *azh, *bzh;
 };
 void launch_el_snapshot(const ElSnapArgs& a, cudaStream_t st);
-// d J / d (vp, vs, rho) on interior cells, [3][nz][nx], from the per-shot
-// coefficient adjoints (FP64 sum over shots); padding held fixed.
-void launch_el_grad(const Geom& g, const float* gacc, const float* model, int padded, float dx,
+// d J / d (vp, vs, rho) on interior cells, [3][nz][nx], from the FP64
+// coefficient adjoints; padding held fixed.
+void launch_el_grad(const Geom& g, const double* gacc, const float* model, int padded, float dx,
                     float dt, float* grad, const int* status, cudaStream_t st);
 
 }  // namespace sweep

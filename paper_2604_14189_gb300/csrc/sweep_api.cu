@@ -168,7 +168,7 @@ Layout layout(const sweep_problem* p, int mode) {
       while ((long long)C * C < g.nt) ++C;
       L.el_C = C;
       L.el_ncp = (g.nt + C - 1) / C;
-      L.el_g = b.take(5 * F);
+      L.el_g = b.take(5 * sizeof(double) * (size_t)g.fstride);  // FP64, summed over shots
       L.data = b.take(sizeof(float) * (size_t)g.nshot * 2 * g.nrec * g.nt);
       L.el_ck = b.take((L.fwd_hi - L.fwd_lo) * (size_t)L.el_ncp);
       L.el_seg = b.take((L.fwd_hi - L.fwd_lo) * (size_t)C);
@@ -569,8 +569,8 @@ int elastic_reverse_loop(const sweep_problem* p, const Layout& L, void* ws, cons
     }
     return SWEEP_OK;
   }
-  a.gacc = at<float>(ws, L.el_g);
-  cudaMemsetAsync(a.gacc, 0, 5 * F, st);
+  a.gacc = at<double>(ws, L.el_g);
+  cudaMemsetAsync(a.gacc, 0, 5 * sizeof(double) * (size_t)g.fstride, st);
   char* state = at<char>(ws, L.fwd_lo);
   char* ck = at<char>(ws, L.el_ck);
   char* seg = at<char>(ws, L.el_seg);
@@ -724,7 +724,7 @@ int sweep_gradient(const sweep_problem* p, const float* model, const float* wave
     note_launches(2);
     rc = elastic_reverse_loop(p, L, ws, wavelet, src, rec, d, nullptr, true, st);
     if (rc) return rc;
-    launch_el_grad(g, at<float>(ws, L.el_g), model, (p->flags & SWEEP_F_PADDED_MODEL) ? 1 : 0,
+    launch_el_grad(g, at<double>(ws, L.el_g), model, (p->flags & SWEEP_F_PADDED_MODEL) ? 1 : 0,
                    p->dx, p->dt, grad, at<int>(ws, L.status), st);
     return cuda_rc(cudaGetLastError());
   }
