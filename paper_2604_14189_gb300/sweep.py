@@ -166,6 +166,36 @@ def _check_dtype(t, dt, name):
         raise TypeError(f"sweep: {name} must be {dt}, got {t.dtype}")
 
 
+def _check_size(t, shape, name):
+    """The C ABI sees only pointers, so a tensor with fewer elements than the
+    call touches would be read or written out of bounds on the GPU: the
+    element count must be that of `shape` (any view of the same layout)."""
+    if t is None:
+        return
+    n = 1
+    for d in shape:
+        n *= int(d)
+    if t.numel() != n:
+        raise ValueError(f"sweep: {name} must hold {n} elements {tuple(shape)}, "
+                         f"got shape {tuple(t.shape)}")
+
+
+def _model_shape(p: Problem):
+    npar = 3 if p.physics == ELASTIC else 1
+    if p.flags & F_PADDED_MODEL:
+        nz, nx = p.nz + 2 * p.pml, p.nx + 2 * p.pml
+    else:
+        nz, nx = p.nz, p.nx
+    return (npar, nz, nx)
+
+
+def _check_inputs(p: Problem, model, wavelet=None, src=None, rec=None):
+    _check_size(model, _model_shape(p), "model")
+    _check_size(wavelet, (p.nshot, p.nt), "wavelet")
+    _check_size(src, (p.nshot, 2), "src")
+    _check_size(rec, (p.nshot, p.nrec, 2), "rec")
+
+
 def _stream(stream):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -219,9 +249,12 @@ def sweep_forward(p: Problem, model, wavelet, src, rec, data=None, ws=None, stre
     _check_dtype(src, torch.int32, "src")
     _check_dtype(rec, torch.int32, "rec")
     ncomp = 2 if p.physics == ELASTIC else 1
+    _check_inputs(p, model, wavelet, src, rec)
     if data is None:
         data = torch.empty((p.nshot, ncomp, p.nrec, p.nt), dtype=torch.float32,
                            device=model.device)
+    _check_dtype(data, torch.float32, "data")
+    _check_size(data, (p.nshot, ncomp, p.nrec, p.nt), "data")
     if ws is None:
         ws = alloc_workspace(p, MODE_FORWARD, model.device)
     w, wn = _ws_args(ws)
@@ -236,8 +269,15 @@ def sweep_adjoint(p: Problem, model, adj_data, src, rec, wavelet_grad=None, ws=N
     """wavelet_grad [nshot][nt]."""
     _check_dtype(model, torch.float32, "model")
     _check_dtype(adj_data, torch.float32, "adj_data")
+    _check_dtype(src, torch.int32, "src")
+    _check_dtype(rec, torch.int32, "rec")
+    ncomp = 2 if p.physics == ELASTIC else 1
+    _check_inputs(p, model, None, src, rec)
+    _check_size(adj_data, (p.nshot, ncomp, p.nrec, p.nt), "adj_data")
     if wavelet_grad is None:
         wavelet_grad = torch.empty((p.nshot, p.nt), dtype=torch.float32, device=model.device)
+    _check_dtype(wavelet_grad, torch.float32, "wavelet_grad")
+    _check_size(wavelet_grad, (p.nshot, p.nt), "wavelet_grad")
     if ws is None:
         ws = alloc_workspace(p, MODE_ADJOINT, model.device)
     w, wn = _ws_args(ws)
@@ -252,15 +292,28 @@ def sweep_gradient(p: Problem, model, wavelet, src, rec, d_obs, grad=None, misfi
     """Returns (grad, misfit (device float64 scalar), illum or None); grad is
     [nz][nx] (acoustic: d J / d vp) or [3][nz][nx] (elastic: vp, vs, rho)."""
     _check_dtype(model, torch.float32, "model")
+    _check_dtype(wavelet, torch.float32, "wavelet")
+    _check_dtype(src, torch.int32, "src")
+    _check_dtype(rec, torch.int32, "rec")
     _check_dtype(d_obs, torch.float32, "d_obs")
+    ncomp = 2 if p.physics == ELASTIC else 1
+    _check_inputs(p, model, wavelet, src, rec)
+    _check_size(d_obs, (p.nshot, ncomp, p.nrec, p.nt), "d_obs")
     dev = model.device
+    shape = (3, p.nz, p.nx) if p.physics == ELASTIC else (p.nz, p.nx)
     if grad is None:
-        shape = (3, p.nz, p.nx) if p.physics == ELASTIC else (p.nz, p.nx)
         grad = torch.empty(shape, dtype=torch.float32, device=dev)
     if misfit is None:
         misfit = torch.empty((), dtype=torch.float64, device=dev)
     if illum is None and want_illum:
         illum = torch.empty((p.nz, p.nx), dtype=torch.float32, device=dev)
+    _check_dtype(grad, torch.float32, "grad")
+    _check_size(grad, shape, "grad")
+    _check_dtype(misfit, torch.float64, "misfit")
+    if misfit.numel() != 1:
+        raise ValueError("sweep: misfit must be a one-element float64 tensor")
+    _check_dtype(illum, torch.float32, "illum")
+    _check_size(illum, (p.nz, p.nx), "illum")
     if ws is None:
         ws = alloc_workspace(p, MODE_GRADIENT, dev)
     w, wn = _ws_args(ws)

@@ -96,3 +96,37 @@ def test_wait_timeout_diagnostic_checks_workspace(lib):
     assert L.sweep_check_wait_timeout(None, 1024, None) == sweep.EWORKSPACE
     assert L.sweep_check_wait_timeout(ctypes.c_void_p(256), 2, None) == sweep.EWORKSPACE
     assert L.sweep_check_wait_timeout(ctypes.c_void_p(257), 1024, None) == sweep.EWORKSPACE
+
+
+def test_binding_rejects_wrong_sizes_before_any_call():
+    """The binding checks every tensor's element count against the problem
+    before it reaches the C ABI (which sees only pointers); CPU tensors are
+    enough: the size check comes before the device check."""
+    import torch
+    from paper_2604_14189_gb300 import sweep
+    p = _prob(sweep)  # nz 20, nx 30, nt 10, 2 shots, 3 receivers
+    f32, i32 = torch.float32, torch.int32
+    good = dict(model=torch.zeros(20, 30, dtype=f32), wavelet=torch.zeros(2, 10, dtype=f32),
+                src=torch.zeros(2, 2, dtype=i32), rec=torch.zeros(2, 3, 2, dtype=i32))
+    bad = dict(model=torch.zeros(20, 29, dtype=f32), wavelet=torch.zeros(2, 9, dtype=f32),
+               src=torch.zeros(1, 2, dtype=i32), rec=torch.zeros(2, 2, 2, dtype=i32))
+    for k in bad:
+        args = dict(good, **{k: bad[k]})
+        with pytest.raises(ValueError, match=k):
+            sweep.sweep_forward(p, args["model"], args["wavelet"], args["src"], args["rec"])
+    with pytest.raises(ValueError, match="data"):
+        sweep.sweep_forward(p, **good, data=torch.zeros(2, 1, 3, 9, dtype=f32))
+    with pytest.raises(ValueError, match="d_obs"):
+        sweep.sweep_gradient(p, good["model"], good["wavelet"], good["src"], good["rec"],
+                             torch.zeros(2, 1, 3, 11, dtype=f32))
+    with pytest.raises(ValueError, match="grad"):
+        sweep.sweep_gradient(p, good["model"], good["wavelet"], good["src"], good["rec"],
+                             torch.zeros(2, 1, 3, 10, dtype=f32),
+                             grad=torch.zeros(20, 31, dtype=f32))
+    with pytest.raises(ValueError, match="adj_data"):
+        sweep.sweep_adjoint(p, good["model"], torch.zeros(2, 3, 11, dtype=f32), good["src"],
+                            good["rec"])
+    # a padded model has the padded size
+    q = _prob(sweep, flags=sweep.F_PADDED_MODEL)
+    with pytest.raises(ValueError, match="model"):
+        sweep.sweep_forward(q, good["model"], good["wavelet"], good["src"], good["rec"])
