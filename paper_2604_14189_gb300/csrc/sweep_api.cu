@@ -124,10 +124,15 @@ bool valid_problem(const sweep_problem* p) {
   if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return false;
   if (!(p->f_ref >= 0.f) || !std::isfinite(p->f_ref)) return false;
   if (!std::isfinite(p->v_pml)) return false;
-  // keep every per-shot index within 32-bit loops where they are used
+  // keep every index within one shot's field (z * NXp + x, on the padded
+  // row pitch) and the count of (tile, shot) units within 32 bits
   const long long NZ = (long long)p->nz + 2LL * p->pml, NX = (long long)p->nx + 2LL * p->pml;
-  if (NZ > (1 << 20) || NX > (1 << 20) || NZ * NX > (1LL << 31)) return false;
+  if (NZ > (1 << 20) || NX > (1 << 20)) return false;
+  const long long NXp = (NX + 31) / 32 * 32;
+  if (NZ * NXp >= (1LL << 31)) return false;
   if (p->nshot > 65535) return false;  // gridDim.y / z
+  const long long tiles = (NZ + 15) / 16 * ((NX + 127) / 128);  // smallest tiles in use
+  if (tiles * p->nshot >= (1LL << 31)) return false;
   return true;
 }
 

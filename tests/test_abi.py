@@ -50,10 +50,18 @@ def test_workspace_size_and_validation():
     grd = sweep.workspace_bytes(p, sweep.MODE_GRADIENT)
     assert 0 < fwd < grd and 0 < adj < grd
     for bad in (dict(nz=0), dict(nx=-1), dict(pml=-1), dict(nt=0), dict(nshot=-1),
-                dict(dx=0.0), dict(dt=-1.0), dict(dx=float("nan"))):
+                dict(dx=0.0), dict(dt=-1.0), dict(dx=float("nan")),
+                # one shot's field beyond 32-bit indices on the padded row pitch
+                dict(nz=46341, nx=46341, pml=0, nshot=1),
+                # (tile, shot) units beyond 32 bits
+                dict(nz=20000, nx=20000, pml=0, nshot=65535),
+                dict(nshot=65536)):
         q = _prob(sweep, **bad)
         assert sweep.lib().sweep_workspace_bytes(ctypes.byref(q), 0) == 0, bad
     assert sweep.lib().sweep_workspace_bytes(ctypes.byref(p), 7) == 0
+    # the largest sizes still accepted
+    big = _prob(sweep, nz=46000, nx=46000, pml=0, nshot=1)
+    assert sweep.lib().sweep_workspace_bytes(ctypes.byref(big), 0) > 0
 
 
 def test_host_errors_before_launch():
