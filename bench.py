@@ -399,7 +399,7 @@ def run_sweep(args, w, rank, world, local_rank):
     path_gbs = (alg_bytes_fwd(c) + alg_bytes_bwd(c)) * nshot * nt / (ms_step * 1e-3) / 1e9
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        g, el, cores, sample = oracle_sample(w, nshot, 600)
+        g, el, cores, sample = oracle_sample(w, nshot, 700)
         cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
