@@ -76,18 +76,22 @@ __global__ void el_params_kernel(const ElParamArgs a) {
 
 // ------------------------------------------------------------------ tiles
 // Persistent CTAs (one per SM) take (tile, shot) units round-robin; tiles are
-// TB_Z rows x TB_X cells, a warp owns TB_Z / 8 rows, a lane 4 consecutive
-// cells.  The fields each kernel differentiates (and the coefficients) are
+// TB_Z rows x TB_X cells, a warp owns E_RPW rows, a lane 4 consecutive
+// cells.  Shape, threads and stages chosen by a sweep on GB300 (500x1500+40,
+// 64 shots): 16 rows x 3 stages x 256 threads 72.0 Gpts/s, 16 x 4 x 256 68.1,
+// 16 x 3 x 512 76.7, 24 x 3 x 256 70.6, 32 x 2 x 256 80.4, 48 x 1 x 256 83.2,
+// 32 x 2 x 512 83.5 (taller tiles read fewer halo rows per output row; 48 and
+// 64 rows spill at 512 threads).  The fields each kernel differentiates (and the coefficients) are
 // staged by a TMA pipeline of E_STAGES stages; the fields it updates in place
 // and the CPML memory variables (read only on tiles that meet a border
 // strip) are read with 16-byte loads issued before the stage wait.
 constexpr int TB_X = 128;
-constexpr int TB_Z = 16;
-constexpr int E_THREADS = 256;
+constexpr int TB_Z = 32;
+constexpr int E_THREADS = 512;
 constexpr int E_RPW = TB_Z / (E_THREADS / 32);  // rows per warp
 constexpr int E_HW = TB_X + 8;                  // x-halo width
 constexpr int E_HZ = TB_Z + 8;                  // z-halo height
-constexpr int E_STAGES = 3;
+constexpr int E_STAGES = 2;
 constexpr int E_TABLE = 256;                    // unit descriptors per CTA
 
 struct __align__(128) VelStage {
