@@ -38,7 +38,7 @@ struct Geom {
 // cells of a row.  Halo tiles are IN_HW wide and 8 rows taller.
 constexpr int IN_BX = 128;
 constexpr int IN_BZ_F = 32;
-constexpr int IN_BZ_B = 16;
+constexpr int IN_BZ_B = 32;
 constexpr int IN_HW = IN_BX + 8;  // halo tile width
 
 struct AcInFwdArgs {
