@@ -149,6 +149,26 @@ int sweep_gradient(const sweep_problem* prob, const float* model,
 /* FP64 dot product sum_i a[i] b[i] of two device float arrays into the device
  * double *out (for dot-product and finite-difference tests).  ws: at least
  * sweep_dot_workspace_bytes() bytes of device scratch. */
+/* Gradients of several acoustic problems in one call (heterogeneous batch:
+ * the shot / model dimension of Sec. 2.2 with each model of its own size,
+ * border, record length and shot count).  Problem i takes the arguments of
+ * sweep_gradient: probs[i], models[i], wavelets[i], srcs[i], recs[i],
+ * d_obs[i], grads[i], misfits[i] (device double, required) and its own
+ * workspace ws[i] of ws_bytes[i] >= sweep_workspace_bytes(&probs[i],
+ * SWEEP_MODE_GRADIENT) bytes (no two problems share one); no illumination.
+ * The problems run in groups of up to 16 in lockstep: every time-step kernel
+ * launch carries the step of each problem of the group (a problem past its
+ * record length drops out), so the launches' fixed cost is shared.  Results
+ * equal separate sweep_gradient calls to rounding.  Every problem is checked
+ * on the host before any launch (first error returned; acoustic only, else
+ * SWEEP_EUNSUPPORTED); device errors are latched in each problem's
+ * workspace (sweep_status(ws[i])).  Asynchronous on `stream`. */
+int sweep_gradient_batch(int nprob, const sweep_problem* probs, const float* const* models,
+                         const float* const* wavelets, const int32_t* const* srcs,
+                         const int32_t* const* recs, const float* const* d_obs,
+                         float* const* grads, double* const* misfits, void* const* ws,
+                         const size_t* ws_bytes, void* stream);
+
 size_t sweep_dot_workspace_bytes(void);
 int sweep_dot(const float* a, const float* b, int64_t n, double* out, void* ws,
               size_t ws_bytes, void* stream);

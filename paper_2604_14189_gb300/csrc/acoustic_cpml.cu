@@ -30,6 +30,8 @@
 // cells of a row (16-byte accesses) and reads its 4 + 4 x-neighbours as two
 // more 16-byte loads.  Every load of a thread is issued before its
 // arithmetic, so the memory latency is paid once per thread.
+#include <algorithm>
+
 #include "acoustic_common.cuh"
 
 namespace sweep {
@@ -217,13 +219,17 @@ __device__ __forceinline__ void fwd_ring(const AcFixArgs& a, int s, int bl) {
   }
 }
 
-__global__ void __launch_bounds__(FT) ac_fix_fwd_kernel(const AcFixArgs a) {
+template <int NP>
+__global__ void __launch_bounds__(FT)
+    ac_fix_fwd_kernel(const __grid_constant__ StepBatch<AcFixArgs, NP> m) {
+  int blk, nblk;  // this block's index and the block count of its problem
+  const AcFixArgs& a = m.p[step_problem(m, &blk, &nblk)];
   grid_dep_wait();
   grid_dep_trigger();
   if (*a.status) return;
   const int bps = a.nbz + a.nbx + a.nbr + a.nbs;
-  const int s = blockIdx.x / bps;
-  int b = blockIdx.x - s * bps;
+  const int s = blk / bps;
+  int b = blk - s * bps;
   if (b < a.nbz) {
     fwd_z(a, s, b);
     return;
@@ -373,13 +379,17 @@ __device__ __forceinline__ void bwd_ring(const AcFixArgs& a, int s, int bl) {
   }
 }
 
-__global__ void __launch_bounds__(FT) ac_fix_bwd_kernel(const AcFixArgs a) {
+template <int NP>
+__global__ void __launch_bounds__(FT)
+    ac_fix_bwd_kernel(const __grid_constant__ StepBatch<AcFixArgs, NP> m) {
+  int blk, nblk;  // this block's index and the block count of its problem
+  const AcFixArgs& a = m.p[step_problem(m, &blk, &nblk)];
   grid_dep_wait();
   grid_dep_trigger();
   if (*a.status) return;
   const int bps = a.nbz + a.nbx + a.nbr + a.nbs;
-  const int s = blockIdx.x / bps;
-  int b = blockIdx.x - s * bps;
+  const int s = blk / bps;
+  int b = blk - s * bps;
   if (b < a.nbz) {
     bwd_z(a, s, b);
     return;
@@ -401,9 +411,11 @@ int cdiv(int a, int b) { return (a + b - 1) / b; }
 
 }  // namespace
 
-void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st) {
+// Work split of one problem's step (blocks per shot of each part); returns
+// the blocks per shot, 0 when the step has no CPML, receiver or ring work.
+int fix_fwd_split(AcFixArgs& a) {
   const Geom& g = a.g;
-  if (g.nshot <= 0) return;
+  if (g.nshot <= 0) return 0;
   a.zbx = cdiv(g.NX, FT);
   a.nchz = g.P > 0 ? 2 * cdiv(g.P, ZCH_F) : 0;
   a.xb = x_bands(g.P, g.P + g.nx, g.NX);
@@ -411,17 +423,12 @@ void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st) {
   a.nbx = g.P > 0 ? cdiv(g.NZ, XROWS) : 0;
   a.nbr = (a.data && g.nrec > 0) ? cdiv(g.nrec, FT) : 0;
   a.nbs = (a.save && g.nring > 0) ? cdiv(cdiv(g.nring, 4), FT) : 0;
-  const int bps = a.nbz + a.nbx + a.nbr + a.nbs;
-  if (bps == 0) return;
-  void* tok = profile_begin(SWEEP_K_AC_FWD_FR, st);
-  launch_dependent(ac_fix_fwd_kernel, dim3(bps * g.nshot), dim3(FT), 0, st, a);
-  profile_end(tok, st);
-  note_launches(1);
+  return a.nbz + a.nbx + a.nbr + a.nbs;
 }
 
-void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st) {
+int fix_bwd_split(AcFixArgs& a) {
   const Geom& g = a.g;
-  if (g.nshot <= 0) return;
+  if (g.nshot <= 0) return 0;
   const int lo_end = band_lo_end(g.P, g.NZ), hi_start = band_hi_start(g.P, g.nz, g.NZ);
   a.zbx = cdiv(g.NX, FT);
   a.nchz = g.P > 0 ? cdiv(lo_end, ZCH_B) + cdiv(g.NZ - hi_start, ZCH_B) : 0;
@@ -430,12 +437,55 @@ void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st) {
   a.nbx = g.P > 0 ? cdiv(g.NZ, XROWS) : 0;
   a.nbr = (a.res && g.nrec > 0 && a.n >= 1) ? cdiv(g.nrec, FT) : 0;
   a.nbs = (a.save && a.uring && g.nring > 0) ? cdiv(cdiv(g.nring, 4), FT) : 0;
-  const int bps = a.nbz + a.nbx + a.nbr + a.nbs;
+  return a.nbz + a.nbx + a.nbr + a.nbs;
+}
+
+void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st) {
+  const int bps = fix_fwd_split(a);
   if (bps == 0) return;
-  void* tok = profile_begin(SWEEP_K_AC_BWD_FR, st);
-  launch_dependent(ac_fix_bwd_kernel, dim3(bps * g.nshot), dim3(FT), 0, st, a);
+  StepBatch<AcFixArgs, 1> m;
+  m.p[0] = a;
+  void* tok = profile_begin(SWEEP_K_AC_FWD_FR, st);
+  launch_dependent(ac_fix_fwd_kernel<1>, dim3(bps * a.g.nshot), dim3(FT), 0, st, m);
   profile_end(tok, st);
   note_launches(1);
+}
+
+void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st) {
+  const int bps = fix_bwd_split(a);
+  if (bps == 0) return;
+  StepBatch<AcFixArgs, 1> m;
+  m.p[0] = a;
+  void* tok = profile_begin(SWEEP_K_AC_BWD_FR, st);
+  launch_dependent(ac_fix_bwd_kernel<1>, dim3(bps * a.g.nshot), dim3(FT), 0, st, m);
+  profile_end(tok, st);
+  note_launches(1);
+}
+
+template <int (*SPLIT)(AcFixArgs&), typename K>
+void launch_fix_batch(K kernel, const AcFixArgs* a, int np, cudaStream_t st) {
+  if (np <= 0 || np > kStepBatch) return;
+  StepBatch<AcFixArgs, kStepBatch> m;
+  m.start[0] = 0;
+  for (int i = 0; i < kStepBatch; ++i) {
+    int c = 0;
+    if (i < np) {
+      m.p[i] = a[i];
+      c = SPLIT(m.p[i]) * m.p[i].g.nshot;  // consecutive blocks of problem i
+    }
+    m.start[i + 1] = m.start[i] + c;
+  }
+  if (m.start[kStepBatch] == 0) return;
+  launch_dependent(kernel, dim3(m.start[kStepBatch]), dim3(FT), 0, st, m);
+  note_launches(1);
+}
+
+void launch_ac_fix_fwd_batch(const AcFixArgs* a, int np, cudaStream_t st) {
+  launch_fix_batch<fix_fwd_split>(ac_fix_fwd_kernel<kStepBatch>, a, np, st);
+}
+
+void launch_ac_fix_bwd_batch(const AcFixArgs* a, int np, cudaStream_t st) {
+  launch_fix_batch<fix_bwd_split>(ac_fix_bwd_kernel<kStepBatch>, a, np, st);
 }
 
 }  // namespace sweep

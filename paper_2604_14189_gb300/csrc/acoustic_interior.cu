@@ -13,6 +13,8 @@
 // (4 cells per lane, 16-byte shared-memory reads), walks its rows with a
 // register window for the z stencil, and stores results with 16-byte global
 // stores.
+#include <algorithm>
+
 #include "acoustic_common.cuh"
 #include "tma.cuh"
 
@@ -135,8 +137,11 @@ __device__ __forceinline__ UnitDesc make_desc(const Region& R, const Geom& g, co
 }
 
 // -------------------------------------------------------------- forward
+template <int NP>
 __global__ void __launch_bounds__(FWD_THREADS, 1)
-    ac_in_fwd_kernel(const __grid_constant__ AcInFwdArgs a) {
+    ac_in_fwd_kernel(const __grid_constant__ StepBatch<AcInFwdArgs, NP> m) {
+  int bx, G;  // this CTA's index and the CTA count of its problem
+  const AcInFwdArgs& a = m.p[step_problem(m, &bx, &G)];
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ ShotTable T;
   __shared__ UnitDesc desc[FWD_STAGES];
@@ -148,13 +153,12 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
   if (*a.status) return;
   const Geom& g = a.g;
   const Region& R = g.fin;
-  const int G = gridDim.x;
-  const int count = (a.units - (int)blockIdx.x + G - 1) / G;  // units b, b+G, ...
+  const int count = (a.units - bx + G - 1) / G;  // units b, b+G, ...
   if (count <= 0) return;
   load_shot_table(T, g, a.src, a.wavelet, a.rbox, a.n);
   __syncthreads();  // shot table visible
   for (int i = threadIdx.x; i < count && i < kUnitTable; i += FWD_THREADS)
-    utab[i] = make_desc(R, g, T, &a, nullptr, IN_BZ_F, blockIdx.x + i * G);
+    utab[i] = make_desc(R, g, T, &a, nullptr, IN_BZ_F, bx + i * G);
   if (threadIdx.x == 0) {
     for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
     fence_barrier_init();
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
     if (k < kUnitTable) {
       d = utab[k];
     } else {
-      d = make_desc(R, g, T, &a, nullptr, IN_BZ_F, blockIdx.x + k * G);
+      d = make_desc(R, g, T, &a, nullptr, IN_BZ_F, bx + k * G);
       desc[k % D] = d;
     }
     FwdStage& sg = stg[k % D];
@@ -241,8 +245,11 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
 }
 
 // -------------------------------------------------------------- backward
+template <int NP>
 __global__ void __launch_bounds__(BWD_THREADS, 1)
-    ac_in_bwd_kernel(const __grid_constant__ AcInBwdArgs a) {
+    ac_in_bwd_kernel(const __grid_constant__ StepBatch<AcInBwdArgs, NP> m) {
+  int bx, G;  // this CTA's index and the CTA count of its problem
+  const AcInBwdArgs& a = m.p[step_problem(m, &bx, &G)];
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ ShotTable T;
   __shared__ UnitDesc desc[BWD_STAGES];
@@ -255,14 +262,13 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
   if (*a.status) return;
   const Geom& g = a.g;
   const Region& R = g.bin;
-  const int G = gridDim.x;
-  const int count = (a.units - (int)blockIdx.x + G - 1) / G;
+  const int count = (a.units - bx + G - 1) / G;
   if (count <= 0) return;
   const bool img = a.do_img != 0, adj = a.do_adj != 0;
   load_shot_table(T, g, a.src, img ? a.wavelet : nullptr, a.rbox, a.n);
   __syncthreads();  // shot table visible
   for (int i = threadIdx.x; i < count && i < kUnitTable; i += BWD_THREADS)
-    utab[i] = make_desc(R, g, T, nullptr, &a, IN_BZ_B, blockIdx.x + i * G);
+    utab[i] = make_desc(R, g, T, nullptr, &a, IN_BZ_B, bx + i * G);
   if (threadIdx.x == 0) {
     for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
     fence_barrier_init();
@@ -273,7 +279,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
     if (k < kUnitTable) {
       d = utab[k];
     } else {
-      d = make_desc(R, g, T, nullptr, &a, IN_BZ_B, blockIdx.x + k * G);
+      d = make_desc(R, g, T, nullptr, &a, IN_BZ_B, bx + k * G);
       desc[k % D] = d;
     }
     BwdStage& sg = stg[k % D];
@@ -446,35 +452,101 @@ int device_sms() {
   return n;
 }
 
-void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st) {
-  if (a.units <= 0) return;
+template <int NP>
+void set_fwd_attr() {
   static const bool attr = [] {  // thread-safe one-time initialisation
-    cudaFuncSetAttribute(ac_in_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(ac_in_fwd_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kFwdSmem);
     return true;
   }();
   (void)attr;
+}
+template <int NP>
+void set_bwd_attr() {
+  static const bool attr = [] {  // thread-safe one-time initialisation
+    cudaFuncSetAttribute(ac_in_bwd_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kBwdSmem);
+    return true;
+  }();
+  (void)attr;
+}
+
+void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st) {
+  if (a.units <= 0) return;
+  set_fwd_attr<1>();
   int grid = device_sms();
   if (grid > a.units) grid = a.units;
+  StepBatch<AcInFwdArgs, 1> m;
+  m.p[0] = a;
   void* tok = profile_begin(SWEEP_K_AC_FWD_IN, st);
-  launch_dependent(ac_in_fwd_kernel, dim3(grid), dim3(FWD_THREADS), kFwdSmem, st, a);
+  launch_dependent(ac_in_fwd_kernel<1>, dim3(grid), dim3(FWD_THREADS), kFwdSmem, st, m);
   profile_end(tok, st);
   note_launches(1);
 }
 
 void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st) {
   if (a.units <= 0) return;
-  static const bool attr = [] {  // thread-safe one-time initialisation
-    cudaFuncSetAttribute(ac_in_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kBwdSmem);
-    return true;
-  }();
-  (void)attr;
+  set_bwd_attr<1>();
   int grid = device_sms();
   if (grid > a.units) grid = a.units;
+  StepBatch<AcInBwdArgs, 1> m;
+  m.p[0] = a;
   void* tok = profile_begin(SWEEP_K_AC_BWD_IN, st);
-  launch_dependent(ac_in_bwd_kernel, dim3(grid), dim3(BWD_THREADS), kBwdSmem, st, a);
+  launch_dependent(ac_in_bwd_kernel<1>, dim3(grid), dim3(BWD_THREADS), kBwdSmem, st, m);
   profile_end(tok, st);
+  note_launches(1);
+}
+
+// Several problems in one launch: the persistent CTAs (one wave, one per
+// SM) are shared out in proportion to the problems' units, at least one per
+// problem with work and never more than its units.
+int split_ctas(int units, long long total) {
+  if (units <= 0) return 0;
+  const long long c = (long long)device_sms() * units / total;
+  return (int)std::max(1LL, std::min<long long>(c, units));
+}
+
+void launch_ac_in_fwd_batch(const AcInFwdArgs* a, int np, cudaStream_t st) {
+  if (np <= 0) return;
+  if (np > kStepBatch) return;  // the caller splits larger groups
+  set_fwd_attr<kStepBatch>();
+  StepBatch<AcInFwdArgs, kStepBatch> m;
+  long long total = 0;
+  for (int i = 0; i < np; ++i) total += std::max(a[i].units, 0);
+  if (total <= 0) return;
+  m.start[0] = 0;
+  for (int i = 0; i < kStepBatch; ++i) {
+    int c = 0;
+    if (i < np) {
+      m.p[i] = a[i];
+      c = split_ctas(a[i].units, total);
+    }
+    m.start[i + 1] = m.start[i] + c;
+  }
+  launch_dependent(ac_in_fwd_kernel<kStepBatch>, dim3(m.start[kStepBatch]), dim3(FWD_THREADS),
+                   kFwdSmem, st, m);
+  note_launches(1);
+}
+
+void launch_ac_in_bwd_batch(const AcInBwdArgs* a, int np, cudaStream_t st) {
+  if (np <= 0) return;
+  if (np > kStepBatch) return;
+  set_bwd_attr<kStepBatch>();
+  StepBatch<AcInBwdArgs, kStepBatch> m;
+  long long total = 0;
+  for (int i = 0; i < np; ++i) total += std::max(a[i].units, 0);
+  if (total <= 0) return;
+  m.start[0] = 0;
+  for (int i = 0; i < kStepBatch; ++i) {
+    int c = 0;
+    if (i < np) {
+      m.p[i] = a[i];
+      c = split_ctas(a[i].units, total);
+    }
+    m.start[i + 1] = m.start[i] + c;
+  }
+  launch_dependent(ac_in_bwd_kernel<kStepBatch>, dim3(m.start[kStepBatch]), dim3(BWD_THREADS),
+                   kBwdSmem, st, m);
   note_launches(1);
 }
 

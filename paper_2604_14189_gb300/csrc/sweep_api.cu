@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 #include <mutex>
 
 #include "elastic_internal.cuh"
@@ -295,57 +296,80 @@ int region_units(const Region& R, int nshot, int bz, int* ntx) {
 // kernel over the whole padded grid, then one kernel adding both axes' CPML
 // terms, recording the receivers and saving the ring of u^n.  On
 // return the workspace holds u^{nt} in u[nt % 2] and u^{nt-1} in
-// u[(nt + 1) % 2].
-int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
-                          const float* wavelet, const int32_t* src, const int32_t* rec,
-                          float* data, bool save_ring, cudaStream_t st) {
-  const Geom g = make_geom(p);
-  cudaMemsetAsync(at<char>(ws, L.fwd_lo), 0, L.fwd_hi - L.fwd_lo, st);
-  float* save = save_ring ? at<float>(ws, L.save) : nullptr;
-  if (save) cudaMemsetAsync(save, 0, sizeof(float) * (size_t)g.nshot * g.nring, st);
-  int* status = at<int>(ws, L.status);
-
+// u[(nt + 1) % 2].  AcFwdLoop holds one problem's loop state and fills the
+// two kernels' arguments of step n (the batched entry runs several
+// problems' steps in the same launches).
+struct AcFwdLoop {
+  Geom g;
+  const Layout* L = nullptr;
+  void* ws = nullptr;
+  float* save = nullptr;
   AcInFwdArgs in{};
-  in.g = g;
-  in.units = region_units(g.fin, g.nshot, IN_BZ_F, &in.ntx);
-  CUtensorMap tu_h[2], tu_c[2];
-  for (int b = 0; b < 2; ++b)
-    if (!field_maps(g, at<float>(ws, L.u[b]), &tu_h[b], &tu_c[b], IN_BZ_F)) return SWEEP_ECUDA;
-  if (!map2(&in.tK, g, at<float>(ws, L.K), IN_BX, IN_BZ_F)) return SWEEP_ECUDA;
-  in.wavelet = wavelet;
-  in.src = src;
-  in.rbox = at<int32_t>(ws, L.rbox);
-  in.status = status;
-
   AcFixArgs fx{};
-  fx.g = g;
-  fx.K = at<float>(ws, L.K);
-  fx.ax = at<float>(ws, L.ax);
-  fx.bx = at<float>(ws, L.bx);
-  fx.az = at<float>(ws, L.az);
-  fx.bz = at<float>(ws, L.bz);
-  fx.zzin = fx.zzout = at<float>(ws, L.zez);
-  fx.zxin = fx.zxout = at<float>(ws, L.zex);
-  fx.rec = rec;
-  fx.data = data;
-  fx.status = status;
-  for (int n = 0; n < g.nt; ++n) {
+  CUtensorMap tu_h[2], tu_c[2];
+
+  int init(const sweep_problem* p, const Layout& lay, void* w, const float* wavelet,
+           const int32_t* src, const int32_t* rec, float* data, bool save_ring,
+           cudaStream_t st) {
+    g = make_geom(p);
+    L = &lay;
+    ws = w;
+    cudaMemsetAsync(at<char>(ws, L->fwd_lo), 0, L->fwd_hi - L->fwd_lo, st);
+    save = save_ring ? at<float>(ws, L->save) : nullptr;
+    if (save) cudaMemsetAsync(save, 0, sizeof(float) * (size_t)g.nshot * g.nring, st);
+    int* status = at<int>(ws, L->status);
+    in.g = g;
+    in.units = region_units(g.fin, g.nshot, IN_BZ_F, &in.ntx);
+    for (int b = 0; b < 2; ++b)
+      if (!field_maps(g, at<float>(ws, L->u[b]), &tu_h[b], &tu_c[b], IN_BZ_F))
+        return SWEEP_ECUDA;
+    if (!map2(&in.tK, g, at<float>(ws, L->K), IN_BX, IN_BZ_F)) return SWEEP_ECUDA;
+    in.wavelet = wavelet;
+    in.src = src;
+    in.rbox = at<int32_t>(ws, L->rbox);
+    in.status = status;
+    fx.g = g;
+    fx.K = at<float>(ws, L->K);
+    fx.ax = at<float>(ws, L->ax);
+    fx.bx = at<float>(ws, L->bx);
+    fx.az = at<float>(ws, L->az);
+    fx.bz = at<float>(ws, L->bz);
+    fx.zzin = fx.zzout = at<float>(ws, L->zez);
+    fx.zxin = fx.zxout = at<float>(ws, L->zex);
+    fx.rec = rec;
+    fx.data = data;
+    fx.status = status;
+    return SWEEP_OK;
+  }
+
+  void step(int n) {
     const int A = n & 1, B = (n + 1) & 1;
-    void* tok = profile_begin(SWEEP_K_AC_FWD, st);
     in.n = n;
     in.tu = tu_h[A];
     in.tup = tu_c[B];
-    in.un = at<float>(ws, L.u[B]);
-    launch_ac_in_fwd(in, st);
+    in.un = at<float>(ws, L->u[B]);
     fx.n = n;
-    fx.u = at<float>(ws, L.u[A]);
-    fx.un = at<float>(ws, L.u[B]);
-    fx.pzin = at<float>(ws, L.psz[A]);
-    fx.pzout = at<float>(ws, L.psz[B]);
-    fx.pxin = at<float>(ws, L.psx[A]);
-    fx.pxout = at<float>(ws, L.psx[B]);
+    fx.u = at<float>(ws, L->u[A]);
+    fx.un = at<float>(ws, L->u[B]);
+    fx.pzin = at<float>(ws, L->psz[A]);
+    fx.pzout = at<float>(ws, L->psz[B]);
+    fx.pxin = at<float>(ws, L->psx[A]);
+    fx.pxout = at<float>(ws, L->psx[B]);
     fx.save = save ? save + (size_t)n * g.nshot * g.nring : nullptr;  // ring of u^n
-    launch_ac_fix_fwd(fx, st);
+  }
+};
+
+int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
+                          const float* wavelet, const int32_t* src, const int32_t* rec,
+                          float* data, bool save_ring, cudaStream_t st) {
+  AcFwdLoop f;
+  const int rc = f.init(p, L, ws, wavelet, src, rec, data, save_ring, st);
+  if (rc) return rc;
+  for (int n = 0; n < f.g.nt; ++n) {
+    f.step(n);
+    void* tok = profile_begin(SWEEP_K_AC_FWD, st);
+    launch_ac_in_fwd(f.in, st);
+    launch_ac_fix_fwd(f.fx, st);
     profile_end(tok, st);
   }
   return SWEEP_OK;
@@ -355,58 +379,74 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
 // imaging condition with wavefield reconstruction (gradient) and/or the
 // adjoint source gather (wgrad).  Per step the plain kernel over the whole
 // grid, then one kernel adding both axes' CPML terms of mu^n and the
-// residual injection, and restoring the ring of u^{n-1}.
-int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
-                           const float* wavelet, const int32_t* src, const int32_t* rec,
-                           const float* res, float* wgrad, bool imaging, bool illum,
-                           cudaStream_t st) {
-  const Geom g = make_geom(p);
-  cudaMemsetAsync(at<char>(ws, L.adj_lo), 0, L.adj_hi - L.adj_lo, st);
-  const size_t F = sizeof(float) * (size_t)g.fstride * (size_t)g.nshot;
-  if (imaging) {
-    cudaMemsetAsync(at<float>(ws, L.graw), 0, F, st);
-    if (illum) cudaMemsetAsync(at<float>(ws, L.iraw), 0, F, st);
-  }
-  int* status = at<int>(ws, L.status);
-  float* save = imaging ? at<float>(ws, L.save) : nullptr;
-
+// residual injection, and restoring the ring of u^{n-1}.  Steps run
+// n = nt .. 0; AcBwdLoop::step(n) fills the arguments of step n and says
+// which of the two kernels run.
+struct AcBwdLoop {
+  Geom g;
+  const Layout* L = nullptr;
+  void* ws = nullptr;
+  float* save = nullptr;
+  bool imaging = false;
+  const float* wgrad = nullptr;
   AcInBwdArgs in{};
-  in.g = g;
-  in.units = region_units(g.bin, g.nshot, IN_BZ_B, &in.ntx);
-  CUtensorMap tu_h[2], tu_c[2], tm_h[2], tm_c[2];
-  for (int b = 0; b < 2; ++b) {
-    if (imaging && !field_maps(g, at<float>(ws, L.u[b]), &tu_h[b], &tu_c[b], IN_BZ_B))
-      return SWEEP_ECUDA;
-    if (!field_maps(g, at<float>(ws, L.m[b]), &tm_h[b], &tm_c[b], IN_BZ_B)) return SWEEP_ECUDA;
-  }
-  if (!map2(&in.tK, g, at<float>(ws, L.K), IN_BX, IN_BZ_B)) return SWEEP_ECUDA;
-  if (imaging && !field_maps(g, at<float>(ws, L.graw), nullptr, &in.tG, IN_BZ_B))
-    return SWEEP_ECUDA;
-  in.graw = imaging ? at<float>(ws, L.graw) : nullptr;
-  in.illum = (imaging && illum) ? at<float>(ws, L.iraw) : nullptr;
-  in.wavelet = wavelet;
-  in.src = src;
-  in.rbox = at<int32_t>(ws, L.rbox);
-  in.wgrad = wgrad;
-  in.status = status;
-
   AcFixArgs fx{};
-  fx.g = g;
-  fx.K = at<float>(ws, L.K);
-  fx.ax = at<float>(ws, L.ax);
-  fx.bx = at<float>(ws, L.bx);
-  fx.az = at<float>(ws, L.az);
-  fx.bz = at<float>(ws, L.bz);
-  fx.rec = rec;
-  fx.res = g.nrec > 0 ? res : nullptr;
-  fx.status = status;
-  for (int n = g.nt; n >= 0; --n) {
+  CUtensorMap tu_h[2], tu_c[2], tm_h[2], tm_c[2];
+
+  int init(const sweep_problem* p, const Layout& lay, void* w, const float* wavelet,
+           const int32_t* src, const int32_t* rec, const float* res, float* wg, bool img,
+           bool illum, cudaStream_t st) {
+    g = make_geom(p);
+    L = &lay;
+    ws = w;
+    imaging = img;
+    wgrad = wg;
+    cudaMemsetAsync(at<char>(ws, L->adj_lo), 0, L->adj_hi - L->adj_lo, st);
+    const size_t F = sizeof(float) * (size_t)g.fstride * (size_t)g.nshot;
+    if (imaging) {
+      cudaMemsetAsync(at<float>(ws, L->graw), 0, F, st);
+      if (illum) cudaMemsetAsync(at<float>(ws, L->iraw), 0, F, st);
+    }
+    int* status = at<int>(ws, L->status);
+    save = imaging ? at<float>(ws, L->save) : nullptr;
+    in.g = g;
+    in.units = region_units(g.bin, g.nshot, IN_BZ_B, &in.ntx);
+    for (int b = 0; b < 2; ++b) {
+      if (imaging && !field_maps(g, at<float>(ws, L->u[b]), &tu_h[b], &tu_c[b], IN_BZ_B))
+        return SWEEP_ECUDA;
+      if (!field_maps(g, at<float>(ws, L->m[b]), &tm_h[b], &tm_c[b], IN_BZ_B))
+        return SWEEP_ECUDA;
+    }
+    if (!map2(&in.tK, g, at<float>(ws, L->K), IN_BX, IN_BZ_B)) return SWEEP_ECUDA;
+    if (imaging && !field_maps(g, at<float>(ws, L->graw), nullptr, &in.tG, IN_BZ_B))
+      return SWEEP_ECUDA;
+    in.graw = imaging ? at<float>(ws, L->graw) : nullptr;
+    in.illum = (imaging && illum) ? at<float>(ws, L->iraw) : nullptr;
+    in.wavelet = wavelet;
+    in.src = src;
+    in.rbox = at<int32_t>(ws, L->rbox);
+    in.wgrad = wg;
+    in.status = status;
+    fx.g = g;
+    fx.K = at<float>(ws, L->K);
+    fx.ax = at<float>(ws, L->ax);
+    fx.bx = at<float>(ws, L->bx);
+    fx.az = at<float>(ws, L->az);
+    fx.bz = at<float>(ws, L->bz);
+    fx.rec = rec;
+    fx.res = g.nrec > 0 ? res : nullptr;
+    fx.status = status;
+    return SWEEP_OK;
+  }
+
+  // false: step n has no work; *adj: the CPML kernel runs too
+  bool step(int n, bool* adj) {
     const int A = n & 1, B = (n + 1) & 1;  // u^n in u[A]; mu^{n+1} in m[B]
     const int do_adj = n >= 1;
     const int do_img = imaging && n <= g.nt - 1;
     const int do_rec = imaging && n >= 1 && n <= g.nt - 1;
-    if (!(do_adj || do_img || wgrad)) continue;
-    void* tok = profile_begin(SWEEP_K_AC_BWD, st);
+    *adj = do_adj;
+    if (!(do_adj || do_img || wgrad)) return false;
     in.n = n;
     in.do_adj = do_adj;
     in.do_img = do_img;
@@ -417,26 +457,41 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
     }
     in.tmA = tm_h[B];
     in.tmB = tm_c[A];
-    in.uB = imaging ? at<float>(ws, L.u[B]) : nullptr;
-    in.mB = at<float>(ws, L.m[A]);
-    launch_ac_in_bwd(in, st);
+    in.uB = imaging ? at<float>(ws, L->u[B]) : nullptr;
+    in.mB = at<float>(ws, L->m[A]);
     if (do_adj) {
       // CPML terms of mu^n and the residual injection mu^n(r) += K r^{n-1}
       fx.n = n;
-      fx.u = at<float>(ws, L.m[B]);
-      fx.un = at<float>(ws, L.m[A]);
-      fx.pzin = at<float>(ws, L.pbz[A]);
-      fx.pzout = at<float>(ws, L.pbz[B]);
-      fx.zzin = at<float>(ws, L.zbz[A]);
-      fx.zzout = at<float>(ws, L.zbz[B]);
-      fx.pxin = at<float>(ws, L.pbx[A]);
-      fx.pxout = at<float>(ws, L.pbx[B]);
-      fx.zxin = at<float>(ws, L.zbx[A]);
-      fx.zxout = at<float>(ws, L.zbx[B]);
+      fx.u = at<float>(ws, L->m[B]);
+      fx.un = at<float>(ws, L->m[A]);
+      fx.pzin = at<float>(ws, L->pbz[A]);
+      fx.pzout = at<float>(ws, L->pbz[B]);
+      fx.zzin = at<float>(ws, L->zbz[A]);
+      fx.zzout = at<float>(ws, L->zbz[B]);
+      fx.pxin = at<float>(ws, L->pbx[A]);
+      fx.pxout = at<float>(ws, L->pbx[B]);
+      fx.zxin = at<float>(ws, L->zbx[A]);
+      fx.zxout = at<float>(ws, L->zbx[B]);
       fx.save = do_rec && save ? save + (size_t)(n - 1) * g.nshot * g.nring : nullptr;
-      fx.uring = do_rec ? at<float>(ws, L.u[B]) : nullptr;  // u^{n-1}
-      launch_ac_fix_bwd(fx, st);
+      fx.uring = do_rec ? at<float>(ws, L->u[B]) : nullptr;  // u^{n-1}
     }
+    return true;
+  }
+};
+
+int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
+                           const float* wavelet, const int32_t* src, const int32_t* rec,
+                           const float* res, float* wgrad, bool imaging, bool illum,
+                           cudaStream_t st) {
+  AcBwdLoop b;
+  const int rc = b.init(p, L, ws, wavelet, src, rec, res, wgrad, imaging, illum, st);
+  if (rc) return rc;
+  for (int n = b.g.nt; n >= 0; --n) {
+    bool adj = false;
+    if (!b.step(n, &adj)) continue;
+    void* tok = profile_begin(SWEEP_K_AC_BWD, st);
+    launch_ac_in_bwd(b.in, st);
+    if (adj) launch_ac_fix_bwd(b.fx, st);
     profile_end(tok, st);
   }
   return SWEEP_OK;
@@ -749,6 +804,125 @@ int sweep_gradient(const sweep_problem* p, const float* model, const float* wave
                      (p->flags & SWEEP_F_PADDED_MODEL) ? 1 : 0, grad, illum,
                      at<int>(ws, L.status), st);
   note_launches(1);
+  return cuda_rc(cudaGetLastError());
+}
+
+// Gradients of up to kStepBatch acoustic problems in lockstep: every step
+// kernel launch carries the step of each problem that has it (forward: step
+// t for the problems with t < nt; backward: step nt - t of each).
+static int gradient_group(const sweep_problem* const* P, const float* const* models,
+                          const float* const* wavelets, const int32_t* const* srcs,
+                          const int32_t* const* recs, const float* const* d_obs,
+                          float* const* grads, double* const* misfits, void* const* wss,
+                          int np, cudaStream_t st) {
+  std::vector<Layout> Ls(np);
+  std::vector<AcFwdLoop> F(np);
+  std::vector<AcBwdLoop> Bk(np);
+  std::vector<int> live;
+  int ntmax = 0;
+  for (int i = 0; i < np; ++i) {
+    const sweep_problem* p = P[i];
+    const Geom g = make_geom(p);
+    if (p->nshot == 0) {
+      cudaMemsetAsync(grads[i], 0, sizeof(float) * (size_t)g.nz * g.nx, st);
+      cudaMemsetAsync(misfits[i], 0, sizeof(double), st);
+      continue;
+    }
+    Ls[i] = layout(p, SWEEP_MODE_GRADIENT);
+    launch_setup(setup_args(p, Ls[i], wss[i], models[i], srcs[i], recs[i]), st);
+    float* d = at<float>(wss[i], Ls[i].data);
+    const int rc = F[i].init(p, Ls[i], wss[i], wavelets[i], srcs[i], recs[i],
+                             p->nrec > 0 ? d : nullptr, true, st);
+    if (rc) return rc;
+    live.push_back(i);
+    ntmax = std::max(ntmax, p->nt);
+  }
+  if (live.empty()) return SWEEP_OK;
+  AcInFwdArgs fin[kStepBatch];
+  AcInBwdArgs bin[kStepBatch];
+  AcFixArgs fix[kStepBatch];
+  for (int t = 0; t < ntmax; ++t) {
+    int k = 0;
+    for (int i : live) {
+      if (t >= P[i]->nt) continue;
+      F[i].step(t);
+      fin[k] = F[i].in;
+      fix[k] = F[i].fx;
+      ++k;
+    }
+    launch_ac_in_fwd_batch(fin, k, st);
+    launch_ac_fix_fwd_batch(fix, k, st);
+  }
+  for (int i : live) {
+    const sweep_problem* p = P[i];
+    float* d = at<float>(wss[i], Ls[i].data);
+    const long long nd = (long long)p->nshot * p->nrec * p->nt;
+    launch_residual_misfit(d, d_obs[i], d, nd, (p->flags & SWEEP_F_RESIDUAL_IN) ? 1 : 0,
+                           at<double>(wss[i], Ls[i].partial), RED_BLOCKS, misfits[i],
+                           at<int>(wss[i], Ls[i].status), st);
+    note_launches(2);
+    const int rc = Bk[i].init(p, Ls[i], wss[i], wavelets[i], srcs[i], recs[i], d, nullptr,
+                              true, false, st);
+    if (rc) return rc;
+  }
+  for (int t = 0; t <= ntmax; ++t) {
+    int kb = 0, kf = 0;
+    for (int i : live) {
+      const int n = P[i]->nt - t;
+      bool adj = false;
+      if (n < 0 || !Bk[i].step(n, &adj)) continue;
+      bin[kb++] = Bk[i].in;
+      if (adj) fix[kf++] = Bk[i].fx;
+    }
+    launch_ac_in_bwd_batch(bin, kb, st);
+    launch_ac_fix_bwd_batch(fix, kf, st);
+  }
+  for (int i : live) {
+    const sweep_problem* p = P[i];
+    launch_grad_reduce(make_geom(p), at<float>(wss[i], Ls[i].graw), nullptr, models[i],
+                       (p->flags & SWEEP_F_PADDED_MODEL) ? 1 : 0, grads[i], nullptr,
+                       at<int>(wss[i], Ls[i].status), st);
+    note_launches(1);
+  }
+  return SWEEP_OK;
+}
+
+int sweep_gradient_batch(int nprob, const sweep_problem* probs, const float* const* models,
+                         const float* const* wavelets, const int32_t* const* srcs,
+                         const int32_t* const* recs, const float* const* d_obs,
+                         float* const* grads, double* const* misfits, void* const* ws,
+                         const size_t* ws_bytes, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (nprob < 0) return SWEEP_EINVAL;
+  if (nprob == 0) return SWEEP_OK;
+  if (!probs || !models || !wavelets || !srcs || !recs || !d_obs || !grads || !misfits ||
+      !ws || !ws_bytes)
+    return SWEEP_EINVAL;
+  // every problem checked on the host before anything is launched
+  for (int i = 0; i < nprob; ++i) {
+    const sweep_problem* p = &probs[i];
+    if (!valid_problem(p)) return SWEEP_EINVAL;
+    if (p->physics != SWEEP_ACOUSTIC) return SWEEP_EUNSUPPORTED;
+    const int rc = check_ws(p, SWEEP_MODE_GRADIENT, ws[i], ws_bytes[i]);
+    if (rc) return rc;
+    if (!models[i] || !grads[i] || !misfits[i]) return SWEEP_EINVAL;
+    if (p->nshot > 0 && (!wavelets[i] || !srcs[i])) return SWEEP_EINVAL;
+    if (p->nshot > 0 && p->nrec > 0 && (!recs[i] || !d_obs[i])) return SWEEP_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ws[j] == ws[i]) return SWEEP_EWORKSPACE;  // one workspace per problem
+  }
+  for (int i = 0; i < nprob; ++i) {
+    const int rc = begin(&probs[i], SWEEP_MODE_GRADIENT, ws[i], ws_bytes[i], st);
+    if (rc) return rc;
+  }
+  const sweep_problem* P[kStepBatch];
+  for (int g0 = 0; g0 < nprob; g0 += kStepBatch) {
+    const int np = std::min(kStepBatch, nprob - g0);
+    for (int i = 0; i < np; ++i) P[i] = &probs[g0 + i];
+    const int rc = gradient_group(P, models + g0, wavelets + g0, srcs + g0, recs + g0,
+                                  d_obs + g0, grads + g0, misfits + g0, ws + g0, np, st);
+    if (rc) return rc;
+  }
   return cuda_rc(cudaGetLastError());
 }
 

@@ -121,10 +121,42 @@ struct AcFixArgs {
 };
 void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st);
 void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st);
+// np <= kStepBatch problems in one launch (blockIdx.y = problem)
+void launch_ac_fix_fwd_batch(const AcFixArgs* a, int np, cudaStream_t st);
+void launch_ac_fix_bwd_batch(const AcFixArgs* a, int np, cudaStream_t st);
 
-// Kernel launchers (acoustic_interior.cu)
+// The arguments of up to NP problems for one launch of a step kernel: the
+// launch's 1-D grid is split into consecutive block ranges, problem i owning
+// blocks [start[i], start[i + 1]) (start[np..NP] = the grid size, unused
+// entries of p are never read).
+constexpr int kStepBatch = 16;
+template <typename Args, int NP>
+struct StepBatch {
+  Args p[NP];
+  int start[NP + 1];
+};
+// This block's problem and its block index and block count within it.
+template <typename Args, int NP>
+__device__ __forceinline__ int step_problem(const StepBatch<Args, NP>& m, int* b, int* nb) {
+  if (NP == 1) {
+    *b = blockIdx.x;
+    *nb = gridDim.x;
+    return 0;
+  }
+  int i = 0;
+  while (i + 1 < NP && (int)blockIdx.x >= m.start[i + 1]) ++i;
+  *b = blockIdx.x - m.start[i];
+  *nb = m.start[i + 1] - m.start[i];
+  return i;
+}
+
+// Kernel launchers (acoustic_interior.cu); the _batch forms launch the step
+// of np <= kStepBatch problems at once, the persistent CTAs shared out in
+// proportion to the problems' units
 void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st);
 void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st);
+void launch_ac_in_fwd_batch(const AcInFwdArgs* a, int np, cudaStream_t st);
+void launch_ac_in_bwd_batch(const AcInBwdArgs* a, int np, cudaStream_t st);
 int device_sms();
 
 // Setup (setup.cu)

@@ -36,7 +36,7 @@ EXPORTS = ("sweep_workspace_bytes", "sweep_forward", "sweep_adjoint", "sweep_gra
            "sweep_kernel_launches", "sweep_profile_enable", "sweep_profile_read",
            "sweep_dot_noalloc", "sweep_capture_begin", "sweep_capture_end",
            "sweep_graph_launch", "sweep_graph_kernels", "sweep_graph_destroy",
-           "sweep_check_wait_timeout")
+           "sweep_check_wait_timeout", "sweep_gradient_batch")
 K_AC_FWD, K_AC_BWD, K_EL_VEL, K_EL_STR = 0, 1, 2, 3
 
 
@@ -117,6 +117,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.sweep_graph_destroy.restype = None
     lib.sweep_check_wait_timeout.argtypes = [vp, sz, vp]
     lib.sweep_check_wait_timeout.restype = i32
+    lib.sweep_gradient_batch.argtypes = [i32] + [vp] * 11
+    lib.sweep_gradient_batch.restype = i32
     return lib
 
 
@@ -322,6 +324,56 @@ def sweep_gradient(p: Problem, model, wavelet, src, rec, d_obs, grad=None, misfi
                              _stream(stream))
     _finish(rc, ws, "sweep_gradient", stream, sync)
     return grad, misfit, illum
+
+
+def sweep_gradient_batch(problems, models, wavelets, srcs, recs, d_obs, grads=None,
+                         misfits=None, ws=None, stream=None, sync=True):
+    """Acoustic gradients of several problems in one call (sweep_gradient_batch):
+    lists with one entry per problem; returns (grads, misfits).  Each problem
+    gets its own workspace (allocated here when ``ws`` is None)."""
+    n = len(problems)
+    if not (len(models) == len(wavelets) == len(srcs) == len(recs) == len(d_obs) == n):
+        raise ValueError("sweep_gradient_batch: one entry per problem in every list")
+    if n == 0:
+        return [], []
+    dev = models[0].device
+    grads = list(grads) if grads is not None else [
+        torch.empty((p.nz, p.nx), dtype=torch.float32, device=dev) for p in problems]
+    misfits = list(misfits) if misfits is not None else [
+        torch.empty((), dtype=torch.float64, device=dev) for _ in problems]
+    ws = list(ws) if ws is not None else [
+        alloc_workspace(p, MODE_GRADIENT, dev) for p in problems]
+    for i, p in enumerate(problems):
+        if p.physics != ACOUSTIC:
+            raise SweepError(EUNSUPPORTED, "sweep_gradient_batch")
+        for t, dt, name in ((models[i], torch.float32, "model"),
+                            (wavelets[i], torch.float32, "wavelet"),
+                            (srcs[i], torch.int32, "src"), (recs[i], torch.int32, "rec"),
+                            (d_obs[i], torch.float32, "d_obs"), (grads[i], torch.float32, "grad"),
+                            (misfits[i], torch.float64, "misfit")):
+            _check_dtype(t, dt, f"{name}[{i}]")
+        _check_inputs(p, models[i], wavelets[i], srcs[i], recs[i])
+        _check_size(d_obs[i], (p.nshot, 1, p.nrec, p.nt), f"d_obs[{i}]")
+        _check_size(grads[i], (p.nz, p.nx), f"grad[{i}]")
+        _check_size(misfits[i], (), f"misfit[{i}]")
+    V = ctypes.c_void_p * n
+    arr = (Problem * n)(*problems)
+
+    def ptrs(ts):
+        return V(*[_ptr(t) for t in ts])
+    keep = [ptrs(models), ptrs(wavelets), ptrs(srcs), ptrs(recs), ptrs(d_obs), ptrs(grads),
+            ptrs(misfits), V(*[ctypes.c_void_p(w.data_ptr()) for w in ws]),
+            (ctypes.c_size_t * n)(*[w.numel() for w in ws])]
+    args = [ctypes.cast(arr, ctypes.c_void_p)] + [ctypes.cast(k, ctypes.c_void_p) for k in keep]
+    rc = _lib.sweep_gradient_batch(n, *args, _stream(stream))
+    if rc != OK:
+        raise SweepError(rc, "sweep_gradient_batch")
+    if sync and not getattr(_capture_state, "on", False):
+        for w in ws:
+            st = status(w, stream)
+            if st != OK:
+                raise SweepError(st, "sweep_gradient_batch")
+    return grads, misfits
 
 
 _capture_state = threading.local()

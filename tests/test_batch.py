@@ -39,15 +39,30 @@ def test_schedule_deals_longest_first():
         batch.schedule([1], 0)
 
 
+def test_cohorts_group_similar_record_lengths():
+    from types import SimpleNamespace as NS
+    rng = np.random.default_rng(3)
+    nts = rng.integers(100, 3000, 37)
+    items = [NS(problem=NS(nt=int(t), nz=10, nx=10, pml=2, nshot=1)) for t in nts]
+    groups = batch.cohorts(items, size=16)
+    assert [len(g) for g in groups] == [16, 16, 5]
+    assert sorted(i for g in groups for i in g) == list(range(37))
+    flat = [int(nts[i]) for g in groups for i in g]
+    assert flat == sorted(flat, reverse=True)
+
+
 @pytest.mark.gpu
-def test_batch_matches_individual_runs():
+@pytest.mark.parametrize("count,fused", [(6, True), (6, False), (21, True)])
+def test_batch_matches_individual_runs(count, fused):
+    """Shared-launch cohorts (21 problems: a full cohort of 16 and one of 5)
+    and the one-call-per-problem path give the problems' own gradients."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2604_14189_gb300 import inputs, sweep
 
     rng = np.random.default_rng(7)
     items, refs = [], []
-    for k in range(6):
+    for k in range(count):
         nz, nx = int(rng.integers(40, 90)), int(rng.integers(40, 120))
         pml, nt, ns = int(rng.integers(8, 20)), int(rng.integers(150, 400)), int(rng.integers(1, 4))
         z = np.arange(nz)[:, None] + np.zeros((1, nx))
@@ -66,7 +81,7 @@ def test_batch_matches_individual_runs():
         items.append(batch.Item(p, vt, w, st, rt, d_obs=d_obs))
         g, J, _ = sweep.sweep_gradient(p, vt, w, st, rt, d_obs)
         refs.append((g.clone(), float(J)))
-    codes = batch.run(items, streams=3)
+    codes = batch.run(items, streams=3, fused=fused)
     assert codes == [0] * len(items)
     for it, (g, J) in zip(items, refs):
         assert torch.linalg.norm(it.grad - g) <= 1e-4 * torch.linalg.norm(g)
