@@ -712,7 +712,7 @@ def run_batch(args, local_rank):
             d_obs=torch.zeros((ns, 1, nrec, nt), dtype=torch.float32, device=dev)))
         cells += batch.cost(p)
     # schedule autotuning on a sample of the batch
-    best, times = batch.autotune_streams(items[:48], candidates=(3, 4, 5, 6, 8))
+    best, times = batch.autotune_streams(items[:64], candidates=(1, 2, 3, 4, 6))
     for _ in range(max(args.warmup, 0)):
         batch.run(items, streams=best)
     sampler = ClockSampler(local_rank)
