@@ -138,3 +138,35 @@ def test_binding_rejects_wrong_sizes_before_any_call():
     q = _prob(sweep, flags=sweep.F_PADDED_MODEL)
     with pytest.raises(ValueError, match="model"):
         sweep.sweep_forward(q, good["model"], good["wavelet"], good["src"], good["rec"])
+
+
+def test_gradient_batch_host_checks(lib):
+    """sweep_gradient_batch checks every problem on the host before any
+    launch: bad counts, elastic problems, a workspace shared by two problems,
+    and missing pointers."""
+    from paper_2604_14189_gb300 import sweep
+    L = sweep.lib()
+    V = ctypes.c_void_p
+    assert L.sweep_gradient_batch(-1, *([None] * 11)) == sweep.EINVAL
+    assert L.sweep_gradient_batch(0, *([None] * 11)) == sweep.OK
+    assert L.sweep_gradient_batch(2, *([None] * 11)) == sweep.EINVAL
+    p = _prob(sweep)
+    q = _prob(sweep)
+    need = sweep.workspace_bytes(p, sweep.MODE_GRADIENT)
+    fake = V(1 << 20)  # never dereferenced: every check fails before a launch
+
+    def call(probs, wss, sizes, model=fake):
+        n = len(probs)
+        arr = (sweep.Problem * n)(*probs)
+        ptrs = (V * n)(*([model] * n))
+        wsa = (V * n)(*wss)
+        sza = (ctypes.c_size_t * n)(*sizes)
+        args = [ctypes.cast(arr, V)] + [ctypes.cast(ptrs, V)] * 7 + [ctypes.cast(wsa, V),
+                                                                   ctypes.cast(sza, V)]
+        return L.sweep_gradient_batch(n, *args, None)
+
+    el = _prob(sweep, physics=sweep.ELASTIC)
+    assert call([p, el], [V(256 * 4096), V(512 * 4096)], [need, need]) == sweep.EUNSUPPORTED
+    assert call([p, q], [V(256 * 4096), V(256 * 4096)], [need, need]) == sweep.EWORKSPACE
+    assert call([p, q], [V(256 * 4096), V(512 * 4096)], [need, need - 1]) == sweep.EWORKSPACE
+    assert call([p, q], [V(256 * 4096), V(512 * 4096)], [need, need], model=V(0)) == sweep.EINVAL
