@@ -169,6 +169,18 @@ int sweep_gradient_batch(int nprob, const sweep_problem* probs, const float* con
                          float* const* grads, double* const* misfits, void* const* ws,
                          const size_t* ws_bytes, void* stream);
 
+/* Forward runs of several acoustic problems in one call, the same way:
+ * problem i takes the arguments of sweep_forward (probs[i], models[i],
+ * wavelets[i], srcs[i], recs[i], data[i]) and its own workspace ws[i] of
+ * ws_bytes[i] >= sweep_workspace_bytes(&probs[i], SWEEP_MODE_FORWARD) bytes;
+ * groups of up to 16 in lockstep, each time-step launch carrying the step of
+ * every problem of the group.  Checks, errors and asynchrony as
+ * sweep_gradient_batch. */
+int sweep_forward_batch(int nprob, const sweep_problem* probs, const float* const* models,
+                        const float* const* wavelets, const int32_t* const* srcs,
+                        const int32_t* const* recs, float* const* data, void* const* ws,
+                        const size_t* ws_bytes, void* stream);
+
 size_t sweep_dot_workspace_bytes(void);
 int sweep_dot(const float* a, const float* b, int64_t n, double* out, void* ws,
               size_t ws_bytes, void* stream);

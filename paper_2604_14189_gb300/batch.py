@@ -90,8 +90,8 @@ def cohorts(items: list[Item], size: int = COHORT) -> list[list[int]]:
 def run(items: list[Item], mode: int = sweep.MODE_GRADIENT, streams: int = 8,
         device=None, fused: bool = True) -> list[int]:
     """Runs every item; returns the status code of each (0 = ok).  Outputs
-    are allocated on first use and written in place.  Gradients of acoustic
-    items run as cohorts in shared launches unless ``fused`` is False."""
+    are allocated on first use and written in place.  Acoustic items run as
+    cohorts in shared launches unless ``fused`` is False."""
     device = torch.device(device or "cuda")
     if not items:
         return []
@@ -107,8 +107,7 @@ def run(items: list[Item], mode: int = sweep.MODE_GRADIENT, streams: int = 8,
                                   dtype=torch.float32, device=device)
     codes = torch.zeros(len(items), dtype=torch.int32, device=device)
     errors: list[BaseException] = []
-    if (mode == sweep.MODE_GRADIENT and fused
-            and all(it.problem.physics == sweep.ACOUSTIC for it in items)):
+    if fused and all(it.problem.physics == sweep.ACOUSTIC for it in items):
         groups = cohorts(items)
         gq = [q for q in schedule([sum(cost(items[i].problem) for i in g) for g in groups],
                                   streams) if q]
@@ -119,13 +118,18 @@ def run(items: list[Item], mode: int = sweep.MODE_GRADIENT, streams: int = 8,
                     for gi in queue:
                         idx = groups[gi]
                         ws = [sweep.alloc_workspace(items[i].problem, mode, device) for i in idx]
-                        sweep.sweep_gradient_batch(
-                            [items[i].problem for i in idx], [items[i].model for i in idx],
-                            [items[i].wavelet for i in idx], [items[i].src for i in idx],
-                            [items[i].rec for i in idx], [items[i].d_obs for i in idx],
-                            grads=[items[i].grad for i in idx],
-                            misfits=[items[i].misfit for i in idx], ws=ws, stream=stream,
-                            sync=False)
+                        common = ([items[i].problem for i in idx], [items[i].model for i in idx],
+                                  [items[i].wavelet for i in idx], [items[i].src for i in idx],
+                                  [items[i].rec for i in idx])
+                        if mode == sweep.MODE_GRADIENT:
+                            sweep.sweep_gradient_batch(
+                                *common, [items[i].d_obs for i in idx],
+                                grads=[items[i].grad for i in idx],
+                                misfits=[items[i].misfit for i in idx], ws=ws, stream=stream,
+                                sync=False)
+                        else:
+                            sweep.sweep_forward_batch(*common, data=[items[i].data for i in idx],
+                                                      ws=ws, stream=stream, sync=False)
                         for j, i in enumerate(idx):  # the status word leads the workspace
                             codes[i:i + 1].copy_(ws[j][:4].view(torch.int32), non_blocking=True)
             except BaseException as e:  # reported after the join

@@ -887,6 +887,79 @@ static int gradient_group(const sweep_problem* const* P, const float* const* mod
   return SWEEP_OK;
 }
 
+// Forward runs of up to kStepBatch acoustic problems in lockstep.
+static int forward_group(const sweep_problem* const* P, const float* const* models,
+                         const float* const* wavelets, const int32_t* const* srcs,
+                         const int32_t* const* recs, float* const* data, void* const* wss,
+                         int np, cudaStream_t st) {
+  std::vector<Layout> Ls(np);
+  std::vector<AcFwdLoop> F(np);
+  std::vector<int> live;
+  int ntmax = 0;
+  for (int i = 0; i < np; ++i) {
+    const sweep_problem* p = P[i];
+    if (p->nshot == 0) continue;
+    Ls[i] = layout(p, SWEEP_MODE_FORWARD);
+    launch_setup(setup_args(p, Ls[i], wss[i], models[i], srcs[i], recs[i]), st);
+    const int rc = F[i].init(p, Ls[i], wss[i], wavelets[i], srcs[i], recs[i],
+                             p->nrec > 0 ? data[i] : nullptr, false, st);
+    if (rc) return rc;
+    live.push_back(i);
+    ntmax = std::max(ntmax, p->nt);
+  }
+  AcInFwdArgs fin[kStepBatch];
+  AcFixArgs fix[kStepBatch];
+  for (int t = 0; t < ntmax; ++t) {
+    int k = 0;
+    for (int i : live) {
+      if (t >= P[i]->nt) continue;
+      F[i].step(t);
+      fin[k] = F[i].in;
+      fix[k] = F[i].fx;
+      ++k;
+    }
+    launch_ac_in_fwd_batch(fin, k, st);
+    launch_ac_fix_fwd_batch(fix, k, st);
+  }
+  return SWEEP_OK;
+}
+
+int sweep_forward_batch(int nprob, const sweep_problem* probs, const float* const* models,
+                        const float* const* wavelets, const int32_t* const* srcs,
+                        const int32_t* const* recs, float* const* data, void* const* ws,
+                        const size_t* ws_bytes, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (nprob < 0) return SWEEP_EINVAL;
+  if (nprob == 0) return SWEEP_OK;
+  if (!probs || !models || !wavelets || !srcs || !recs || !data || !ws || !ws_bytes)
+    return SWEEP_EINVAL;
+  for (int i = 0; i < nprob; ++i) {  // every problem checked before any launch
+    const sweep_problem* p = &probs[i];
+    if (!valid_problem(p)) return SWEEP_EINVAL;
+    if (p->physics != SWEEP_ACOUSTIC) return SWEEP_EUNSUPPORTED;
+    const int rc = check_ws(p, SWEEP_MODE_FORWARD, ws[i], ws_bytes[i]);
+    if (rc) return rc;
+    if (!models[i]) return SWEEP_EINVAL;
+    if (p->nshot > 0 && (!wavelets[i] || !srcs[i])) return SWEEP_EINVAL;
+    if (p->nshot > 0 && p->nrec > 0 && (!recs[i] || !data[i])) return SWEEP_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ws[j] == ws[i]) return SWEEP_EWORKSPACE;
+  }
+  for (int i = 0; i < nprob; ++i) {
+    const int rc = begin(&probs[i], SWEEP_MODE_FORWARD, ws[i], ws_bytes[i], st);
+    if (rc) return rc;
+  }
+  const sweep_problem* P[kStepBatch];
+  for (int g0 = 0; g0 < nprob; g0 += kStepBatch) {
+    const int np = std::min(kStepBatch, nprob - g0);
+    for (int i = 0; i < np; ++i) P[i] = &probs[g0 + i];
+    const int rc = forward_group(P, models + g0, wavelets + g0, srcs + g0, recs + g0,
+                                 data + g0, ws + g0, np, st);
+    if (rc) return rc;
+  }
+  return cuda_rc(cudaGetLastError());
+}
+
 int sweep_gradient_batch(int nprob, const sweep_problem* probs, const float* const* models,
                          const float* const* wavelets, const int32_t* const* srcs,
                          const int32_t* const* recs, const float* const* d_obs,

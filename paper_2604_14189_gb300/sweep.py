@@ -36,7 +36,7 @@ EXPORTS = ("sweep_workspace_bytes", "sweep_forward", "sweep_adjoint", "sweep_gra
            "sweep_kernel_launches", "sweep_profile_enable", "sweep_profile_read",
            "sweep_dot_noalloc", "sweep_capture_begin", "sweep_capture_end",
            "sweep_graph_launch", "sweep_graph_kernels", "sweep_graph_destroy",
-           "sweep_check_wait_timeout", "sweep_gradient_batch")
+           "sweep_check_wait_timeout", "sweep_gradient_batch", "sweep_forward_batch")
 K_AC_FWD, K_AC_BWD, K_EL_VEL, K_EL_STR = 0, 1, 2, 3
 
 
@@ -119,6 +119,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.sweep_check_wait_timeout.restype = i32
     lib.sweep_gradient_batch.argtypes = [i32] + [vp] * 11
     lib.sweep_gradient_batch.restype = i32
+    lib.sweep_forward_batch.argtypes = [i32] + [vp] * 9
+    lib.sweep_forward_batch.restype = i32
     return lib
 
 
@@ -374,6 +376,51 @@ def sweep_gradient_batch(problems, models, wavelets, srcs, recs, d_obs, grads=No
             if st != OK:
                 raise SweepError(st, "sweep_gradient_batch")
     return grads, misfits
+
+
+def sweep_forward_batch(problems, models, wavelets, srcs, recs, data=None, ws=None,
+                        stream=None, sync=True):
+    """Acoustic forward runs of several problems in one call
+    (sweep_forward_batch); returns the list of data tensors."""
+    n = len(problems)
+    if not (len(models) == len(wavelets) == len(srcs) == len(recs) == n):
+        raise ValueError("sweep_forward_batch: one entry per problem in every list")
+    if n == 0:
+        return []
+    dev = models[0].device
+    data = list(data) if data is not None else [
+        torch.empty((p.nshot, 1, p.nrec, p.nt), dtype=torch.float32, device=dev)
+        for p in problems]
+    ws = list(ws) if ws is not None else [
+        alloc_workspace(p, MODE_FORWARD, dev) for p in problems]
+    for i, p in enumerate(problems):
+        if p.physics != ACOUSTIC:
+            raise SweepError(EUNSUPPORTED, "sweep_forward_batch")
+        for t, dt, name in ((models[i], torch.float32, "model"),
+                            (wavelets[i], torch.float32, "wavelet"),
+                            (srcs[i], torch.int32, "src"), (recs[i], torch.int32, "rec"),
+                            (data[i], torch.float32, "data")):
+            _check_dtype(t, dt, f"{name}[{i}]")
+        _check_inputs(p, models[i], wavelets[i], srcs[i], recs[i])
+        _check_size(data[i], (p.nshot, 1, p.nrec, p.nt), f"data[{i}]")
+    V = ctypes.c_void_p * n
+    arr = (Problem * n)(*problems)
+
+    def ptrs(ts):
+        return V(*[_ptr(t) for t in ts])
+    keep = [ptrs(models), ptrs(wavelets), ptrs(srcs), ptrs(recs), ptrs(data),
+            V(*[ctypes.c_void_p(w.data_ptr()) for w in ws]),
+            (ctypes.c_size_t * n)(*[w.numel() for w in ws])]
+    args = [ctypes.cast(arr, ctypes.c_void_p)] + [ctypes.cast(k, ctypes.c_void_p) for k in keep]
+    rc = _lib.sweep_forward_batch(n, *args, _stream(stream))
+    if rc != OK:
+        raise SweepError(rc, "sweep_forward_batch")
+    if sync and not getattr(_capture_state, "on", False):
+        for w in ws:
+            st = status(w, stream)
+            if st != OK:
+                raise SweepError(st, "sweep_forward_batch")
+    return data
 
 
 _capture_state = threading.local()

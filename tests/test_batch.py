@@ -88,3 +88,37 @@ def test_batch_matches_individual_runs(count, fused):
         # corner cells receive their two CPML additions in either order, and a
         # small residual amplifies the run-to-run rounding differences
         assert abs(float(it.misfit) - J) <= 1e-4 * J
+
+
+@pytest.mark.gpu
+def test_forward_batch_matches_individual_runs():
+    """Forward modelling of 19 uneven problems as cohorts sharing launches
+    (a cohort of 16 and one of 3) equals each problem's own sweep_forward
+    to rounding (1e-5 of the largest sample)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_14189_gb300 import inputs, sweep
+
+    rng = np.random.default_rng(11)
+    items, refs = [], []
+    dev = "cuda"
+    for k in range(19):
+        nz, nx = int(rng.integers(30, 100)), int(rng.integers(30, 140))
+        pml, nt, ns = int(rng.integers(0, 16)), int(rng.integers(60, 300)), int(rng.integers(1, 4))
+        v = 1800.0 + 600.0 * rng.random((nz, nx))
+        src = np.stack([rng.integers(0, nz, ns), rng.integers(0, nx, ns)], -1).astype(np.int32)
+        rec = np.stack([rng.integers(0, nz, (ns, 5)), rng.integers(0, nx, (ns, 5))],
+                       -1).astype(np.int32)
+        p = sweep.problem(nz=nz, nx=nx, pml=pml, dx=10.0, dt=1e-3, nt=nt, nshot=ns, nrec=5,
+                          f_ref=10.0)
+        w = torch.tensor(np.stack([inputs.ricker(12.0, 1e-3, nt)] * ns), dtype=torch.float32,
+                         device=dev)
+        it = batch.Item(p, torch.tensor(v, dtype=torch.float32, device=dev), w,
+                        torch.tensor(src, device=dev), torch.tensor(rec, device=dev))
+        items.append(it)
+        refs.append(sweep.sweep_forward(p, it.model, it.wavelet, it.src, it.rec).clone())
+    codes = batch.run(items, mode=sweep.MODE_FORWARD, streams=2)
+    assert codes == [0] * len(items)
+    for it, ref in zip(items, refs):
+        scale = float(ref.abs().max())
+        assert scale > 0 and float((it.data - ref).abs().max()) <= 1e-5 * scale
