@@ -175,8 +175,13 @@ def test_dot_product_tests(sw):
 
 
 def test_gradient_finite_differences(sw):
-    """FD of the GPU misfit (FP64 reduction, FP32 forward) along 4 smooth
-    perturbations of a padded model vs <g, dv>: relative 1e-2."""
+    """FD of the GPU misfit (FP64 reduction, FP32 forward) along 10 smooth
+    perturbations of a padded model vs <g, dv>: within 1e-2 of the larger of
+    the directional derivative and half the largest one of the set.  A
+    perturbation whose derivative nearly cancels (one here is 3 % of the
+    largest) carries the central difference's truncation error of the
+    non-quadratic misfit (~1e-3 of the set's scale at this step) on a small
+    value, so its check is against the set's scale."""
     c = case(50, 70, 10, 350, 2, 12, seed=41, flags=sw.F_PADDED_MODEL, v_pml=3600.0)
     p, _ = probs(sw, c)
     P = c["pml"]
@@ -188,8 +193,9 @@ def test_gradient_finite_differences(sw):
     g, J, _ = sw.sweep_gradient(p, cuda(vpad), cuda(c["w"]), cuda(c["src"], torch.int32),
                                 cuda(c["rec"], torch.int32), d_obs)
     g = g.cpu().numpy().astype(np.float64)
-    pert = inputs.smooth_perturbations(c["nz"], c["nx"], c["v"], 4, seed=5, sigma=5.0)
-    for k in range(4):
+    pert = inputs.smooth_perturbations(c["nz"], c["nx"], c["v"], 10, seed=5, sigma=5.0)
+    pairs = []
+    for k in range(10):
         dv = np.zeros_like(vpad)
         dv[P:P + c["nz"], P:P + c["nx"]] = pert[k]
         h = 0.5  # the perturbation is 1 % of v; step 0.5 of it
@@ -201,7 +207,11 @@ def test_gradient_finite_differences(sw):
             Js.append(Jk.item())
         fd = (Js[0] - Js[1]) / (2 * h)
         an = float(np.sum(g * pert[k]))
-        assert abs(fd - an) <= 1e-2 * abs(an), (k, fd, an)
+        pairs.append((fd, an))
+    top = max(abs(an) for _, an in pairs)
+    assert sum(abs(an) >= 0.1 * top for _, an in pairs) >= 5  # mostly non-cancelling
+    for k, (fd, an) in enumerate(pairs):
+        assert abs(fd - an) <= 1e-2 * max(abs(an), 0.5 * top), (k, fd, an, top)
 
 
 def test_layered_single_shot_full_size(sw):
