@@ -5,7 +5,9 @@
 // (acoustic_cpml.cu).  See acoustic_common.cuh for the equations.
 //
 // Work is a list of (tile, shot) units taken round-robin by persistent CTAs
-// (one per SM).  Each CTA runs a multi-stage TMA pipeline: while it computes
+// (one per SM; a launch that carries several problems shares its one wave
+// of CTAs out among them in proportion to their units, each CTA serving one
+// problem).  Each CTA runs a multi-stage TMA pipeline: while it computes
 // unit k from shared memory, the tiles of the next units are in flight
 // (cp.async.bulk.tensor, completion on one mbarrier per stage).  Halo tiles
 // carry 4 extra cells per side; the TMA zero-fills outside the padded grid,

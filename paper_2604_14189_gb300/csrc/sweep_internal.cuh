@@ -121,7 +121,7 @@ struct AcFixArgs {
 };
 void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st);
 void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st);
-// np <= kStepBatch problems in one launch (blockIdx.y = problem)
+// np <= kStepBatch problems in one launch (consecutive block ranges)
 void launch_ac_fix_fwd_batch(const AcFixArgs* a, int np, cudaStream_t st);
 void launch_ac_fix_bwd_batch(const AcFixArgs* a, int np, cudaStream_t st);
 
