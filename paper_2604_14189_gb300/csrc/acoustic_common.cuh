@@ -66,111 +66,44 @@ __device__ __forceinline__ bool interior(const Geom& g, int z, int x) {
   return z >= g.P && z < g.P + g.nz && x >= g.P && x < g.P + g.nx;
 }
 
-// Index of padded cell (z, x) in the saved ring around the interior, or -1.
-__device__ __forceinline__ int ring_index(const Geom& g, int z, int x) {
-  const int w = g.ringw, P = g.P;
-  if (w == 0) return -1;
-  const int zi = z - P, xi = x - P;  // interior coordinates
-  if (zi < -w || zi >= g.nz + w || xi < -w || xi >= g.nx + w) return -1;
-  const int W = g.nx + 2 * w;
-  if (zi < 0) return (zi + w) * W + (xi + w);
-  if (zi >= g.nz) return w * W + (zi - g.nz) * W + (xi + w);
-  if (xi < 0) return 2 * w * W + zi * w + (xi + w);
-  if (xi >= g.nx) return 2 * w * W + g.nz * w + zi * w + (xi - g.nx);
-  return -1;  // interior
-}
-
-// Does the tile [z0, z0+tz) x [x0, x0+tx) meet the receiver box of a shot?
-__device__ __forceinline__ bool tile_meets_box(const int32_t* box, int z0, int tz, int x0,
-                                               int tx) {
-  return box[0] < z0 + tz && box[1] >= z0 && box[2] < x0 + tx && box[3] >= x0;
-}
-
 // Per-shot values a step kernel needs for every unit (source cell, this
-// step's wavelet sample, receiver box), staged in shared memory once per
+// step's wavelet sample), staged in shared memory once per
 // launch so that no unit waits on a dependent global load for them.
 constexpr int kShotTable = 128;  // shots held in shared memory; more: global
 struct ShotTable {
   int sz[kShotTable], sx[kShotTable];
   float fn[kShotTable];
-  int4 box[kShotTable];
 };
 
 __device__ __forceinline__ void load_shot_table(ShotTable& T, const Geom& g,
                                                 const int32_t* src, const float* wavelet,
-                                                const int32_t* rbox, int n) {
+                                                int n) {
   if (g.nshot > kShotTable) return;
   for (int s = threadIdx.x; s < g.nshot; s += blockDim.x) {
     T.sz[s] = src[2 * s] + g.P;
     T.sx[s] = src[2 * s + 1] + g.P;
     T.fn[s] = (wavelet && n < g.nt) ? wavelet[(long long)s * g.nt + n] : 0.f;
-    T.box[s] = make_int4(rbox[4 * s], rbox[4 * s + 1], rbox[4 * s + 2], rbox[4 * s + 3]);
   }
 }
 
 struct ShotInfo {
   int sz, sx;
   float fn;
-  int4 box;
 };
 __device__ __forceinline__ ShotInfo shot_info(const ShotTable& T, const Geom& g,
-                                              const int32_t* src, const float* wavelet,
-                                              const int32_t* rbox, int n, int s) {
+                                              const int32_t* src, const float* wavelet, int n,
+                                              int s) {
   ShotInfo i;
   if (g.nshot <= kShotTable) {
     i.sz = T.sz[s];
     i.sx = T.sx[s];
     i.fn = T.fn[s];
-    i.box = T.box[s];
   } else {
     i.sz = src[2 * s] + g.P;
     i.sx = src[2 * s + 1] + g.P;
     i.fn = (wavelet && n < g.nt) ? wavelet[(long long)s * g.nt + n] : 0.f;
-    i.box = make_int4(rbox[4 * s], rbox[4 * s + 1], rbox[4 * s + 2], rbox[4 * s + 3]);
   }
   return i;
-}
-
-__device__ __forceinline__ bool tile_meets(const int4& b, int z0, int tz, int x0, int tx) {
-  return b.x < z0 + tz && b.y >= z0 && b.z < x0 + tx && b.w >= x0;
-}
-
-// CPML profile values of the border cells (2 P per axis) in shared memory;
-// index x < P -> x, x >= P + nx -> x - nx.  Wider borders read global memory.
-constexpr int kProfMax = 512;
-struct BorderProfiles {
-  float ax[kProfMax], bx[kProfMax], az[kProfMax], bz[kProfMax];
-};
-
-__device__ __forceinline__ void load_profiles(BorderProfiles& T, const Geom& g, const float* ax,
-                                              const float* bx, const float* az,
-                                              const float* bz) {
-  if (2 * g.P > kProfMax) return;
-  for (int i = threadIdx.x; i < 2 * g.P; i += blockDim.x) {
-    const int x = i < g.P ? i : g.nx + i;
-    const int z = i < g.P ? i : g.nz + i;
-    T.ax[i] = ax[x];
-    T.bx[i] = bx[x];
-    T.az[i] = az[z];
-    T.bz[i] = bz[z];
-  }
-}
-// a, b of a border column x / border row z (caller checks it is a border cell)
-__device__ __forceinline__ float2 prof_x(const BorderProfiles& T, const Geom& g, const float* ax,
-                                         const float* bx, int x) {
-  if (2 * g.P <= kProfMax) {
-    const int i = x < g.P ? x : x - g.nx;
-    return make_float2(T.ax[i], T.bx[i]);
-  }
-  return make_float2(ax[x], bx[x]);
-}
-__device__ __forceinline__ float2 prof_z(const BorderProfiles& T, const Geom& g, const float* az,
-                                         const float* bz, int z) {
-  if (2 * g.P <= kProfMax) {
-    const int i = z < g.P ? z : z - g.nz;
-    return make_float2(T.az[i], T.bz[i]);
-  }
-  return make_float2(az[z], bz[z]);
 }
 
 }  // namespace sweep

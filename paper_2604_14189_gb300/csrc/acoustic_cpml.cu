@@ -182,8 +182,10 @@ __device__ __forceinline__ void fwd_rec(const AcFixArgs& a, int s, int bl) {
   a.data[i * g.nt + a.n] = a.un[(size_t)s * g.fstride + (size_t)rz * g.NXp + rx];
 }
 
-// Interior coordinates (zi, xi) of ring cell ri: the inverse of ring_index
-// (rows above, rows below, then the left and right side columns).
+// Interior coordinates (zi, xi) of ring cell ri.  The ring (w = ringw cells
+// around the interior) is stored as the w rows above it and the w rows below
+// it, each nx + 2w cells wide, then for every interior row its w cells on
+// the left, then for every interior row its w cells on the right.
 __device__ __forceinline__ void ring_cell(const Geom& g, int ri, int& zi, int& xi) {
   const int w = g.ringw, W = g.nx + 2 * w;
   if (ri < 2 * w * W) {

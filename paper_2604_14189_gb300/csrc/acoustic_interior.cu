@@ -116,8 +116,8 @@ __device__ __forceinline__ UnitDesc make_desc(const Region& R, const Geom& g, co
   const UnitPos p = unit_pos(R, S, ntx, bz, unit);
   const bool img = ab && ab->do_img;
   const ShotInfo si =
-      af ? shot_info(T, g, af->src, af->wavelet, af->rbox, af->n, p.s)
-         : shot_info(T, g, ab->src, img ? ab->wavelet : nullptr, ab->rbox, ab->n, p.s);
+      af ? shot_info(T, g, af->src, af->wavelet, af->n, p.s)
+         : shot_info(T, g, ab->src, img ? ab->wavelet : nullptr, ab->n, p.s);
   UnitDesc d;
   d.s = p.s;
   d.z0 = p.z0;
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
   const Region& R = g.fin;
   const int count = (a.units - bx + G - 1) / G;  // units b, b+G, ...
   if (count <= 0) return;
-  load_shot_table(T, g, a.src, a.wavelet, a.rbox, a.n);
+  load_shot_table(T, g, a.src, a.wavelet, a.n);
   __syncthreads();  // shot table visible
   for (int i = threadIdx.x; i < count && i < kUnitTable; i += FWD_THREADS)
     utab[i] = make_desc(R, g, T, &a, nullptr, IN_BZ_F, bx + i * G);
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
   const int count = (a.units - bx + G - 1) / G;
   if (count <= 0) return;
   const bool img = a.do_img != 0, adj = a.do_adj != 0;
-  load_shot_table(T, g, a.src, img ? a.wavelet : nullptr, a.rbox, a.n);
+  load_shot_table(T, g, a.src, img ? a.wavelet : nullptr, a.n);
   __syncthreads();  // shot table visible
   for (int i = threadIdx.x; i < count && i < kUnitTable; i += BWD_THREADS)
     utab[i] = make_desc(R, g, T, nullptr, &a, IN_BZ_B, bx + i * G);

@@ -33,7 +33,6 @@ struct ElStepArgs {
   const float* wavelet;
   const int32_t* src;
   const int32_t* rec;
-  const int32_t* rbox;
   float* data;                             // [S][2][R][nt] or null
   float src_scale;                         // dt / dx^2
   int* status;

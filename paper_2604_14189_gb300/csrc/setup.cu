@@ -104,25 +104,7 @@ __global__ void setup_geometry_kernel(const SetupArgs a) {
     const int z = a.rec[2 * r], x = a.rec[2 * r + 1];
     if (z < 0 || z >= g.nz || x < 0 || x >= g.nx) {
       latch(a.status, SWEEP_EBOUNDS);
-      continue;
     }
-    if (a.rbox) {
-      // bounding box of each shot's receivers in padded coordinates
-      int32_t* b = a.rbox + 4 * (r / g.nrec);
-      atomicMin(b + 0, z + g.P);
-      atomicMax(b + 1, z + g.P);
-      atomicMin(b + 2, x + g.P);
-      atomicMax(b + 3, x + g.P);
-    }
-  }
-}
-
-__global__ void rbox_init_kernel(int32_t* rbox, int nshot) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nshot; s += gridDim.x * blockDim.x) {
-    rbox[4 * s + 0] = 0x7fffffff;
-    rbox[4 * s + 1] = -1;
-    rbox[4 * s + 2] = 0x7fffffff;
-    rbox[4 * s + 3] = -1;
   }
 }
 
@@ -133,10 +115,9 @@ void launch_setup(const SetupArgs& a, cudaStream_t st) {
   const long long n = (long long)a.g.NZ * a.g.NXp;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 1216) blocks = 1216;
-  if (a.rbox) rbox_init_kernel<<<1, 256, 0, st>>>(a.rbox, a.g.nshot);
   setup_model_kernel<<<blocks, 256, 0, st>>>(a);
   setup_geometry_kernel<<<8, 256, 0, st>>>(a);
-  note_launches(a.rbox ? 3 : 2);
+  note_launches(2);
 }
 
 }  // namespace sweep

@@ -67,7 +67,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t status = 0, partial = 0, vmax = 0, rbox = 0, K = 0;
+  size_t status = 0, partial = 0, vmax = 0, K = 0;
   size_t ax = 0, bx = 0, az = 0, bz = 0, axh = 0, bxh = 0, azh = 0, bzh = 0;
   size_t u[2] = {0, 0}, psx[2] = {0, 0}, psz[2] = {0, 0}, zex = 0, zez = 0;
   size_t m[2] = {0, 0}, pbx[2] = {0, 0}, pbz[2] = {0, 0}, zbx[2] = {0, 0}, zbz[2] = {0, 0};
@@ -145,7 +145,6 @@ Layout layout(const sweep_problem* p, int mode) {
   L.status = b.take(sizeof(int) * 4);
   L.vmax = b.take(sizeof(unsigned int));
   L.partial = b.take(sizeof(double) * RED_BLOCKS);
-  L.rbox = b.take(sizeof(int32_t) * 4 * (size_t)(g.nshot > 0 ? g.nshot : 1));
   L.K = b.take(sizeof(float) * (size_t)g.fstride);
   L.ax = b.take(sizeof(float) * g.NXp);
   L.bx = b.take(sizeof(float) * g.NXp);
@@ -256,7 +255,6 @@ SetupArgs setup_args(const sweep_problem* p, const Layout& L, void* ws, const fl
     s.azh = at<float>(ws, L.azh);
     s.bzh = at<float>(ws, L.bzh);
   }
-  s.rbox = at<int32_t>(ws, L.rbox);
   s.vmax_bits = at<unsigned int>(ws, L.vmax);
   s.status = at<int>(ws, L.status);
   return s;
@@ -326,7 +324,6 @@ struct AcFwdLoop {
     if (!map2(&in.tK, g, at<float>(ws, L->K), IN_BX, IN_BZ_F)) return SWEEP_ECUDA;
     in.wavelet = wavelet;
     in.src = src;
-    in.rbox = at<int32_t>(ws, L->rbox);
     in.status = status;
     fx.g = g;
     fx.K = at<float>(ws, L->K);
@@ -424,7 +421,6 @@ struct AcBwdLoop {
     in.illum = (imaging && illum) ? at<float>(ws, L->iraw) : nullptr;
     in.wavelet = wavelet;
     in.src = src;
-    in.rbox = at<int32_t>(ws, L->rbox);
     in.wgrad = wg;
     in.status = status;
     fx.g = g;
@@ -548,7 +544,6 @@ ElStepArgs elastic_step_args(const sweep_problem* p, const Layout& L, void* ws, 
   a.wavelet = wavelet;
   a.src = src;
   a.rec = rec;
-  a.rbox = at<int32_t>(ws, L.rbox);
   a.data = data;
   a.src_scale = (float)((double)p->dt / ((double)p->dx * p->dx));
   a.status = at<int>(ws, L.status);

@@ -49,7 +49,6 @@ struct AcInFwdArgs {
   float* un;         // out u^{n+1} (the u^{n-1} buffer)
   const float* wavelet;
   const int32_t* src;
-  const int32_t* rbox;  // [S][4] receiver bounding box (z0, z1, x0, x1) padded
   int* status;
   int n;
   int units, ntx;       // (tile, shot) units; tiles along x
@@ -69,7 +68,6 @@ struct AcInBwdArgs {
   float* illum;      // [S][NZ][NXp] or null
   const float* wavelet;
   const int32_t* src;
-  const int32_t* rbox;
   float* wgrad;      // [S][nt] or null
   int* status;
   int n;
@@ -178,7 +176,6 @@ struct SetupArgs {
   float* bxh;
   float* azh;
   float* bzh;
-  int32_t* rbox;       // out [S][4] receiver bounding boxes (padded coords)
   unsigned int* vmax_bits;  // scratch: max vp as float bits
   int* status;
 };
