@@ -39,7 +39,10 @@ namespace {
 
 // Block size and rows per z-part thread: chosen by a sweep on GB300 (ZCH 4,
 // 8, 12 x 128, 256 threads; 301x901+40, 20 shots): forward 8 rows, backward
-// 4 rows (its thread keeps three windows), 128 threads.
+// 4 rows (its thread keeps three windows), 128 threads.  The minimum blocks
+// per SM in the kernels' launch bounds (8 forward, 7 backward) hold them at
+// 64 and 72 registers without spills; unbounded, the backward kernel takes
+// 80 and one block per SM fewer fits.
 constexpr int FT = 128;     // threads per block
 constexpr int ZCH_F = 8;    // rows per thread, forward z part
 constexpr int ZCH_B = 4;    // rows per thread, backward z part
@@ -85,35 +88,31 @@ __host__ __device__ __forceinline__ XBands x_bands(int lo_end, int hi_start, int
 // Work split: block b of the grid belongs to shot b / bps (bps = blocks per
 // shot, one division per block); within a shot the blocks are, in order,
 // nbz z-part blocks (row chunk = block / zbx, columns (block % zbx) * FT +
-// thread), nbx x-part blocks (8 rows each, a warp per row, a lane per 4-cell
-// column group), nbr receiver blocks and nbs ring blocks.
-constexpr int XROWS = FT / 32;
+// thread), nbx x-part blocks (a thread per (row, 4-cell column group of the
+// two bands), row-major, so that no lane idles when a row has fewer than 32
+// groups), nbr receiver blocks and nbs ring blocks.
 
 // ------------------------------------------------------------------ forward
-__device__ __forceinline__ void fwd_z(const AcFixArgs& a, int s, int bl) {
+// One forward z-part chunk: rows [zs, ze) of column x, window zs-4 ..
+// zs+ZCH+3.  FULL: the window lies inside the grid and the chunk is whole, so
+// no row needs a bounds test.
+template <bool FULL>
+__device__ __forceinline__ void fwd_z_chunk(const AcFixArgs& a, size_t so, int x, int zs,
+                                            int ze) {
   const Geom& g = a.g;
-  const int ch = bl / a.zbx;
-  const int x = (bl - ch * a.zbx) * FT + threadIdx.x;
-  if (x >= g.NX) return;
   constexpr int ZCH = ZCH_F, ZW = ZCH + 8;
-  const int nch = (g.P + ZCH - 1) / ZCH;  // chunks per strip
-  const int strip = ch >= nch ? 1 : 0;
-  const int base = strip ? g.P + g.nz : 0;
-  const int zs = base + (ch - strip * nch) * ZCH;
-  const int ze = min(zs + ZCH, base + g.P);
-  const size_t so = (size_t)s * g.fstride + x;  // this column of this shot
   float wu[ZW], wp[ZW], zt[ZCH], kk[ZCH];
 #pragma unroll
   for (int k = 0; k < ZW; ++k) {
     const int zz = zs - 4 + k;
-    const bool ok = zz >= 0 && zz < g.NZ;
+    const bool ok = FULL || (zz >= 0 && zz < g.NZ);
     const int o = zz * g.NXp;
     wu[k] = ok ? __ldg(a.u + so + o) : 0.f;
     wp[k] = ok ? __ldg(a.pzin + so + o) : 0.f;
   }
 #pragma unroll
   for (int q = 0; q < ZCH; ++q) {
-    const bool ok = zs + q < ze;
+    const bool ok = FULL || zs + q < ze;
     const int o = (zs + q) * g.NXp;
     zt[q] = ok ? a.zzin[so + o] : 0.f;
     kk[q] = ok ? __ldg(a.K + x + o) : 0.f;
@@ -121,7 +120,7 @@ __device__ __forceinline__ void fwd_z(const AcFixArgs& a, int s, int bl) {
 #pragma unroll
   for (int q = 0; q < ZCH; ++q) {
     const int z = zs + q;
-    if (z >= ze) break;
+    if (!FULL && z >= ze) break;
     const float A = __ldg(a.az + z), B = __ldg(a.bz + z);
     const float* w = wu + q;
     const float* p = wp + q;
@@ -134,6 +133,24 @@ __device__ __forceinline__ void fwd_z(const AcFixArgs& a, int s, int bl) {
     a.zzout[o] = zn;
     atomicAdd(a.un + o, kk[q] * (dp + zn));
   }
+}
+
+__device__ __forceinline__ void fwd_z(const AcFixArgs& a, int s, int bl) {
+  const Geom& g = a.g;
+  const int ch = bl / a.zbx;
+  const int x = (bl - ch * a.zbx) * FT + threadIdx.x;
+  if (x >= g.NX) return;
+  constexpr int ZCH = ZCH_F;
+  const int nch = (g.P + ZCH - 1) / ZCH;  // chunks per strip
+  const int strip = ch >= nch ? 1 : 0;
+  const int base = strip ? g.P + g.nz : 0;
+  const int zs = base + (ch - strip * nch) * ZCH;
+  const int ze = min(zs + ZCH, base + g.P);
+  const size_t so = (size_t)s * g.fstride + x;  // this column of this shot
+  if (ze == zs + ZCH && zs >= 4 && zs + ZCH + 4 <= g.NZ)
+    fwd_z_chunk<true>(a, so, x, zs, ze);
+  else
+    fwd_z_chunk<false>(a, so, x, zs, ze);
 }
 
 __device__ __forceinline__ void fwd_x_group(const AcFixArgs& a, int s, int z, int x) {
@@ -165,12 +182,19 @@ __device__ __forceinline__ void fwd_x_group(const AcFixArgs& a, int s, int z, in
   red4(a.un + ro + x, du);
 }
 
+// (row, group) pair t of the x part: row t / ngr, group t % ngr of the two
+// bands; false past the last row
+__device__ __forceinline__ bool x_pair(const AcFixArgs& a, int bl, int* z, int* x) {
+  const int t = bl * FT + threadIdx.x;
+  const int r = t / a.xb.ngr, j = t - r * a.xb.ngr;
+  *z = r;
+  *x = 4 * (j < a.xb.gl ? j : a.xb.gr0 + (j - a.xb.gl));
+  return r < a.g.NZ;
+}
+
 __device__ __forceinline__ void fwd_x(const AcFixArgs& a, int s, int bl) {
-  const Geom& g = a.g;
-  const int z = bl * XROWS + (threadIdx.x >> 5);
-  if (z >= g.NZ) return;
-  for (int j = threadIdx.x & 31; j < a.xb.ngr; j += 32)
-    fwd_x_group(a, s, z, 4 * (j < a.xb.gl ? j : a.xb.gr0 + (j - a.xb.gl)));
+  int z, x;
+  if (x_pair(a, bl, &z, &x)) fwd_x_group(a, s, z, x);
 }
 
 __device__ __forceinline__ void fwd_rec(const AcFixArgs& a, int s, int bl) {
@@ -222,7 +246,7 @@ __device__ __forceinline__ void fwd_ring(const AcFixArgs& a, int s, int bl) {
 }
 
 template <int NP>
-__global__ void __launch_bounds__(FT)
+__global__ void __launch_bounds__(FT, 8)
     ac_fix_fwd_kernel(const __grid_constant__ StepBatch<AcFixArgs, NP> m) {
   int blk, nblk;  // this block's index and the block count of its problem
   const AcFixArgs& a = m.p[step_problem(m, &blk, &nblk)];
@@ -250,24 +274,19 @@ __global__ void __launch_bounds__(FT)
 }
 
 // ----------------------------------------------------------------- backward
-__device__ __forceinline__ void bwd_z(const AcFixArgs& a, int s, int bl) {
+// One backward z-part chunk: rows [zs, ze) of column x, window zs-4 .. zs+ZCH+3.
+// FULL: the window lies inside the grid and inside one strip and the chunk
+// is whole, so no row needs a bounds or strip test.
+template <bool FULL>
+__device__ __forceinline__ void bwd_z_chunk(const AcFixArgs& a, size_t so, int x, int zs,
+                                            int ze) {
   const Geom& g = a.g;
-  const int ch = bl / a.zbx;
-  const int x = (bl - ch * a.zbx) * FT + threadIdx.x;
-  if (x >= g.NX) return;
-  const int lo_end = band_lo_end(g.P, g.NZ), hi_start = band_hi_start(g.P, g.nz, g.NZ);
   constexpr int ZCH = ZCH_B, ZW = ZCH + 8;
-  const int nlo = (lo_end + ZCH - 1) / ZCH;
-  const int band = ch >= nlo ? 1 : 0;
-  const int zs = (band ? hi_start : 0) + (ch - band * nlo) * ZCH;
-  const int ze = min(zs + ZCH, band ? g.NZ : lo_end);
-  if (zs >= ze) return;
-  const size_t so = (size_t)s * g.fstride + x;  // this column of this shot
   float wm[ZW], wz[ZW], wp[ZW], kk[ZCH], bb[ZW];
 #pragma unroll
   for (int k = 0; k < ZW; ++k) {
     const int zz = zs - 4 + k;
-    const bool ok = zz >= 0 && zz < g.NZ;
+    const bool ok = FULL || (zz >= 0 && zz < g.NZ);
     const int o = zz * g.NXp;
     wm[k] = ok ? __ldg(a.u + so + o) : 0.f;
     wz[k] = ok ? __ldg(a.zzin + so + o) : 0.f;
@@ -276,7 +295,7 @@ __device__ __forceinline__ void bwd_z(const AcFixArgs& a, int s, int bl) {
   }
 #pragma unroll
   for (int q = 0; q < ZCH; ++q) {
-    const bool ok = zs + q < ze;
+    const bool ok = FULL || zs + q < ze;
     kk[q] = ok ? __ldg(a.K + x + (zs + q) * g.NXp) : 0.f;
   }
   float wc[ZW], wb[ZW], wg[ZW];
@@ -286,12 +305,12 @@ __device__ __forceinline__ void bwd_z(const AcFixArgs& a, int s, int bl) {
     wc[k] = bb[k] * (wm[k] + wz[k]);
     wb[k] = bb[k] * wp[k];
     // m G: zero off the strip rows
-    wg[k] = (zz >= 0 && zz < g.NZ && z_border(g, zz)) ? wm[k] + wc[k] : 0.f;
+    wg[k] = (FULL || (zz >= 0 && zz < g.NZ && z_border(g, zz))) ? wm[k] + wc[k] : 0.f;
   }
 #pragma unroll
   for (int q = 0; q < ZCH; ++q) {
     const int z = zs + q;
-    if (z >= ze) break;
+    if (!FULL && z >= ze) break;
     const size_t o = so + z * g.NXp;
     const float* C = wc + q;
     const float* B = wb + q;
@@ -299,12 +318,33 @@ __device__ __forceinline__ void bwd_z(const AcFixArgs& a, int s, int bl) {
     const float corr = d2(C[0], C[1], C[2], C[3], C[4], C[5], C[6], C[7], C[8]) -
                        d1(B[0], B[1], B[2], B[3], B[5], B[6], B[7], B[8]);
     atomicAdd(a.un + o, kk[q] * corr);  // mu^n
-    if (z_border(g, z)) {
+    if (FULL || z_border(g, z)) {
       const float A = __ldg(a.az + z);
       a.pzout[o] = A * wp[q + 4] - d1(G[0], G[1], G[2], G[3], G[5], G[6], G[7], G[8]);
       a.zzout[o] = A * (wm[q + 4] + wz[q + 4]);
     }
   }
+}
+
+__device__ __forceinline__ void bwd_z(const AcFixArgs& a, int s, int bl) {
+  const Geom& g = a.g;
+  const int ch = bl / a.zbx;
+  const int x = (bl - ch * a.zbx) * FT + threadIdx.x;
+  if (x >= g.NX) return;
+  const int lo_end = band_lo_end(g.P, g.NZ), hi_start = band_hi_start(g.P, g.nz, g.NZ);
+  constexpr int ZCH = ZCH_B;
+  const int nlo = (lo_end + ZCH - 1) / ZCH;
+  const int band = ch >= nlo ? 1 : 0;
+  const int zs = (band ? hi_start : 0) + (ch - band * nlo) * ZCH;
+  const int ze = min(zs + ZCH, band ? g.NZ : lo_end);
+  if (zs >= ze) return;
+  const size_t so = (size_t)s * g.fstride + x;  // this column of this shot
+  const bool full = ze == zs + ZCH && zs >= 4 && zs + ZCH + 4 <= g.NZ &&
+                    (zs + ZCH + 4 <= g.P || zs - 4 >= g.P + g.nz);
+  if (full)
+    bwd_z_chunk<true>(a, so, x, zs, ze);
+  else
+    bwd_z_chunk<false>(a, so, x, zs, ze);
 }
 
 __device__ __forceinline__ void bwd_x_group(const AcFixArgs& a, int s, int z, int x) {
@@ -346,11 +386,8 @@ __device__ __forceinline__ void bwd_x_group(const AcFixArgs& a, int s, int z, in
 }
 
 __device__ __forceinline__ void bwd_x(const AcFixArgs& a, int s, int bl) {
-  const Geom& g = a.g;
-  const int z = bl * XROWS + (threadIdx.x >> 5);
-  if (z >= g.NZ) return;
-  for (int j = threadIdx.x & 31; j < a.xb.ngr; j += 32)
-    bwd_x_group(a, s, z, 4 * (j < a.xb.gl ? j : a.xb.gr0 + (j - a.xb.gl)));
+  int z, x;
+  if (x_pair(a, bl, &z, &x)) bwd_x_group(a, s, z, x);
 }
 
 __device__ __forceinline__ void bwd_rec(const AcFixArgs& a, int s, int bl) {
@@ -382,7 +419,7 @@ __device__ __forceinline__ void bwd_ring(const AcFixArgs& a, int s, int bl) {
 }
 
 template <int NP>
-__global__ void __launch_bounds__(FT)
+__global__ void __launch_bounds__(FT, 7)
     ac_fix_bwd_kernel(const __grid_constant__ StepBatch<AcFixArgs, NP> m) {
   int blk, nblk;  // this block's index and the block count of its problem
   const AcFixArgs& a = m.p[step_problem(m, &blk, &nblk)];
@@ -422,7 +459,7 @@ int fix_fwd_split(AcFixArgs& a) {
   a.nchz = g.P > 0 ? 2 * cdiv(g.P, ZCH_F) : 0;
   a.xb = x_bands(g.P, g.P + g.nx, g.NX);
   a.nbz = a.zbx * a.nchz;
-  a.nbx = g.P > 0 ? cdiv(g.NZ, XROWS) : 0;
+  a.nbx = (g.P > 0 && a.xb.ngr > 0) ? cdiv(g.NZ * a.xb.ngr, FT) : 0;
   a.nbr = (a.data && g.nrec > 0) ? cdiv(g.nrec, FT) : 0;
   a.nbs = (a.save && g.nring > 0) ? cdiv(cdiv(g.nring, 4), FT) : 0;
   return a.nbz + a.nbx + a.nbr + a.nbs;
@@ -436,7 +473,7 @@ int fix_bwd_split(AcFixArgs& a) {
   a.nchz = g.P > 0 ? cdiv(lo_end, ZCH_B) + cdiv(g.NZ - hi_start, ZCH_B) : 0;
   a.xb = x_bands(band_lo_end(g.P, g.NX), band_hi_start(g.P, g.nx, g.NX), g.NX);
   a.nbz = a.zbx * a.nchz;
-  a.nbx = g.P > 0 ? cdiv(g.NZ, XROWS) : 0;
+  a.nbx = (g.P > 0 && a.xb.ngr > 0) ? cdiv(g.NZ * a.xb.ngr, FT) : 0;
   a.nbr = (a.res && g.nrec > 0 && a.n >= 1) ? cdiv(g.nrec, FT) : 0;
   a.nbs = (a.save && a.uring && g.nring > 0) ? cdiv(cdiv(g.nring, 4), FT) : 0;
   return a.nbz + a.nbx + a.nbr + a.nbs;
