@@ -64,17 +64,22 @@ def test_elastic_forward_matches_oracle(sw, shape):
     assert rel(d, ref) <= 1e-4, rel(d, ref)
 
 
-def test_elastic_three_layer_fluid_top(sw):
-    """The paper's acoustic-elastic three-layer setting: Vp 1500/2000/2500,
-    Vs 0/1200/1400, rho 1000/1600/2000, 10 Hz Ricker (no-shear top layer)."""
+def layered_model(ex, nz, nx):
+    """The three-layer model of tests/golden/layered_example.json (the
+    paper's Sec. 3.6.1 example: a fluid over two solids) on an nz x nx
+    grid, layers of equal thickness: [3][nz][nx]."""
+    z = np.arange(nz)[:, None] * 3 // nz + np.zeros((1, nx), dtype=int)
+    return np.stack([np.asarray(ex[k])[z] for k in ("vp_m_s", "vs_m_s", "rho_kg_m3")])
+
+
+def test_elastic_three_layer_fluid_top(sw, golden):
+    """Forward on the paper's three-layer example (no-shear top layer)."""
+    ex = golden("layered_example.json")
     nz, nx = 90, 120
-    z = np.arange(nz)[:, None] + np.zeros((1, nx))
-    vp = np.where(z < 30, 1500.0, np.where(z < 60, 2000.0, 2500.0))
-    vs = np.where(z < 30, 0.0, np.where(z < 60, 1200.0, 1400.0))
-    rho = np.where(z < 30, 1000.0, np.where(z < 60, 1600.0, 2000.0))
     src = np.array([[10, 60]])
     rec = inputs.surface_line(1, 5, np.arange(0, nx, 4))
-    d, ref = run_both(sw, np.stack([vp, vs, rho]), nz, nx, 20, 10.0, 1e-3, 500, 10.0, src, rec)
+    d, ref = run_both(sw, layered_model(ex, nz, nx), nz, nx, 20, 10.0, 1e-3, 500,
+                      ex["ricker_peak_hz"], src, rec)
     assert rel(d, ref) <= 1e-4, rel(d, ref)
 
 
@@ -186,6 +191,42 @@ def test_elastic_gradient_matches_oracle(sw, seed, nt):
     g = g.cpu().numpy()
     gref, Jref = oracle.elastic_gradient(q, f32(m), f32(w), src, rec, dobs.astype(np.float64))
     assert abs(float(J) - Jref) <= 2e-3 * Jref, (float(J), Jref)
+    for k in range(3):
+        assert np.abs(gref[k]).max() > 0
+        assert rel(g[k], gref[k]) <= 1e-3, (k, rel(g[k], gref[k]))
+
+
+def test_elastic_gradient_layered_fluid_top(sw, golden):
+    """(vp, vs, rho) gradient on the paper's three-layer example, whose top
+    layer has no shear modulus: the harmonic shear average and its chain rule
+    must skip the fluid on both sides; relative L2 per parameter <= 1e-3."""
+    ex = golden("layered_example.json")
+    nz, nx, pml, dx, dt, nt, f0 = 48, 56, 8, 10.0, 1e-3, 400, ex["ricker_peak_hz"]
+    m = layered_model(ex, nz, nx)   # fluid rows 0..15, solids 16..31, 32..47
+    mt = m.copy()
+    mt[0, 20:28, 20:34] *= 1.05   # middle layer
+    mt[1, 22:30, 10:24] *= 0.95   # middle layer
+    mt[2, 4:12, 30:44] *= 1.04    # fluid layer
+    # sources in the middle layer (P and S in the solid, converted at the
+    # fluid interface); receivers in the fluid and in the bottom layer, so
+    # that the three gradients are of like size
+    src = np.array([[24, 15], [24, 40]])
+    xs = np.arange(1, nx, 4)
+    rec = np.concatenate([inputs.surface_line(2, 2, xs), inputs.surface_line(2, 40, xs)], axis=1)
+    nshot, nrec = src.shape[0], rec.shape[1]
+    w = np.stack([inputs.ricker(f0 * (1 + 0.05 * k), dt, nt) for k in range(nshot)]) * 1e6
+    p = sw.problem(sw.ELASTIC, nz=nz, nx=nx, pml=pml, dx=dx, dt=dt, nt=nt, nshot=nshot,
+                   nrec=nrec, f_ref=f0, v_pml=3000.0)
+    q = oracle.make_problem(1, nz, nx, pml, np.float32(dx), np.float32(dt), nt, nshot, nrec,
+                            np.float32(f0), v_pml=3000.0)
+    dobs = oracle.elastic_forward(q, f32(mt), f32(w), src, rec).astype(np.float32)
+    mtt, wt, st, rt = _tensors(sw, m, w, src, rec)
+    g, J, _ = sw.sweep_gradient(p, mtt, wt, st, rt, torch.tensor(dobs, device="cuda"))
+    g = g.cpu().numpy()
+    gref, Jref = oracle.elastic_gradient(q, f32(m), f32(w), src, rec, dobs.astype(np.float64))
+    assert np.all(np.isfinite(g))
+    assert abs(float(J) - Jref) <= 2e-3 * Jref, (float(J), Jref)
+    assert np.all(gref[1][:16] == 0.0)   # no Vs sensitivity inside the fluid
     for k in range(3):
         assert np.abs(gref[k]).max() > 0
         assert rel(g[k], gref[k]) <= 1e-3, (k, rel(g[k], gref[k]))

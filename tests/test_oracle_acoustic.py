@@ -85,10 +85,13 @@ def _green_trace(f, r, v, ts):
     return out
 
 
-def test_green_function_convergence():
-    """Homogeneous 2000 m/s, 20 Hz Ricker at the centre (the paper's
-    first-vs-second-order example setting); trace 200 m away."""
-    f0, v, dx, T = 20.0, 2000.0, 5.0, 0.2
+def test_green_function_convergence(golden):
+    """The paper's acoustic example setting (Sec. 3.1.3: homogeneous 2000 m/s,
+    20 Hz Ricker at the centre, from tests/golden/acoustic_example.json);
+    trace 200 m away."""
+    ex = golden("acoustic_example.json")
+    assert ex["source"] == "centre"
+    f0, v, dx, T = ex["ricker_peak_hz"], ex["vp_m_s"], 5.0, 0.2
     n = 161
     errs = []
     for dt in (5e-4, 2.5e-4):

@@ -8,7 +8,12 @@
   (scaling and timing of the explosive source);
 * in a homogeneous medium an explosive source radiates P waves only, so the
   recorded particle velocities do not depend on Vs (signs of the shear terms);
-* the CPML absorbs (energy decays, no late growth).
+* the CPML absorbs (energy decays, no late growth);
+* on the paper's three-layer model with a fluid top layer (Sec. 3.6.1) the
+  energy, with the fluid's strain energy tau_xx^2 / (2 lambda), is still
+  conserved exactly, the shear stress stays exactly zero wherever the
+  harmonic shear average touches the fluid, and tau_xx = tau_zz in the fluid
+  (no deviatoric stress without shear modulus).
 """
 import numpy as np
 import pytest
@@ -63,6 +68,60 @@ def test_energy_conserved_without_pml():
     assert np.abs(E - E[0]).max() / E[0] < 1e-11
 
 
+def layered_model(ex, nz, nx):
+    """The three-layer model of tests/golden/layered_example.json on an
+    nz x nx grid, layers of equal thickness top to bottom: [3][nz][nx]."""
+    z = np.arange(nz)[:, None] * 3 // nz + np.zeros((1, nx), dtype=int)
+    return np.stack([np.asarray(ex[k])[z] for k in ("vp_m_s", "vs_m_s", "rho_kg_m3")])
+
+
+def test_layered_example_fluid_top_energy_and_stress(golden):
+    ex = golden("layered_example.json")
+    assert ex["vs_m_s"][0] == 0.0 and min(ex["vs_m_s"][1:]) > 0
+    nz, nx, dx, dt = 36, 40, 5.0, 4e-4
+    model = layered_model(ex, nz, nx)
+    vp, vs, rho = model
+    f0 = ex["ricker_peak_hz"]
+    nsrc = int(round(3.0 / f0 / dt))  # the wavelet over [0, 2 t0], then zero
+    nt = nsrc + 150
+    w = np.zeros(nt)
+    w[:nsrc] = inputs.ricker(f0, dt, nsrc)
+    p = oracle.make_problem(1, nz, nx, 0, dx, dt, nt, 1, 1, f0)
+    # source in the middle (solid) layer: P and converted S waves meet the
+    # fluid-solid interface
+    _, wf = oracle.elastic_forward(p, model, w[None], np.array([[18, 20]]),
+                                   np.array([[[3, 3]]]), wavefield=True)
+    f = wf[0]  # [nt+1][5][nz][nx]
+    with np.errstate(divide="ignore"):
+        lam, mu, mx, mz, muxz = _mats(vp, vs, rho)
+    fluid = mu == 0.0
+    assert fluid.sum() == 12 * nx and np.all(fluid[:12])
+    noshear = muxz == 0.0  # txz points touching a fluid cell (rows 0..11)
+    assert np.all(noshear[:12]) and not noshear[12:].any()
+    assert np.abs(f[:, 4][:, ~noshear]).max() > 0
+    assert np.all(f[:, 4][:, noshear] == 0.0)
+    assert np.abs(f[:, 2][:, fluid]).max() > 0
+    assert np.array_equal(f[:, 2][:, fluid], f[:, 3][:, fluid])
+    l2m = lam + 2 * mu
+    solid = ~fluid
+    det = (l2m ** 2 - lam ** 2)[solid]
+    E = []
+    for k in range(nsrc + 2, nt):
+        vx1, vz1 = f[k + 1, 0], f[k + 1, 1]   # v^{k+1/2}
+        vx0, vz0 = f[k, 0], f[k, 1]           # v^{k-1/2}
+        txx, tzz, txz = f[k, 2], f[k, 3], f[k, 4]  # tau^k
+        kin = 0.5 * np.sum(mx * vx1 * vx0 + mz * vz1 * vz0)
+        ts, zs = txx[solid], tzz[solid]
+        pot = 0.5 * (np.sum((l2m[solid] * ts ** 2 - 2 * lam[solid] * ts * zs
+                             + l2m[solid] * zs ** 2) / det)
+                     + np.sum(txx[fluid] ** 2 / lam[fluid])
+                     + np.sum(txz[~noshear] ** 2 / muxz[~noshear]))
+        E.append(kin + pot)
+    E = np.array(E)
+    assert E[0] > 0
+    assert np.abs(E - E[0]).max() / E[0] < 1e-11
+
+
 def _green_pressure(fdot, r, v, ts):
     """P(r,t) for P_tt = v^2 Lap P - f'(t) delta: the 2D Green's function with
     source term v^2 g, g = -f'/v^2."""
@@ -75,13 +134,17 @@ def _green_pressure(fdot, r, v, ts):
     return out
 
 
-def test_zero_shear_pressure_matches_green_function():
-    f0, v, dx, T = 20.0, 2000.0, 5.0, 0.2
+def test_zero_shear_pressure_matches_green_function(golden):
+    """The paper's acoustic example setting (Sec. 3.1.3, from
+    tests/golden/acoustic_example.json) run through the elastic engine
+    with Vs = 0; source at the centre, trace 200 m away."""
+    ex = golden("acoustic_example.json")
+    f0, v, dx, T = ex["ricker_peak_hz"], ex["vp_m_s"], 5.0, 0.2
     n = 161
     dt = 2.5e-4
     nt = int(round(T / dt))
     vp = np.full((n, n), v)
-    model = np.stack([vp, 0 * vp, np.full((n, n), 1000.0)])
+    model = np.stack([vp, 0 * vp, np.full((n, n), ex["rho_kg_m3"])])
     p = oracle.make_problem(1, n, n, 0, dx, dt, nt, 1, 1, f0)
     # the stress update from n to n+1 is centred at (n + 1/2) dt
     w = inputs.ricker(f0, dt, nt, shift=0.5)
