@@ -582,7 +582,6 @@ int elastic_reverse_loop(const sweep_problem* p, const Layout& L, void* ws, cons
                          const int32_t* src, const int32_t* rec, const float* res, float* wgrad,
                          bool gradient, cudaStream_t st) {
   const Geom g = make_geom(p);
-  const size_t F = sizeof(float) * (size_t)g.fstride * (size_t)g.nshot;
   char* adj = at<char>(ws, L.el_a);
   const size_t sb = L.fwd_hi - L.fwd_lo;
   cudaMemsetAsync(adj, 0, sb, st);

@@ -16,7 +16,6 @@
   (no deviatoric stress without shear modulus).
 """
 import numpy as np
-import pytest
 from scipy import integrate
 
 import oracle
