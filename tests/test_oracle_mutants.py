@@ -66,6 +66,10 @@ CASES = [
      "grad[(size_t)i * nx + j] = sum * v * p->dt * p->dt / (p->dx * p->dx);", [FD]),
     ("cpml_b_sign", "common.c", "b[j] = sigma / (sigma + alpha) * (a[j] - 1.0);",
      "b[j] = sigma / (sigma + alpha) * (1.0 - a[j]);", [DECAY, REFLECT]),
+    ("cpml_alpha_reversed", "common.c", "const double alpha = M_PI * f_ref * (1.0 - rho);",
+     "const double alpha = M_PI * f_ref * rho;", [DECAY, REFLECT]),
+    ("adjoint_zeta_a_for_b", "acoustic.c", "aout->zex[c] += g->ax[j] * tzx;",
+     "aout->zex[c] += g->bx[j] * tzx;", [TRANSPOSE, REACH]),
     ("arithmetic_shear_mean", "elastic.c",
      ": 4.0 / (1.0 / m00 + 1.0 / m01 + 1.0 / m10 + 1.0 / m11);",
      ": 0.25 * (m00 + m01 + m10 + m11);", [E_ENERGY, E_LAYERED]),
@@ -86,6 +90,12 @@ CASES = [
     ("vx_shear_stagger", "elastic.c",
      "const double dzt = dmz(&g, txz, i, j) * idx; /* at (i, j+1/2) */",
      "const double dzt = dpz(&g, txz, i, j) * idx; /* at (i, j+1/2) */", [E_ENERGY, E_VS]),
+    ("p1_integer_point_profile", "elastic.c",
+     "p1[c] = g.axh[j] * p1[c] + g.bxh[j] * dxt;",
+     "p1[c] = g.ax[j] * p1[c] + g.bx[j] * dxt;", [E_DOT, E_ONE]),
+    ("txz_without_dt", "elastic.c",
+     "txz[c] += dt * g.muxz[c] * (ezx + p7[c] + exz + p8[c]);",
+     "txz[c] += g.muxz[c] * (ezx + p7[c] + exz + p8[c]);", [E_ENERGY, E_VS]),
     ("adjoint_hooke_transposed", "elastic.c",
      "const double Ex = dt * (l2m * atxx[c] + g->lam[c] * atzz[c]);",
      "const double Ex = dt * (g->lam[c] * atxx[c] + l2m * atzz[c]);", [E_DOT, E_ONE]),
