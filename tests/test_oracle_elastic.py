@@ -9,6 +9,8 @@
 * in a homogeneous medium an explosive source radiates P waves only, so the
   recorded particle velocities do not depend on Vs (signs of the shear terms);
 * the CPML absorbs (energy decays, no late growth);
+* the stability limit vp dt / dx <= 1 / (sqrt(2) (9/8 + 1/24)) of the
+  4th-order staggered scheme (stable just below it, blow-up just above);
 * on the paper's three-layer model with a fluid top layer (Sec. 3.6.1) the
   energy, with the fluid's strain energy tau_xx^2 / (2 lambda), is still
   conserved exactly, the shear stress stays exactly zero wherever the
@@ -16,6 +18,7 @@
   (no deviatoric stress without shear modulus).
 """
 import numpy as np
+import pytest
 from scipy import integrate
 
 import oracle
@@ -65,6 +68,32 @@ def test_energy_conserved_without_pml():
     E = np.array(E)
     assert E[0] > 0
     assert np.abs(E - E[0]).max() / E[0] < 1e-11
+
+
+@pytest.mark.parametrize("factor,stable", [(0.995, True), (1.01, False)])
+def test_elastic_cfl_limit(factor, stable):
+    """Von Neumann limit of the staggered 4th-order scheme in 2D: the P mode
+    at the Nyquist wavenumber of both axes is the first to grow."""
+    n, dx, vp = 30, 10.0, 2500.0
+    limit = 1.0 / (np.sqrt(2.0) * (9.0 / 8.0 + 1.0 / 24.0))
+    dt = factor * limit * dx / vp
+    nt = 2000
+    rng = np.random.default_rng(4)
+    w = np.zeros(nt)
+    w[:5] = rng.standard_normal(5)
+    model = np.stack([np.full((n, n), vp), np.full((n, n), vp / 1.8), np.full((n, n), 2000.0)])
+    p = oracle.make_problem(1, n, n, 0, dx, dt, nt, 1, 1, 10.0)
+    with np.errstate(all="ignore"):
+        d = oracle.elastic_forward(p, model, w[None], np.array([[15, 15]]),
+                                   np.array([[[10, 12]]]))[0]
+        early = np.abs(d[:, :, :50]).max()
+        tail = d[:, :, -200:]
+        late = np.abs(tail).max() if np.all(np.isfinite(tail)) else np.inf
+    assert early > 0
+    if stable:
+        assert late < 10 * early
+    else:
+        assert late > 1e6 * early
 
 
 def layered_model(ex, nz, nx):
