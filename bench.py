@@ -70,6 +70,20 @@ def alg_bytes_fwd(c):
     return 16 * c["N_pad"] + 16 * (c["N_x"] + c["N_z"]) + 4 * c["N_ring"]
 
 
+def alg_bytes_k_once(per_shot, c, nshot):
+    """Algorithmic bytes of one step of nshot shots when the velocity
+    coefficient K (4 B per padded cell, one model for all shots) is counted
+    once for the batch instead of once per shot.  The imaging accumulator is
+    per shot, so nothing else is shared."""
+    return per_shot * nshot - 4 * c["N_pad"] * (nshot - 1)
+
+
+def interior_gpts(value, c):
+    """The throughput in interior cell-steps: the padded figure times the
+    interior share of the padded grid."""
+    return value * c["N_int"] / c["N_pad"]
+
+
 # the sources the acoustic time-step kernels are compiled from
 KERNEL_SOURCES = ("acoustic_common.cuh", "acoustic_cpml.cu", "acoustic_interior.cu",
                   "sweep_internal.cuh", "tma.cuh")
@@ -195,11 +209,12 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------- oracle
-def oracle_sample(w, nshot_max, nt_sample):
+def oracle_sample(w, nshot_max, nt_sample, threads=None):
     """Time the FP64 oracle gradient on a bounded sample of the workload: the
-    same grid and geometry, min(cores, 20) shots, nt_sample steps."""
+    same grid and geometry, min(threads, nshot_max) shots, nt_sample steps,
+    on `threads` host threads (default: every core)."""
     import oracle
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     ns = max(1, min(nshot_max, cores))
     oracle.set_threads(cores)
     q = oracle.make_problem(0, w["nz"], w["nx"], w["pml"], w["dx"], w["dt"], nt_sample, ns,
@@ -397,10 +412,13 @@ def run_sweep(args, w, rank, world, local_rank):
     achieved = alg_bytes_bwd(c) * nshot / (bwd_avg_ms * 1e-3) / 1e9
     traffic = read_traffic()
     path_gbs = (alg_bytes_fwd(c) + alg_bytes_bwd(c)) * nshot * nt / (ms_step * 1e-3) / 1e9
+    k_once = alg_bytes_k_once(alg_bytes_bwd(c), c, nshot)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         g, el, cores, sample = oracle_sample(w, nshot, 700)
-        cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        g1, _, _, sample1 = oracle_sample(w, 1, 200, threads=1)
+        cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread": {"value": g1, "unit": UNIT, "cores": 1, "sample": sample1}}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -422,6 +440,11 @@ def run_sweep(args, w, rank, world, local_rank):
                      "avg_launch_ms": bwd_avg_ms,
                      "timing": "CUDA events around each backward step of %d profiled "
                                "gradient steps after the timed region" % prof_steps},
+        "interior_gpts": interior_gpts(value, c),
+        "k_once": {"alg_bytes_per_launch": k_once,
+                   "achieved": k_once / (bwd_avg_ms * 1e-3) / 1e9,
+                   "frac": k_once / (bwd_avg_ms * 1e-3) / 1e9 / peak,
+                   "note": "backward step bytes with K read once for all shots"},
         "path_roofline": {"achieved": path_gbs, "frac": path_gbs / peak,
                           "note": "algorithmic bytes of all forward and backward steps "
                                   "x steps / timed step time"},

@@ -35,6 +35,16 @@ def test_cell_counts_and_algorithmic_bytes():
     assert 20 * bwd == 263725520  # the backward step of 20 shots
 
 
+def test_interior_and_shared_k_figures():
+    """Interior Gpts/s is the padded figure scaled by the interior share;
+    with K counted once for the 20 shots the backward step of the workload
+    reads 19 x 4 B fewer per padded cell."""
+    c = bench.counts(301, 901, 40)
+    assert bench.interior_gpts(373761.0, c) == pytest.approx(271201.0)
+    assert bench.alg_bytes_k_once(bench.alg_bytes_bwd(c), c, 1) == bench.alg_bytes_bwd(c)
+    assert bench.alg_bytes_k_once(bench.alg_bytes_bwd(c), c, 20) == 263725520 - 19 * 4 * 373761
+
+
 def _scratch_root(tmp_name):
     d = os.path.join(ROOT, "_build", tmp_name)
     if os.path.exists(d):
