@@ -146,9 +146,6 @@ int sweep_gradient(const sweep_problem* prob, const float* model,
                    const float* d_obs, float* grad, double* misfit, float* illum,
                    void* ws, size_t ws_bytes, void* stream);
 
-/* FP64 dot product sum_i a[i] b[i] of two device float arrays into the device
- * double *out (for dot-product and finite-difference tests).  ws: at least
- * sweep_dot_workspace_bytes() bytes of device scratch. */
 /* Gradients of several acoustic problems in one call (heterogeneous batch:
  * the shot / model dimension of Sec. 2.2 with each model of its own size,
  * border, record length and shot count).  Problem i takes the arguments of
@@ -181,6 +178,16 @@ int sweep_forward_batch(int nprob, const sweep_problem* probs, const float* cons
                         const int32_t* const* recs, float* const* data, void* const* ws,
                         const size_t* ws_bytes, void* stream);
 
+/* FP64 dot product sum_i a[i] b[i] of two device float arrays a, b of n
+ * elements into the device double *out, with fixed-order partial sums (the
+ * same inputs give the same bits); used by the dot-product test of the
+ * adjoint and by the misfit of an FWI line-search trial.  The paper has no
+ * separate counterpart: it is the inner product that test is stated in.
+ * ws: device scratch of at least sweep_dot_workspace_bytes() bytes, 8-byte
+ * aligned, owned by the caller; calls that overlap on the GPU must not share
+ * one.  n = 0 gives 0.  SWEEP_EINVAL (n < 0, NULL out, or NULL a or b with
+ * n > 0) and SWEEP_EWORKSPACE are returned before any launch.  Asynchronous
+ * on `stream`. */
 size_t sweep_dot_workspace_bytes(void);
 int sweep_dot(const float* a, const float* b, int64_t n, double* out, void* ws,
               size_t ws_bytes, void* stream);

@@ -492,14 +492,23 @@ _dot_ws = {}
 
 
 def sweep_dot(a, b, out=None, stream=None):
-    """FP64 sum(a * b) of two float32 CUDA tensors, as a device float64 scalar."""
+    """FP64 sum(a * b) of two float32 CUDA tensors, as a device float64 scalar.
+
+    The partial sums go to one scratch buffer per device, allocated on the
+    first call and shared by later calls: calls on different streams must
+    not overlap on the GPU (pass sweep_dot's C workspace yourself for that)."""
     _check_dtype(a, torch.float32, "a")
     _check_dtype(b, torch.float32, "b")
     if a.numel() != b.numel():
         raise ValueError("sweep_dot: size mismatch")
     dev = a.device
+    if b.device != dev:
+        raise ValueError("sweep_dot: a and b on different devices")
     if out is None:
         out = torch.empty((), dtype=torch.float64, device=dev)
+    _check_dtype(out, torch.float64, "out")
+    if out.numel() != 1:
+        raise ValueError("sweep_dot: out must be a one-element float64 tensor")
     key = (dev.index if dev.index is not None else torch.cuda.current_device())
     ws = _dot_ws.get(key)
     if ws is None:

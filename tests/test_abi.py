@@ -170,3 +170,18 @@ def test_gradient_batch_host_checks(lib):
     assert call([p, q], [V(256 * 4096), V(256 * 4096)], [need, need]) == sweep.EWORKSPACE
     assert call([p, q], [V(256 * 4096), V(512 * 4096)], [need, need - 1]) == sweep.EWORKSPACE
     assert call([p, q], [V(256 * 4096), V(512 * 4096)], [need, need], model=V(0)) == sweep.EINVAL
+
+
+def test_dot_binding_checks_out_before_any_launch():
+    """sweep_dot writes 8 bytes to `out`: a float32 or multi-element `out`
+    is rejected on the host, as are mismatched sizes."""
+    import torch
+
+    from paper_2604_14189_gb300 import sweep
+    a = torch.zeros(4, dtype=torch.float32)
+    with pytest.raises(TypeError, match="out"):
+        sweep.sweep_dot(a, a, out=torch.zeros((), dtype=torch.float32))
+    with pytest.raises(ValueError, match="out"):
+        sweep.sweep_dot(a, a, out=torch.zeros(2, dtype=torch.float64))
+    with pytest.raises(ValueError, match="size"):
+        sweep.sweep_dot(a, torch.zeros(5, dtype=torch.float32))
