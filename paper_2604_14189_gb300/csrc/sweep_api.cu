@@ -693,11 +693,11 @@ int sweep_forward(const sweep_problem* p, const float* model, const float* wavel
                   const int32_t* src, const int32_t* rec, float* data, void* ws,
                   size_t ws_bytes, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = begin(p, SWEEP_MODE_FORWARD, ws, ws_bytes, st);
-  if (rc) return rc;
-  if (!model) return SWEEP_EINVAL;
+  if (!valid_problem(p) || !model) return SWEEP_EINVAL;
   if (p->nshot > 0 && (!wavelet || !src)) return SWEEP_EINVAL;
   if (p->nshot > 0 && p->nrec > 0 && (!rec || !data)) return SWEEP_EINVAL;
+  int rc = begin(p, SWEEP_MODE_FORWARD, ws, ws_bytes, st);
+  if (rc) return rc;
   if (p->nshot == 0) return SWEEP_OK;
   const Layout L = layout(p, SWEEP_MODE_FORWARD);
   if (p->physics == SWEEP_ELASTIC) {
@@ -720,11 +720,11 @@ int sweep_adjoint(const sweep_problem* p, const float* model, const float* adj_d
                   const int32_t* src, const int32_t* rec, float* wavelet_grad, void* ws,
                   size_t ws_bytes, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = begin(p, SWEEP_MODE_ADJOINT, ws, ws_bytes, st);
-  if (rc) return rc;
-  if (!model) return SWEEP_EINVAL;
+  if (!valid_problem(p) || !model) return SWEEP_EINVAL;
   if (p->nshot > 0 && (!src || !wavelet_grad)) return SWEEP_EINVAL;
   if (p->nshot > 0 && p->nrec > 0 && (!rec || !adj_data)) return SWEEP_EINVAL;
+  int rc = begin(p, SWEEP_MODE_ADJOINT, ws, ws_bytes, st);
+  if (rc) return rc;
   if (p->nshot == 0) return SWEEP_OK;
   const Layout L = layout(p, SWEEP_MODE_ADJOINT);
   if (p->physics == SWEEP_ELASTIC) {
@@ -748,12 +748,12 @@ int sweep_gradient(const sweep_problem* p, const float* model, const float* wave
                    const int32_t* src, const int32_t* rec, const float* d_obs, float* grad,
                    double* misfit, float* illum, void* ws, size_t ws_bytes, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = begin(p, SWEEP_MODE_GRADIENT, ws, ws_bytes, st);
-  if (rc) return rc;
-  if (!model || !grad) return SWEEP_EINVAL;
+  if (!valid_problem(p) || !model || !grad) return SWEEP_EINVAL;
   if (p->nshot > 0 && (!wavelet || !src)) return SWEEP_EINVAL;
   if (p->nshot > 0 && p->nrec > 0 && (!rec || !d_obs)) return SWEEP_EINVAL;
   if (p->physics == SWEEP_ELASTIC && illum) return SWEEP_EUNSUPPORTED;
+  int rc = begin(p, SWEEP_MODE_GRADIENT, ws, ws_bytes, st);
+  if (rc) return rc;
   const Geom g = make_geom(p);
   const int npar = p->physics == SWEEP_ELASTIC ? 3 : 1;
   if (p->nshot == 0) {

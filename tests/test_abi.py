@@ -83,6 +83,35 @@ def test_host_errors_before_launch():
     assert sweep.strerror(sweep.ECFL).startswith("time step")
 
 
+def test_null_arrays_rejected_before_device_work():
+    """With a workspace that passes every host check, a NULL array is still
+    reported as SWEEP_EINVAL before the call touches the device (on a host
+    without a GPU, any device call would return SWEEP_ECUDA instead)."""
+    from paper_2604_14189_gb300 import sweep
+    L = sweep.lib()
+    p = _prob(sweep)
+    fake = ctypes.c_void_p(1 << 20)  # 256-byte aligned, never dereferenced
+    big = 1 << 40
+    V = None
+    assert L.sweep_forward(ctypes.byref(p), V, fake, fake, fake, fake, fake, big,
+                           None) == sweep.EINVAL
+    assert L.sweep_forward(ctypes.byref(p), fake, V, fake, fake, fake, fake, big,
+                           None) == sweep.EINVAL
+    assert L.sweep_forward(ctypes.byref(p), fake, fake, fake, fake, V, fake, big,
+                           None) == sweep.EINVAL
+    assert L.sweep_adjoint(ctypes.byref(p), fake, fake, fake, fake, V, fake, big,
+                           None) == sweep.EINVAL
+    assert L.sweep_adjoint(ctypes.byref(p), fake, V, fake, fake, fake, fake, big,
+                           None) == sweep.EINVAL
+    assert L.sweep_gradient(ctypes.byref(p), fake, fake, fake, fake, fake, V, fake, fake,
+                            fake, big, None) == sweep.EINVAL
+    assert L.sweep_gradient(ctypes.byref(p), fake, fake, fake, fake, V, fake, fake, fake,
+                            fake, big, None) == sweep.EINVAL
+    el = _prob(sweep, physics=sweep.ELASTIC)
+    assert L.sweep_gradient(ctypes.byref(el), fake, fake, fake, fake, fake, fake, fake,
+                            fake, fake, big, None) == sweep.EUNSUPPORTED  # illum, elastic
+
+
 def test_capture_rejects_bad_arguments(lib):
     """Host-side checks of the graph calls, before any CUDA call: the legacy
     default stream cannot be captured, and ending or launching needs a
