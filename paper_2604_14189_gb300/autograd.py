@@ -11,8 +11,10 @@ written by hand instead of taped.
 
 The velocity gradient is taken with the absorbing-border padding and the
 CPML profile held fixed (the library's definition): it is exact for
-perturbations of interior cells that do not move the edge-replicated border
-(or with ``F_PADDED_MODEL``, where the border is an input of its own).
+perturbations of interior cells that do not move the edge-replicated border.
+A padded model (``F_PADDED_MODEL``) can be modelled and differentiated with
+respect to the wavelets, but not with respect to ``v``: its border cells are
+inputs of their own, and the library gives no gradient for them.
 """
 from __future__ import annotations
 
@@ -21,6 +23,13 @@ import copy
 import torch
 
 from . import sweep
+
+
+def _check_differentiable(problem) -> None:
+    if int(problem.flags) & sweep.F_PADDED_MODEL:
+        raise ValueError("acoustic_modelling: no velocity gradient for a padded model "
+                         "(F_PADDED_MODEL); pass the interior model to differentiate "
+                         "with respect to v")
 
 
 class AcousticModelling(torch.autograd.Function):
@@ -37,6 +46,7 @@ class AcousticModelling(torch.autograd.Function):
         g = grad_data.contiguous()
         grad_v = grad_w = None
         if ctx.needs_input_grad[0]:
+            _check_differentiable(ctx.problem)
             p = copy.copy(ctx.problem)
             p.flags = int(p.flags) | sweep.F_RESIDUAL_IN
             grad_v, _, _ = sweep.sweep_gradient(p, v.contiguous(), wavelet.contiguous(), src, rec,
@@ -48,4 +58,6 @@ class AcousticModelling(torch.autograd.Function):
 
 def acoustic_modelling(v, wavelet, problem, src, rec):
     """Differentiable acoustic forward modelling (see AcousticModelling)."""
+    if v.requires_grad:
+        _check_differentiable(problem)
     return AcousticModelling.apply(v, wavelet, problem, src, rec)
