@@ -1,5 +1,6 @@
-"""Heterogeneous batches: many independent acoustic problems of uneven grid
-size, border width, record length and shot count in one call.
+"""Heterogeneous batches: many independent problems of uneven grid size,
+border width, record length and shot count in one call (acoustic problems
+share launches; elastic ones run one problem per call).
 
 Batch modelling is the shot / model dimension of Sec. 2.2; the paper also
 runs several velocity models at once.  Here every problem keeps its own
@@ -57,6 +58,15 @@ class Item:
     data: torch.Tensor | None = None    # out (forward mode)
 
 
+def out_shapes(p: sweep.Problem) -> tuple[tuple[int, ...], tuple[int, ...]]:
+    """Shapes of (gradient, recorded data) of a problem: acoustic [nz][nx]
+    and [nshot][1][nrec][nt]; elastic [3][nz][nx] (vp, vs, rho) and
+    [nshot][2][nrec][nt] (vx, vz)."""
+    if p.physics == sweep.ELASTIC:
+        return (3, p.nz, p.nx), (p.nshot, 2, p.nrec, p.nt)
+    return (p.nz, p.nx), (p.nshot, 1, p.nrec, p.nt)
+
+
 def cost(p: sweep.Problem) -> int:
     """Padded cell-steps of a problem (the unit of work of the solver)."""
     return (p.nz + 2 * p.pml) * (p.nx + 2 * p.pml) * p.nt * p.nshot
@@ -91,20 +101,20 @@ def run(items: list[Item], mode: int = sweep.MODE_GRADIENT, streams: int = 8,
         device=None, fused: bool = True) -> list[int]:
     """Runs every item; returns the status code of each (0 = ok).  Outputs
     are allocated on first use and written in place.  Acoustic items run as
-    cohorts in shared launches unless ``fused`` is False."""
+    cohorts in shared launches unless ``fused`` is False; a batch with an
+    elastic item runs one problem per call."""
     device = torch.device(device or "cuda")
     if not items:
         return []
     for it in items:
+        gshape, dshape = out_shapes(it.problem)
         if mode == sweep.MODE_GRADIENT:
             if it.grad is None:
-                it.grad = torch.empty((it.problem.nz, it.problem.nx), dtype=torch.float32,
-                                      device=device)
+                it.grad = torch.empty(gshape, dtype=torch.float32, device=device)
             if it.misfit is None:
                 it.misfit = torch.empty((), dtype=torch.float64, device=device)
         elif mode == sweep.MODE_FORWARD and it.data is None:
-            it.data = torch.empty((it.problem.nshot, 1, it.problem.nrec, it.problem.nt),
-                                  dtype=torch.float32, device=device)
+            it.data = torch.empty(dshape, dtype=torch.float32, device=device)
     codes = torch.zeros(len(items), dtype=torch.int32, device=device)
     errors: list[BaseException] = []
     if fused and all(it.problem.physics == sweep.ACOUSTIC for it in items):

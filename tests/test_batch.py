@@ -51,6 +51,15 @@ def test_cohorts_group_similar_record_lengths():
     assert flat == sorted(flat, reverse=True)
 
 
+def test_output_shapes_follow_the_physics():
+    """Outputs allocated by run() have the sizes the C ABI writes: an
+    elastic problem has three gradients and two data components."""
+    from paper_2604_14189_gb300 import sweep
+    kw = dict(nz=7, nx=9, pml=3, dx=10.0, dt=1e-3, nt=11, nshot=2, nrec=5)
+    assert batch.out_shapes(sweep.problem(sweep.ACOUSTIC, **kw)) == ((7, 9), (2, 1, 5, 11))
+    assert batch.out_shapes(sweep.problem(sweep.ELASTIC, **kw)) == ((3, 7, 9), (2, 2, 5, 11))
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("count,fused", [(6, True), (6, False), (21, True)])
 def test_batch_matches_individual_runs(count, fused):
