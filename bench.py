@@ -722,7 +722,7 @@ def run_batch(args, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     items = []
-    cells = 0
+    cells = alg = 0
     for w in inputs.workload_batch():
         ns, nrec, nt = w["src"].shape[0], w["rec"].shape[1], w["nt"]
         p = sweep.problem(nz=w["nz"], nx=w["nx"], pml=w["pml"], dx=w["dx"], dt=w["dt"], nt=nt,
@@ -734,6 +734,8 @@ def run_batch(args, local_rank):
             torch.tensor(w["src"], device=dev), torch.tensor(w["rec"], device=dev),
             d_obs=torch.zeros((ns, 1, nrec, nt), dtype=torch.float32, device=dev)))
         cells += batch.cost(p)
+        cb = counts(w["nz"], w["nx"], w["pml"])
+        alg += (alg_bytes_fwd(cb) + alg_bytes_bwd(cb)) * ns * nt
     # schedule autotuning on a sample of the batch
     best, times = batch.autotune_streams(items[:64], candidates=(1, 2, 3, 4, 6))
     for _ in range(max(args.warmup, 0)):
@@ -765,6 +767,9 @@ def run_batch(args, local_rank):
                    "streams": best, "autotune_seconds": times,
                    "step": "one pass over the whole batch"},
         "roofline": None,
+        "path_roofline": {"achieved": alg / sec / 1e9, "frac": alg / sec / 1e9 / peaks()[0],
+                          "note": "algorithmic bytes of every forward and backward step of "
+                                  "the 256 problems / pass time"},
         "cpu_baseline": None,
         "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 4 * len(items)},
