@@ -20,6 +20,14 @@ and three FP64 dot products of the library (no host round trip of the data).
 The line search and the preconditioner are host logic, testable without a
 GPU (``line_search`` takes any misfit function).
 
+With ``checkpoint=<directory>``, ``run`` writes the state after every
+iteration (``model.npy``: the current model; ``state.json``: the iterations
+done, the next first-trial step and the history) and, called again with the
+same directory, resumes from it: the iterations already done are not
+repeated, and the step carries on from where it stopped.  Each file is
+written to a temporary name and renamed into place, so an interrupted
+write leaves the previous state whole.
+
 With ``graphs=True`` (the default) the gradient call and the trial-misfit
 calls (forward + two dot products) are recorded once as CUDA graphs over
 fixed buffers; each evaluation copies the model into its buffer and replays
@@ -29,9 +37,12 @@ thousands of launches.
 from __future__ import annotations
 
 import dataclasses
+import json
+import os
 import time
 from typing import Callable
 
+import numpy as np
 import torch
 
 from . import sweep
@@ -67,6 +78,43 @@ def line_search(misfit: Callable[[torch.Tensor], float], model: torch.Tensor,
             return trial, j, step, k + 1, True
         step *= 0.5
     return model, j0, step, max_halvings + 1, False
+
+
+STATE_VERSION = 1
+
+
+def save_state(directory: str, model: torch.Tensor, done: int, step: float,
+               history: list) -> None:
+    """Writes the loop state after `done` iterations (model as float32
+    ``.npy``, the rest as JSON); the model file is replaced first and the
+    JSON last, so the JSON never names a model that is not on disk."""
+    os.makedirs(directory, exist_ok=True)
+    mpath = os.path.join(directory, "model.npy")
+    tmp = mpath + ".tmp.npy"
+    np.save(tmp, model.detach().to("cpu", torch.float32).numpy())
+    os.replace(tmp, mpath)
+    spath = os.path.join(directory, "state.json")
+    with open(spath + ".tmp", "w") as f:
+        json.dump({"version": STATE_VERSION, "iterations_done": int(done), "step": float(step),
+                   "shape": list(model.shape), "history": history}, f)
+    os.replace(spath + ".tmp", spath)
+
+
+def load_state(directory: str):
+    """(model as a CPU float32 tensor, iterations done, step, history), or
+    None if the directory holds no state."""
+    spath = os.path.join(directory, "state.json")
+    if not os.path.exists(spath):
+        return None
+    with open(spath) as f:
+        st = json.load(f)
+    if st.get("version") != STATE_VERSION:
+        raise ValueError(f"fwi state in {directory}: unknown version {st.get('version')}")
+    model = torch.from_numpy(np.load(os.path.join(directory, "model.npy")))
+    if list(model.shape) != st["shape"]:
+        raise ValueError(f"fwi state in {directory}: model shape {list(model.shape)} "
+                         f"does not match {st['shape']}")
+    return model, int(st["iterations_done"]), float(st["step"]), list(st["history"])
 
 
 class Fwi:
@@ -149,14 +197,28 @@ class Fwi:
         return g, float(j), illum
 
     def run(self, model0: torch.Tensor, cfg: FwiConfig,
-            callback: Callable[[int, torch.Tensor, dict], None] | None = None):
+            callback: Callable[[int, torch.Tensor, dict], None] | None = None,
+            checkpoint: str | None = None):
         """Returns (model, history); history[i] = dict(misfit, step, trials,
-        accepted, seconds) of iteration i (misfit before the update)."""
+        accepted, seconds) of iteration i (misfit before the update).  With
+        `checkpoint`, resumes from the state saved there (if any) and saves
+        the state after every iteration; `seconds` counts from the start of
+        this call."""
         model = model0.clone().contiguous()
         step = cfg.step
         history = []
+        start = 0
+        if checkpoint is not None:
+            saved = load_state(checkpoint)
+            if saved is not None:
+                m, start, step, history = saved
+                if m.shape != model.shape:
+                    raise ValueError("fwi: the saved model's shape differs from model0's")
+                model = m.to(model0.device, model0.dtype).contiguous()
+                if history and not history[-1]["accepted"]:
+                    return model, history  # the saved run had already stopped
         t0 = time.perf_counter()
-        for it in range(cfg.iterations):
+        for it in range(start, cfg.iterations):
             g, j, illum = self.gradient(model)
             d = precondition(g, illum, cfg.eps)
             model, jn, used, trials, ok = line_search(self.misfit, model, d, j, step,
@@ -166,6 +228,8 @@ class Fwi:
             rec = dict(misfit=j, misfit_after=jn, step=used, trials=trials, accepted=ok,
                        seconds=time.perf_counter() - t0)
             history.append(rec)
+            if checkpoint is not None:
+                save_state(checkpoint, model, it + 1, step, history)
             if callback is not None:
                 callback(it, model, rec)
             if not ok:

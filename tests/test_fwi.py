@@ -53,6 +53,93 @@ def test_precondition_divides_by_stabilised_illumination():
     assert float(d.abs().max()) == 1.0
 
 
+class _Quadratic:
+    """Stand-in for the solver in Fwi.run (CPU): J = 1/2 |m - m*|^2 with a
+    non-uniform illumination, counting gradient evaluations."""
+
+    def __init__(self):
+        g = torch.Generator().manual_seed(5)
+        self.target = 2000.0 + 300.0 * torch.rand(6, 7, generator=g)
+        self.illum = 0.5 + torch.rand(6, 7, generator=g)
+        self.calls = 0
+
+    def misfit(self, m):
+        return 0.5 * float(((m.double() - self.target.double()) ** 2).sum())
+
+    def gradient(self, m):
+        self.calls += 1
+        return (m - self.target), self.misfit(m), self.illum.clone()
+
+
+def _fake_fwi(q):
+    f = object.__new__(fwi.Fwi)  # no solver: Fwi.run calls only these two
+    f.gradient, f.misfit = q.gradient, q.misfit
+    return f
+
+
+def _strip_times(history):
+    return [{k: v for k, v in h.items() if k != "seconds"} for h in history]
+
+
+def test_checkpoint_resume_equals_uninterrupted_run(tmp_path):
+    cfg = fwi.FwiConfig(iterations=6, step=40.0, vmin=1500.0, vmax=3000.0)
+    m0 = torch.full((6, 7), 2100.0)
+    q = _Quadratic()
+    ref, href = _fake_fwi(q).run(m0, cfg)
+    assert q.calls == 6 and href[-1]["misfit_after"] < href[0]["misfit"]
+
+    ck = str(tmp_path / "state")
+    q1 = _Quadratic()
+    m3, h3 = _fake_fwi(q1).run(m0, fwi.FwiConfig(**{**cfg.__dict__, "iterations": 3}),
+                               checkpoint=ck)
+    assert q1.calls == 3 and len(h3) == 3
+    q2 = _Quadratic()
+    m6, h6 = _fake_fwi(q2).run(m0, cfg, checkpoint=ck)
+    assert q2.calls == 3  # the three iterations already done are not repeated
+    assert torch.equal(m6, ref)
+    assert _strip_times(h6) == _strip_times(href)
+    # a finished run resumes to itself without any solver call
+    q3 = _Quadratic()
+    m6b, _ = _fake_fwi(q3).run(m0, cfg, checkpoint=ck)
+    assert q3.calls == 0 and torch.equal(m6b, ref)
+
+
+def test_checkpoint_survives_a_crash_after_saving(tmp_path):
+    cfg = fwi.FwiConfig(iterations=5, step=40.0, vmin=1500.0, vmax=3000.0)
+    m0 = torch.full((6, 7), 2100.0)
+    ref, href = _fake_fwi(_Quadratic()).run(m0, cfg)
+    ck = str(tmp_path / "state")
+
+    def crash(it, model, rec):
+        if it == 2:
+            raise RuntimeError("host died")
+    with pytest.raises(RuntimeError, match="host died"):
+        _fake_fwi(_Quadratic()).run(m0, cfg, callback=crash, checkpoint=ck)
+    model, done, step, hist = fwi.load_state(ck)
+    assert done == 3 and len(hist) == 3
+    m, h = _fake_fwi(_Quadratic()).run(m0, cfg, checkpoint=ck)
+    assert torch.equal(m, ref) and _strip_times(h) == _strip_times(href)
+
+
+def test_load_state_rejects_what_it_cannot_resume(tmp_path):
+    assert fwi.load_state(str(tmp_path / "none")) is None
+    ck = str(tmp_path / "s")
+    fwi.save_state(ck, torch.zeros(2, 3), 1, 10.0, [])
+    model, done, step, hist = fwi.load_state(ck)
+    assert model.shape == (2, 3) and done == 1 and step == 10.0 and hist == []
+    with pytest.raises(ValueError, match="shape"):
+        _fake_fwi(_Quadratic()).run(torch.zeros(6, 7), fwi.FwiConfig(iterations=2),
+                                    checkpoint=ck)
+    import json
+    import os
+    path = os.path.join(ck, "state.json")
+    st = json.load(open(path))
+    st["version"] = 99
+    json.dump(st, open(path, "w"))
+    with pytest.raises(ValueError, match="version"):
+        fwi.load_state(ck)
+
+
 def _small_case():
     from paper_2604_14189_gb300 import sweep
     from scipy.ndimage import gaussian_filter
