@@ -36,6 +36,9 @@ varies between batches.
 from __future__ import annotations
 
 import dataclasses
+import hashlib
+import json
+import os
 import threading
 import time
 
@@ -189,9 +192,43 @@ def _run_threads(queues, worker, codes, errors, device) -> list[int]:
     return [int(c) for c in codes.cpu()]
 
 
+def tune_key(items: list[Item], candidates, mode: int, fused: bool, device_name: str) -> str:
+    """Key of a tuning result: the GPU's name, the mode, the candidates and
+    every problem's sizes (geometry, border, record length, shots,
+    receivers), in order."""
+    sig = [device_name, int(mode), bool(fused), [int(c) for c in candidates]]
+    sig += [[it.problem.physics, it.problem.nz, it.problem.nx, it.problem.pml, it.problem.nt,
+             it.problem.nshot, it.problem.nrec] for it in items]
+    return hashlib.sha256(json.dumps(sig).encode()).hexdigest()[:32]
+
+
+def _read_cache(path: str) -> dict:
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
 def autotune_streams(items: list[Item], candidates=(2, 4, 8, 16),
-                     mode: int = sweep.MODE_GRADIENT, device=None, fused: bool = True):
-    """Times ``run`` for each stream count; returns (best, {count: seconds})."""
+                     mode: int = sweep.MODE_GRADIENT, device=None, fused: bool = True,
+                     cache: str | None = None):
+    """Times ``run`` for each stream count; returns (best, {count: seconds}).
+
+    ``cache`` (default: the ``SWEEP_TUNE_CACHE`` environment variable) names
+    a JSON file of earlier results: a batch of the same problem sizes on the
+    same GPU model with the same candidates takes the stored choice without
+    timing anything, and a new result is added to the file (rewritten under
+    a temporary name and renamed into place)."""
+    cache = cache if cache is not None else os.environ.get("SWEEP_TUNE_CACHE")
+    key = None
+    if cache:
+        dev = torch.device(device or "cuda")
+        key = tune_key(items, candidates, mode, fused, torch.cuda.get_device_name(dev))
+        hit = _read_cache(cache).get(key)
+        if hit is not None:
+            return int(hit["best"]), {int(k): float(v) for k, v in hit["seconds"].items()}
     times = {}
     for n in candidates:
         torch.cuda.synchronize()
@@ -200,4 +237,11 @@ def autotune_streams(items: list[Item], candidates=(2, 4, 8, 16),
         torch.cuda.synchronize()
         times[n] = time.perf_counter() - t0
     best = min(times, key=lambda n: (times[n], n))
+    if key is not None:
+        d = _read_cache(cache)
+        d[key] = {"best": best, "seconds": {str(k): v for k, v in times.items()}}
+        tmp = f"{cache}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(d, f)
+        os.replace(tmp, cache)
     return best, times

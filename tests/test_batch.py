@@ -1,6 +1,7 @@
 """Heterogeneous batches: the LPT schedule (CPU) and batch runs equal to
 one-by-one runs (GPU)."""
 import itertools
+import json
 
 import numpy as np
 import pytest
@@ -49,6 +50,39 @@ def test_cohorts_group_similar_record_lengths():
     assert sorted(i for g in groups for i in g) == list(range(37))
     flat = [int(nts[i]) for g in groups for i in g]
     assert flat == sorted(flat, reverse=True)
+
+
+def test_tune_cache_skips_timing_for_a_known_batch(tmp_path, monkeypatch):
+    """The stream-count autotuner stores its choice per (GPU model, mode,
+    candidates, problem sizes) and takes it from the cache next time without
+    running anything; another batch or GPU model is timed afresh."""
+    from types import SimpleNamespace as NS
+
+    from paper_2604_14189_gb300 import sweep
+    ran = []
+    monkeypatch.setattr(batch, "run", lambda items, mode, n, device, fused: ran.append(n))
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    gpu = ["GB300"]
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: gpu[0])
+    items = [NS(problem=sweep.problem(nz=40 + i, nx=50, pml=10, dx=10.0, dt=1e-3, nt=100,
+                                      nshot=1, nrec=5)) for i in range(3)]
+    path = str(tmp_path / "tune.json")
+    best, times = batch.autotune_streams(items, candidates=(1, 2, 3), cache=path)
+    assert ran == [1, 2, 3] and best in (1, 2, 3) and set(times) == {1, 2, 3}
+    ran.clear()
+    assert batch.autotune_streams(items, candidates=(1, 2, 3), cache=path) == (best, times)
+    assert ran == []  # taken from the cache
+    batch.autotune_streams(items[:2], candidates=(1, 2, 3), cache=path)
+    assert ran == [1, 2, 3]  # other problem sizes
+    ran.clear()
+    gpu[0] = "another GPU"
+    batch.autotune_streams(items, candidates=(1, 2, 3), cache=path)
+    assert ran == [1, 2, 3]
+    ran.clear()
+    monkeypatch.setenv("SWEEP_TUNE_CACHE", path)  # the default cache location
+    batch.autotune_streams(items, candidates=(1, 2, 3))
+    assert ran == []
+    assert len(json.load(open(path))) == 3
 
 
 def test_output_shapes_follow_the_physics():
