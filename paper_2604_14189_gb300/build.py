@@ -2,7 +2,9 @@
 
 Each CUDA translation unit is compiled in parallel to an object file under
 ``_build/`` and the objects are linked into ``paper_2604_14189_gb300/libsweep.so``.
-Rebuilds only when a source or header is newer than the library.
+Rebuilds only when a source or header is newer than the library.  With the
+environment variable SWEEP_NVTX=1 (and a forced rebuild) the host code marks
+each forward and backward phase of a call with an NVTX range.
 """
 from __future__ import annotations
 
@@ -54,6 +56,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     flags = NVCC_FLAGS + list(extra_flags or [])
+    if os.environ.get("SWEEP_NVTX") == "1":  # NVTX ranges around the solver phases
+        flags.append("-DSWEEP_NVTX")
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")

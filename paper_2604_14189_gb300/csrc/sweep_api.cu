@@ -14,7 +14,25 @@
 #include "elastic_internal.cuh"
 #include "tma.cuh"
 
+#ifdef SWEEP_NVTX
+#include <nvtx3/nvToolsExt.h>
+#endif
+
 namespace sweep {
+
+// A named range on the host timeline around the enqueueing of one phase of
+// a call (forward loop, backward loop), for Nsight tools; compiled in only
+// with -DSWEEP_NVTX (build with SWEEP_NVTX=1), otherwise it is empty.
+struct PhaseRange {
+#ifdef SWEEP_NVTX
+  explicit PhaseRange(const char* name) { nvtxRangePushA(name); }
+  ~PhaseRange() { nvtxRangePop(); }
+#else
+  explicit PhaseRange(const char*) {}
+#endif
+  PhaseRange(const PhaseRange&) = delete;
+  PhaseRange& operator=(const PhaseRange&) = delete;
+};
 
 std::atomic<unsigned long long> g_launches{0};
 void note_launches(int k) {
@@ -359,6 +377,7 @@ struct AcFwdLoop {
 int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
                           const float* wavelet, const int32_t* src, const int32_t* rec,
                           float* data, bool save_ring, cudaStream_t st) {
+  PhaseRange r("sweep acoustic forward");
   AcFwdLoop f;
   const int rc = f.init(p, L, ws, wavelet, src, rec, data, save_ring, st);
   if (rc) return rc;
@@ -479,6 +498,7 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
                            const float* wavelet, const int32_t* src, const int32_t* rec,
                            const float* res, float* wgrad, bool imaging, bool illum,
                            cudaStream_t st) {
+  PhaseRange r("sweep acoustic backward");
   AcBwdLoop b;
   const int rc = b.init(p, L, ws, wavelet, src, rec, res, wgrad, imaging, illum, st);
   if (rc) return rc;
@@ -557,6 +577,7 @@ ElStepArgs elastic_step_args(const sweep_problem* p, const Layout& L, void* ws, 
 int elastic_forward_loop(const sweep_problem* p, const Layout& L, void* ws, const float* model,
                          const float* wavelet, const int32_t* src, const int32_t* rec,
                          float* data, bool checkpoints, cudaStream_t st) {
+  PhaseRange r("sweep elastic forward");
   const Geom g = make_geom(p);
   char* state = at<char>(ws, L.fwd_lo);
   const size_t sb = L.fwd_hi - L.fwd_lo;
@@ -581,6 +602,7 @@ int elastic_forward_loop(const sweep_problem* p, const Layout& L, void* ws, cons
 int elastic_reverse_loop(const sweep_problem* p, const Layout& L, void* ws, const float* wavelet,
                          const int32_t* src, const int32_t* rec, const float* res, float* wgrad,
                          bool gradient, cudaStream_t st) {
+  PhaseRange r("sweep elastic reverse");
   const Geom g = make_geom(p);
   char* adj = at<char>(ws, L.el_a);
   const size_t sb = L.fwd_hi - L.fwd_lo;
