@@ -230,6 +230,30 @@ def oracle_sample(w, nshot_max, nt_sample, threads=None):
                                       f"{w['nz']}x{w['nx']} workload ({el:.1f} s)")
 
 
+def oracle_batch_sample(problems, nt_cap):
+    """Time the FP64 oracle gradient of 1/2 |d|^2 on a bounded sample of the
+    heterogeneous batch: the given problems, each with its record cut to
+    nt_cap steps, run one after another on every core (shots in parallel).
+    Returns (padded cell-steps / s in G, seconds, cores, description)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    cells = 0
+    t = time.perf_counter()
+    for w in problems:
+        nt = min(w["nt"], nt_cap)
+        ns, nrec = w["src"].shape[0], w["rec"].shape[1]
+        q = oracle.make_problem(0, w["nz"], w["nx"], w["pml"], w["dx"], w["dt"], nt, ns, nrec,
+                                w["f0"])
+        wav = np.stack([inputs.ricker(w["f0"], w["dt"], nt)] * ns)
+        oracle.acoustic_gradient(q, w["model"], wav, w["src"], w["rec"],
+                                 np.zeros((ns, nrec, nt)))
+        cells += (w["nz"] + 2 * w["pml"]) * (w["nx"] + 2 * w["pml"]) * nt * ns
+    el = time.perf_counter() - t
+    return cells / el / 1e9, el, cores, (f"oracle gradient of the first {len(problems)} "
+                                         f"problems, records cut to {nt_cap} steps ({el:.1f} s)")
+
+
 def run_reference(args, w, rank):
     """Reference arm: the FP64 oracle as it stands, on the host cores."""
     if rank != 0:
@@ -723,7 +747,8 @@ def run_batch(args, local_rank):
     torch.cuda.set_device(dev)
     items = []
     cells = alg = 0
-    for w in inputs.workload_batch():
+    problems = inputs.workload_batch()
+    for w in problems:
         ns, nrec, nt = w["src"].shape[0], w["rec"].shape[1], w["nt"]
         p = sweep.problem(nz=w["nz"], nx=w["nx"], pml=w["pml"], dx=w["dx"], dt=w["dt"], nt=nt,
                           nshot=ns, nrec=nrec, f_ref=w["f0"])
@@ -756,6 +781,10 @@ def run_batch(args, local_rank):
     if any(codes):
         raise RuntimeError(f"batch errors: {sorted(set(codes))}")
     value = cells / sec / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        g, _, cores, sample = oracle_batch_sample(problems[:16], 60)
+        cpu = {"value": g, "unit": "Gpts/s", "cores": cores, "kind": "oracle", "sample": sample}
     out = {
         "metric": "Gpts/s fwd+adj (heterogeneous batch)", "value": value, "unit": "Gpts/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
@@ -770,7 +799,7 @@ def run_batch(args, local_rank):
         "path_roofline": {"achieved": alg / sec / 1e9, "frac": alg / sec / 1e9 / peaks()[0],
                           "note": "algorithmic bytes of every forward and backward step of "
                                   "the 256 problems / pass time"},
-        "cpu_baseline": None,
+        "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 4 * len(items)},
         "gpu_launches": int(launches),
