@@ -100,7 +100,7 @@ typedef struct {
   int32_t nrec;    /* receivers per shot (>= 0)                              */
   float f_ref;     /* CPML alpha reference frequency, Hz (>= 0)              */
   float v_pml;     /* CPML reference velocity, m/s; <= 0: max vp of model    */
-  int32_t flags;   /* SWEEP_F_*                                              */
+  int32_t flags;   /* SWEEP_F_*; any other bit: SWEEP_EINVAL                 */
 } sweep_problem;
 
 /* Bytes of device workspace a call of `mode` needs for `prob` (0 on invalid

@@ -143,6 +143,7 @@ bool valid_problem(const sweep_problem* p) {
   if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return false;
   if (!(p->f_ref >= 0.f) || !std::isfinite(p->f_ref)) return false;
   if (!std::isfinite(p->v_pml)) return false;
+  if (p->flags & ~(SWEEP_F_PADDED_MODEL | SWEEP_F_RESIDUAL_IN)) return false;  // unknown bits
   // keep every index within one shot's field (z * NXp + x, on the padded
   // row pitch) and the count of (tile, shot) units within 32 bits
   const long long NZ = (long long)p->nz + 2LL * p->pml, NX = (long long)p->nx + 2LL * p->pml;

@@ -55,7 +55,9 @@ def test_workspace_size_and_validation():
                 dict(nz=46341, nx=46341, pml=0, nshot=1),
                 # (tile, shot) units beyond 32 bits
                 dict(nz=20000, nx=20000, pml=0, nshot=65535),
-                dict(nshot=65536)):
+                dict(nshot=65536),
+                # a flag bit the library does not define
+                dict(flags=0x4), dict(flags=-1)):
         q = _prob(sweep, **bad)
         assert sweep.lib().sweep_workspace_bytes(ctypes.byref(q), 0) == 0, bad
     assert sweep.lib().sweep_workspace_bytes(ctypes.byref(p), 7) == 0
