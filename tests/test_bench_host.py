@@ -45,7 +45,7 @@ def test_interior_and_shared_k_figures():
     assert bench.alg_bytes_k_once(bench.alg_bytes_bwd(c), c, 20) == 263725520 - 19 * 4 * 373761
 
 
-def test_oracle_batch_sample_counts_padded_cell_steps(monkeypatch):
+def test_oracle_batch_sample_counts_padded_cell_steps():
     """The batch's CPU baseline times the oracle on the given problems with
     their records cut to nt_cap steps and counts padded cell-steps."""
     from paper_2604_14189_gb300 import inputs
@@ -53,11 +53,10 @@ def test_oracle_batch_sample_counts_padded_cell_steps(monkeypatch):
     for w in probs:  # keep it small: 12 x 14 interiors, 3-cell borders
         w.update(nz=12, nx=14, pml=3, model=w["model"][:12, :14],
                  src=w["src"][:1] % [12, 14], rec=w["rec"][:1, :14] % [12, 14])
-    clock = iter([10.0, 12.5])
-    monkeypatch.setattr(bench.time, "perf_counter", lambda: next(clock))
     g, el, cores, sample = bench.oracle_batch_sample(probs, 7)
-    assert el == 2.5 and cores >= 1
-    assert g == pytest.approx(2 * 18 * 20 * 7 * 1 / 2.5 / 1e9)
+    assert el > 0 and cores >= 1
+    # two problems of 18 x 20 padded cells, 7 steps, one shot each
+    assert g == pytest.approx(2 * 18 * 20 * 7 * 1 / el / 1e9)
     assert "first 2 problems" in sample and "7 steps" in sample
 
 
