@@ -66,11 +66,20 @@ double* g_slots_dev[kMaxDevices] = {};
 // Device address of g_dot_slots on the current device (looked up once).
 int slots_address(double** p) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SWEEP_ECUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SWEEP_ECUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return SWEEP_ECUDA;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_slots_dev[dev]) {
     void* addr = nullptr;
-    if (cudaGetSymbolAddress(&addr, g_dot_slots) != cudaSuccess || !addr) return SWEEP_ECUDA;
+    if (cudaGetSymbolAddress(&addr, g_dot_slots) != cudaSuccess || !addr) {
+      // take the failed lookup's error out of the runtime's last-error slot,
+      // so that the next call's launch check does not report it again
+      (void)cudaGetLastError();
+      return SWEEP_ECUDA;
+    }
     g_slots_dev[dev] = static_cast<double*>(addr);
   }
   *p = g_slots_dev[dev];

@@ -165,3 +165,52 @@ def test_forward_batch_matches_individual_runs():
     for it, ref in zip(items, refs):
         scale = float(ref.abs().max())
         assert scale > 0 and float((it.data - ref).abs().max()) <= 1e-5 * scale
+
+
+@pytest.mark.gpu
+def test_batch_cohort_matches_oracle():
+    """One shared-launch cohort of 16 uneven problems (the persistent CTAs
+    split per problem, the CPML blocks laid end to end): 4 of its problems'
+    gradients and misfits against the FP64 oracle (relative L2 <= 1e-3 for
+    the gradient, and the misfit within the bound the seismogram tolerance
+    gives), not only against the library's one-problem calls."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_2604_14189_gb300 import inputs, sweep
+
+    rng = np.random.default_rng(17)
+    items, cases = [], []
+    dev = "cuda"
+    for k in range(16):
+        nz, nx = int(rng.integers(30, 80)), int(rng.integers(30, 110))
+        pml, nt, ns = int(rng.integers(6, 18)), int(rng.integers(120, 260)), int(rng.integers(1, 4))
+        z = np.arange(nz)[:, None]
+        v = np.clip(1800.0 + 900.0 * z / nz + 100.0 * rng.standard_normal((nz, nx)), 1500, 3000)
+        vt = v * (1 + 0.03 * rng.standard_normal(v.shape))
+        src = np.stack([np.full(ns, 2), rng.integers(0, nx, ns)], -1).astype(np.int32)
+        rec = inputs.surface_line(ns, 1, np.arange(0, nx, 3))
+        wav = np.stack([inputs.ricker(12.0, 1e-3, nt)] * ns).astype(np.float32)
+        p = sweep.problem(nz=nz, nx=nx, pml=pml, dx=10.0, dt=1e-3, nt=nt, nshot=ns,
+                          nrec=rec.shape[1], f_ref=12.0)
+        q = oracle.make_problem(0, nz, nx, pml, np.float32(10.0), np.float32(1e-3), nt, ns,
+                                rec.shape[1], np.float32(12.0))
+        v32 = np.float32(v).astype(np.float64)
+        w64 = wav.astype(np.float64)
+        d_obs = oracle.acoustic_forward(q, np.float32(vt).astype(np.float64), w64, src, rec)
+        items.append(batch.Item(p, torch.tensor(v, dtype=torch.float32, device=dev),
+                                torch.tensor(wav, device=dev), torch.tensor(src, device=dev),
+                                torch.tensor(rec, device=dev),
+                                d_obs=torch.tensor(d_obs[:, None], dtype=torch.float32,
+                                                   device=dev)))
+        cases.append((q, v32, w64, src, rec, np.float32(d_obs).astype(np.float64)))
+    assert batch.run(items, streams=1, fused=True) == [0] * 16
+    for k in (0, 5, 10, 15):
+        q, v32, w64, src, rec, d_obs = cases[k]
+        gref, Jref = oracle.acoustic_gradient(q, v32, w64, src, rec, d_obs)
+        d_ref = oracle.acoustic_forward(q, v32, w64, src, rec)
+        nd, nr = np.linalg.norm(d_ref), np.linalg.norm(d_ref - d_obs)
+        g = items[k].grad.double().cpu().numpy()
+        err = np.linalg.norm(g - gref) / np.linalg.norm(gref)
+        assert err <= 1e-3, (k, err)
+        assert abs(float(items[k].misfit) - Jref) <= 1e-4 * nd * nr + 0.5e-8 * nd ** 2, k

@@ -13,6 +13,7 @@ import torch
 
 import oracle
 from paper_2604_14189_gb300 import inputs
+from parity_util import region_errors, worst_trace
 
 pytestmark = pytest.mark.gpu
 
@@ -84,6 +85,7 @@ def test_forward_matches_oracle(sw, shape):
     ref = oracle.acoustic_forward(q, f32(c["v"]), f32(c["w"]), c["src"], c["rec"])
     assert np.abs(ref).max() > 0
     assert rel(d, ref) <= 1e-4, rel(d, ref)
+    assert worst_trace(d, ref) <= 1e-3, worst_trace(d, ref)
 
 
 def test_forward_without_border_and_padded_model(sw):
@@ -132,6 +134,8 @@ def test_gradient_matches_oracle(sw, shape):
     nd, nr = np.linalg.norm(d_ref), np.linalg.norm(d_ref - f32(d_obs))
     assert abs(J.item() - Jref) <= 1e-4 * nd * nr + 0.5e-8 * nd ** 2
     assert rel(g.cpu().numpy(), gref) <= 1e-3, rel(g.cpu().numpy(), gref)
+    errs = region_errors(g.cpu().numpy(), gref, c["src"])
+    assert max(errs.values()) <= 1e-3, errs
 
 
 def test_gradient_residual_mode_and_illumination(sw):

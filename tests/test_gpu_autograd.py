@@ -1,10 +1,12 @@
 """torch.autograd.Function over the C ABI: gradients of arbitrary losses of
-the seismograms with respect to velocity and wavelets, checked by the
-dot-product test, by the direct gradient call and by finite differences."""
+the seismograms with respect to velocity and wavelets, checked against the
+FP64 oracle, by the dot-product test, by the direct gradient call and by
+finite differences along 10 random smooth perturbations."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2604_14189_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -94,3 +96,67 @@ def test_nonquadratic_loss_finite_differences(env):
         fd = (8 * (f[2] - f[1]) - (f[3] - f[0])) / 12
     an = (gw.double() * dw.double()).sum()
     assert abs(fd.item() - an.item()) <= 2e-2 * abs(an.item()), (fd.item(), an.item())
+
+
+def _taper(nz, nx, width=6.0):
+    """1 away from the interior edge, 0 on it: the gradient holds the
+    edge-replicated border fixed, so finite differences must not move it."""
+    tz = np.minimum(np.arange(nz), np.arange(nz)[::-1])
+    tx = np.minimum(np.arange(nx), np.arange(nx)[::-1])
+    return np.clip(np.minimum(tz[:, None], tx[None, :]) / width - 0.5, 0.0, 1.0)
+
+
+def test_autograd_l2_gradient_matches_oracle(env):
+    """loss = 1/2 |d - d_obs|^2 through AcousticModelling, backward(): the
+    velocity gradient against the FP64 oracle's (relative L2 <= 1e-3) and
+    the loss against the oracle's misfit."""
+    sw, ag, p, t, _ = env
+    q = oracle.make_problem(0, p.nz, p.nx, p.pml, np.float32(p.dx), np.float32(p.dt), p.nt,
+                            p.nshot, p.nrec, np.float32(p.f_ref), v_pml=np.float32(p.v_pml))
+    v64 = t["v"].double().cpu().numpy()
+    w64 = t["w"].double().cpu().numpy()
+    src, rec = t["src"].cpu().numpy(), t["rec"].cpu().numpy()
+    # observed data from the oracle (a model 3 % faster), rounded to FP32
+    dob = np.float32(oracle.acoustic_forward(q, np.float32(v64 * 1.03).astype(np.float64),
+                                             w64, src, rec)).astype(np.float64)
+    d_obs = torch.tensor(dob[:, None], dtype=torch.float32, device="cuda")
+    v = t["v"].clone().requires_grad_(True)
+    d = ag.acoustic_modelling(v, t["w"], p, t["src"], t["rec"])
+    loss = 0.5 * ((d - d_obs).double() ** 2).sum()
+    loss.backward()
+    gref, Jref = oracle.acoustic_gradient(q, v64, w64, src, rec, dob)
+    g = v.grad.double().cpu().numpy()
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) <= 1e-3
+    d_ref = oracle.acoustic_forward(q, v64, w64, src, rec)
+    nd, nr = np.linalg.norm(d_ref), np.linalg.norm(d_ref - dob)
+    assert abs(loss.item() - Jref) <= 1e-4 * nd * nr + 0.5e-8 * nd ** 2
+
+
+def test_autograd_l2_finite_differences_ten_perturbations(env):
+    """Central differences of the L2 loss (FP64 sum of FP32 records) along
+    10 seeded smooth perturbations (1 % of v, tapered to zero at the
+    interior edge) against <grad, dv> from backward(): within 1e-2 of the
+    larger of the directional derivative and half the largest of the set
+    (a derivative that nearly cancels carries the central difference's
+    truncation error of the non-quadratic misfit on a small value)."""
+    sw, ag, p, t, d_obs = env
+
+    def loss_of(v):
+        d = ag.acoustic_modelling(v, t["w"], p, t["src"], t["rec"])
+        return 0.5 * ((d - d_obs).double() ** 2).sum()
+
+    v = t["v"].clone().requires_grad_(True)
+    (gv,) = torch.autograd.grad(loss_of(v), v)
+    pert = inputs.smooth_perturbations(p.nz, p.nx, t["v"].cpu().numpy(), 10, seed=14,
+                                       sigma=5.0) * _taper(p.nz, p.nx)
+    pairs = []
+    for k in range(10):
+        dv = torch.tensor(pert[k], dtype=torch.float32, device="cuda")
+        h = 0.5
+        with torch.no_grad():
+            fd = (loss_of(t["v"] + h * dv) - loss_of(t["v"] - h * dv)) / (2 * h)
+        pairs.append((fd.item(), (gv.double() * dv.double()).sum().item()))
+    top = max(abs(an) for _, an in pairs)
+    assert sum(abs(an) >= 0.1 * top for _, an in pairs) >= 5
+    for k, (fd, an) in enumerate(pairs):
+        assert abs(fd - an) <= 1e-2 * max(abs(an), 0.5 * top), (k, fd, an, top)
