@@ -7,7 +7,9 @@ path (``paper_2604_14189_gb300``) never imports it and shares no code with it.
 The numerics live in plain C (``acoustic.c``, ``elastic.c``, ``common.c``),
 compiled here with gcc (no fast-math) into ``liboracle.so`` on first use; this
 module only marshals numpy arrays through ctypes.  What each routine computes,
-and the readings of the paper it follows, are stated in ``oracle.h``.
+and the readings of the paper it follows, are stated in ``oracle.h``.  The
+learned gradient preconditioner's network (U-Net forward, backward, MSE loss,
+Adam) is plain numpy in FP64: ``oracle/unet.py``.
 """
 from __future__ import annotations
 
