@@ -12,11 +12,15 @@ from paper_2604_14189_gb300 import build
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared_functions():
-    txt = open(os.path.join(ROOT, "include", "sweep.h")).read()
+def _declared_functions(header="sweep.h"):
+    txt = open(os.path.join(ROOT, "include", header)).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    names = re.findall(r"\b(sweep_[a-z_]+)\s*\(", txt)
+    names = re.findall(r"\b(sweep_[a-z0-9_]+)\s*\(", txt)
     return sorted(set(names))
+
+
+def _headers():
+    return sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -25,15 +29,56 @@ def lib():
 
 
 def test_every_declared_symbol_is_exported(lib):
-    names = _declared_functions()
-    assert len(names) >= 9
-    for n in names:
-        assert hasattr(lib, n), n
+    assert _headers() == ["sweep.h", "unet.h"]
+    for h in _headers():
+        names = _declared_functions(h)
+        assert len(names) >= 8, h
+        for n in names:
+            assert hasattr(lib, n), (h, n)
 
 
 def test_binding_lists_every_symbol():
-    from paper_2604_14189_gb300 import sweep
-    assert set(sweep.EXPORTS) == set(_declared_functions())
+    from paper_2604_14189_gb300 import sweep, unet
+    assert set(sweep.EXPORTS) == set(_declared_functions("sweep.h"))
+    assert set(unet.EXPORTS) == set(_declared_functions("unet.h"))
+
+
+def test_unet_host_validation():
+    """U-Net entry points: parameter count, workspace sizes and host-side
+    rejection of bad shapes, before any launch."""
+    from paper_2604_14189_gb300 import sweep, unet
+    from oracle import unet as ounet
+    L = sweep.lib()
+    assert L.sweep_unet_param_count() == unet.PARAMS == ounet.param_count()
+    ok = unet.shape(2, 256, 256, 2)
+    inf = unet.workspace_bytes(ok, False)
+    trn = unet.workspace_bytes(ok, True)
+    assert 0 < inf < trn
+    for bad in ((0, 256, 256, 2), (1, 100, 256, 2), (1, 256, 192, 2), (1, 256, 64, 2),
+                (1, 256, 256, 0), (1, 256, 256, 33), (1, 64, 128, 1)):
+        assert unet.workspace_bytes(unet.shape(*bad), True) == 0, bad
+    fake = ctypes.c_void_p(256)
+    assert L.sweep_unet_forward(ctypes.byref(unet.shape(0, 256, 256, 2)), fake, fake, fake,
+                                fake, 1 << 40, None) == sweep.EINVAL
+    assert L.sweep_unet_forward(ctypes.byref(ok), fake, fake, fake, None, 1 << 40,
+                                None) == sweep.EWORKSPACE
+    assert L.sweep_unet_forward(ctypes.byref(ok), fake, fake, fake, fake, inf - 1,
+                                None) == sweep.EWORKSPACE
+    assert L.sweep_unet_gradient(ctypes.byref(ok), fake, fake, None, fake, fake, fake, fake,
+                                 1 << 40, None) == sweep.EINVAL
+    # single-layer kernels: channel counts and tile shapes
+    assert L.sweep_unet_conv3x3(1, 128, 128, 48, 32, fake, fake, None, 1, None, fake, fake,
+                                256, None) == sweep.EINVAL
+    assert L.sweep_unet_conv3x3(1, 128, 128, 32, 512, fake, fake, None, 1, None, fake, fake,
+                                256, None) == sweep.EINVAL
+    assert L.sweep_unet_conv3x3(1, 12, 16, 32, 32, fake, fake, None, 1, None, fake, fake,
+                                256, None) == sweep.EINVAL
+    assert L.sweep_unet_conv3x3(1, 128, 128, 32, 32, fake, fake, None, 2, None, fake, fake,
+                                256, None) == sweep.EINVAL  # mask op without a mask
+    assert L.sweep_unet_wgrad_workspace_bytes(1, 128, 128, 32, 32) > 0
+    assert L.sweep_unet_wgrad_workspace_bytes(1, 128, 100, 32, 32) == 0
+    assert L.sweep_unet_adam(fake, fake, fake, fake, 10, 0, 1e-3, 0.9, 0.999, 1e-8,
+                             None) == sweep.EINVAL
 
 
 def _prob(sweep, **kw):
