@@ -733,6 +733,206 @@ def run_fwi(args, local_rank):
     print(json.dumps(out), flush=True)
 
 
+# -------------------------------------------------------- learned preconditioner
+UNET_LAYERS = [  # (level, cin, cout) of the 17 convolutions, forward order
+    (1, 32, 32), (1, 32, 32), (2, 32, 64), (2, 64, 64), (3, 64, 128), (3, 128, 128),
+    (4, 128, 256), (4, 256, 256), (3, 256, 128), (3, 256, 128), (3, 128, 128),
+    (2, 128, 64), (2, 128, 64), (2, 64, 64), (1, 64, 32), (1, 64, 32), (1, 32, 32)]
+
+
+def unet_conv_flops(B, H, W, training):
+    """FLOPs (2 per multiply-add) of the U-Net's 3 x 3 convolutions: one
+    forward pass, or a training step (forward, data gradients of every layer
+    but the first, weight gradients)."""
+    f = [2.0 * B * (H >> (lv - 1)) * (W >> (lv - 1)) * 9 * ci * co for lv, ci, co in UNET_LAYERS]
+    return sum(f) * 3 - f[0] if training else sum(f)
+
+
+def bf16_peaks():
+    try:
+        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(m["bf16_tflops"]), float(m["bf16_tflops_sustained"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, 1700.0, "fallback"
+
+
+def time_conv(unet, B, H, W, cin, cout, reps=30):
+    """Average device time (ms) of one tensor-core convolution launch on
+    the launching stream (CUDA events), inputs resident."""
+    import ctypes
+
+    import torch
+    x = torch.randn((B, H, W, cin), device="cuda").to(torch.bfloat16)
+    w = (torch.randn((cout, 9, cin), device="cuda") * (2.0 / (9 * cin)) ** 0.5).to(torch.bfloat16)
+    b = torch.zeros(cout, device="cuda")
+    out = torch.empty((B, H, W, cout), dtype=torch.bfloat16, device="cuda")
+    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def call():
+        rc = unet._lib.sweep_unet_conv3x3(B, H, W, cin, cout, ctypes.c_void_p(x.data_ptr()),
+                                          ctypes.c_void_p(w.data_ptr()),
+                                          ctypes.c_void_p(b.data_ptr()), unet.OP_RELU, None,
+                                          ctypes.c_void_p(out.data_ptr()),
+                                          ctypes.c_void_p(ws.data_ptr()), 256,
+                                          ctypes.c_void_p(st.cuda_stream))
+        assert rc == 0
+    for _ in range(3):
+        call()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        call()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def oracle_unet_sample(n=256):
+    """The FP64 oracle's U-Net training step (forward + backward) on one
+    n x n two-channel image: seconds per image on the host cores."""
+    from oracle import unet as U
+    rng = np.random.default_rng(0)
+    theta = U.init_params(0)
+    x = rng.standard_normal((1, n, n, 2))
+    t = rng.standard_normal((1, n, n))
+    t0 = time.perf_counter()
+    U.loss_and_grad(theta, x, t, rounding=True)
+    return time.perf_counter() - t0
+
+
+def run_fwi_learned(args, local_rank):
+    """Learned gradient preconditioner: training pairs from the solver
+    (seeded 256 x 256 layered + anomaly models, 16 shots, nt 1500), U-Net
+    training on the tensor cores, then 20-iteration FWI on held-out seeded
+    models, plain (illumination-preconditioned) against learned (gated by
+    the plain direction and the solver's misfit, plain fallback).  value =
+    median over the held-out models of the learned run's wall seconds to
+    reach the plain run's 20-iteration model error."""
+    import torch
+
+    from paper_2604_14189_gb300 import fwi, precond, sweep, unet
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n, nshot, nt = 256, 16, 1500
+    # 1. pairs
+    pairs = precond.generate_pairs(args.pairs, seed=200000, n=n, nshot=nshot, nt=nt,
+                                   device=dev)
+    # 2. training
+    tr = precond.train(pairs.inputs, pairs.targets, epochs=args.epochs, batch=8, lr=1e-3,
+                       seed=1)
+    step_flops = unet_conv_flops(8, n, n, True)
+    train_tflops = step_flops * tr.steps / tr.seconds / 1e12
+    # 3. the tensor-core convolution in isolation (the largest-N layer at
+    # level 3: 256 -> 128 channels on 64 x 64, batch 8), and a level-1 layer
+    t_dec3a = time_conv(unet, 8, 64, 64, 256, 128)
+    f_dec3a = 2.0 * 8 * 64 * 64 * 9 * 256 * 128
+    t_enc1b = time_conv(unet, 8, 256, 256, 32, 32)
+    f_enc1b = 2.0 * 8 * 256 * 256 * 9 * 32 * 32
+    t_bot = time_conv(unet, 8, 32, 32, 256, 256)
+    f_bot = 2.0 * 8 * 32 * 32 * 9 * 256 * 256
+    # 4. held-out FWI, plain vs learned
+    p, wav, src, rec = precond.solver_setup(n, nshot, nt, dev)
+    cfg = fwi.FwiConfig(iterations=20, step=50.0, vmin=1400.0, vmax=4700.0)
+    pre = precond.Preconditioner(tr.theta, n)
+    rows = []
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    l0 = sweep.kernel_launches()
+    models = list(inputs.precond_heldout(args.heldout + 1, seed=900000, n=n))
+    for k, (vt_np, v0_np) in enumerate(models):
+        vt = torch.tensor(vt_np, dtype=torch.float32, device=dev)
+        v0 = torch.tensor(v0_np, dtype=torch.float32, device=dev)
+        d_obs = sweep.sweep_forward(p, vt, wav, src, rec)
+        inv = fwi.Fwi(p, wav, src, rec, d_obs)
+        if k == 0:  # warm-up run (graphs, lazy loading), not reported
+            precond.run_plain(inv, v0, fwi.FwiConfig(iterations=2, step=50.0, vmin=1400.0,
+                                                     vmax=4700.0), vt)
+            precond.run_learned(inv, pre, v0, fwi.FwiConfig(iterations=2, step=50.0,
+                                                            vmin=1400.0, vmax=4700.0), vt)
+            inv.close()
+            sampler.mark()
+            continue
+        torch.cuda.synchronize()
+        _, hp = precond.run_plain(inv, v0, cfg, vt)
+        target = hp[-1]["model_error"]  # the plain method's 20-iteration error
+        tp = precond.seconds_to(hp, target)
+        _, hl = precond.run_learned(inv, pre, v0, cfg, vt, cos_min=args.cos_min,
+                                    target_error=target)
+        tl = precond.seconds_to(hl, target)
+        inv.close()
+        rows.append(dict(e0=precond.model_error(v0, vt), target=target, plain_s=tp,
+                         learned_s=tl, plain_iters=len(hp), learned_iters=len(hl),
+                         learned_used=sum(h["used"] == "learned" for h in hl),
+                         cos_mean=float(np.mean([h["cosine"] for h in hl]))))
+    torch.cuda.synchronize()
+    sampler.mark()
+    clocks = sampler.stop()
+    launches = sweep.kernel_launches() - l0
+    reached = [r for r in rows if r["learned_s"] is not None]
+    lsec = [r["learned_s"] for r in reached]
+    psec = [r["plain_s"] for r in rows]
+    speed = [r["plain_s"] / r["learned_s"] for r in reached]
+    burst, sustained, psrc = bf16_peaks()
+    ach = f_dec3a / (t_dec3a * 1e-3) / 1e12
+    cpu_s = oracle_unet_sample(n) if not args.no_cpu_baseline else None
+    out = {
+        "metric": "FWI s to target model error (learned vs plain)",
+        "value": statistics.median(lsec) if lsec else None, "unit": "s",
+        "n_gpus": 1, "steps": len(rows), "warmup": 1,
+        "ms_per_step": 1e3 * statistics.median(lsec) if lsec else None,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {
+            "workload": f"learned U-Net gradient preconditioner: {args.pairs} solver-generated "
+                        f"pairs on seeded {n}x{n} layered + anomaly models (16 shots, nt {nt}, "
+                        f"dx 10 m), {args.epochs} epochs, then 20-iteration FWI on "
+                        f"{len(rows)} held-out models, plain vs learned",
+            "target": "each held-out model's plain 20-iteration relative model error "
+                      "(starting model: the true one blurred by a 20-cell Gaussian)",
+            "plain_s_median": statistics.median(psec) if psec else None,
+            "learned_s_median": statistics.median(lsec) if lsec else None,
+            "learned_reached_target": f"{len(reached)}/{len(rows)}",
+            "speedup_median": statistics.median(speed) if speed else None,
+            "learned_steps_used": sum(r["learned_used"] for r in rows),
+            "iterations_total": sum(r["learned_iters"] for r in rows),
+            "cosine_mean": float(np.mean([r["cos_mean"] for r in rows])) if rows else None,
+            "pairs_seconds": pairs.seconds,
+            "pairs_gpts_fwd_adj": pairs.cell_steps / pairs.seconds / 1e9,
+            "train_seconds": tr.seconds, "train_steps": tr.steps,
+            "train_loss_final": tr.epochs[-1]["train_loss"] if tr.epochs else None,
+            "val_loss_first": tr.epochs[0]["val_loss"] if tr.epochs else None,
+            "val_loss_final": tr.epochs[-1]["val_loss"] if tr.epochs else None,
+            "per_model": rows,
+        },
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": burst, "unit": "TFLOP/s",
+                     "frac": ach / burst, "traffic": None, "peak_source": psrc,
+                     "kernel": "conv_kernel (tcgen05 implicit GEMM), 3x3 256->128 channels "
+                               "on 8 x 64 x 64, timed alone (burst peak)",
+                     "avg_launch_ms": t_dec3a},
+        "other_convs": {
+            "3x3 32->32 on 8 x 256 x 256": {"ms": t_enc1b,
+                                            "tflops": f_enc1b / (t_enc1b * 1e-3) / 1e12},
+            "3x3 256->256 on 8 x 32 x 32": {"ms": t_bot,
+                                            "tflops": f_bot / (t_bot * 1e-3) / 1e12}},
+        "training_roofline": {"achieved": train_tflops, "peak": sustained, "unit": "TFLOP/s",
+                              "frac": train_tflops / sustained,
+                              "note": "3x3 convolution FLOPs of a batch-8 training step "
+                                      "(forward, data and weight gradients) x steps / "
+                                      "training wall time (sustained peak)"},
+        "cpu_baseline": None if cpu_s is None else {
+            "value": cpu_s, "unit": "s per 256x256 training sample", "cores": os.cpu_count(),
+            "kind": "oracle", "sample": "FP64 numpy U-Net forward + backward, one image"},
+        "e2e": {"value": statistics.median(lsec) if lsec else None, "unit": "s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+
+
 # ---------------------------------------------------------------------- batch
 def run_batch(args, local_rank):
     """Heterogeneous batch: 256 seeded layered models of uneven size, border,
@@ -820,9 +1020,16 @@ def main():
                     help="time direct sweep_gradient calls instead of a graph replay")
     ap.add_argument("--workload", default="acoustic-gradient",
                     choices=["acoustic-gradient", "elastic-forward", "elastic-gradient", "fwi",
-                             "batch"],
+                             "batch", "fwi-learned"],
                     help="acoustic-gradient is the headline; the elastic workloads are "
                          "measured on request")
+    ap.add_argument("--pairs", type=int, default=2000,
+                    help="fwi-learned: solver-generated training pairs")
+    ap.add_argument("--epochs", type=int, default=20, help="fwi-learned: training epochs")
+    ap.add_argument("--heldout", type=int, default=50, help="fwi-learned: held-out models")
+    ap.add_argument("--cos-min", type=float, default=0.0,
+                    help="fwi-learned: smallest cosine with the plain direction at which the "
+                         "learned direction is tried")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -838,6 +1045,8 @@ def main():
             run_fwi(args, local_rank)
         elif args.workload == "batch":
             run_batch(args, local_rank)
+        elif args.workload == "fwi-learned":
+            run_fwi_learned(args, local_rank)
         else:
             run_elastic(args, rank, 1, local_rank)
         return

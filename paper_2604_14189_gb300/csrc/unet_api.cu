@@ -130,6 +130,14 @@ struct View {
 
 int kchunk(int c) { return c >= 64 ? 64 : 32; }
 
+// Pipeline depth of a convolution: as many stages (2..4) as let two CTAs
+// share an SM, so that one CTA's epilogue overlaps the other's main loop.
+int conv_stages(int cout, int kc) {
+  const int stage = 128 * kc * 2 + cout * kc * 2;
+  const int budget = 112 * 1024 - 1024;  // half an SM's shared memory
+  return std::max(2, std::min(kStages, budget / stage));
+}
+
 bool act_map(CUtensorMap* m, const View& v, int B, int H, int W, int kc, int bw, int bh) {
   const uint64_t dims[4] = {(uint64_t)v.C, (uint64_t)W, (uint64_t)H, (uint64_t)B};
   const uint64_t str[3] = {(uint64_t)v.ps, (uint64_t)W * v.ps, (uint64_t)H * W * v.ps};
@@ -157,7 +165,7 @@ int run_conv(int B, int H, int W, const View& in, const bf16* w, int cin, int co
   a.kc = kchunk(cin);
   a.bw = std::min(W, 128);
   a.bh = 128 / a.bw;
-  a.stages = kStages;
+  a.stages = conv_stages(cout, a.kc);
   a.bias = bias;
   a.op = op;
   a.mask = mask;

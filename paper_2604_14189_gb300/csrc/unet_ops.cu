@@ -259,16 +259,35 @@ __global__ void head_backward_total_kernel(const double* lpart, const float* hpa
   }
 }
 
-// partial[block][co] = sum over the block's pixels of dy[p][co]
-__global__ void bias_grad_kernel(const bf16* __restrict__ dy, int ps, int cout, long long npix,
-                                 float* __restrict__ partial) {
+// partial[block][co] = sum over the block's pixels of dy[p][co]: a thread
+// owns 8 channels (one 16-byte load per pixel) and every (256 / (cout / 8))-th
+// pixel of the block's range; the block then adds its rows in a fixed order.
+__global__ void __launch_bounds__(256) bias_grad_kernel(const bf16* __restrict__ dy, int ps,
+                                                        int cout, long long npix,
+                                                        float* __restrict__ partial) {
+  __shared__ float red[256][9];
+  const int groups = cout / 8;                  // 4 .. 32
+  const int rows = blockDim.x / groups;         // pixels in flight per block
+  const int g = threadIdx.x % groups, r = threadIdx.x / groups;
   const long long per = (npix + gridDim.x - 1) / gridDim.x;
   const long long p0 = blockIdx.x * per;
   const long long p1 = p0 + per < npix ? p0 + per : npix;
-  for (int co = threadIdx.x; co < cout; co += blockDim.x) {
+  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (r < rows)
+    for (long long p = p0 + r; p < p1; p += rows) {
+      float f[8];
+      unpack8(ld8(dy + p * ps + 8 * g), f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] += f[k];
+    }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) red[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < cout) {
+    const int gg = threadIdx.x / 8, k = threadIdx.x % 8;
     float t = 0.f;
-    for (long long p = p0; p < p1; ++p) t += __bfloat162float(dy[p * ps + co]);
-    partial[(long long)blockIdx.x * cout + co] = t;
+    for (int rr = 0; rr < rows; ++rr) t += red[rr * groups + gg][k];
+    partial[(long long)blockIdx.x * cout + threadIdx.x] = t;
   }
 }
 
