@@ -859,14 +859,18 @@ def run_fwi_learned(args, local_rank):
         _, hp = precond.run_plain(inv, v0, cfg, vt)
         target = hp[-1]["model_error"]  # the plain method's 20-iteration error
         tp = precond.seconds_to(hp, target)
-        _, hl = precond.run_learned(inv, pre, v0, cfg, vt, cos_min=args.cos_min,
+        # up to twice the plain run's iterations, to time the learned run to
+        # the target even where it needs more iterations than the plain one
+        cfg_l = fwi.FwiConfig(iterations=2 * cfg.iterations, step=cfg.step, vmin=cfg.vmin,
+                              vmax=cfg.vmax)
+        _, hl = precond.run_learned(inv, pre, v0, cfg_l, vt, cos_min=args.cos_min,
                                     target_error=target)
         tl = precond.seconds_to(hl, target)
         inv.close()
         rows.append(dict(e0=precond.model_error(v0, vt), target=target, plain_s=tp,
                          learned_s=tl, plain_iters=len(hp), learned_iters=len(hl),
                          learned_used=sum(h["used"] == "learned" for h in hl),
-                         cos_mean=float(np.mean([h["cosine"] for h in hl]))))
+                         cos_mean=float(np.nanmean([h["cosine"] for h in hl]))))
     torch.cuda.synchronize()
     sampler.mark()
     clocks = sampler.stop()

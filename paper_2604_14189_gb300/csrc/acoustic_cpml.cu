@@ -117,9 +117,11 @@ __device__ __forceinline__ void fwd_z_chunk(const AcFixArgs& a, size_t so, int x
     zt[q] = ok ? a.zzin[so + o] : 0.f;
     kk[q] = ok ? __ldg(a.K + x + o) : 0.f;
   }
+  float corr[ZCH];
 #pragma unroll
   for (int q = 0; q < ZCH; ++q) {
     const int z = zs + q;
+    corr[q] = 0.f;
     if (!FULL && z >= ze) break;
     const float A = __ldg(a.az + z), B = __ldg(a.bz + z);
     const float* w = wu + q;
@@ -131,7 +133,15 @@ __device__ __forceinline__ void fwd_z_chunk(const AcFixArgs& a, size_t so, int x
     const size_t o = so + z * g.NXp;
     a.pzout[o] = A * p[4] + B * d1u;
     a.zzout[o] = zn;
-    atomicAdd(a.un + o, kk[q] * (dp + zn));
+    corr[q] = kk[q] * (dp + zn);
+  }
+  // the additions land on the stencil kernel's output: wait for it here,
+  // after this thread's loads and arithmetic
+  grid_dep_wait();
+#pragma unroll
+  for (int q = 0; q < ZCH; ++q) {
+    if (!FULL && zs + q >= ze) break;
+    atomicAdd(a.un + so + (zs + q) * g.NXp, corr[q]);
   }
 }
 
@@ -179,6 +189,7 @@ __device__ __forceinline__ void fwd_x_group(const AcFixArgs& a, int s, int z, in
   }
   st4(a.pxout + ro + x, po);
   st4(a.zxout + ro + x, zo);
+  grid_dep_wait();  // the addition lands on the stencil kernel's output
   red4(a.un + ro + x, du);
 }
 
@@ -250,22 +261,29 @@ __global__ void __launch_bounds__(FT, 8)
     ac_fix_fwd_kernel(const __grid_constant__ StepBatch<AcFixArgs, NP> m) {
   int blk, nblk;  // this block's index and the block count of its problem
   const AcFixArgs& a = m.p[step_problem(m, &blk, &nblk)];
-  grid_dep_wait();
   grid_dep_trigger();
-  if (*a.status) return;
   const int bps = a.nbz + a.nbx + a.nbr + a.nbs;
   const int s = blk / bps;
   int b = blk - s * bps;
-  if (b < a.nbz) {
-    fwd_z(a, s, b);
+  // The z and x parts read only the step's inputs (the previous step's
+  // fields, complete before the stencil kernel of this step started) and
+  // write memory variables nothing else touches during the step; they wait
+  // for the stencil kernel only before adding into its output.
+  if (b < a.nbz + a.nbx) {
+    if (!*a.status) {
+      if (b < a.nbz)
+        fwd_z(a, s, b);
+      else
+        fwd_x(a, s, b - a.nbz);
+    }
+    // One thread always waits, so that this kernel never completes before
+    // the stencil kernel does (the next step's kernels rely on that order).
+    if (blockIdx.x == 0 && threadIdx.x == 0) grid_dep_wait();
     return;
   }
-  b -= a.nbz;
-  if (b < a.nbx) {
-    fwd_x(a, s, b);
-    return;
-  }
-  b -= a.nbx;
+  grid_dep_wait();
+  if (*a.status) return;
+  b -= a.nbz + a.nbx;
   if (b < a.nbr) {
     fwd_rec(a, s, b);
     return;
@@ -307,22 +325,29 @@ __device__ __forceinline__ void bwd_z_chunk(const AcFixArgs& a, size_t so, int x
     // m G: zero off the strip rows
     wg[k] = (FULL || (zz >= 0 && zz < g.NZ && z_border(g, zz))) ? wm[k] + wc[k] : 0.f;
   }
+  float corr[ZCH];
 #pragma unroll
   for (int q = 0; q < ZCH; ++q) {
     const int z = zs + q;
+    corr[q] = 0.f;
     if (!FULL && z >= ze) break;
     const size_t o = so + z * g.NXp;
     const float* C = wc + q;
     const float* B = wb + q;
     const float* G = wg + q;
-    const float corr = d2(C[0], C[1], C[2], C[3], C[4], C[5], C[6], C[7], C[8]) -
-                       d1(B[0], B[1], B[2], B[3], B[5], B[6], B[7], B[8]);
-    atomicAdd(a.un + o, kk[q] * corr);  // mu^n
+    corr[q] = kk[q] * (d2(C[0], C[1], C[2], C[3], C[4], C[5], C[6], C[7], C[8]) -
+                       d1(B[0], B[1], B[2], B[3], B[5], B[6], B[7], B[8]));
     if (FULL || z_border(g, z)) {
       const float A = __ldg(a.az + z);
       a.pzout[o] = A * wp[q + 4] - d1(G[0], G[1], G[2], G[3], G[5], G[6], G[7], G[8]);
       a.zzout[o] = A * (wm[q + 4] + wz[q + 4]);
     }
+  }
+  grid_dep_wait();  // mu^n is the stencil kernel's output
+#pragma unroll
+  for (int q = 0; q < ZCH; ++q) {
+    if (!FULL && zs + q >= ze) break;
+    atomicAdd(a.un + so + (zs + q) * g.NXp, corr[q]);
   }
 }
 
@@ -380,9 +405,10 @@ __device__ __forceinline__ void bwd_x_group(const AcFixArgs& a, int s, int z, in
               : 0.f;
     zo[c] = m ? A[c] * (em[c + 4] + ez[c + 4]) : 0.f;
   }
-  red4(a.un + ro + x, du);
   st4(a.pxout + ro + x, po);
   st4(a.zxout + ro + x, zo);
+  grid_dep_wait();  // mu^n is the stencil kernel's output
+  red4(a.un + ro + x, du);
 }
 
 __device__ __forceinline__ void bwd_x(const AcFixArgs& a, int s, int bl) {
@@ -423,22 +449,29 @@ __global__ void __launch_bounds__(FT, 7)
     ac_fix_bwd_kernel(const __grid_constant__ StepBatch<AcFixArgs, NP> m) {
   int blk, nblk;  // this block's index and the block count of its problem
   const AcFixArgs& a = m.p[step_problem(m, &blk, &nblk)];
-  grid_dep_wait();
   grid_dep_trigger();
-  if (*a.status) return;
   const int bps = a.nbz + a.nbx + a.nbr + a.nbs;
   const int s = blk / bps;
   int b = blk - s * bps;
-  if (b < a.nbz) {
-    bwd_z(a, s, b);
+  // The z and x parts read only the step's inputs (the previous step's
+  // fields, complete before the stencil kernel of this step started) and
+  // write memory variables nothing else touches during the step; they wait
+  // for the stencil kernel only before adding into its output.
+  if (b < a.nbz + a.nbx) {
+    if (!*a.status) {
+      if (b < a.nbz)
+        bwd_z(a, s, b);
+      else
+        bwd_x(a, s, b - a.nbz);
+    }
+    // One thread always waits, so that this kernel never completes before
+    // the stencil kernel does (the next step's kernels rely on that order).
+    if (blockIdx.x == 0 && threadIdx.x == 0) grid_dep_wait();
     return;
   }
-  b -= a.nbz;
-  if (b < a.nbx) {
-    bwd_x(a, s, b);
-    return;
-  }
-  b -= a.nbx;
+  grid_dep_wait();
+  if (*a.status) return;
+  b -= a.nbz + a.nbx;
   if (b < a.nbr) {
     bwd_rec(a, s, b);
     return;

@@ -291,33 +291,55 @@ __global__ void __launch_bounds__(256) bias_grad_kernel(const bf16* __restrict__
   }
 }
 
-__global__ void bias_grad_total_kernel(const float* partial, int nb, int cout, float* db) {
-  for (int co = threadIdx.x; co < cout; co += blockDim.x) {
+// db[c] = sum_j partial[j][c]: warp w of the block adds the partials
+// j = w, w + 8, ... for 32 channels (one per lane); the 8 warp sums are then
+// added in a fixed order.
+__global__ void __launch_bounds__(256) bias_grad_total_kernel(const float* partial, int nb,
+                                                              int cout, float* db) {
+  __shared__ float red[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  float t0 = 0.f, t1 = 0.f;
+  int j = w;
+  for (; j + 8 < nb; j += 16) {
+    t0 += partial[(long long)j * cout + c];
+    t1 += partial[(long long)(j + 8) * cout + c];
+  }
+  if (j < nb) t0 += partial[(long long)j * cout + c];
+  red[w][lane] = t0 + t1;
+  __syncthreads();
+  if (w == 0) {
     float t = 0.f;
-    for (int i = 0; i < nb; ++i) t += partial[(long long)i * cout + co];
-    db[co] = t;
+    for (int k = 0; k < 8; ++k) t += red[k][lane];
+    db[c] = t;
   }
 }
 
-// dW[co][row] = sum_s partial[s][row][co], row = tap cin + ci; 32 x 32 tiles
-// through shared memory so that both the reads (along co) and the writes
-// (along row) are contiguous.
-__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int splits, int rows_pad,
-                                    int rows, int cout, float* __restrict__ dW) {
-  __shared__ float tile[32][33];
-  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  for (int i = ty; i < 32; i += 8) {
-    const int r = r0 + i, c = c0 + tx;
-    float t = 0.f;
-    if (r < rows && c < cout)
-      for (int s = 0; s < splits; ++s) t += partial[((long long)s * rows_pad + r) * cout + c];
-    tile[i][tx] = t;
+// dW[co][row] = sum_s partial[s][row][co], row = tap cin + ci.  Block
+// (row, 32 output channels): warp w adds the splits s = w, w + 8, ... with
+// one coalesced 128-byte load per split; the 8 warp sums are added in a
+// fixed order.
+__global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* __restrict__ partial,
+                                                           int splits, int rows_pad, int rows,
+                                                           int cout, float* __restrict__ dW) {
+  __shared__ float red[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = blockIdx.x, c = blockIdx.y * 32 + lane;
+  const float* p = partial + (long long)r * cout + c;
+  const long long stride = (long long)rows_pad * cout;
+  float t0 = 0.f, t1 = 0.f;
+  int s = w;
+  for (; s + 8 < splits; s += 16) {
+    t0 += p[s * stride];
+    t1 += p[(s + 8) * stride];
   }
+  if (s < splits) t0 += p[s * stride];
+  red[w][lane] = t0 + t1;
   __syncthreads();
-  for (int i = ty; i < 32; i += 8) {
-    const int c = c0 + i, r = r0 + tx;
-    if (r < rows && c < cout) dW[(long long)c * rows + r] = tile[tx][i];
+  if (w == 0) {
+    float t = 0.f;
+    for (int k = 0; k < 8; ++k) t += red[k][lane];
+    dW[(long long)c * rows + r] = t;
   }
 }
 
@@ -396,15 +418,15 @@ void launch_head_backward(const bf16* x, const float* theta_head, const float* o
 void launch_bias_grad(const bf16* dy, int dy_ps, int cout, long long npix, float* partial,
                       int nblocks, float* db, cudaStream_t st) {
   bias_grad_kernel<<<nblocks, 256, 0, st>>>(dy, dy_ps, cout, npix, partial);
-  bias_grad_total_kernel<<<1, 256, 0, st>>>(partial, nblocks, cout, db);
+  bias_grad_total_kernel<<<cout / 32, 256, 0, st>>>(partial, nblocks, cout, db);
   note_launches(2);
 }
 
 void launch_wgrad_reduce(const float* partial, int splits, int rows_padded, int cin, int cout,
                          float* dW, cudaStream_t st) {
   const int rows = 9 * cin;
-  dim3 grid((rows + 31) / 32, (cout + 31) / 32);
-  wgrad_reduce_kernel<<<grid, 256, 0, st>>>(partial, splits, rows_padded, rows, cout, dW);
+  wgrad_reduce_kernel<<<dim3(rows, cout / 32), 256, 0, st>>>(partial, splits, rows_padded, rows,
+                                                             cout, dW);
   note_launches(1);
 }
 

@@ -128,7 +128,7 @@ class Fwi:
         self.ws_f = sweep.alloc_workspace(problem, sweep.MODE_FORWARD, dev)
         self.data = torch.empty_like(d_obs)
         self.dd_obs = float(sweep.sweep_dot(d_obs.reshape(-1), d_obs.reshape(-1)))
-        self._gg = self._gf = None
+        self._gg = self._gg0 = self._gf = None
         if graphs:
             self._record(dev)
 
@@ -151,6 +151,10 @@ class Fwi:
                                  grad=self._g, misfit=self._j, illum=self._il, ws=self.ws_g,
                                  stream=side)
         self._gg = c.graph
+        with sweep.capture(side) as c:  # the same gradient without the illumination
+            sweep.sweep_gradient(p, self._mg, self.wavelet, self.src, self.rec, self.d_obs,
+                                 grad=self._g, misfit=self._j, ws=self.ws_g, stream=side)
+        self._gg0 = c.graph
         with sweep.capture(side) as c:
             sweep.sweep_forward(p, self._mt, self.wavelet, self.src, self.rec, data=self.data,
                                 ws=self.ws_f, stream=side)
@@ -161,10 +165,10 @@ class Fwi:
 
     def close(self) -> None:
         """Frees the recorded graphs (none of their replays may be pending)."""
-        for g in (self._gg, self._gf):
+        for g in (self._gg, self._gg0, self._gf):
             if g is not None:
                 g.close()
-        self._gg = self._gf = None
+        self._gg = self._gg0 = self._gf = None
 
     @staticmethod
     def _checked(ws):
@@ -185,15 +189,17 @@ class Fwi:
         do = float(sweep.sweep_dot(d.reshape(-1), self.d_obs.reshape(-1)))
         return 0.5 * (dd - 2.0 * do + self.dd_obs)
 
-    def gradient(self, model: torch.Tensor):
-        """(gradient, misfit, illumination) of `model`; new tensors."""
+    def gradient(self, model: torch.Tensor, want_illum: bool = True):
+        """(gradient, misfit, illumination or None) of `model`; new tensors.
+        Without the illumination the backward pass skips its accumulation."""
         if self._gg is not None:
             self._mg.copy_(model)
-            self._gg.launch()
+            (self._gg if want_illum else self._gg0).launch()
             self._checked(self.ws_g)
-            return self._g.clone(), float(self._j), self._il.clone()
+            return (self._g.clone(), float(self._j),
+                    self._il.clone() if want_illum else None)
         g, j, illum = sweep.sweep_gradient(self.p, model, self.wavelet, self.src, self.rec,
-                                           self.d_obs, want_illum=True, ws=self.ws_g)
+                                           self.d_obs, want_illum=want_illum, ws=self.ws_g)
         return g, float(j), illum
 
     def run(self, model0: torch.Tensor, cfg: FwiConfig,

@@ -15,13 +15,14 @@ the illumination I = sum over shots and steps of u^2.  The pair is
     target = p / max|p|,  p = g / (I + eps max I)  (the plain preconditioned
                                                     gradient)
 
-Use in FWI (``LearnedFwi``).  Each iteration takes g and I from one solver
-call and forms both the plain direction -p / max|p| and the learned one
--net(input) / max|net(input)|.  The learned direction is tried only if its
-cosine with the plain direction is at least ``cos_min`` (the plain
-preconditioned gradient judges its error), and it is kept only if the
-solver's misfit confirms the step in the line search; otherwise the
-iteration takes the plain direction (the fallback).
+Use in FWI (``run_learned``).  The network stands in for the illumination:
+a learned iteration takes the gradient alone from the solver (the backward
+pass then skips the illumination accumulation) and the direction
+-net(input) / max|net(input)|.  The plain preconditioned gradient judges it
+(every few iterations its cosine with the learned direction must be at
+least ``cos_min`` for the network to stay trusted) and is the fallback: a
+learned step that the solver's misfit does not confirm in the line search,
+or an untrusted network, gives the iteration to the plain direction.
 
 Everything that touches a tensor element runs in the library's kernels
 (the solver, the U-Net's tcgen05 convolutions and Adam) or in torch's
@@ -218,26 +219,42 @@ def run_plain(inv: fwi.Fwi, model0, cfg: fwi.FwiConfig, v_true):
 
 
 def run_learned(inv: fwi.Fwi, pre: Preconditioner, model0, cfg: fwi.FwiConfig, v_true,
-                cos_min: float = 0.0, target_error: float | None = None):
-    """FWI with the learned direction where the plain direction and the
-    solver's misfit confirm it (module docstring); stops early once the
-    model error reaches `target_error`."""
+                cos_min: float = 0.0, target_error: float | None = None, judge_every: int = 5):
+    """FWI with the learned direction (module docstring); stops early once
+    the model error reaches `target_error`.
+
+    The network stands in for the illumination, so a learned iteration asks
+    the solver for the gradient alone.  Every `judge_every`-th iteration
+    (and the first) also computes the illumination and the plain direction,
+    whose cosine with the learned one decides whether the learned direction
+    is trusted until the next check (cos >= cos_min).  A learned step the
+    solver's misfit does not confirm, or an untrusted network, falls back to
+    the plain direction (with the illumination computed for it)."""
     model = model0.clone().contiguous()
     step, hist = cfg.step, []
+    trusted, cos = True, float("nan")
     t0 = time.perf_counter()
     for it in range(cfg.iterations):
-        g, j, illum = inv.gradient(model)
-        d_plain = fwi.precondition(g, illum, cfg.eps)
-        d_learn = pre.direction(g, model)
-        cos = float((d_learn * d_plain).sum() / (d_learn.norm() * d_plain.norm() + 1e-30))
-        used, trials = "plain", 0
-        if cos >= cos_min:
+        judge = it % max(judge_every, 1) == 0
+        need_plain = judge or not trusted
+        g, j, illum = inv.gradient(model, want_illum=need_plain)
+        d_plain = fwi.precondition(g, illum, cfg.eps) if need_plain else None
+        if judge or trusted:
+            d_learn = pre.direction(g, model)
+        if judge:
+            cos = float((d_learn * d_plain).sum() / (d_learn.norm() * d_plain.norm() + 1e-30))
+            trusted = cos >= cos_min
+        used, trials, ok = "plain", 0, False
+        if trusted:
             m1, jn, st, k, ok = fwi.line_search(inv.misfit, model, d_learn, j, step,
                                                 cfg.max_halvings, cfg.vmin, cfg.vmax)
             trials += k
             if ok:
                 used = "learned"
         if used == "plain":
+            if d_plain is None:
+                g, j, illum = inv.gradient(model, want_illum=True)
+                d_plain = fwi.precondition(g, illum, cfg.eps)
             m1, jn, st, k, ok = fwi.line_search(inv.misfit, model, d_plain, j, step,
                                                 cfg.max_halvings, cfg.vmin, cfg.vmax)
             trials += k
@@ -245,7 +262,7 @@ def run_learned(inv: fwi.Fwi, pre: Preconditioner, model0, cfg: fwi.FwiConfig, v
         step = st * (cfg.grow if ok and k == 1 else 1.0)
         err = model_error(model, v_true)
         hist.append(dict(misfit=j, misfit_after=jn, step=st, trials=trials, accepted=ok,
-                         used=used, cosine=cos, model_error=err,
+                         used=used, judged=judge, cosine=cos, model_error=err,
                          seconds=time.perf_counter() - t0))
         if not ok or (target_error is not None and err <= target_error):
             break

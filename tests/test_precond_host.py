@@ -17,12 +17,14 @@ class _Quadratic:
         g = torch.Generator().manual_seed(3)
         self.target = 2000.0 + 300.0 * torch.rand(8, 8, generator=g)
         self.illum = 0.5 + torch.rand(8, 8, generator=g)
+        self.calls = []  # want_illum of every gradient request
 
     def misfit(self, m):
         return 0.5 * float(((m.double() - self.target.double()) ** 2).sum())
 
-    def gradient(self, m):
-        return (m - self.target), self.misfit(m), self.illum.clone()
+    def gradient(self, m, want_illum=True):
+        self.calls.append(want_illum)
+        return (m - self.target), self.misfit(m), self.illum.clone() if want_illum else None
 
 
 def _fake_fwi(q):
@@ -132,3 +134,29 @@ def test_init_params_layout(precond):
         assert float(th[k:k + co].abs().max()) == 0.0
         k += co
     assert k + 33 == unet.PARAMS
+
+
+def test_learned_iterations_skip_the_illumination(precond):
+    """A trusted network needs the illumination only on judging iterations
+    (the first and every judge_every-th); an untrusted one gets it with every
+    gradient (the plain fallback), and a learned step the misfit rejects
+    asks for it once more."""
+    q = _Quadratic()
+    m0 = torch.full((8, 8), 2150.0)
+    cfg = fwi.FwiConfig(iterations=7, step=40.0, vmin=1000.0, vmax=4000.0)
+    _, hist = precond.run_learned(_fake_fwi(q), _Pre(lambda g: -g), m0, cfg, q.target,
+                                  judge_every=3)
+    assert q.calls == [True, False, False, True, False, False, True]
+    assert [h["judged"] for h in hist] == q.calls
+    q2 = _Quadratic()
+    _, hist = precond.run_learned(_fake_fwi(q2), _Pre(lambda g: g), m0, cfg, q2.target,
+                                  judge_every=3)
+    # distrusted from the first check on: every gradient comes with it
+    assert q2.calls == [True] * 7
+    assert all(h["used"] == "plain" for h in hist)
+    q3 = _Quadratic()
+    _, hist = precond.run_learned(_fake_fwi(q3), _Pre(lambda g: g), m0, cfg, q3.target,
+                                  judge_every=3, cos_min=-1.0)
+    # trusted but rejected by the misfit: the fallback asks for it again
+    assert q3.calls == [True, False, True, False, True, True, False, True, False, True, True]
+    assert all(h["used"] == "plain" for h in hist)
