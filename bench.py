@@ -12,9 +12,10 @@ time (Gpts/s).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sweep|reference]
 
-Under torchrun (N > 1) every rank runs its own 20-shot batch (weak scaling)
-and the gradients and misfits are summed over ranks with one all-reduce per
-step (the shot sum, the only exchange of the method).
+Under torchrun (N > 1) the survey has 20 N surface shots and every rank
+models its own contiguous block of 20 of them (weak scaling); the gradients
+and misfits are summed over ranks with one all-reduce per step (the shot
+sum, the only exchange of the method), which gives the survey's gradient.
 """
 from __future__ import annotations
 
@@ -481,6 +482,8 @@ def run_sweep(args, w, rank, world, local_rank):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if world == 1 and not args.no_extras:
+        out["extras"] = run_extras(args, local_rank)
     print(json.dumps(out), flush=True)
 
 
@@ -492,7 +495,7 @@ def alg_bytes_elastic_fwd(c):
     return 60 * c["N_pad"] + 32 * (c["N_x"] + c["N_z"])
 
 
-def run_elastic(args, rank, world, local_rank):
+def run_elastic(args, rank, world, local_rank, emit=True):
     """Elastic forward (isotropic velocity-stress, 500 x 1500 + 40, 64 shots,
     nt 4000, 750 receivers) or elastic gradient (same grid, 8 shots,
     nt = --nt or 1000: the checkpointed replay keeps sqrt(nt) forward
@@ -649,12 +652,13 @@ def run_elastic(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    if rank == 0:
+    if emit and rank == 0:
         print(json.dumps(out), flush=True)
+    return out
 
 
 # ------------------------------------------------------------------------ fwi
-def run_fwi(args, local_rank):
+def run_fwi(args, local_rank, emit=True):
     """Plain (illumination-preconditioned) FWI: 20 iterations on the seeded
     256 x 256 layered + anomaly model, 16 shots, nt 1500.  The relative model
     error after 20 plain iterations is the target error of the comparison
@@ -730,7 +734,9 @@ def run_fwi(args, local_rank):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    print(json.dumps(out), flush=True)
+    if emit:
+        print(json.dumps(out), flush=True)
+    return out
 
 
 # -------------------------------------------------------- learned preconditioner
@@ -787,6 +793,79 @@ def time_conv(unet, B, H, W, cin, cout, reps=30):
     e1.record(st)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+def time_train_steps(unet, precond, B, n, steps, warmup):
+    """Average wall time (ms) of one U-Net training step (gradient + Adam),
+    batch B of n x n two-channel images resident on the GPU."""
+    import torch
+    s = unet.shape(B, n, n, 2)
+    th = precond.init_params(0)
+    m, v = torch.zeros_like(th), torch.zeros_like(th)
+    x = torch.randn(B, n, n, 2, device="cuda")
+    t = torch.randn(B, n, n, device="cuda") * 0.1
+    ws = unet.alloc_workspace(s, True)
+    grad = torch.empty_like(th)
+    out = torch.empty((B, n, n), device="cuda")
+    loss = torch.empty((), dtype=torch.float64, device="cuda")
+    k = 0
+    for _ in range(warmup):
+        k += 1
+        unet.gradient(s, th, x, t, grad=grad, out=out, loss=loss, ws=ws, sync=False)
+        unet.adam(th, grad, m, v, k, 1e-4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        k += 1
+        unet.gradient(s, th, x, t, grad=grad, out=out, loss=loss, ws=ws, sync=False)
+        unet.adam(th, grad, m, v, k, 1e-4)
+    e1.record()
+    torch.cuda.synchronize()
+    if sweep_status_of(ws) != 0:
+        raise RuntimeError("unet training step reported an error")
+    return e0.elapsed_time(e1) / steps
+
+
+def sweep_status_of(ws):
+    from paper_2604_14189_gb300 import sweep
+    return sweep.status(ws)
+
+
+def run_unet(args, local_rank):
+    """The U-Net's tensor-core kernels alone: --workload unet-conv times one
+    3 x 3 convolution launch (--conv B,H,W,cin,cout) against the burst BF16
+    peak; --workload unet-train times training steps of batch 8 on 256 x 256
+    images against the sustained peak."""
+    import torch
+
+    from paper_2604_14189_gb300 import precond, sweep, unet
+    torch.cuda.set_device(local_rank)
+    burst, sustained, psrc = bf16_peaks()
+    l0 = sweep.kernel_launches()
+    if args.workload == "unet-conv":
+        B, H, W, ci, co = (int(v) for v in args.conv.split(","))
+        ms = time_conv(unet, B, H, W, ci, co, reps=max(args.steps, 1))
+        flops = 2.0 * B * H * W * 9 * ci * co
+        val = flops / (ms * 1e-3) / 1e12
+        desc = f"3x3 convolution {ci}->{co} channels on {B} x {H} x {W} (BF16, FP32 accumulation)"
+        peak, note = burst, "burst"
+    else:
+        ms = time_train_steps(unet, precond, 8, 256, max(args.steps, 1), max(args.warmup, 1))
+        val = unet_conv_flops(8, 256, 256, True) / (ms * 1e-3) / 1e12
+        desc = "U-Net training step (forward, backward, Adam), batch 8 of 256 x 256 x 2"
+        peak, note = sustained, "sustained"
+    out = {"metric": "TFLOP/s (3x3 convolution FLOPs)", "value": val, "unit": "TFLOP/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+           "data": "synthetic", "config": {"workload": desc},
+           "roofline": {"bound": "tensor", "achieved": val, "peak": peak, "unit": "TFLOP/s",
+                        "frac": val / peak, "traffic": None, "peak_source": f"{psrc} ({note})"},
+           "cpu_baseline": None,
+           "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0},
+           "gpu_launches": int(sweep.kernel_launches() - l0)}
+    print(json.dumps(out), flush=True)
 
 
 def oracle_unet_sample(n=256):
@@ -938,7 +1017,7 @@ def run_fwi_learned(args, local_rank):
 
 
 # ---------------------------------------------------------------------- batch
-def run_batch(args, local_rank):
+def run_batch(args, local_rank, emit=True):
     """Heterogeneous batch: 256 seeded layered models of uneven size, border,
     record length and shot count, forward + adjoint gradient of 1/2 |d|^2
     each, run concurrently (batch.run); value = padded cell-steps of the
@@ -1009,7 +1088,201 @@ def run_batch(args, local_rank):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    print(json.dumps(out), flush=True)
+    if emit:
+        print(json.dumps(out), flush=True)
+    return out
+
+
+# --------------------------------------------------------------------- extras
+def run_forward200(args, local_rank, emit=True):
+    """Single-shot acoustic forward on the 200 x 200 three-layer model (+40
+    CPML, nt 1000, 200 receivers): microseconds per time step, replayed from
+    a recorded graph (one call per run)."""
+    import torch
+
+    from paper_2604_14189_gb300 import sweep
+    w = inputs.workload_layered3()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    nt, nrec = w["nt"], w["rec"].shape[1]
+    p = sweep.problem(nz=w["nz"], nx=w["nx"], pml=w["pml"], dx=w["dx"], dt=w["dt"], nt=nt,
+                      nshot=1, nrec=nrec, f_ref=w["f0"])
+    model = torch.tensor(w["model"], dtype=torch.float32, device=dev)
+    wav_h = inputs.ricker(w["f0"], w["dt"], nt)[None].astype(np.float32)
+    wav = torch.tensor(wav_h, device=dev)
+    src = torch.tensor(w["src"], device=dev)
+    rec = torch.tensor(w["rec"], device=dev)
+    ws = sweep.alloc_workspace(p, sweep.MODE_FORWARD, dev)
+    data = torch.empty((1, 1, nrec, nt), dtype=torch.float32, device=dev)
+    side = torch.cuda.Stream(dev)
+    with sweep.capture(side) as cap:
+        sweep.sweep_forward(p, model, wav, src, rec, data=data, ws=ws, stream=side)
+    torch.cuda.current_stream(dev).wait_stream(side)
+    graph, stream = cap.graph, torch.cuda.current_stream(dev)
+    runs = max(args.steps, 1) * 4
+    for _ in range(max(args.warmup, 1)):
+        graph.launch(stream)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    l0 = sweep.kernel_launches()
+    torch.cuda.synchronize()
+    sampler.mark()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(runs):
+        graph.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark()
+    clocks = sampler.stop()
+    launches = sweep.kernel_launches() - l0
+    if sweep.status(ws) != sweep.OK:
+        raise sweep.SweepError(sweep.status(ws), "forward 200")
+    ms_run = e0.elapsed_time(e1) / runs
+    c = counts(w["nz"], w["nx"], w["pml"])
+    peak, psrc = peaks()
+    # end to end: model and wavelet from pinned host memory, record back
+    mh = torch.tensor(w["model"], dtype=torch.float32).pin_memory()
+    whh = torch.tensor(wav_h).pin_memory()
+    dh = torch.empty((1, 1, nrec, nt), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(runs):
+        model.copy_(mh, non_blocking=True)
+        wav.copy_(whh, non_blocking=True)
+        graph.launch(stream)
+        dh.copy_(data, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / runs
+    graph.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        q = oracle.make_problem(0, w["nz"], w["nx"], w["pml"], w["dx"], w["dt"], 200, 1, nrec,
+                                w["f0"])
+        oracle.set_threads(1)
+        t = time.perf_counter()
+        oracle.acoustic_forward(q, w["model"], wav_h[:, :200].astype(np.float64), w["src"],
+                                w["rec"])
+        el = time.perf_counter() - t
+        cpu = {"value": el / 200 * 1e6, "unit": "us per step", "cores": 1, "kind": "oracle",
+               "sample": f"oracle forward, 200 of the 1000 steps ({el:.2f} s)"}
+    us = ms_run * 1e3 / nt
+    out = {"metric": "us per time step (single-shot forward)", "value": us,
+           "unit": "us/step", "higher_is_better": False, "ms_per_step": ms_run,
+           "config": {"workload": "acoustic forward, 200x200 + 40-cell CPML, nt 1000, 1 shot, "
+                                  "200 receivers, three-layer 1500/2500/3500 m/s",
+                      "launch": "CUDA-graph replay of one recorded sweep_forward call",
+                      "l2": "working set L2-resident (launch-bound size)"},
+           "path_roofline": {"achieved": alg_bytes_fwd(c) / (us * 1e-6) / 1e9,
+                             "frac": alg_bytes_fwd(c) / (us * 1e-6) / 1e9 / peak,
+                             "note": "algorithmic bytes of a forward step / step time (the "
+                                     "data stay in L2, so this can pass the HBM peak)"},
+           "cpu_baseline": cpu,
+           "e2e": {"value": ms_e2e * 1e3 / nt, "unit": "us/step",
+                   "h2d_bytes_per_step": (mh.numel() + whh.numel()) * 4 // nt,
+                   "d2h_bytes_per_step": dh.numel() * 4 // nt},
+           "gpu_launches": int(launches), "clocks": clocks}
+    if emit:
+        print(json.dumps(out), flush=True)
+    return out
+
+
+def run_autograd(args, local_rank, emit=True):
+    """The 301 x 901, 20-shot gradient through the torch.autograd.Function
+    (the differentiable-solver path): loss = 1/2 |d - d_obs|^2 of the
+    modelled data, backward() for dJ/dv; end to end with the model and
+    wavelets from pinned host memory and the gradient copied back."""
+    import torch
+
+    from paper_2604_14189_gb300 import autograd, sweep
+    w = inputs.workload_marmousi(nshot=20, nt=3000)
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    nshot, nt, nrec = 20, 3000, w["rec"].shape[1]
+    p = sweep.problem(nz=w["nz"], nx=w["nx"], pml=w["pml"], dx=w["dx"], dt=w["dt"], nt=nt,
+                      nshot=nshot, nrec=nrec, f_ref=w["f0"])
+    wav_h = torch.tensor(np.stack([inputs.ricker(w["f0"], w["dt"], nt)] * nshot),
+                         dtype=torch.float32).pin_memory()
+    v_h = torch.tensor(w["model"], dtype=torch.float32).pin_memory()
+    src = torch.tensor(w["src"], device=dev)
+    rec = torch.tensor(w["rec"], device=dev)
+    d_obs = sweep.sweep_forward(p, torch.tensor(w["v_true"], dtype=torch.float32, device=dev),
+                                wav_h.to(dev), src, rec)
+    g_h = torch.empty((w["nz"], w["nx"]), dtype=torch.float32).pin_memory()
+
+    def once():
+        v = v_h.to(dev, non_blocking=True).requires_grad_(True)
+        wav = wav_h.to(dev, non_blocking=True)
+        d = autograd.acoustic_modelling(v, wav, p, src, rec)
+        loss = 0.5 * ((d - d_obs).double() ** 2).sum()
+        loss.backward()
+        g_h.copy_(v.grad, non_blocking=True)
+        return loss
+
+    for _ in range(max(args.warmup, 1)):
+        once()
+    torch.cuda.synchronize()
+    l0 = sweep.kernel_launches()
+    t0 = time.perf_counter()
+    runs = max(args.steps, 1)
+    for _ in range(runs):
+        loss = once()
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / runs
+    c = counts(w["nz"], w["nx"], w["pml"])
+    val = c["N_pad"] * nt * nshot / sec / 1e9
+    out = {"metric": "Gpts/s fwd+adj (autograd.Function)", "value": val, "unit": "Gpts/s",
+           "ms_per_step": sec * 1e3, "higher_is_better": True,
+           "config": {"workload": "acoustic gradient 301x901 + 40 CPML, nt 3000, 20 shots, "
+                                  "through AcousticModelling (forward, then backward = "
+                                  "sweep_gradient with the data-space gradient as residual)",
+                      "loss": float(loss)},
+           "e2e": {"value": val, "unit": "Gpts/s",
+                   "h2d_bytes_per_step": (v_h.numel() + wav_h.numel()) * 4,
+                   "d2h_bytes_per_step": g_h.numel() * 4},
+           "gpu_launches": int(sweep.kernel_launches() - l0)}
+    if emit:
+        print(json.dumps(out), flush=True)
+    return out
+
+
+def compact(out):
+    keep = ("metric", "value", "unit", "ms_per_step", "higher_is_better", "roofline",
+            "path_roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks")
+    r = {k: out[k] for k in keep if k in out}
+    r["workload"] = out.get("config", {}).get("workload")
+    return r
+
+
+def run_extras(args, local_rank):
+    """The other configurations of the solver, one short run each, attached
+    to the headline line: the 200 x 200 single-shot forward, the 20-shot
+    gradient through autograd, the 64-shot elastic forward, the 256-model
+    heterogeneous batch and the plain FWI."""
+    base = dict(vars(args))
+    out = {}
+    runs = (
+        ("acoustic_forward_200x200", dict(steps=5, warmup=3),
+         lambda a: run_forward200(a, local_rank, emit=False)),
+        ("acoustic_gradient_autograd_301x901", dict(steps=1, warmup=1),
+         lambda a: run_autograd(a, local_rank, emit=False)),
+        ("elastic_forward_500x1500_64shots", dict(steps=1, warmup=1, nt=3000,
+                                                  workload="elastic-forward"),
+         lambda a: run_elastic(a, 0, 1, local_rank, emit=False)),
+        ("batch_256_models", dict(steps=1, warmup=1),
+         lambda a: run_batch(a, local_rank, emit=False)),
+        ("fwi_plain_256x256", dict(steps=1, warmup=1),
+         lambda a: run_fwi(a, local_rank, emit=False)),
+    )
+    for name, over, fn in runs:
+        a = argparse.Namespace(**dict(base, **over))
+        try:
+            out[name] = compact(fn(a))
+        except Exception as e:  # one failing extra must not hide the headline
+            out[name] = {"error": repr(e)[:400]}
+    return out
 
 
 def main():
@@ -1020,17 +1293,21 @@ def main():
     ap.add_argument("--impl", choices=["sweep", "reference"], default="sweep")
     ap.add_argument("--nt", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline line only, without the other configurations' runs")
     ap.add_argument("--no-graph", action="store_true",
                     help="time direct sweep_gradient calls instead of a graph replay")
     ap.add_argument("--workload", default="acoustic-gradient",
                     choices=["acoustic-gradient", "elastic-forward", "elastic-gradient", "fwi",
-                             "batch", "fwi-learned"],
+                             "batch", "fwi-learned", "unet-conv", "unet-train"],
                     help="acoustic-gradient is the headline; the elastic workloads are "
                          "measured on request")
     ap.add_argument("--pairs", type=int, default=2000,
                     help="fwi-learned: solver-generated training pairs")
     ap.add_argument("--epochs", type=int, default=20, help="fwi-learned: training epochs")
     ap.add_argument("--heldout", type=int, default=50, help="fwi-learned: held-out models")
+    ap.add_argument("--conv", default="8,64,64,256,128",
+                    help="unet-conv: B,H,W,cin,cout of the timed convolution")
     ap.add_argument("--cos-min", type=float, default=0.0,
                     help="fwi-learned: smallest cosine with the plain direction at which the "
                          "learned direction is tried")
@@ -1038,7 +1315,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    w = inputs.workload_marmousi(nshot=20, nt=args.nt)
+    # one survey of 20 shots per GPU; each rank models its own block of it
+    # (weak scaling: 20 shots per GPU whatever the GPU count)
+    from paper_2604_14189_gb300 import shots as _shots
+    w = inputs.workload_marmousi(nt=args.nt, total_shots=20 * world,
+                                 shots=_shots.shard(20 * world, rank, world))
     if args.impl == "reference":
         run_reference(args, w, rank)
         return
@@ -1051,6 +1332,8 @@ def main():
             run_batch(args, local_rank)
         elif args.workload == "fwi-learned":
             run_fwi_learned(args, local_rank)
+        elif args.workload in ("unet-conv", "unet-train"):
+            run_unet(args, local_rank)
         else:
             run_elastic(args, rank, 1, local_rank)
         return

@@ -116,15 +116,27 @@ def workload_layered3():
                 rec=surface_line(1, 2, np.arange(200)))
 
 
-def workload_marmousi(nshot: int = 20, nt: int = 3000, seed: int = 1001):
-    """Acoustic forward + adjoint gradient: 301 x 901, nt = 3000, 20 shots."""
+def surface_survey(nx: int, total_shots: int, rec_step: int = 3, z: int = 2):
+    """A surface acquisition: `total_shots` sources at depth z evenly spaced
+    over the whole width (x = round(linspace(0, nx - 1, total_shots))), and
+    receivers at depth z every `rec_step` cells, the same for every shot."""
+    sx = np.round(np.linspace(0, nx - 1, total_shots)).astype(np.int32)
+    src = np.stack([np.full_like(sx, z), sx], axis=-1).astype(np.int32)
+    return src, surface_line(total_shots, z, np.arange(0, nx, rec_step))
+
+
+def workload_marmousi(nshot: int = 20, nt: int = 3000, seed: int = 1001,
+                      total_shots: int = 20, shots: slice | None = None):
+    """Acoustic forward + adjoint gradient: 301 x 901, nt = 3000.  The survey
+    has `total_shots` surface shots (20: the single-GPU workload); `shots`
+    selects a contiguous block of them (one rank's share), else the first
+    `nshot`."""
     nz, nx = 301, 901
     v_true, v0 = marmousi_like(nz, nx, seed)
-    sx = np.round(np.linspace(0, nx - 1, 20)).astype(np.int32)[:nshot]
-    src = np.stack([np.full_like(sx, 2), sx], axis=-1).astype(np.int32)
-    rec = surface_line(nshot, 2, np.arange(0, nx, 3))
+    src, rec = surface_survey(nx, total_shots)
+    sl = shots if shots is not None else slice(0, nshot)
     return dict(nz=nz, nx=nx, pml=40, dx=10.0, dt=1e-3, nt=nt, f0=10.0,
-                v_true=v_true, model=v0, src=src, rec=rec)
+                v_true=v_true, model=v0, src=src[sl], rec=rec[sl])
 
 
 def workload_elastic(nshot: int = 64, nt: int = 4000, seed: int = 1002,
