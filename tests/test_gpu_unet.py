@@ -51,6 +51,10 @@ CONV_CASES = [  # B, H, W, cin, cout
     (4, 16, 16, 128, 256),
     (1, 32, 32, 256, 128),
     (2, 16, 64, 64, 32),
+    # more tiles than resident CTAs: each persistent CTA takes several tiles
+    # through both tensor-memory accumulators
+    (8, 256, 256, 32, 32),
+    (4, 128, 128, 64, 128),
 ]
 
 
