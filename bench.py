@@ -1045,8 +1045,11 @@ def run_batch(args, local_rank, emit=True):
         cells += batch.cost(p)
         cb = counts(w["nz"], w["nx"], w["pml"])
         alg += (alg_bytes_fwd(cb) + alg_bytes_bwd(cb)) * ns * nt
-    # schedule autotuning on a sample of the batch
+    # schedule and tile-height autotuning on a sample of the batch; the
+    # tile threshold chosen on the sample is applied to every problem
     best, times = batch.autotune_streams(items[:64], candidates=(1, 2, 3, 4, 6))
+    tile_th, tile_times = batch.autotune_tiles(items[:64], streams=best)
+    batch.set_tiles(items, tile_th)
     sampler = ClockSampler(local_rank)
     sampler.start()  # its start-up overlaps the warm-up, not the timed region
     for _ in range(max(args.warmup, 0)):
@@ -1078,6 +1081,7 @@ def run_batch(args, local_rank, emit=True):
                                "20..40-cell CPML, nt 800..3000, 1..8 shots, gradient of "
                                "1/2 |d|^2 each", "padded_cell_steps": cells,
                    "streams": best, "autotune_seconds": times,
+                   "rows16_below_units": tile_th, "tile_autotune_seconds": tile_times,
                    "step": "one pass over the whole batch"},
         "roofline": None,
         "path_roofline": {"achieved": alg / sec / 1e9, "frac": alg / sec / 1e9 / peaks()[0],

@@ -74,6 +74,10 @@ typedef enum {
 /* sweep_gradient: d_obs holds the data residual r itself; the gradient is
  * (dd/dv)^T r and misfit = 1/2 sum r^2 */
 #define SWEEP_F_RESIDUAL_IN 0x2
+/* acoustic: stencil tiles of 16 rows instead of 32 (twice the work units;
+ * faster for small grids that leave SMs idle with 32-row tiles).  A tuning
+ * choice only: the results are identical.  Ignored for elastic physics. */
+#define SWEEP_F_ROWS16 0x4
 
 enum {
   SWEEP_OK = 0,

@@ -30,8 +30,12 @@ small problem's step) is paid once per cohort, not once per problem.
 Cohorts are dealt to the streams by the same LPT rule.
 
 ``autotune_streams`` times the batch (or a sample of it) for a few stream
-counts and returns the fastest: the schedule, not the kernels, is what
-varies between batches.
+counts and returns the fastest.  ``autotune_tiles`` then chooses the
+stencil tile height per problem size: problems with fewer 32-row work
+units than a threshold get 16-row tiles (``SWEEP_F_ROWS16``: twice the
+units, so a small grid spreads over more SMs), and the threshold is timed
+over a few candidates (0 = 32-row tiles everywhere).  Both keep their
+results in the JSON file named by ``SWEEP_TUNE_CACHE``.
 """
 from __future__ import annotations
 
@@ -192,11 +196,14 @@ def _run_threads(queues, worker, codes, errors, device) -> list[int]:
     return [int(c) for c in codes.cpu()]
 
 
-def tune_key(items: list[Item], candidates, mode: int, fused: bool, device_name: str) -> str:
-    """Key of a tuning result: the GPU's name, the mode, the candidates and
-    every problem's sizes (geometry, border, record length, shots,
-    receivers), in order."""
+def tune_key(items: list[Item], candidates, mode: int, fused: bool, device_name: str,
+             kind: str = "streams") -> str:
+    """Key of a tuning result: what is tuned, the GPU's name, the mode, the
+    candidates and every problem's sizes (geometry, border, record length,
+    shots, receivers), in order."""
     sig = [device_name, int(mode), bool(fused), [int(c) for c in candidates]]
+    if kind != "streams":
+        sig.insert(0, kind)
     sig += [[it.problem.physics, it.problem.nz, it.problem.nx, it.problem.pml, it.problem.nt,
              it.problem.nshot, it.problem.nrec] for it in items]
     return hashlib.sha256(json.dumps(sig).encode()).hexdigest()[:32]
@@ -209,6 +216,15 @@ def _read_cache(path: str) -> dict:
         return d if isinstance(d, dict) else {}
     except (OSError, ValueError):
         return {}
+
+
+def _write_cache(path: str, key: str, value: dict) -> None:
+    d = _read_cache(path)
+    d[key] = value
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(d, f)
+    os.replace(tmp, path)
 
 
 def autotune_streams(items: list[Item], candidates=(2, 4, 8, 16),
@@ -238,10 +254,58 @@ def autotune_streams(items: list[Item], candidates=(2, 4, 8, 16),
         times[n] = time.perf_counter() - t0
     best = min(times, key=lambda n: (times[n], n))
     if key is not None:
-        d = _read_cache(cache)
-        d[key] = {"best": best, "seconds": {str(k): v for k, v in times.items()}}
-        tmp = f"{cache}.tmp{os.getpid()}"
-        with open(tmp, "w") as f:
-            json.dump(d, f)
-        os.replace(tmp, cache)
+        _write_cache(cache, key, {"best": best, "seconds": {str(k): v for k, v in times.items()}})
+    return best, times
+
+
+def stencil_units(p: sweep.Problem) -> int:
+    """(tile, shot) work units of a problem's stencil launch in 32-row tiles
+    (128-cell wide tiles over the padded grid)."""
+    nz, nx = p.nz + 2 * p.pml, p.nx + 2 * p.pml
+    return -(-nz // 32) * -(-nx // 128) * p.nshot
+
+
+def set_tiles(items: list[Item], threshold: int) -> None:
+    """16-row stencil tiles for the acoustic problems with fewer than
+    `threshold` 32-row units, 32-row tiles for every other problem."""
+    for it in items:
+        f = it.problem.flags & ~sweep.F_ROWS16
+        if it.problem.physics == sweep.ACOUSTIC and stencil_units(it.problem) < threshold:
+            f |= sweep.F_ROWS16
+        it.problem.flags = f
+
+
+TILE_THRESHOLDS = (0, 152, 608, 2 ** 31 - 1)  # 0: 32 rows everywhere; max: 16 everywhere
+
+
+def autotune_tiles(items: list[Item], thresholds=TILE_THRESHOLDS, streams: int = 2,
+                   mode: int = sweep.MODE_GRADIENT, device=None, fused: bool = True,
+                   cache: str | None = None):
+    """Times ``run`` (at `streams` streams) with each threshold of
+    ``set_tiles``, leaves the fastest set on the items and returns
+    (best threshold, {threshold: seconds}).  Cached like
+    ``autotune_streams``."""
+    cache = cache if cache is not None else os.environ.get("SWEEP_TUNE_CACHE")
+    key = None
+    if cache:
+        dev = torch.device(device or "cuda")
+        key = tune_key(items, list(thresholds) + [streams], mode, fused,
+                       torch.cuda.get_device_name(dev), kind="tiles")
+        hit = _read_cache(cache).get(key)
+        if hit is not None:
+            best = int(hit["best"])
+            set_tiles(items, best)
+            return best, {int(k): float(v) for k, v in hit["seconds"].items()}
+    times = {}
+    for th in thresholds:
+        set_tiles(items, th)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run(items, mode, streams, device, fused)
+        torch.cuda.synchronize()
+        times[int(th)] = time.perf_counter() - t0
+    best = min(times, key=lambda t: (times[t], t))
+    set_tiles(items, best)
+    if key is not None:
+        _write_cache(cache, key, {"best": best, "seconds": {str(k): v for k, v in times.items()}})
     return best, times

@@ -26,37 +26,53 @@ namespace {
 constexpr int FWD_THREADS = 256;
 constexpr int BWD_ROLE_WARPS = 8;  // backward: 8 adjoint + 8 imaging warps
 constexpr int BWD_THREADS = 64 * BWD_ROLE_WARPS;
-constexpr int RPW_F = IN_BZ_F / (FWD_THREADS / 32);  // rows per warp, forward
-constexpr int RPW_B = IN_BZ_B / BWD_ROLE_WARPS;      // rows per warp, backward
-constexpr int HF_F = IN_HW * (IN_BZ_F + 8);          // floats, forward halo tile
-constexpr int CF_F = IN_BX * IN_BZ_F;                // floats, forward centre tile
-constexpr int HF_B = IN_HW * (IN_BZ_B + 8);
-constexpr int CF_B = IN_BX * IN_BZ_B;
-static_assert((HF_F * 4) % 128 == 0 && (CF_F * 4) % 128 == 0, "alignment");
-static_assert((HF_B * 4) % 128 == 0 && (CF_B * 4) % 128 == 0, "alignment");
 
-struct __align__(128) FwdStage {
-  float u[HF_F];   // u^n with halo
-  float up[CF_F];  // u^{n-1}
-  float k[CF_F];   // K
+// Shared-memory stages of a tile height BZ.  Heights and stage counts chosen
+// by sweeps on GB300 (301x901+40, 20 shots): forward 32 rows x 4 stages
+// (16 x 6, 32 x 3, 48 x 2, 64 x 2 no better); backward 32 rows x 2 stages,
+// 230 KB of shared memory with the static tables (16 x 3 was 0.5 % slower
+// over the whole gradient).  The 16-row tiles (forward 7 stages, backward
+// 3) give small grids twice the units.
+template <int BZ>
+struct FwdTile {
+  static constexpr int RPW = BZ / (FWD_THREADS / 32);  // rows per warp
+  static constexpr int HF = IN_HW * (BZ + 8);          // floats, halo tile
+  static constexpr int CF = IN_BX * BZ;                // floats, centre tile
+  static constexpr int STAGES = BZ == IN_BZ ? 4 : 7;
+  static constexpr uint32_t BYTES = (HF + 2 * CF) * 4;
+  struct __align__(128) Stage {
+    float u[HF];   // u^n with halo
+    float up[CF];  // u^{n-1}
+    float k[CF];   // K
+  };
+  static constexpr size_t SMEM = STAGES * sizeof(Stage) + 8 * STAGES;
+  static_assert((HF * 4) % 128 == 0 && (CF * 4) % 128 == 0, "alignment");
+  static_assert(RPW * (FWD_THREADS / 32) == BZ, "rows per warp");
 };
-struct __align__(128) BwdStage {
-  float ua[HF_B];  // u^n with halo
-  float ma[HF_B];  // mu^{n+1} with halo
-  float ub[CF_B];  // u^{n+1}
-  float mb[CF_B];  // mu^{n+2}
-  float k[CF_B];   // K
-  float gr[CF_B];  // imaging accumulator of this shot
+template <int BZ>
+struct BwdTile {
+  static constexpr int RPW = BZ / BWD_ROLE_WARPS;
+  static constexpr int HF = IN_HW * (BZ + 8);
+  static constexpr int CF = IN_BX * BZ;
+  static constexpr int STAGES = BZ == IN_BZ ? 2 : 3;
+  struct __align__(128) Stage {
+    float ua[HF];  // u^n with halo
+    float ma[HF];  // mu^{n+1} with halo
+    float ub[CF];  // u^{n+1}
+    float mb[CF];  // mu^{n+2}
+    float k[CF];   // K
+    float gr[CF];  // imaging accumulator of this shot
+  };
+  static constexpr size_t SMEM = STAGES * sizeof(Stage) + 8 * STAGES;
+  static_assert((HF * 4) % 128 == 0 && (CF * 4) % 128 == 0, "alignment");
+  static_assert(RPW * BWD_ROLE_WARPS == BZ, "rows per warp");
+  static_assert(STAGES >= 2, "the ring prefetch reads a descriptor written two barriers earlier");
 };
-// Tile heights and stages chosen by sweeps on GB300 (301x901+40, 20 shots):
-// forward 32 rows x 4 stages (16 x 6, 32 x 3, 48 x 2, 64 x 2 no better);
-// backward 32 rows x 2 stages, 230 KB of shared memory with the static
-// tables (16 x 3 was 0.5 % slower over the whole gradient).
-constexpr int FWD_STAGES = 4;
-constexpr int BWD_STAGES = 2;
-constexpr uint32_t kFwdBytes = (HF_F + 2 * CF_F) * 4;
-constexpr size_t kFwdSmem = FWD_STAGES * sizeof(FwdStage) + 8 * FWD_STAGES;
-constexpr size_t kBwdSmem = BWD_STAGES * sizeof(BwdStage) + 8 * BWD_STAGES;
+constexpr size_t kFwdSmem = std::max(FwdTile<IN_BZ>::SMEM, FwdTile<IN_BZ_SMALL>::SMEM);
+constexpr size_t kBwdSmem = std::max(BwdTile<IN_BZ>::SMEM, BwdTile<IN_BZ_SMALL>::SMEM);
+constexpr int kMaxStages = 7;
+static_assert(FwdTile<IN_BZ_SMALL>::STAGES <= kMaxStages && BwdTile<IN_BZ_SMALL>::STAGES <= kMaxStages,
+              "descriptor ring");
 
 __device__ __forceinline__ float4 lds4(const float* t, int pitch, int r, int c) {
   return *reinterpret_cast<const float4*>(t + r * pitch + c);
@@ -71,8 +87,8 @@ struct BwdFlags {
   bool imgt, needu1;
 };
 __device__ __forceinline__ BwdFlags bwd_flags(const Geom& g, bool img, bool rec,
-                                              const UnitPos& p) {
-  const int z1 = p.z0 + IN_BZ_B, x1 = p.x0 + IN_BX;
+                                              const UnitPos& p, int bz) {
+  const int z1 = p.z0 + bz, x1 = p.x0 + IN_BX;
   const bool touch_int = z1 > g.P && p.z0 < g.P + g.nz && x1 > g.P && p.x0 < g.P + g.nx;
   BwdFlags f;
   f.imgt = img && touch_int;
@@ -131,7 +147,7 @@ __device__ __forceinline__ UnitDesc make_desc(const Region& R, const Geom& g, co
       in_region(R, si.sz, si.sx))
     f |= U_SRC;
   if (ab) {
-    const BwdFlags b = bwd_flags(g, img, ab->do_rec != 0, p);
+    const BwdFlags b = bwd_flags(g, img, ab->do_rec != 0, p, bz);
     f |= (b.imgt ? U_IMG : 0) | (b.needu1 ? U_U1 : 0);
   }
   d.flags = f;
@@ -139,20 +155,17 @@ __device__ __forceinline__ UnitDesc make_desc(const Region& R, const Geom& g, co
 }
 
 // -------------------------------------------------------------- forward
-template <int NP>
-__global__ void __launch_bounds__(FWD_THREADS, 1)
-    ac_in_fwd_kernel(const __grid_constant__ StepBatch<AcInFwdArgs, NP> m) {
-  int bx, G;  // this CTA's index and the CTA count of its problem
-  const AcInFwdArgs& a = m.p[step_problem(m, &bx, &G)];
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ ShotTable T;
-  __shared__ UnitDesc desc[FWD_STAGES];
-  __shared__ UnitDesc utab[kUnitTable];
-  constexpr int D = FWD_STAGES;
-  FwdStage* stg = reinterpret_cast<FwdStage*>(smem_raw);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(FwdStage));
-  grid_dep_wait();
-  if (*a.status) return;
+// One CTA's units of a forward launch, for tiles of BZ rows.  T, desc and
+// utab are the kernel's static shared tables (one set for both heights).
+template <int BZ>
+__device__ __forceinline__ void fwd_body(const AcInFwdArgs& a, int bx, int G, ShotTable& T,
+                                         UnitDesc* desc, UnitDesc* utab,
+                                         unsigned char* smem_raw) {
+  using C = FwdTile<BZ>;
+  using Stage = typename C::Stage;
+  constexpr int D = C::STAGES;
+  Stage* stg = reinterpret_cast<Stage*>(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(Stage));
   const Geom& g = a.g;
   const Region& R = g.fin;
   const int count = (a.units - bx + G - 1) / G;  // units b, b+G, ...
@@ -160,7 +173,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
   load_shot_table(T, g, a.src, a.wavelet, a.n);
   __syncthreads();  // shot table visible
   for (int i = threadIdx.x; i < count && i < kUnitTable; i += FWD_THREADS)
-    utab[i] = make_desc(R, g, T, &a, nullptr, IN_BZ_F, bx + i * G);
+    utab[i] = make_desc(R, g, T, &a, nullptr, BZ, bx + i * G);
   if (threadIdx.x == 0) {
     for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
     fence_barrier_init();
@@ -173,12 +186,12 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
     if (k < kUnitTable) {
       d = utab[k];
     } else {
-      d = make_desc(R, g, T, &a, nullptr, IN_BZ_F, bx + k * G);
+      d = make_desc(R, g, T, &a, nullptr, BZ, bx + k * G);
       desc[k % D] = d;
     }
-    FwdStage& sg = stg[k % D];
+    Stage& sg = stg[k % D];
     uint64_t* b = &bar[k % D];
-    mbar_arrive_expect_tx(b, kFwdBytes);
+    mbar_arrive_expect_tx(b, C::BYTES);
     tma_load_3d(sg.u, &a.tu, b, d.x0 - 4, d.z0 - 4, d.s);
     tma_load_3d(sg.up, &a.tup, b, d.x0, d.z0, d.s);
     tma_load_2d(sg.k, &a.tK, b, d.x0, d.z0);
@@ -186,21 +199,21 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
   if (threadIdx.x == 0)
     for (int k = 0; k < D && k < count; ++k) issue(k);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int lx = 4 * lane, r0 = warp * RPW_F;
+  const int lx = 4 * lane, r0 = warp * C::RPW;
   int k = 0;
   for (; k < count; ++k) {
     if (k == count - 1) grid_dep_trigger();  // the next kernel may start
     const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
     if (__syncthreads_or(!got)) break;
     const UnitDesc d = k < kUnitTable ? utab[k] : desc[k % D];
-    const FwdStage& sg = stg[k % D];
+    const Stage& sg = stg[k % D];
     const long long so = (long long)d.s * g.fstride;
     const int gx = d.x0 + lx;
     float w[9][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) f4a(lds4(sg.u, IN_HW, r0 + j, lx + 4), w[j]);
 #pragma unroll
-    for (int q = 0; q < RPW_F; ++q) {
+    for (int q = 0; q < C::RPW; ++q) {
       f4a(lds4(sg.u, IN_HW, r0 + q + 8, lx + 4), w[8]);
       const int gz = d.z0 + r0 + q;
       if (gz < R.z1 && gx < R.x1) {
@@ -246,22 +259,34 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
   }
 }
 
-// -------------------------------------------------------------- backward
 template <int NP>
-__global__ void __launch_bounds__(BWD_THREADS, 1)
-    ac_in_bwd_kernel(const __grid_constant__ StepBatch<AcInBwdArgs, NP> m) {
+__global__ void __launch_bounds__(FWD_THREADS, 1)
+    ac_in_fwd_kernel(const __grid_constant__ StepBatch<AcInFwdArgs, NP> m) {
   int bx, G;  // this CTA's index and the CTA count of its problem
-  const AcInBwdArgs& a = m.p[step_problem(m, &bx, &G)];
+  const AcInFwdArgs& a = m.p[step_problem(m, &bx, &G)];
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ ShotTable T;
-  __shared__ UnitDesc desc[BWD_STAGES];
+  __shared__ UnitDesc desc[kMaxStages];
   __shared__ UnitDesc utab[kUnitTable];
-  constexpr int D = BWD_STAGES;
-  static_assert(D >= 2, "the ring prefetch reads a descriptor written two barriers earlier");
-  BwdStage* stg = reinterpret_cast<BwdStage*>(smem_raw);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(BwdStage));
   grid_dep_wait();
   if (*a.status) return;
+  if (a.bz == IN_BZ_SMALL)  // uniform over the CTA: one problem per CTA
+    fwd_body<IN_BZ_SMALL>(a, bx, G, T, desc, utab, smem_raw);
+  else
+    fwd_body<IN_BZ>(a, bx, G, T, desc, utab, smem_raw);
+}
+
+// -------------------------------------------------------------- backward
+template <int BZ>
+__device__ __forceinline__ void bwd_body(const AcInBwdArgs& a, int bx, int G, ShotTable& T,
+                                         UnitDesc* desc, UnitDesc* utab,
+                                         unsigned char* smem_raw) {
+  using C = BwdTile<BZ>;
+  using Stage = typename C::Stage;
+  constexpr int D = C::STAGES;
+  constexpr int HF = C::HF, CF = C::CF, RPW = C::RPW;
+  Stage* stg = reinterpret_cast<Stage*>(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(Stage));
   const Geom& g = a.g;
   const Region& R = g.bin;
   const int count = (a.units - bx + G - 1) / G;
@@ -270,7 +295,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
   load_shot_table(T, g, a.src, img ? a.wavelet : nullptr, a.n);
   __syncthreads();  // shot table visible
   for (int i = threadIdx.x; i < count && i < kUnitTable; i += BWD_THREADS)
-    utab[i] = make_desc(R, g, T, nullptr, &a, IN_BZ_B, bx + i * G);
+    utab[i] = make_desc(R, g, T, nullptr, &a, BZ, bx + i * G);
   if (threadIdx.x == 0) {
     for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
     fence_barrier_init();
@@ -281,14 +306,14 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
     if (k < kUnitTable) {
       d = utab[k];
     } else {
-      d = make_desc(R, g, T, nullptr, &a, IN_BZ_B, bx + k * G);
+      d = make_desc(R, g, T, nullptr, &a, BZ, bx + k * G);
       desc[k % D] = d;
     }
-    BwdStage& sg = stg[k % D];
+    Stage& sg = stg[k % D];
     uint64_t* b = &bar[k % D];
     const bool imgt = d.flags & U_IMG;
-    mbar_arrive_expect_tx(b, (HF_B + CF_B) * 4 + (imgt ? (HF_B + CF_B) * 4 : 0) +
-                                 ((d.flags & U_U1) ? CF_B * 4 : 0) + (adj ? CF_B * 4 : 0));
+    mbar_arrive_expect_tx(b, (HF + CF) * 4 + (imgt ? (HF + CF) * 4 : 0) +
+                                 ((d.flags & U_U1) ? CF * 4 : 0) + (adj ? CF * 4 : 0));
     tma_load_3d(sg.ma, &a.tmA, b, d.x0 - 4, d.z0 - 4, d.s);
     tma_load_2d(sg.k, &a.tK, b, d.x0, d.z0);
     if (imgt) {
@@ -303,9 +328,9 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
   __syncthreads();  // first descriptors visible before the ring prefetch below
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // warps 0..7: adjoint update of mu; warps 8..15: imaging and the
-  // reconstruction of u.  Each owns RPW_B rows of the tile.
+  // reconstruction of u.  Each owns RPW rows of the tile.
   const bool adj_warp = warp < BWD_ROLE_WARPS;
-  const int lx = 4 * lane, r0 = (warp % BWD_ROLE_WARPS) * RPW_B;
+  const int lx = 4 * lane, r0 = (warp % BWD_ROLE_WARPS) * RPW;
   int k = 0;
   for (; k < count; ++k) {
     if (k == count - 1) grid_dep_trigger();  // the next kernel may start
@@ -314,7 +339,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
     const int gx = d.x0 + lx;
     const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
     if (__syncthreads_or(!got)) break;
-    const BwdStage& sg = stg[k % D];
+    const Stage& sg = stg[k % D];
     const long long so = (long long)d.s * g.fstride;
     if (adj_warp) {
       if (adj) {
@@ -323,7 +348,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
 #pragma unroll
         for (int j = 0; j < 8; ++j) f4a(lds4(sg.ma, IN_HW, r0 + j, lx + 4), wm[j]);
 #pragma unroll
-        for (int q = 0; q < RPW_B; ++q) {
+        for (int q = 0; q < RPW; ++q) {
           f4a(lds4(sg.ma, IN_HW, r0 + q + 8, lx + 4), wm[8]);
           const int gz = d.z0 + r0 + q;
           if (gz < R.z1 && gx < R.x1) {
@@ -364,7 +389,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
         for (int j = 0; j < 8; ++j) f4a(lds4(sg.ua, IN_HW, r0 + j, lx + 4), wu[j]);
       }
 #pragma unroll
-      for (int q = 0; q < RPW_B; ++q) {
+      for (int q = 0; q < RPW; ++q) {
         if (imgt) f4a(lds4(sg.ua, IN_HW, r0 + q + 8, lx + 4), wu[8]);
         const int gz = d.z0 + r0 + q;
         if (gz < R.z1 && gx < R.x1) {
@@ -442,6 +467,23 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
   }
 }
 
+template <int NP>
+__global__ void __launch_bounds__(BWD_THREADS, 1)
+    ac_in_bwd_kernel(const __grid_constant__ StepBatch<AcInBwdArgs, NP> m) {
+  int bx, G;  // this CTA's index and the CTA count of its problem
+  const AcInBwdArgs& a = m.p[step_problem(m, &bx, &G)];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ ShotTable T;
+  __shared__ UnitDesc desc[kMaxStages];
+  __shared__ UnitDesc utab[kUnitTable];
+  grid_dep_wait();
+  if (*a.status) return;
+  if (a.bz == IN_BZ_SMALL)  // uniform over the CTA: one problem per CTA
+    bwd_body<IN_BZ_SMALL>(a, bx, G, T, desc, utab, smem_raw);
+  else
+    bwd_body<IN_BZ>(a, bx, G, T, desc, utab, smem_raw);
+}
+
 }  // namespace
 
 int device_sms() {
@@ -500,56 +542,47 @@ void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st) {
 }
 
 // Several problems in one launch: the persistent CTAs (one wave, one per
-// SM) are shared out in proportion to the problems' units, at least one per
+// SM) are shared out in proportion to the problems' cells (units x tile
+// rows: a 16-row unit is half the work of a 32-row one), at least one per
 // problem with work and never more than its units.
-int split_ctas(int units, long long total) {
+int split_ctas(int units, long long cells, long long total) {
   if (units <= 0) return 0;
-  const long long c = (long long)device_sms() * units / total;
+  const long long c = (long long)device_sms() * cells / total;
   return (int)std::max(1LL, std::min<long long>(c, units));
+}
+
+template <typename Args, typename K>
+void launch_in_batch(K kernel, const Args* a, int np, int threads, size_t smem,
+                     cudaStream_t st) {
+  StepBatch<Args, kStepBatch> m;
+  long long total = 0;
+  for (int i = 0; i < np; ++i) total += (long long)std::max(a[i].units, 0) * a[i].bz;
+  if (total <= 0) return;
+  m.start[0] = 0;
+  for (int i = 0; i < kStepBatch; ++i) {
+    int c = 0;
+    if (i < np) {
+      m.p[i] = a[i];
+      c = split_ctas(a[i].units, (long long)std::max(a[i].units, 0) * a[i].bz, total);
+    }
+    m.start[i + 1] = m.start[i] + c;
+  }
+  launch_dependent(kernel, dim3(m.start[kStepBatch]), dim3(threads), smem, st, m);
+  note_launches(1);
 }
 
 void launch_ac_in_fwd_batch(const AcInFwdArgs* a, int np, cudaStream_t st) {
   if (np <= 0) return;
   if (np > kStepBatch) return;  // the caller splits larger groups
   set_fwd_attr<kStepBatch>();
-  StepBatch<AcInFwdArgs, kStepBatch> m;
-  long long total = 0;
-  for (int i = 0; i < np; ++i) total += std::max(a[i].units, 0);
-  if (total <= 0) return;
-  m.start[0] = 0;
-  for (int i = 0; i < kStepBatch; ++i) {
-    int c = 0;
-    if (i < np) {
-      m.p[i] = a[i];
-      c = split_ctas(a[i].units, total);
-    }
-    m.start[i + 1] = m.start[i] + c;
-  }
-  launch_dependent(ac_in_fwd_kernel<kStepBatch>, dim3(m.start[kStepBatch]), dim3(FWD_THREADS),
-                   kFwdSmem, st, m);
-  note_launches(1);
+  launch_in_batch(ac_in_fwd_kernel<kStepBatch>, a, np, FWD_THREADS, kFwdSmem, st);
 }
 
 void launch_ac_in_bwd_batch(const AcInBwdArgs* a, int np, cudaStream_t st) {
   if (np <= 0) return;
   if (np > kStepBatch) return;
   set_bwd_attr<kStepBatch>();
-  StepBatch<AcInBwdArgs, kStepBatch> m;
-  long long total = 0;
-  for (int i = 0; i < np; ++i) total += std::max(a[i].units, 0);
-  if (total <= 0) return;
-  m.start[0] = 0;
-  for (int i = 0; i < kStepBatch; ++i) {
-    int c = 0;
-    if (i < np) {
-      m.p[i] = a[i];
-      c = split_ctas(a[i].units, total);
-    }
-    m.start[i + 1] = m.start[i] + c;
-  }
-  launch_dependent(ac_in_bwd_kernel<kStepBatch>, dim3(m.start[kStepBatch]), dim3(BWD_THREADS),
-                   kBwdSmem, st, m);
-  note_launches(1);
+  launch_in_batch(ac_in_bwd_kernel<kStepBatch>, a, np, BWD_THREADS, kBwdSmem, st);
 }
 
 }  // namespace sweep

@@ -167,7 +167,8 @@ bool valid_problem(const sweep_problem* p) {
   if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return false;
   if (!(p->f_ref >= 0.f) || !std::isfinite(p->f_ref)) return false;
   if (!std::isfinite(p->v_pml)) return false;
-  if (p->flags & ~(SWEEP_F_PADDED_MODEL | SWEEP_F_RESIDUAL_IN)) return false;  // unknown bits
+  if (p->flags & ~(SWEEP_F_PADDED_MODEL | SWEEP_F_RESIDUAL_IN | SWEEP_F_ROWS16))
+    return false;  // unknown bits
   // keep every index within one shot's field (z * NXp + x, on the padded
   // row pitch) and the count of (tile, shot) units within 32 bits
   const long long NZ = (long long)p->nz + 2LL * p->pml, NX = (long long)p->nx + 2LL * p->pml;
@@ -323,6 +324,11 @@ bool map2(CUtensorMap* m, const Geom& g, const float* base, uint32_t bx, uint32_
   return make_tensor_map(m, base, 2, g.NX, g.NZ, 1, g.NXp, (uint64_t)g.fstride, bx, bz, 1);
 }
 
+// Rows of the acoustic stencil tiles of a problem.
+int tile_rows(const sweep_problem* p) {
+  return (p->flags & SWEEP_F_ROWS16) ? IN_BZ_SMALL : IN_BZ;
+}
+
 int region_units(const Region& R, int nshot, int bz, int* ntx) {
   if (R.z1 <= R.z0 || R.x1 <= R.x0) {
     *ntx = 0;
@@ -360,11 +366,12 @@ struct AcFwdLoop {
     if (save) cudaMemsetAsync(save, 0, sizeof(float) * (size_t)g.nshot * g.nring, st);
     int* status = at<int>(ws, L->status);
     in.g = g;
-    in.units = region_units(g.fin, g.nshot, IN_BZ_F, &in.ntx);
+    in.bz = tile_rows(p);
+    in.units = region_units(g.fin, g.nshot, in.bz, &in.ntx);
     for (int b = 0; b < 2; ++b)
-      if (!field_maps(g, at<float>(ws, L->u[b]), &tu_h[b], &tu_c[b], IN_BZ_F))
+      if (!field_maps(g, at<float>(ws, L->u[b]), &tu_h[b], &tu_c[b], in.bz))
         return SWEEP_ECUDA;
-    if (!map2(&in.tK, g, at<float>(ws, L->K), IN_BX, IN_BZ_F)) return SWEEP_ECUDA;
+    if (!map2(&in.tK, g, at<float>(ws, L->K), IN_BX, in.bz)) return SWEEP_ECUDA;
     in.wavelet = wavelet;
     in.src = src;
     in.status = status;
@@ -451,15 +458,16 @@ struct AcBwdLoop {
     int* status = at<int>(ws, L->status);
     save = imaging ? at<float>(ws, L->save) : nullptr;
     in.g = g;
-    in.units = region_units(g.bin, g.nshot, IN_BZ_B, &in.ntx);
+    in.bz = tile_rows(p);
+    in.units = region_units(g.bin, g.nshot, in.bz, &in.ntx);
     for (int b = 0; b < 2; ++b) {
-      if (imaging && !field_maps(g, at<float>(ws, L->u[b]), &tu_h[b], &tu_c[b], IN_BZ_B))
+      if (imaging && !field_maps(g, at<float>(ws, L->u[b]), &tu_h[b], &tu_c[b], in.bz))
         return SWEEP_ECUDA;
-      if (!field_maps(g, at<float>(ws, L->m[b]), &tm_h[b], &tm_c[b], IN_BZ_B))
+      if (!field_maps(g, at<float>(ws, L->m[b]), &tm_h[b], &tm_c[b], in.bz))
         return SWEEP_ECUDA;
     }
-    if (!map2(&in.tK, g, at<float>(ws, L->K), IN_BX, IN_BZ_B)) return SWEEP_ECUDA;
-    if (imaging && !field_maps(g, at<float>(ws, L->graw), nullptr, &in.tG, IN_BZ_B))
+    if (!map2(&in.tK, g, at<float>(ws, L->K), IN_BX, in.bz)) return SWEEP_ECUDA;
+    if (imaging && !field_maps(g, at<float>(ws, L->graw), nullptr, &in.tG, in.bz))
       return SWEEP_ECUDA;
     in.graw = imaging ? at<float>(ws, L->graw) : nullptr;
     in.illum = (imaging && illum) ? at<float>(ws, L->iraw) : nullptr;

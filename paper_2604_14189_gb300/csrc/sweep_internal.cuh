@@ -33,12 +33,13 @@ struct Geom {
 };
 
 // ------------------------------------------------------------------ interior
-// Tiles of IN_BZ_F (forward) or IN_BZ_B (backward) rows x IN_BX cells;
-// each warp owns a band of rows, each lane 4 consecutive
-// cells of a row.  Halo tiles are IN_HW wide and 8 rows taller.
+// Tiles of bz rows x IN_BX cells, bz = IN_BZ (the default) or IN_BZ_SMALL
+// (chosen per problem: more units for small grids, see SWEEP_F_ROWS16);
+// each warp owns a band of rows, each lane 4 consecutive cells of a row.
+// Halo tiles are IN_HW wide and 8 rows taller.
 constexpr int IN_BX = 128;
-constexpr int IN_BZ_F = 32;
-constexpr int IN_BZ_B = 32;
+constexpr int IN_BZ = 32;
+constexpr int IN_BZ_SMALL = 16;
 constexpr int IN_HW = IN_BX + 8;  // halo tile width
 
 struct AcInFwdArgs {
@@ -52,6 +53,7 @@ struct AcInFwdArgs {
   int* status;
   int n;
   int units, ntx;       // (tile, shot) units; tiles along x
+  int bz;               // tile rows: IN_BZ or IN_BZ_SMALL
 };
 
 struct AcInBwdArgs {
@@ -73,6 +75,7 @@ struct AcInBwdArgs {
   int n;
   int do_adj, do_img, do_rec;
   int units, ntx;
+  int bz;            // tile rows: IN_BZ or IN_BZ_SMALL
 };
 
 // Second kernel of an acoustic time step (acoustic_cpml.cu): the CPML terms

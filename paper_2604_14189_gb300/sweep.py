@@ -23,6 +23,7 @@ MODE_ADJOINT = 1
 MODE_GRADIENT = 2
 F_PADDED_MODEL = 0x1
 F_RESIDUAL_IN = 0x2
+F_ROWS16 = 0x4
 
 OK = 0
 EINVAL, ECFL, EBOUNDS, EWORKSPACE, ECUDA, ETIMEOUT, ENONFINITE, EMODEL, EUNSUPPORTED = (

@@ -102,10 +102,13 @@ def test_workspace_size_and_validation():
                 dict(nz=20000, nx=20000, pml=0, nshot=65535),
                 dict(nshot=65536),
                 # a flag bit the library does not define
-                dict(flags=0x4), dict(flags=-1)):
+                dict(flags=0x8), dict(flags=-1)):
         q = _prob(sweep, **bad)
         assert sweep.lib().sweep_workspace_bytes(ctypes.byref(q), 0) == 0, bad
     assert sweep.lib().sweep_workspace_bytes(ctypes.byref(p), 7) == 0
+    # the tuning flag changes neither validity nor the workspace
+    q = _prob(sweep, flags=sweep.F_ROWS16)
+    assert sweep.lib().sweep_workspace_bytes(ctypes.byref(q), 2) == grd
     # the largest sizes still accepted
     big = _prob(sweep, nz=46000, nx=46000, pml=0, nshot=1)
     assert sweep.lib().sweep_workspace_bytes(ctypes.byref(big), 0) > 0

@@ -85,6 +85,48 @@ def test_tune_cache_skips_timing_for_a_known_batch(tmp_path, monkeypatch):
     assert len(json.load(open(path))) == 3
 
 
+def test_tile_tuner_sets_flags_by_size_and_caches(tmp_path, monkeypatch):
+    """The tile-height tuner times each threshold with the items' flags set
+    by it (16-row tiles below the threshold only, acoustic only, other flag
+    bits kept), leaves the fastest setting on the items and takes it from
+    the cache next time without running anything."""
+    from types import SimpleNamespace as NS
+
+    from paper_2604_14189_gb300 import sweep
+    seen = []
+
+    def fake_run(items, mode, n, device, fused):
+        seen.append([bool(it.problem.flags & sweep.F_ROWS16) for it in items])
+    monkeypatch.setattr(batch, "run", fake_run)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "GB300")
+    clock = iter(range(1000))
+    monkeypatch.setattr(batch.time, "perf_counter", lambda: float(next(clock)) ** 2)
+    kw = dict(dx=10.0, dt=1e-3, nt=100, nrec=5)
+    # 32-row units: 1 x 1 x 1 = 1, 4 x 2 x 2 = 16, 10 x 3 x 4 = 120; elastic 1
+    items = [NS(problem=sweep.problem(nz=20, nx=20, pml=4, nshot=1, **kw)),
+             NS(problem=sweep.problem(nz=100, nx=200, pml=10, nshot=2,
+                                      flags=sweep.F_PADDED_MODEL, **kw)),
+             NS(problem=sweep.problem(nz=300, nx=300, pml=10, nshot=4, **kw)),
+             NS(problem=sweep.problem(sweep.ELASTIC, nz=20, nx=20, pml=4, nshot=1, **kw))]
+    assert [batch.stencil_units(it.problem) for it in items] == [1, 16, 120, 1]
+    path = str(tmp_path / "tune.json")
+    best, times = batch.autotune_tiles(items, thresholds=(0, 2, 100, 1000), cache=path)
+    assert seen == [[False, False, False, False], [True, False, False, False],
+                    [True, True, False, False], [True, True, True, False]]
+    # the fake clock makes later candidates slower: threshold 0 wins
+    assert best == 0 and sorted(times) == [0, 2, 100, 1000]
+    assert not any(it.problem.flags & sweep.F_ROWS16 for it in items)
+    assert items[1].problem.flags == sweep.F_PADDED_MODEL  # other bits kept
+    seen.clear()
+    batch.set_tiles(items, 1000)
+    assert batch.autotune_tiles(items, thresholds=(0, 2, 100, 1000), cache=path) == (best, times)
+    assert seen == []  # taken from the cache, and applied
+    assert not any(it.problem.flags & sweep.F_ROWS16 for it in items)
+    batch.autotune_tiles(items, thresholds=(0, 2, 100, 1000), streams=3, cache=path)
+    assert len(seen) == 4  # another stream count is another key
+
+
 def test_output_shapes_follow_the_physics():
     """Outputs allocated by run() have the sizes the C ABI writes: an
     elastic problem has three gradients and two data components."""

@@ -138,6 +138,43 @@ def test_gradient_matches_oracle(sw, shape):
     assert max(errs.values()) <= 1e-3, errs
 
 
+@pytest.mark.parametrize("shape", SHAPES[:3])
+def test_16_row_tiles_match_oracle(sw, shape):
+    """SWEEP_F_ROWS16 (stencil tiles of 16 rows) changes the work split only:
+    forward, adjoint and gradient meet the oracle at the same tolerances and
+    agree with the 32-row path to FP32 rounding (the CPML corner cells take
+    two atomic additions in either order)."""
+    c = case(*shape, seed=31 + sum(shape))
+    p, q = probs(sw, c)
+    p16, _ = probs(sw, dict(c, flags=sw.F_ROWS16))
+    v, w = cuda(c["v"]), cuda(c["w"])
+    src, rec = cuda(c["src"], torch.int32), cuda(c["rec"], torch.int32)
+    d16 = sw.sweep_forward(p16, v, w, src, rec).cpu().numpy()[:, 0]
+    d32 = sw.sweep_forward(p, v, w, src, rec).cpu().numpy()[:, 0]
+    ref = oracle.acoustic_forward(q, f32(c["v"]), f32(c["w"]), c["src"], c["rec"])
+    assert rel(d16, ref) <= 1e-4 and worst_trace(d16, ref) <= 1e-3
+    assert rel(d16, d32) <= 1e-6, rel(d16, d32)
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal((c["nshot"], c["nrec"], c["nt"]))
+    wg = sw.sweep_adjoint(p16, v, cuda(r), src, rec).cpu().numpy()
+    wref = oracle.acoustic_adjoint(q, f32(c["v"]), f32(r), c["src"], c["rec"])
+    assert rel(wg, wref) <= 1e-4, rel(wg, wref)
+    v_true = c["v"] * (1 + 0.03 * rng.standard_normal(c["v"].shape))
+    d_obs = oracle.acoustic_forward(q, f32(v_true), f32(c["w"]), c["src"], c["rec"])
+    g16, J16, _ = sw.sweep_gradient(p16, v, w, src, rec, cuda(d_obs))
+    g32, J32, _ = sw.sweep_gradient(p, v, w, src, rec, cuda(d_obs))
+    gref, Jref = oracle.acoustic_gradient(q, f32(c["v"]), f32(c["w"]), c["src"], c["rec"],
+                                          f32(d_obs))
+    g16 = g16.cpu().numpy()
+    assert rel(g16, gref) <= 1e-3, rel(g16, gref)
+    assert max(region_errors(g16, gref, c["src"]).values()) <= 1e-3
+    assert rel(g16, g32.cpu().numpy()) <= 1e-5
+    # the misfit bound of test_gradient_matches_oracle (J is a difference of
+    # nearly equal data, so its relative rounding is |d| / |r| times larger)
+    nd, nr = np.linalg.norm(ref), np.linalg.norm(ref - f32(d_obs))
+    assert abs(J16.item() - Jref) <= 1e-4 * nd * nr + 0.5e-8 * nd ** 2
+
+
 def test_gradient_residual_mode_and_illumination(sw):
     c = case(45, 60, 8, 260, 2, 5, seed=21, flags=0)
     p, q = probs(sw, c)

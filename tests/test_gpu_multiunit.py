@@ -1,7 +1,8 @@
 """Oracle parity of the acoustic kernels on their multi-unit paths.
 
 The stencil kernels are persistent: one CTA per SM takes (tile, shot) units
-round-robin through a 4-stage (forward) or 2-stage (backward) TMA pipeline.
+round-robin through a 4-stage (forward) or 2-stage (backward) TMA pipeline
+(32-row tiles; 7 and 3 stages with the 16-row tiles of SWEEP_F_ROWS16).
 Small parity cases give every CTA at most one unit, so the stage reuse, the
 mbarrier phase flips and the descriptor tables only run when there are many
 more units than SMs.  These cases compare the CUDA path with the FP64 oracle
@@ -18,7 +19,9 @@ exactly there:
 * 150 shots, more than the shared-memory shot table holds (128): the
   kernels read the source cell and wavelet sample from global memory;
 * 48 000 one-tile shots: > 256 units per CTA, beyond the per-CTA table of
-  unit descriptors, so later units are described into the stage ring.
+  unit descriptors, so later units are described into the stage ring;
+* the 5-shot full-size gradient, the 64-shot and the 48 000-shot cases again
+  in 16-row tiles.
 
 Beside the global relative L2 (<= 1e-4 seismograms, <= 1e-3 gradients) each
 case checks every trace on its own (<= 1e-3), and the gradient in the 4-cell
@@ -70,23 +73,28 @@ def full(sw):
     oracle.set_threads(len(PICK5))
     d_obs5 = oracle.acoustic_forward(q5, f32(w["v_true"]), wav[PICK5].astype(np.float64),
                                      w["src"][PICK5], w["rec"][PICK5])
-    return w, wav, d_obs5
+    return w, wav, d_obs5, {}
 
 
-def test_fullsize_five_shot_gradient_matches_oracle(sw, full):
-    w, wav, d_obs5 = full
+@pytest.mark.parametrize("rows16", [False, True])
+def test_fullsize_five_shot_gradient_matches_oracle(sw, full, rows16):
+    """Both stencil tile heights: 32 rows (12 x 8 = 96 units per shot) and
+    16 rows (24 x 8 = 192 units per shot, 7 forward and 3 backward stages)."""
+    w, wav, d_obs5, memo = full
     nz, nx, nrec = w["nz"], w["nx"], w["rec"].shape[1]
     assert list(w["src"][[PICK5[0], PICK5[-1]], 1]) == [0, 900]
     p = sw.problem(nz=nz, nx=nx, pml=w["pml"], dx=w["dx"], dt=w["dt"], nt=NT_FULL, nshot=5,
-                   nrec=nrec, f_ref=w["f0"])
+                   nrec=nrec, f_ref=w["f0"], flags=sw.F_ROWS16 if rows16 else 0)
     q = oracle.make_problem(0, nz, nx, w["pml"], np.float32(w["dx"]), np.float32(w["dt"]),
                             NT_FULL, 5, nrec, np.float32(w["f0"]))
     src, rec = w["src"][PICK5], w["rec"][PICK5]
     g, J, _ = sw.sweep_gradient(p, cuda(w["model"]), cuda(wav[PICK5]), cuda(src, torch.int32),
                                 cuda(rec, torch.int32), cuda(d_obs5[:, None]))
-    oracle.set_threads(5)
-    gref, Jref = oracle.acoustic_gradient(q, f32(w["model"]), f32(wav[PICK5]), src, rec,
-                                          f32(d_obs5))
+    if "g5" not in memo:  # the oracle's gradient serves both tile heights
+        oracle.set_threads(5)
+        memo["g5"] = oracle.acoustic_gradient(q, f32(w["model"]), f32(wav[PICK5]), src, rec,
+                                              f32(d_obs5))
+    gref, Jref = memo["g5"]
     assert abs(J.item() - Jref) <= 1e-4 * Jref, (J.item(), Jref)
     assert_gradient(g.cpu().numpy(), gref, src)
 
@@ -94,7 +102,7 @@ def test_fullsize_five_shot_gradient_matches_oracle(sw, full):
 def test_fullsize_twenty_shot_launch_matches_oracle(sw, full):
     """The benchmark's 20-shot launch (1920 units per stencil launch),
     residual mode: shots 0, 10, 19 carry a residual, the others none."""
-    w, wav, d_obs5 = full
+    w, wav, d_obs5, _ = full
     nz, nx, nrec = w["nz"], w["nx"], w["rec"].shape[1]
     carry = [0, 10, 19]
     r = np.zeros((20, 1, nrec, NT_FULL), dtype=np.float32)
@@ -124,14 +132,14 @@ def layered_case(nz, nx, nshot, nrec, seed):
     return v, src.astype(np.int32), rec.astype(np.int32)
 
 
-def run_case(sw, nz, nx, pml, nt, nshot, nrec, seed, f0=15.0, threads=None):
+def run_case(sw, nz, nx, pml, nt, nshot, nrec, seed, f0=15.0, threads=None, flags=0):
     v, src, rec = layered_case(nz, nx, nshot, nrec, seed)
     rng = np.random.default_rng(seed + 1)
     wav = np.stack([inputs.ricker(f0 * (1 + 0.2 * rng.random()), 1e-3, nt)
                     for _ in range(nshot)]).astype(np.float32)
     v_true = v * (1 + 0.03 * rng.standard_normal(v.shape))
     p = sw.problem(nz=nz, nx=nx, pml=pml, dx=10.0, dt=1e-3, nt=nt, nshot=nshot, nrec=nrec,
-                   f_ref=f0)
+                   f_ref=f0, flags=flags)
     q = oracle.make_problem(0, nz, nx, pml, np.float32(10.0), np.float32(1e-3), nt, nshot, nrec,
                             np.float32(f0))
     oracle.set_threads(threads)
@@ -155,6 +163,12 @@ def test_stage_reuse_64_shots(sw):
     run_case(sw, 129, 133, 11, 220, 64, 9, seed=101)
 
 
+def test_stage_reuse_64_shots_16_row_tiles(sw):
+    """The same grid in 16-row tiles: 10 x 2 tiles per shot, 1280 units,
+    ~8.4 per CTA through 7 forward and 3 backward stages."""
+    run_case(sw, 129, 133, 11, 220, 64, 9, seed=104, flags=sw.F_ROWS16)
+
+
 def test_more_shots_than_the_shot_table(sw):
     """150 shots > 128: source cells and wavelet samples come from global
     memory in every unit descriptor."""
@@ -168,3 +182,9 @@ def test_more_units_than_the_descriptor_table(sw):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert nshot / sms > 256
     run_case(sw, 10, 12, 4, 40, nshot, 2, seed=103)
+
+
+def test_more_units_than_the_descriptor_table_16_row_tiles(sw):
+    """16-row tiles of the same 18 x 20 padded grid: 2 tiles per shot,
+    ~632 units per CTA, most of them described into the stage ring."""
+    run_case(sw, 10, 12, 4, 40, 48000, 2, seed=105, flags=sw.F_ROWS16)
