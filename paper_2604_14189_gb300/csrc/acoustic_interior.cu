@@ -169,7 +169,10 @@ __device__ __forceinline__ void fwd_body(const AcInFwdArgs& a, int bx, int G, Sh
   const Geom& g = a.g;
   const Region& R = g.fin;
   const int count = (a.units - bx + G - 1) / G;  // units b, b+G, ...
-  if (count <= 0) return;
+  if (count <= 0) {
+    grid_dep_wait();
+    return;
+  }
   load_shot_table(T, g, a.src, a.wavelet, a.n);
   __syncthreads();  // shot table visible
   for (int i = threadIdx.x; i < count && i < kUnitTable; i += FWD_THREADS)
@@ -178,7 +181,11 @@ __device__ __forceinline__ void fwd_body(const AcInFwdArgs& a, int bx, int G, Sh
     for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
     fence_barrier_init();
   }
-  __syncthreads();
+  // The prologue above reads only the call's inputs (geometry, sources,
+  // wavelets), which no kernel of the library writes, so it overlaps the
+  // previous kernel's tail; the fields are read after this wait.
+  grid_dep_wait();
+  if (__syncthreads_or(threadIdx.x == 0 && *a.status != 0)) return;
   // the unit's descriptor is stored before the arrive on its barrier, so a
   // thread that has waited on the barrier sees it
   auto issue = [&](int k) {
@@ -268,8 +275,6 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
   __shared__ ShotTable T;
   __shared__ UnitDesc desc[kMaxStages];
   __shared__ UnitDesc utab[kUnitTable];
-  grid_dep_wait();
-  if (*a.status) return;
   if (a.bz == IN_BZ_SMALL)  // uniform over the CTA: one problem per CTA
     fwd_body<IN_BZ_SMALL>(a, bx, G, T, desc, utab, smem_raw);
   else
@@ -290,7 +295,10 @@ __device__ __forceinline__ void bwd_body(const AcInBwdArgs& a, int bx, int G, Sh
   const Geom& g = a.g;
   const Region& R = g.bin;
   const int count = (a.units - bx + G - 1) / G;
-  if (count <= 0) return;
+  if (count <= 0) {
+    grid_dep_wait();
+    return;
+  }
   const bool img = a.do_img != 0, adj = a.do_adj != 0;
   load_shot_table(T, g, a.src, img ? a.wavelet : nullptr, a.n);
   __syncthreads();  // shot table visible
@@ -300,7 +308,9 @@ __device__ __forceinline__ void bwd_body(const AcInBwdArgs& a, int bx, int G, Sh
     for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
     fence_barrier_init();
   }
-  __syncthreads();
+  // inputs only above (see the forward body); the fields after the wait
+  grid_dep_wait();
+  if (__syncthreads_or(threadIdx.x == 0 && *a.status != 0)) return;
   auto issue = [&](int k) {
     UnitDesc d;
     if (k < kUnitTable) {
@@ -476,8 +486,6 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
   __shared__ ShotTable T;
   __shared__ UnitDesc desc[kMaxStages];
   __shared__ UnitDesc utab[kUnitTable];
-  grid_dep_wait();
-  if (*a.status) return;
   if (a.bz == IN_BZ_SMALL)  // uniform over the CTA: one problem per CTA
     bwd_body<IN_BZ_SMALL>(a, bx, G, T, desc, utab, smem_raw);
   else
