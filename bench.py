@@ -86,8 +86,8 @@ def interior_gpts(value, c):
 
 
 # the sources the acoustic time-step kernels are compiled from
-KERNEL_SOURCES = ("acoustic_common.cuh", "acoustic_cpml.cu", "acoustic_interior.cu",
-                  "sweep_internal.cuh", "tma.cuh")
+KERNEL_SOURCES = ("acoustic_common.cuh", "acoustic_cpml.cu", "acoustic_cpml.cuh",
+                  "acoustic_interior.cu", "acoustic_stencil.cuh", "sweep_internal.cuh", "tma.cuh")
 
 
 def kernel_source_hash():

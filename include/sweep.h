@@ -78,6 +78,16 @@ typedef enum {
  * faster for small grids that leave SMs idle with 32-row tiles).  A tuning
  * choice only: the results are identical.  Ignored for elastic physics. */
 #define SWEEP_F_ROWS16 0x4
+/* acoustic sweep_forward, sweep_gradient (without illumination) and the
+ * batched calls: each direction's whole time loop runs as one cooperative
+ * launch (one CTA per SM, grid-wide barriers between each step's stencil
+ * and CPML phases, every wait bounded) instead of two launches per step.
+ * The results equal the per-step path's up to the order of the CPML corner
+ * additions.  A batched call's problems must all set it or all clear it
+ * (else SWEEP_EINVAL); sweep_adjoint and illumination requests return
+ * SWEEP_EUNSUPPORTED with it; SWEEP_EUNSUPPORTED also when the device
+ * cannot hold one CTA per SM.  Ignored for elastic physics. */
+#define SWEEP_F_ONE_LAUNCH 0x8
 
 enum {
   SWEEP_OK = 0,
@@ -224,6 +234,14 @@ int sweep_status(void* ws, void* stream);
  * of this library (256-byte aligned, >= 4 bytes); only its status word is
  * written.  Takes ~0.5 s of one SM.  Asynchronous on `stream`. */
 int sweep_check_wait_timeout(void* ws, size_t ws_bytes, void* stream);
+
+/* Diagnostic of the SWEEP_F_ONE_LAUNCH kernels' grid barrier: launches two
+ * co-resident CTAs, one of which leaves without arriving, so the other's
+ * bounded barrier wait runs out and latches SWEEP_ETIMEOUT in the status word
+ * of ws.  ws: any workspace of this library (256-byte aligned, >= 128 bytes);
+ * its status word and bytes 64..79 are written.  Takes ~2 s of one SM.
+ * Asynchronous on `stream`. */
+int sweep_check_barrier_timeout(void* ws, size_t ws_bytes, void* stream);
 
 /* Static description of a code. */
 const char* sweep_strerror(int code);

@@ -21,6 +21,10 @@ problems concurrently:
   every problem the library's status word is copied to a per-problem slot,
   so an error is attributed to its problem without synchronising.
 
+With ``SWEEP_F_ONE_LAUNCH`` set on the items (all of them, for fused
+runs) each cohort's forward and backward time loops run as one cooperative
+launch each, and the cohorts run one after the other on one stream.
+
 Gradients (``fused=True``, the default) go further: problems of similar
 record length are grouped into cohorts of up to 16, and each cohort is one
 ``sweep_gradient_batch`` call whose every time-step launch carries the step
@@ -124,6 +128,10 @@ def run(items: list[Item], mode: int = sweep.MODE_GRADIENT, streams: int = 8,
             it.data = torch.empty(dshape, dtype=torch.float32, device=device)
     codes = torch.zeros(len(items), dtype=torch.int32, device=device)
     errors: list[BaseException] = []
+    if any(it.problem.flags & sweep.F_ONE_LAUNCH for it in items):
+        # a time-loop launch holds every SM until its loop ends: two of them
+        # on different streams would each wait for SMs the other holds
+        streams = 1
     if fused and all(it.problem.physics == sweep.ACOUSTIC for it in items):
         groups = cohorts(items)
         gq = [q for q in schedule([sum(cost(items[i].problem) for i in g) for g in groups],

@@ -35,3 +35,17 @@ extern "C" int sweep_check_wait_timeout(void* ws, size_t ws_bytes, void* stream)
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? SWEEP_OK : SWEEP_ECUDA;
 }
+
+extern "C" int sweep_check_barrier_timeout(void* ws, size_t ws_bytes, void* stream) {
+  using namespace sweep;
+  if (!ws || ws_bytes < 128 || (reinterpret_cast<uintptr_t>(ws) % 256) != 0)
+    return SWEEP_EWORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* status = static_cast<int*>(ws);
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return SWEEP_ECUDA;
+  // scratch words past the status word (the status area is 16 bytes; the
+  // workspace's next region starts 256 bytes in)
+  unsigned* bar = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + 64);
+  const int rc = launch_barrier_timeout_check(bar, status, st);
+  return rc ? rc : (cudaGetLastError() == cudaSuccess ? SWEEP_OK : SWEEP_ECUDA);
+}

@@ -122,6 +122,7 @@ struct Layout {
   // the forward replay (each a copy of the range [fwd_lo, fwd_hi))
   size_t el_a = 0, el_e[4] = {0, 0, 0, 0}, el_g = 0, el_ck = 0, el_seg = 0;
   int el_C = 0, el_ncp = 0;
+  size_t loop = 0, loopbar = 0;   // acoustic time-loop arguments, barrier words
   size_t fwd_lo = 0, fwd_hi = 0;  // contiguous range of forward fields
   size_t adj_lo = 0, adj_hi = 0;  // contiguous range of adjoint fields
   size_t total = 0;
@@ -167,7 +168,8 @@ bool valid_problem(const sweep_problem* p) {
   if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return false;
   if (!(p->f_ref >= 0.f) || !std::isfinite(p->f_ref)) return false;
   if (!std::isfinite(p->v_pml)) return false;
-  if (p->flags & ~(SWEEP_F_PADDED_MODEL | SWEEP_F_RESIDUAL_IN | SWEEP_F_ROWS16))
+  if (p->flags &
+      ~(SWEEP_F_PADDED_MODEL | SWEEP_F_RESIDUAL_IN | SWEEP_F_ROWS16 | SWEEP_F_ONE_LAUNCH))
     return false;  // unknown bits
   // keep every index within one shot's field (z * NXp + x, on the padded
   // row pitch) and the count of (tile, shot) units within 32 bits
@@ -225,6 +227,8 @@ Layout layout(const sweep_problem* p, int mode) {
     L.total = b.off;
     return L;
   }
+  L.loop = b.take(sizeof(LoopProblem));  // time-loop kernels' arguments
+  L.loopbar = b.take(sizeof(unsigned) * 4);
   if (mode == SWEEP_MODE_FORWARD || mode == SWEEP_MODE_GRADIENT) {
     L.fwd_lo = b.off;
     L.u[0] = b.take(F);
@@ -744,6 +748,20 @@ static int begin(const sweep_problem* p, int mode, void* ws, size_t ws_bytes,
   return cuda_rc(cudaMemsetAsync(at<int>(ws, L.status), 0, sizeof(int), st));
 }
 
+static int gradient_group(const sweep_problem* const* P, const float* const* models,
+                          const float* const* wavelets, const int32_t* const* srcs,
+                          const int32_t* const* recs, const float* const* d_obs,
+                          float* const* grads, double* const* misfits, void* const* wss,
+                          int np, cudaStream_t st);
+static int forward_group(const sweep_problem* const* P, const float* const* models,
+                         const float* const* wavelets, const int32_t* const* srcs,
+                         const int32_t* const* recs, float* const* data, void* const* wss,
+                         int np, cudaStream_t st);
+
+static bool one_launch(const sweep_problem* p) {
+  return p->physics == SWEEP_ACOUSTIC && (p->flags & SWEEP_F_ONE_LAUNCH);
+}
+
 int sweep_forward(const sweep_problem* p, const float* model, const float* wavelet,
                   const int32_t* src, const int32_t* rec, float* data, void* ws,
                   size_t ws_bytes, void* stream) {
@@ -754,6 +772,10 @@ int sweep_forward(const sweep_problem* p, const float* model, const float* wavel
   int rc = begin(p, SWEEP_MODE_FORWARD, ws, ws_bytes, st);
   if (rc) return rc;
   if (p->nshot == 0) return SWEEP_OK;
+  if (one_launch(p)) {  // a group of one problem: the time-loop kernel
+    rc = forward_group(&p, &model, &wavelet, &src, &rec, &data, &ws, 1, st);
+    return rc ? rc : cuda_rc(cudaGetLastError());
+  }
   const Layout L = layout(p, SWEEP_MODE_FORWARD);
   if (p->physics == SWEEP_ELASTIC) {
     SetupArgs sa = setup_args(p, L, ws, model, src, rec);
@@ -778,6 +800,7 @@ int sweep_adjoint(const sweep_problem* p, const float* model, const float* adj_d
   if (!valid_problem(p) || !model) return SWEEP_EINVAL;
   if (p->nshot > 0 && (!src || !wavelet_grad)) return SWEEP_EINVAL;
   if (p->nshot > 0 && p->nrec > 0 && (!rec || !adj_data)) return SWEEP_EINVAL;
+  if (one_launch(p)) return SWEEP_EUNSUPPORTED;
   int rc = begin(p, SWEEP_MODE_ADJOINT, ws, ws_bytes, st);
   if (rc) return rc;
   if (p->nshot == 0) return SWEEP_OK;
@@ -807,6 +830,7 @@ int sweep_gradient(const sweep_problem* p, const float* model, const float* wave
   if (p->nshot > 0 && (!wavelet || !src)) return SWEEP_EINVAL;
   if (p->nshot > 0 && p->nrec > 0 && (!rec || !d_obs)) return SWEEP_EINVAL;
   if (p->physics == SWEEP_ELASTIC && illum) return SWEEP_EUNSUPPORTED;
+  if (one_launch(p) && illum) return SWEEP_EUNSUPPORTED;
   int rc = begin(p, SWEEP_MODE_GRADIENT, ws, ws_bytes, st);
   if (rc) return rc;
   const Geom g = make_geom(p);
@@ -816,6 +840,10 @@ int sweep_gradient(const sweep_problem* p, const float* model, const float* wave
     if (illum) cudaMemsetAsync(illum, 0, sizeof(float) * (size_t)g.nz * g.nx, st);
     if (misfit) cudaMemsetAsync(misfit, 0, sizeof(double), st);
     return cuda_rc(cudaGetLastError());
+  }
+  if (one_launch(p)) {  // a group of one problem: the time-loop kernels
+    rc = gradient_group(&p, &model, &wavelet, &src, &rec, &d_obs, &grad, &misfit, &ws, 1, st);
+    return rc ? rc : cuda_rc(cudaGetLastError());
   }
   const Layout L = layout(p, SWEEP_MODE_GRADIENT);
   if (p->physics == SWEEP_ELASTIC) {
@@ -856,6 +884,64 @@ int sweep_gradient(const sweep_problem* p, const float* model, const float* wave
   return cuda_rc(cudaGetLastError());
 }
 
+// The time-loop kernels' path (SWEEP_F_ONE_LAUNCH): the arguments of both
+// step parities of each live problem go into its workspace, then one
+// launch runs the whole forward loop.  lp[i] keeps problem i's arguments
+// for the backward half.
+static int loop_forward(const sweep_problem* const* P, std::vector<AcFwdLoop>& F,
+                        const std::vector<Layout>& Ls, void* const* wss,
+                        const std::vector<int>& live, std::vector<LoopProblem>& lp, int ntmax,
+                        cudaStream_t st) {
+  LoopArgs la{};
+  for (int i : live) {
+    LoopProblem& h = lp[i];
+    for (int k = 0; k < 2; ++k) {
+      F[i].step(k);
+      h.fin[k] = F[i].in;
+      h.ffix[k] = F[i].fx;
+      fix_fwd_split(h.ffix[k]);
+    }
+    h.fsave = F[i].save;
+    h.slot = (long long)F[i].g.nshot * F[i].g.nring;
+    h.nt = P[i]->nt;
+    LoopProblem* d = at<LoopProblem>(wss[i], Ls[i].loop);
+    launch_loop_install(h, d, st);
+    la.p[la.np++] = d;
+  }
+  la.nsteps = ntmax;
+  la.bar = at<unsigned>(wss[live[0]], Ls[live[0]].loopbar);
+  cudaMemsetAsync(la.bar, 0, sizeof(unsigned) * 4, st);
+  return launch_ac_loop_fwd(la, st);
+}
+
+static int loop_backward(const sweep_problem* const* P, std::vector<AcBwdLoop>& B,
+                         const std::vector<Layout>& Ls, void* const* wss,
+                         const std::vector<int>& live, std::vector<LoopProblem>& lp, int ntmax,
+                         cudaStream_t st) {
+  LoopArgs la{};
+  for (int i : live) {
+    LoopProblem& h = lp[i];
+    for (int k = 0; k < 2; ++k) {
+      bool adj = false;
+      B[i].step(k + 2, &adj);  // buffers of the steps with n % 2 == k
+      h.bin[k] = B[i].in;
+      AcFixArgs& f = h.bfix[k];
+      f = B[i].fx;
+      f.n = 1;  // a step with a residual injection ...
+      f.save = B[i].save;  // ... and a ring restore: slot n - 1 set per step
+      f.uring = at<float>(wss[i], Ls[i].u[(k + 1) & 1]);
+      fix_bwd_split(f);
+    }
+    LoopProblem* d = at<LoopProblem>(wss[i], Ls[i].loop);
+    launch_loop_install(h, d, st);
+    la.p[la.np++] = d;
+  }
+  la.nsteps = ntmax + 1;
+  la.bar = at<unsigned>(wss[live[0]], Ls[live[0]].loopbar);
+  cudaMemsetAsync(la.bar, 0, sizeof(unsigned) * 4, st);
+  return launch_ac_loop_bwd(la, st);
+}
+
 // Gradients of up to kStepBatch acoustic problems in lockstep: every step
 // kernel launch carries the step of each problem that has it (forward: step
 // t for the problems with t < nt; backward: step nt - t of each).
@@ -864,6 +950,7 @@ static int gradient_group(const sweep_problem* const* P, const float* const* mod
                           const int32_t* const* recs, const float* const* d_obs,
                           float* const* grads, double* const* misfits, void* const* wss,
                           int np, cudaStream_t st) {
+  const bool one_launch = (P[0]->flags & SWEEP_F_ONE_LAUNCH) != 0;
   std::vector<Layout> Ls(np);
   std::vector<AcFwdLoop> F(np);
   std::vector<AcBwdLoop> Bk(np);
@@ -890,17 +977,23 @@ static int gradient_group(const sweep_problem* const* P, const float* const* mod
   AcInFwdArgs fin[kStepBatch];
   AcInBwdArgs bin[kStepBatch];
   AcFixArgs fix[kStepBatch];
-  for (int t = 0; t < ntmax; ++t) {
-    int k = 0;
-    for (int i : live) {
-      if (t >= P[i]->nt) continue;
-      F[i].step(t);
-      fin[k] = F[i].in;
-      fix[k] = F[i].fx;
-      ++k;
+  std::vector<LoopProblem> lp(one_launch ? np : 0);
+  if (one_launch) {
+    const int rc = loop_forward(P, F, Ls, wss, live, lp, ntmax, st);
+    if (rc) return rc;
+  } else {
+    for (int t = 0; t < ntmax; ++t) {
+      int k = 0;
+      for (int i : live) {
+        if (t >= P[i]->nt) continue;
+        F[i].step(t);
+        fin[k] = F[i].in;
+        fix[k] = F[i].fx;
+        ++k;
+      }
+      launch_ac_in_fwd_batch(fin, k, st);
+      launch_ac_fix_fwd_batch(fix, k, st);
     }
-    launch_ac_in_fwd_batch(fin, k, st);
-    launch_ac_fix_fwd_batch(fix, k, st);
   }
   for (int i : live) {
     const sweep_problem* p = P[i];
@@ -914,17 +1007,22 @@ static int gradient_group(const sweep_problem* const* P, const float* const* mod
                               true, false, st);
     if (rc) return rc;
   }
-  for (int t = 0; t <= ntmax; ++t) {
-    int kb = 0, kf = 0;
-    for (int i : live) {
-      const int n = P[i]->nt - t;
-      bool adj = false;
-      if (n < 0 || !Bk[i].step(n, &adj)) continue;
-      bin[kb++] = Bk[i].in;
-      if (adj) fix[kf++] = Bk[i].fx;
+  if (one_launch) {
+    const int rc = loop_backward(P, Bk, Ls, wss, live, lp, ntmax, st);
+    if (rc) return rc;
+  } else {
+    for (int t = 0; t <= ntmax; ++t) {
+      int kb = 0, kf = 0;
+      for (int i : live) {
+        const int n = P[i]->nt - t;
+        bool adj = false;
+        if (n < 0 || !Bk[i].step(n, &adj)) continue;
+        bin[kb++] = Bk[i].in;
+        if (adj) fix[kf++] = Bk[i].fx;
+      }
+      launch_ac_in_bwd_batch(bin, kb, st);
+      launch_ac_fix_bwd_batch(fix, kf, st);
     }
-    launch_ac_in_bwd_batch(bin, kb, st);
-    launch_ac_fix_bwd_batch(fix, kf, st);
   }
   for (int i : live) {
     const sweep_problem* p = P[i];
@@ -956,6 +1054,11 @@ static int forward_group(const sweep_problem* const* P, const float* const* mode
     live.push_back(i);
     ntmax = std::max(ntmax, p->nt);
   }
+  if (live.empty()) return SWEEP_OK;
+  if (P[0]->flags & SWEEP_F_ONE_LAUNCH) {
+    std::vector<LoopProblem> lp(np);
+    return loop_forward(P, F, Ls, wss, live, lp, ntmax, st);
+  }
   AcInFwdArgs fin[kStepBatch];
   AcFixArgs fix[kStepBatch];
   for (int t = 0; t < ntmax; ++t) {
@@ -986,6 +1089,7 @@ int sweep_forward_batch(int nprob, const sweep_problem* probs, const float* cons
     const sweep_problem* p = &probs[i];
     if (!valid_problem(p)) return SWEEP_EINVAL;
     if (p->physics != SWEEP_ACOUSTIC) return SWEEP_EUNSUPPORTED;
+    if ((p->flags ^ probs[0].flags) & SWEEP_F_ONE_LAUNCH) return SWEEP_EINVAL;
     const int rc = check_ws(p, SWEEP_MODE_FORWARD, ws[i], ws_bytes[i]);
     if (rc) return rc;
     if (!models[i]) return SWEEP_EINVAL;
@@ -1025,6 +1129,7 @@ int sweep_gradient_batch(int nprob, const sweep_problem* probs, const float* con
     const sweep_problem* p = &probs[i];
     if (!valid_problem(p)) return SWEEP_EINVAL;
     if (p->physics != SWEEP_ACOUSTIC) return SWEEP_EUNSUPPORTED;
+    if ((p->flags ^ probs[0].flags) & SWEEP_F_ONE_LAUNCH) return SWEEP_EINVAL;
     const int rc = check_ws(p, SWEEP_MODE_GRADIENT, ws[i], ws_bytes[i]);
     if (rc) return rc;
     if (!models[i] || !grads[i] || !misfits[i]) return SWEEP_EINVAL;

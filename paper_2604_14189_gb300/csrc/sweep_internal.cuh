@@ -126,6 +126,11 @@ void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st);
 void launch_ac_fix_fwd_batch(const AcFixArgs* a, int np, cudaStream_t st);
 void launch_ac_fix_bwd_batch(const AcFixArgs* a, int np, cudaStream_t st);
 
+// Work split of one problem's CPML step (acoustic_cpml.cu): fills the part
+// counts of `a` and returns the blocks per shot (0: no work).
+int fix_fwd_split(AcFixArgs& a);
+int fix_bwd_split(AcFixArgs& a);
+
 // The arguments of up to NP problems for one launch of a step kernel: the
 // launch's 1-D grid is split into consecutive block ranges, problem i owning
 // blocks [start[i], start[i + 1]) (start[np..NP] = the grid size, unused
@@ -159,6 +164,39 @@ void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st);
 void launch_ac_in_fwd_batch(const AcInFwdArgs* a, int np, cudaStream_t st);
 void launch_ac_in_bwd_batch(const AcInBwdArgs* a, int np, cudaStream_t st);
 int device_sms();
+
+// Time-loop kernels (acoustic_loop.cu): one cooperative launch runs every
+// forward (or backward) step of up to kStepBatch problems, each step as a
+// stencil phase and a CPML phase separated by grid-wide barriers.
+// LoopProblem holds one problem's arguments for the steps of either parity
+// (n % 2 selects the buffers); the kernel sets the per-step scalars (n, the
+// ring slot, the backward step's flags) itself.  It lives in the problem's
+// workspace, written by launch_loop_install.
+struct LoopProblem {
+  AcInFwdArgs fin[2];   // forward stencil arguments of steps with n % 2 == k
+  AcFixArgs ffix[2];    // forward CPML arguments (work split set)
+  AcInBwdArgs bin[2];   // backward stencil arguments
+  AcFixArgs bfix[2];    // backward CPML arguments, split for a step that
+                        // restores the ring (save = slot of u^0, uring set)
+  float* fsave;         // forward: ring slot of u^0 (null: no save)
+  long long slot;       // floats per ring slot (nshot * nring)
+  int nt;
+  int pad;
+};
+struct LoopArgs {
+  LoopProblem* p[kStepBatch];  // device copies
+  int np;
+  int nsteps;                  // forward: max nt; backward: max nt + 1
+  unsigned* bar;               // barrier words (arrivals, generation, abort),
+                               // arrivals and abort zero at launch
+};
+void launch_loop_install(const LoopProblem& h, LoopProblem* d, cudaStream_t st);
+// SWEEP_OK, or SWEEP_EUNSUPPORTED when the grid cannot be co-resident
+int launch_ac_loop_fwd(const LoopArgs& a, cudaStream_t st);
+int launch_ac_loop_bwd(const LoopArgs& a, cudaStream_t st);
+// Diagnostic: a grid barrier that one CTA never reaches runs out (~2 s) and
+// latches SWEEP_ETIMEOUT in *status; bar: 4 words of scratch.
+int launch_barrier_timeout_check(unsigned* bar, int* status, cudaStream_t st);
 
 // Setup (setup.cu)
 struct SetupArgs {

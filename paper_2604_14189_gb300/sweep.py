@@ -24,6 +24,7 @@ MODE_GRADIENT = 2
 F_PADDED_MODEL = 0x1
 F_RESIDUAL_IN = 0x2
 F_ROWS16 = 0x4
+F_ONE_LAUNCH = 0x8
 
 OK = 0
 EINVAL, ECFL, EBOUNDS, EWORKSPACE, ECUDA, ETIMEOUT, ENONFINITE, EMODEL, EUNSUPPORTED = (
@@ -37,7 +38,8 @@ EXPORTS = ("sweep_workspace_bytes", "sweep_forward", "sweep_adjoint", "sweep_gra
            "sweep_kernel_launches", "sweep_profile_enable", "sweep_profile_read",
            "sweep_dot_noalloc", "sweep_capture_begin", "sweep_capture_end",
            "sweep_graph_launch", "sweep_graph_kernels", "sweep_graph_destroy",
-           "sweep_check_wait_timeout", "sweep_gradient_batch", "sweep_forward_batch")
+           "sweep_check_wait_timeout", "sweep_check_barrier_timeout", "sweep_gradient_batch",
+           "sweep_forward_batch")
 K_AC_FWD, K_AC_BWD, K_EL_VEL, K_EL_STR = 0, 1, 2, 3
 
 
@@ -118,6 +120,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.sweep_graph_destroy.restype = None
     lib.sweep_check_wait_timeout.argtypes = [vp, sz, vp]
     lib.sweep_check_wait_timeout.restype = i32
+    lib.sweep_check_barrier_timeout.argtypes = [vp, sz, vp]
+    lib.sweep_check_barrier_timeout.restype = i32
     lib.sweep_gradient_batch.argtypes = [i32] + [vp] * 11
     lib.sweep_gradient_batch.restype = i32
     lib.sweep_forward_batch.argtypes = [i32] + [vp] * 9
@@ -231,6 +235,15 @@ def check_wait_timeout(ws: torch.Tensor, stream=None) -> None:
     rc = _lib.sweep_check_wait_timeout(w, wn, _stream(stream))
     if rc != OK:
         raise SweepError(rc, "sweep_check_wait_timeout")
+
+
+def check_barrier_timeout(ws: torch.Tensor, stream=None) -> None:
+    """Runs the grid-barrier timeout diagnostic on `ws` (see
+    sweep_check_barrier_timeout)."""
+    w, wn = _ws_args(ws)
+    rc = _lib.sweep_check_barrier_timeout(w, wn, _stream(stream))
+    if rc != OK:
+        raise SweepError(rc, "sweep_check_barrier_timeout")
 
 
 def status(ws: torch.Tensor, stream=None) -> int:

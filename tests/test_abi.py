@@ -102,7 +102,7 @@ def test_workspace_size_and_validation():
                 dict(nz=20000, nx=20000, pml=0, nshot=65535),
                 dict(nshot=65536),
                 # a flag bit the library does not define
-                dict(flags=0x8), dict(flags=-1)):
+                dict(flags=0x10), dict(flags=-1)):
         q = _prob(sweep, **bad)
         assert sweep.lib().sweep_workspace_bytes(ctypes.byref(q), 0) == 0, bad
     assert sweep.lib().sweep_workspace_bytes(ctypes.byref(p), 7) == 0
@@ -183,6 +183,34 @@ def test_wait_timeout_diagnostic_checks_workspace(lib):
     assert L.sweep_check_wait_timeout(None, 1024, None) == sweep.EWORKSPACE
     assert L.sweep_check_wait_timeout(ctypes.c_void_p(256), 2, None) == sweep.EWORKSPACE
     assert L.sweep_check_wait_timeout(ctypes.c_void_p(257), 1024, None) == sweep.EWORKSPACE
+    assert L.sweep_check_barrier_timeout(None, 1024, None) == sweep.EWORKSPACE
+    assert L.sweep_check_barrier_timeout(ctypes.c_void_p(256), 64, None) == sweep.EWORKSPACE
+    assert L.sweep_check_barrier_timeout(ctypes.c_void_p(257), 1024, None) == sweep.EWORKSPACE
+
+
+def test_one_launch_flag_rules():
+    """SWEEP_F_ONE_LAUNCH: accepted by validation (same workspace size);
+    with an illumination request or in sweep_adjoint the call is refused
+    before anything is launched; a batch whose problems disagree on the flag
+    is refused too."""
+    from paper_2604_14189_gb300 import sweep
+    L = sweep.lib()
+    p = _prob(sweep)
+    q = _prob(sweep, flags=sweep.F_ONE_LAUNCH)
+    for mode in (0, 1, 2):
+        assert (L.sweep_workspace_bytes(ctypes.byref(q), mode)
+                == L.sweep_workspace_bytes(ctypes.byref(p), mode))
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: refused before a launch
+    big = ctypes.c_size_t(1 << 40)
+    assert L.sweep_gradient(ctypes.byref(q), fake, fake, fake, fake, fake, fake, fake, fake,
+                            fake, big, None) == sweep.EUNSUPPORTED
+    assert L.sweep_adjoint(ctypes.byref(q), fake, fake, fake, fake, fake, fake, big,
+                           None) == sweep.EUNSUPPORTED
+    probs = (sweep.Problem * 2)(p, q)
+    ptrs = (ctypes.c_void_p * 2)(fake, fake)
+    sizes = (ctypes.c_size_t * 2)(1 << 40, 1 << 40)
+    assert L.sweep_forward_batch(2, probs, ptrs, ptrs, ptrs, ptrs, ptrs, ptrs, sizes,
+                                 None) == sweep.EINVAL
 
 
 def test_binding_rejects_wrong_sizes_before_any_call():

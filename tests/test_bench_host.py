@@ -76,7 +76,7 @@ def test_kernel_source_hash_ignores_comments_not_code(monkeypatch):
     root, csrc = _scratch_root("hash_check")
     monkeypatch.setattr(bench, "ROOT", root)
     assert bench.kernel_source_hash() == base
-    path = os.path.join(csrc, "acoustic_cpml.cu")
+    path = os.path.join(csrc, "acoustic_cpml.cuh")
     src = open(path).read()
     with open(path, "w") as f:
         f.write("// a new comment\n/* and a block\n comment */\n" + src.replace("\n", "\n\n", 3))

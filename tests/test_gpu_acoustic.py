@@ -168,7 +168,7 @@ def test_16_row_tiles_match_oracle(sw, shape):
     g16 = g16.cpu().numpy()
     assert rel(g16, gref) <= 1e-3, rel(g16, gref)
     assert max(region_errors(g16, gref, c["src"]).values()) <= 1e-3
-    assert rel(g16, g32.cpu().numpy()) <= 1e-5
+    assert rel(g16, g32.cpu().numpy()) <= 1e-4  # corner additions in either order
     # the misfit bound of test_gradient_matches_oracle (J is a difference of
     # nearly equal data, so its relative rounding is |d| / |r| times larger)
     nd, nr = np.linalg.norm(ref), np.linalg.norm(ref - f32(d_obs))
