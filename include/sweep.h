@@ -295,7 +295,12 @@ enum {
   SWEEP_K_AC_FWD_FR = 5,  /* acoustic forward, CPML correction kernels */
   SWEEP_K_AC_BWD_IN = 6,  /* acoustic backward, stencil kernel         */
   SWEEP_K_AC_BWD_FR = 7,  /* acoustic backward, CPML correction kernels*/
-  SWEEP_K_COUNT = 8
+  SWEEP_K_AC_FWD_LOOP = 8, /* a whole acoustic forward time loop (one
+                              record per call: the events sit before its
+                              first and after its last step, so the steps
+                              keep their programmatic overlap)           */
+  SWEEP_K_AC_BWD_LOOP = 9, /* a whole acoustic backward time loop        */
+  SWEEP_K_COUNT = 10
 };
 int sweep_profile_enable(int mask);
 int sweep_profile_read(int kernel, double* ms, long long* launches);

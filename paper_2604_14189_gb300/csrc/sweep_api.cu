@@ -417,6 +417,7 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
   AcFwdLoop f;
   const int rc = f.init(p, L, ws, wavelet, src, rec, data, save_ring, st);
   if (rc) return rc;
+  void* loop = profile_begin(SWEEP_K_AC_FWD_LOOP, st);
   for (int n = 0; n < f.g.nt; ++n) {
     f.step(n);
     void* tok = profile_begin(SWEEP_K_AC_FWD, st);
@@ -424,6 +425,7 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
     launch_ac_fix_fwd(f.fx, st);
     profile_end(tok, st);
   }
+  profile_end(loop, st);
   return SWEEP_OK;
 }
 
@@ -539,6 +541,7 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
   AcBwdLoop b;
   const int rc = b.init(p, L, ws, wavelet, src, rec, res, wgrad, imaging, illum, st);
   if (rc) return rc;
+  void* loop = profile_begin(SWEEP_K_AC_BWD_LOOP, st);
   for (int n = b.g.nt; n >= 0; --n) {
     bool adj = false;
     if (!b.step(n, &adj)) continue;
@@ -547,6 +550,7 @@ int acoustic_backward_loop(const sweep_problem* p, const Layout& L, void* ws,
     if (adj) launch_ac_fix_bwd(b.fx, st);
     profile_end(tok, st);
   }
+  profile_end(loop, st);
   return SWEEP_OK;
 }
 

@@ -41,6 +41,7 @@ EXPORTS = ("sweep_workspace_bytes", "sweep_forward", "sweep_adjoint", "sweep_gra
            "sweep_check_wait_timeout", "sweep_check_barrier_timeout", "sweep_gradient_batch",
            "sweep_forward_batch")
 K_AC_FWD, K_AC_BWD, K_EL_VEL, K_EL_STR = 0, 1, 2, 3
+K_AC_FWD_LOOP, K_AC_BWD_LOOP = 8, 9
 
 
 class Problem(ctypes.Structure):
