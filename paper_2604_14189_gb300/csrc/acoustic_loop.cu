@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
       S.vs[L.np] = acc;
     }
     __syncthreads();
-    for (int vb = blockIdx.x * NSUB + sub; vb < S.vs[L.np]; vb += gridDim.x * NSUB) {
+    for (int vb = blockIdx.x * NSUB + sub; sub < NSUB && vb < S.vs[L.np];
+         vb += gridDim.x * NSUB) {
       int k = 0;
       while (vb >= S.vs[k + 1]) ++k;
       const AcFixArgs& a = fx[k];
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ LoopShared S;
   __shared__ int fixlive_any;
-  constexpr int NSUB = BWD_THREADS / FT;
+  constexpr int NSUB = (BWD_THREADS / FT);  // the last, partial slice sits out
   const int sub = threadIdx.x / FT;
   if (threadIdx.x < L.np) {
     S.u[threadIdx.x] = L.p[threadIdx.x]->bin[0].units;
@@ -317,7 +318,8 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
       S.vs[L.np] = acc;
     }
     __syncthreads();
-    for (int vb = blockIdx.x * NSUB + sub; vb < S.vs[L.np]; vb += gridDim.x * NSUB) {
+    for (int vb = blockIdx.x * NSUB + sub; sub < NSUB && vb < S.vs[L.np];
+         vb += gridDim.x * NSUB) {
       int k = 0;
       while (vb >= S.vs[k + 1]) ++k;
       const AcFixArgs& a = fx[k];
