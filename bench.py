@@ -1056,7 +1056,7 @@ def run_batch(args, local_rank, emit=True):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     items = []
-    cells = alg = 0
+    cells = alg = alg_b = 0
     problems = inputs.workload_batch()
     for w in problems:
         ns, nrec, nt = w["src"].shape[0], w["rec"].shape[1], w["nt"]
@@ -1071,6 +1071,7 @@ def run_batch(args, local_rank, emit=True):
         cells += batch.cost(p)
         cb = counts(w["nz"], w["nx"], w["pml"])
         alg += (alg_bytes_fwd(cb) + alg_bytes_bwd(cb)) * ns * nt
+        alg_b += alg_bytes_bwd(cb) * ns * nt
     # schedule and tile-height autotuning on a sample of the batch; the
     # tile threshold chosen on the sample is applied to every problem
     best, times = batch.autotune_streams(items[:64], candidates=(1, 2, 3, 4, 6))
@@ -1094,6 +1095,48 @@ def run_batch(args, local_rank, emit=True):
     if any(codes):
         raise RuntimeError(f"batch errors: {sorted(set(codes))}")
     value = cells / sec / 1e9
+
+    # the dominant kernels: every cohort's backward time loop (stencil + CPML
+    # launches of up to 16 problems per step) timed as a whole with CUDA
+    # events on its stream, one more pass at one stream so that the loops do
+    # not share the GPU with each other
+    sweep.profile_enable((1 << sweep.K_AC_BWD_LOOP) | (1 << sweep.K_AC_FWD_LOOP))
+    batch.run(items, streams=1)
+    torch.cuda.synchronize()
+    bwd_loop_ms, bwd_loops = sweep.profile_read(sweep.K_AC_BWD_LOOP)
+    fwd_loop_ms, _ = sweep.profile_read(sweep.K_AC_FWD_LOOP)
+    sweep.profile_enable(False)
+    cohort_steps = sum(max(items[i].problem.nt for i in g) + 1 for g in batch.cohorts(items))
+    peak, peak_src = peaks()
+    b_gbs = alg_b / (bwd_loop_ms * 1e-3) / 1e9
+
+    # end to end: every problem's model, wavelets, geometry and observed data
+    # copied from pinned host memory, and its gradient and misfit copied back,
+    # inside the timed pass
+    host = [tuple(t.cpu().pin_memory() for t in (it.model, it.wavelet, it.src, it.rec, it.d_obs))
+            for it in items]
+    h2d = sum(t.numel() * t.element_size() for h in host for t in h)
+    g_host = [torch.empty(it.grad.shape, dtype=torch.float32).pin_memory() for it in items]
+    m_host = torch.empty(len(items), dtype=torch.float64).pin_memory()
+    d2h = sum(g.numel() * 4 for g in g_host) + 8 * len(items)
+
+    def e2e_pass():
+        for it, h in zip(items, host):
+            for dst, src_h in zip((it.model, it.wavelet, it.src, it.rec, it.d_obs), h):
+                dst.copy_(src_h, non_blocking=True)
+        c = batch.run(items, streams=best)
+        for it, gh in zip(items, g_host):
+            gh.copy_(it.grad, non_blocking=True)
+        m_host.copy_(torch.stack([it.misfit for it in items]), non_blocking=True)
+        torch.cuda.synchronize()
+        return c
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    codes = e2e_pass()
+    sec_e2e = time.perf_counter() - t0
+    if any(codes) or not np.isfinite(m_host.numpy()).all():
+        raise RuntimeError("batch end-to-end pass failed")
     cpu = None
     if not args.no_cpu_baseline:
         g, _, cores, sample = oracle_batch_sample(problems[:16], 60)
@@ -1109,13 +1152,23 @@ def run_batch(args, local_rank, emit=True):
                    "streams": best, "autotune_seconds": times,
                    "rows16_below_units": tile_th, "tile_autotune_seconds": tile_times,
                    "step": "one pass over the whole batch"},
-        "roofline": None,
-        "path_roofline": {"achieved": alg / sec / 1e9, "frac": alg / sec / 1e9 / peaks()[0],
+        "roofline": {"bound": "hbm", "achieved": b_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": b_gbs / peak, "traffic": None,
+                     "kernel": "acoustic backward time steps of the cohorts (stencil + CPML "
+                               "launches carrying up to 16 problems' steps)",
+                     "peak_source": peak_src,
+                     "alg_bytes_per_launch": alg_b / cohort_steps,
+                     "avg_launch_ms": bwd_loop_ms / cohort_steps,
+                     "timing": "CUDA events around every cohort's whole backward time loop "
+                               "(%d loops, %d cohort steps) in a pass at one stream after the "
+                               "timed region" % (bwd_loops, cohort_steps),
+                     "forward_loops_ms": fwd_loop_ms},
+        "path_roofline": {"achieved": alg / sec / 1e9, "frac": alg / sec / 1e9 / peak,
                           "note": "algorithmic bytes of every forward and backward step of "
                                   "the 256 problems / pass time"},
         "cpu_baseline": cpu,
-        "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 4 * len(items)},
+        "e2e": {"value": cells / sec_e2e / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }

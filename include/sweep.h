@@ -296,9 +296,10 @@ enum {
   SWEEP_K_AC_BWD_IN = 6,  /* acoustic backward, stencil kernel         */
   SWEEP_K_AC_BWD_FR = 7,  /* acoustic backward, CPML correction kernels*/
   SWEEP_K_AC_FWD_LOOP = 8, /* a whole acoustic forward time loop (one
-                              record per call: the events sit before its
-                              first and after its last step, so the steps
-                              keep their programmatic overlap)           */
+                              record per call, or per group of a batched
+                              call: the events sit before its first and
+                              after its last step, so the steps keep
+                              their programmatic overlap)                */
   SWEEP_K_AC_BWD_LOOP = 9, /* a whole acoustic backward time loop        */
   SWEEP_K_COUNT = 10
 };

@@ -982,6 +982,7 @@ static int gradient_group(const sweep_problem* const* P, const float* const* mod
   AcInBwdArgs bin[kStepBatch];
   AcFixArgs fix[kStepBatch];
   std::vector<LoopProblem> lp(one_launch ? np : 0);
+  void* ftok = profile_begin(SWEEP_K_AC_FWD_LOOP, st);
   if (one_launch) {
     const int rc = loop_forward(P, F, Ls, wss, live, lp, ntmax, st);
     if (rc) return rc;
@@ -999,6 +1000,7 @@ static int gradient_group(const sweep_problem* const* P, const float* const* mod
       launch_ac_fix_fwd_batch(fix, k, st);
     }
   }
+  profile_end(ftok, st);
   for (int i : live) {
     const sweep_problem* p = P[i];
     float* d = at<float>(wss[i], Ls[i].data);
@@ -1011,6 +1013,7 @@ static int gradient_group(const sweep_problem* const* P, const float* const* mod
                               true, false, st);
     if (rc) return rc;
   }
+  void* btok = profile_begin(SWEEP_K_AC_BWD_LOOP, st);
   if (one_launch) {
     const int rc = loop_backward(P, Bk, Ls, wss, live, lp, ntmax, st);
     if (rc) return rc;
@@ -1028,6 +1031,7 @@ static int gradient_group(const sweep_problem* const* P, const float* const* mod
       launch_ac_fix_bwd_batch(fix, kf, st);
     }
   }
+  profile_end(btok, st);
   for (int i : live) {
     const sweep_problem* p = P[i];
     launch_grad_reduce(make_geom(p), at<float>(wss[i], Ls[i].graw), nullptr, models[i],
