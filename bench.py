@@ -231,6 +231,35 @@ def oracle_sample(w, nshot_max, nt_sample, threads=None):
                                       f"{w['nz']}x{w['nx']} workload ({el:.1f} s)")
 
 
+def oracle_fwi_sample(w, nshot_max, nt_sample, grads, forwards):
+    """The FP64 oracle's cost of the plain FWI run, from a bounded sample:
+    its gradient and its forward modelling timed on min(cores, nshot_max)
+    shots x nt_sample steps of the same problem, scaled to `grads` full
+    gradients and `forwards` full forward runs (the line-search trials).
+    Returns (estimated seconds, sample seconds, cores, description)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    ns = max(1, min(nshot_max, cores))
+    oracle.set_threads(cores)
+    nrec = w["rec"].shape[1]
+    q = oracle.make_problem(0, w["nz"], w["nx"], w["pml"], w["dx"], w["dt"], nt_sample, ns, nrec,
+                            w["f0"], v_pml=4500.0)
+    wav = np.stack([inputs.ricker(w["f0"], w["dt"], nt_sample)] * ns)
+    t = time.perf_counter()
+    oracle.acoustic_gradient(q, w["model"], wav, w["src"][:ns], w["rec"][:ns],
+                             np.zeros((ns, nrec, nt_sample)))
+    tg = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.acoustic_forward(q, w["model"], wav, w["src"][:ns], w["rec"][:ns])
+    tf = time.perf_counter() - t
+    scale = (w["src"].shape[0] / ns) * (w["nt"] / nt_sample)
+    est = (grads * tg + forwards * tf) * scale
+    return est, tg + tf, ns, (f"oracle gradient ({tg:.1f} s) and forward ({tf:.1f} s) on {ns} "
+                              f"shots x {nt_sample} steps of the same problem, scaled to "
+                              f"{grads} gradients and {forwards} forward runs of "
+                              f"{w['src'].shape[0]} shots x {w['nt']} steps")
+
+
 def oracle_batch_sample(problems, nt_cap):
     """Time the FP64 oracle gradient of 1/2 |d|^2 on a bounded sample of the
     heterogeneous batch: the given problems, each with its record cut to
@@ -722,6 +751,21 @@ def run_fwi(args, local_rank, emit=True):
     launches = sweep.kernel_launches() - l0
     e0 = float((m0 - vt).norm() / vt.norm())
     e1 = float((model - vt).norm() / vt.norm())
+    # end to end: the starting model, the observed data and the wavelets
+    # copied from pinned host memory into the loop's buffers, the final model
+    # copied back, in a second timed run
+    m0_h, do_h, wav_h = (t.cpu().pin_memory() for t in (m0, d_obs, wav))
+    out_h = torch.empty(m0.shape, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m0_d = m0_h.to(dev, non_blocking=True)
+    d_obs.copy_(do_h, non_blocking=True)  # the buffers the recorded graphs read
+    wav.copy_(wav_h, non_blocking=True)
+    model_e2e, _ = inv.run(m0_d, cfg)
+    out_h.copy_(model_e2e, non_blocking=True)
+    torch.cuda.synchronize()
+    seconds_e2e = time.perf_counter() - t0
+    h2d = sum(t.numel() * t.element_size() for t in (m0_h, do_h, wav_h))
     c = counts(w["nz"], w["nx"], w["pml"])
     # the backward time loop timed as a whole (events before its first and
     # after its last step), divided by its nt - 1 full steps
@@ -737,6 +781,10 @@ def run_fwi(args, local_rank, emit=True):
     achieved = alg_bytes_bwd(c) * nshot / (bms / max(bn, 1) * 1e-3) / 1e9
     grads = len(hist)
     trials = sum(h["trials"] for h in hist)
+    cpu = None
+    if not args.no_cpu_baseline:
+        est, el, cores, sample = oracle_fwi_sample(w, 16, 200, grads, trials)
+        cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample}
     out = {
         "metric": "FWI s to target model error (plain)", "value": seconds, "unit": "s",
         "n_gpus": 1, "steps": grads, "warmup": args.warmup,
@@ -755,9 +803,9 @@ def run_fwi(args, local_rank, emit=True):
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "acoustic backward time step (as in the headline workload)",
                      "peak_source": peak_src, "avg_launch_ms": bms / max(bn, 1)},
-        "cpu_baseline": None,
-        "e2e": {"value": seconds, "unit": "s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
+        "cpu_baseline": cpu,
+        "e2e": {"value": seconds_e2e, "unit": "s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": out_h.numel() * 4},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
