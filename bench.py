@@ -1380,11 +1380,13 @@ def run_autograd(args, local_rank, emit=True):
     return out
 
 
-def run_one_launch(args, local_rank, emit=True):
+def run_one_launch(args, local_rank, emit=True, deterministic=False):
     """The 301 x 901, 20-shot gradient through the time-loop kernels
     (SWEEP_F_ONE_LAUNCH: one cooperative launch per direction, grid barriers
     between each step's stencil and CPML phases) instead of two launches per
-    step; inputs resident on the device, one call per step."""
+    step, or (deterministic=True) through the per-step kernels in their
+    bitwise-reproducible mode (SWEEP_F_DETERMINISTIC); inputs resident on the
+    device, one call per step."""
     import torch
 
     from paper_2604_14189_gb300 import sweep
@@ -1392,8 +1394,9 @@ def run_one_launch(args, local_rank, emit=True):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     nshot, nt, nrec = 20, args.nt, w["rec"].shape[1]
+    flag = sweep.F_DETERMINISTIC if deterministic else sweep.F_ONE_LAUNCH
     p = sweep.problem(nz=w["nz"], nx=w["nx"], pml=w["pml"], dx=w["dx"], dt=w["dt"], nt=nt,
-                      nshot=nshot, nrec=nrec, f_ref=w["f0"], flags=sweep.F_ONE_LAUNCH)
+                      nshot=nshot, nrec=nrec, f_ref=w["f0"], flags=flag)
     wav = torch.tensor(np.stack([inputs.ricker(w["f0"], w["dt"], nt)] * nshot),
                        dtype=torch.float32, device=dev)
     v = torch.tensor(w["model"], dtype=torch.float32, device=dev)
@@ -1417,10 +1420,13 @@ def run_one_launch(args, local_rank, emit=True):
         raise RuntimeError(f"one-launch gradient: status {sweep.status(ws)}")
     c = counts(w["nz"], w["nx"], w["pml"])
     val = c["N_pad"] * nt * nshot / sec / 1e9
-    out = {"metric": "Gpts/s fwd+adj (time-loop kernels)", "value": val, "unit": "Gpts/s",
-           "ms_per_step": sec * 1e3, "higher_is_better": True,
+    what = ("SWEEP_F_DETERMINISTIC (one writer per cell and phase)" if deterministic else
+            "SWEEP_F_ONE_LAUNCH (one cooperative launch per direction)")
+    out = {"metric": "Gpts/s fwd+adj (%s)" % ("deterministic mode" if deterministic
+                                               else "time-loop kernels"),
+           "value": val, "unit": "Gpts/s", "ms_per_step": sec * 1e3, "higher_is_better": True,
            "config": {"workload": f"acoustic gradient 301x901 + 40 CPML, nt {nt}, 20 shots, "
-                                  "SWEEP_F_ONE_LAUNCH (one cooperative launch per direction)"},
+                                  + what},
            "gpu_launches": int(sweep.kernel_launches() - l0) // runs}
     if emit:
         print(json.dumps(out), flush=True)
@@ -1457,6 +1463,8 @@ def run_extras(args, local_rank):
          lambda a: run_elastic(a, 0, 1, local_rank, emit=False)),
         ("acoustic_gradient_one_launch_301x901", dict(steps=1, warmup=1),
          lambda a: run_one_launch(a, local_rank, emit=False)),
+        ("acoustic_gradient_deterministic_301x901", dict(steps=2, warmup=1),
+         lambda a: run_one_launch(a, local_rank, emit=False, deterministic=True)),
         ("batch_256_models", dict(steps=1, warmup=1),
          lambda a: run_batch(a, local_rank, emit=False)),
         ("fwi_plain_256x256", dict(steps=1, warmup=1),
@@ -1486,7 +1494,8 @@ def main():
     ap.add_argument("--workload", default="acoustic-gradient",
                     choices=["acoustic-gradient", "elastic-forward", "elastic-gradient", "fwi",
                              "batch", "fwi-learned", "unet-conv", "unet-train",
-                             "acoustic-gradient-one-launch"],
+                             "acoustic-gradient-one-launch",
+                             "acoustic-gradient-deterministic"],
                     help="acoustic-gradient is the headline; the elastic workloads are "
                          "measured on request")
     ap.add_argument("--pairs", type=int, default=2000,
@@ -1523,6 +1532,8 @@ def main():
             run_unet(args, local_rank)
         elif args.workload == "acoustic-gradient-one-launch":
             run_one_launch(args, local_rank)
+        elif args.workload == "acoustic-gradient-deterministic":
+            run_one_launch(args, local_rank, deterministic=True)
         else:
             run_elastic(args, rank, 1, local_rank)
         return

@@ -88,6 +88,17 @@ typedef enum {
  * SWEEP_EUNSUPPORTED with it; SWEEP_EUNSUPPORTED also when the device
  * cannot hold one CTA per SM.  Ignored for elastic physics. */
 #define SWEEP_F_ONE_LAUNCH 0x8
+/* acoustic: bitwise reproducible results.  Every cell of the CPML border
+ * gets one writer per step (the corners' two axis terms added by one
+ * thread) and the backward stencil kernel injects the residual at the
+ * receivers, in receiver order, so that no two additions to a cell race.
+ * Costs time (about 16 % on a 301x901 + 40 gradient).  Without it, a corner
+ * cell of the border and a receiver cell inside the backward band take two
+ * additions in either order, and runs agree to FP32 rounding only.  Not with
+ * SWEEP_F_ONE_LAUNCH (SWEEP_EUNSUPPORTED); a batched call's problems must
+ * all set it or all clear it (else SWEEP_EINVAL).  Ignored for elastic
+ * physics (its kernels have one writer per cell already). */
+#define SWEEP_F_DETERMINISTIC 0x10
 
 enum {
   SWEEP_OK = 0,

@@ -37,7 +37,7 @@
 namespace sweep {
 namespace {
 
-template <int NP>
+template <int NP, bool OWN>
 __global__ void __launch_bounds__(FT, 8)
     ac_fix_fwd_kernel(const __grid_constant__ StepBatch<AcFixArgs, NP> m) {
   int blk, nblk;  // this block's index and the block count of its problem
@@ -53,9 +53,9 @@ __global__ void __launch_bounds__(FT, 8)
   if (b < a.nbz + a.nbx) {
     if (!*a.status) {
       if (b < a.nbz)
-        fwd_z<true>(a, s, b);
+        fwd_z<true, OWN>(a, s, b);
       else
-        fwd_x<true>(a, s, b - a.nbz);
+        fwd_x<true, OWN>(a, s, b - a.nbz);
     }
     // One thread always waits, so that this kernel never completes before
     // the stencil kernel does (the next step's kernels rely on that order).
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(FT, 8)
   fwd_ring(a, s, b - a.nbr);
 }
 
-template <int NP>
+template <int NP, bool OWN>
 __global__ void __launch_bounds__(FT, 7)
     ac_fix_bwd_kernel(const __grid_constant__ StepBatch<AcFixArgs, NP> m) {
   int blk, nblk;  // this block's index and the block count of its problem
@@ -88,9 +88,9 @@ __global__ void __launch_bounds__(FT, 7)
   if (b < a.nbz + a.nbx) {
     if (!*a.status) {
       if (b < a.nbz)
-        bwd_z<true>(a, s, b);
+        bwd_z<true, OWN>(a, s, b);
       else
-        bwd_x<true>(a, s, b - a.nbz);
+        bwd_x<true, OWN>(a, s, b - a.nbz);
     }
     // One thread always waits, so that this kernel never completes before
     // the stencil kernel does (the next step's kernels rely on that order).
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(FT, 7)
   grid_dep_wait();
   if (*a.status) return;
   b -= a.nbz + a.nbx;
-  if (b < a.nbr) {
+  if (b < a.nbr) {  // (no receiver part in deterministic mode)
     bwd_rec(a, s, b);
     return;
   }
@@ -133,7 +133,8 @@ int fix_bwd_split(AcFixArgs& a) {
   a.xb = x_bands(band_lo_end(g.P, g.NX), band_hi_start(g.P, g.nx, g.NX), g.NX);
   a.nbz = a.zbx * a.nchz;
   a.nbx = (g.P > 0 && a.xb.ngr > 0) ? cdiv(g.NZ * a.xb.ngr, FT) : 0;
-  a.nbr = (a.res && g.nrec > 0 && a.n >= 1) ? cdiv(g.nrec, FT) : 0;
+  // deterministic mode: the stencil kernel injects the residual
+  a.nbr = (!a.own && a.res && g.nrec > 0 && a.n >= 1) ? cdiv(g.nrec, FT) : 0;
   a.nbs = (a.save && a.uring && g.nring > 0) ? cdiv(cdiv(g.nring, 4), FT) : 0;
   return a.nbz + a.nbx + a.nbr + a.nbs;
 }
@@ -144,7 +145,8 @@ void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st) {
   StepBatch<AcFixArgs, 1> m;
   m.p[0] = a;
   void* tok = profile_begin(SWEEP_K_AC_FWD_FR, st);
-  launch_dependent(ac_fix_fwd_kernel<1>, dim3(bps * a.g.nshot), dim3(FT), 0, st, m);
+  launch_dependent(a.own ? ac_fix_fwd_kernel<1, true> : ac_fix_fwd_kernel<1, false>,
+                   dim3(bps * a.g.nshot), dim3(FT), 0, st, m);
   profile_end(tok, st);
   note_launches(1);
 }
@@ -155,7 +157,8 @@ void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st) {
   StepBatch<AcFixArgs, 1> m;
   m.p[0] = a;
   void* tok = profile_begin(SWEEP_K_AC_BWD_FR, st);
-  launch_dependent(ac_fix_bwd_kernel<1>, dim3(bps * a.g.nshot), dim3(FT), 0, st, m);
+  launch_dependent(a.own ? ac_fix_bwd_kernel<1, true> : ac_fix_bwd_kernel<1, false>,
+                   dim3(bps * a.g.nshot), dim3(FT), 0, st, m);
   profile_end(tok, st);
   note_launches(1);
 }
@@ -178,12 +181,20 @@ void launch_fix_batch(K kernel, const AcFixArgs* a, int np, cudaStream_t st) {
   note_launches(1);
 }
 
+// (the problems of one launch share the mode: the batched entry points
+// require it)
 void launch_ac_fix_fwd_batch(const AcFixArgs* a, int np, cudaStream_t st) {
-  launch_fix_batch<fix_fwd_split>(ac_fix_fwd_kernel<kStepBatch>, a, np, st);
+  if (np <= 0) return;
+  launch_fix_batch<fix_fwd_split>(a[0].own ? ac_fix_fwd_kernel<kStepBatch, true>
+                                           : ac_fix_fwd_kernel<kStepBatch, false>,
+                                  a, np, st);
 }
 
 void launch_ac_fix_bwd_batch(const AcFixArgs* a, int np, cudaStream_t st) {
-  launch_fix_batch<fix_bwd_split>(ac_fix_bwd_kernel<kStepBatch>, a, np, st);
+  if (np <= 0) return;
+  launch_fix_batch<fix_bwd_split>(a[0].own ? ac_fix_bwd_kernel<kStepBatch, true>
+                                           : ac_fix_bwd_kernel<kStepBatch, false>,
+                                  a, np, st);
 }
 
 }  // namespace sweep

@@ -28,6 +28,16 @@ constexpr int ZCH_B = 4;    // rows per thread, backward z part
 __device__ __forceinline__ float4 ldg4(const float* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
 }
+// The 9-point weights of d2 and d1 (acoustic_common.cuh) by offset k - 4.
+__host__ __device__ constexpr float kD2w(int k) {
+  return k == 4 ? kC0 : (k == 3 || k == 5) ? kC1 : (k == 2 || k == 6) ? kC2
+       : (k == 1 || k == 7) ? kC3 : kC4;
+}
+__host__ __device__ constexpr float kD1w(int k) {
+  return k == 4 ? 0.f : k == 5 ? kD1 : k == 6 ? kD2 : k == 7 ? kD3 : k == 8 ? kD4
+       : k == 3 ? -kD1 : k == 2 ? -kD2 : k == 1 ? -kD3 : -kD4;
+}
+
 // field loads: non-coherent (NC) or coherent
 template <bool NC>
 __device__ __forceinline__ float ldf(const float* p) {
@@ -50,6 +60,21 @@ __device__ __forceinline__ void st4(float* p, const float* v) {
 __device__ __forceinline__ void red4(float* p, const float* v) {
   atomicAdd(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
 }
+// Deterministic mode: only the nonzero terms are added.  An atomic float
+// addition flushes a subnormal result to zero, so an added 0.0 would change
+// a tiny value of a cell that gets no CPML term (an interior cell of a group
+// straddling the border), and a receiver read in the same kernel could see
+// the cell before or after it.
+__device__ __forceinline__ void red4_nonzero(float* p, const float* v) {
+  if (v[0] != 0.f && v[1] != 0.f && v[2] != 0.f && v[3] != 0.f) {
+    red4(p, v);
+    return;
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    if (v[c] != 0.f) atomicAdd(p + c, v[c]);
+}
+
 // 12 cells x-4 .. x+7 of a row (zero outside [0, NXp))
 template <bool NC>
 __device__ __forceinline__ void ldrow12(const float* row, int x, int NXp, float* e) {
@@ -75,6 +100,18 @@ __host__ __device__ __forceinline__ XBands x_bands(int lo_end, int hi_start, int
   if (b.gr0 < b.gl) b.gr0 = b.gl;
   b.ngr = b.gl + (NX + 3) / 4 - b.gr0;
   return b;
+}
+
+// Columns of the x part's 4-cell groups.  Deterministic mode (OWN; the
+// problem flag SWEEP_F_DETERMINISTIC): each border cell has one owner, the x
+// part owning every cell of its columns (in the rows of the z band too,
+// where it adds both axes' terms) and the z part the other columns of the z
+// band, and the backward stencil kernel injects the residual; so every cell
+// receives at most one addition per step, and the results do not depend on
+// the order in which blocks run.  Otherwise a corner cell of the border
+// takes the z and the x part's additions in either order.
+__device__ __forceinline__ bool x_group_col(const AcFixArgs& a, int x) {
+  return x < 4 * a.xb.gl || x >= 4 * a.xb.gr0;
 }
 
 // Work split: block b of the grid belongs to shot b / bps (bps = blocks per
@@ -137,12 +174,13 @@ __device__ __forceinline__ void fwd_z_chunk(const AcFixArgs& a, size_t so, int x
   }
 }
 
-template <bool NC>
+template <bool NC, bool OWN>
 __device__ __forceinline__ void fwd_z(const AcFixArgs& a, int s, int bl) {
   const Geom& g = a.g;
   const int ch = bl / a.zbx;
   const int x = (bl - ch * a.zbx) * FT + ftid();
   if (x >= g.NX) return;
+  if (OWN && x_group_col(a, x)) return;  // the x part owns those columns
   constexpr int ZCH = ZCH_F;
   const int nch = (g.P + ZCH - 1) / ZCH;  // chunks per strip
   const int strip = ch >= nch ? 1 : 0;
@@ -156,7 +194,7 @@ __device__ __forceinline__ void fwd_z(const AcFixArgs& a, int s, int bl) {
     fwd_z_chunk<NC, false>(a, so, x, zs, ze);
 }
 
-template <bool NC>
+template <bool NC, bool OWN>
 __device__ __forceinline__ void fwd_x_group(const AcFixArgs& a, int s, int z, int x) {
   const Geom& g = a.g;
   const size_t ro = (size_t)s * g.fstride + z * g.NXp;
@@ -183,8 +221,46 @@ __device__ __forceinline__ void fwd_x_group(const AcFixArgs& a, int s, int z, in
   }
   st4(a.pxout + ro + x, po);
   st4(a.zxout + ro + x, zo);
+  if (OWN && z_border(g, z)) {
+    // a row of the z strip: this group also owns its cells' z terms (the
+    // z part's arithmetic, as sums streamed over the 9 rows, 4 columns at
+    // a time)
+    const float Az = __ldg(a.az + z), Bz = __ldg(a.bz + z);
+    float d2u[4] = {0.f, 0.f, 0.f, 0.f}, d1u[4] = {0.f, 0.f, 0.f, 0.f};
+    float dp[4] = {0.f, 0.f, 0.f, 0.f}, pc[4] = {0.f, 0.f, 0.f, 0.f};
+    const size_t so = (size_t)s * g.fstride + x;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int zz = z - 4 + k;
+      if (zz < 0 || zz >= g.NZ) continue;  // zero outside the grid
+      float w[4], p[4];
+      f4a(ldf4<NC>(a.u + so + (size_t)zz * g.NXp), w);
+      f4a(ldf4<NC>(a.pzin + so + (size_t)zz * g.NXp), p);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        d2u[c] += kD2w(k) * w[c];
+        d1u[c] += kD1w(k) * w[c];
+        dp[c] += kD1w(k) * p[c];
+        if (k == 4) pc[c] = p[c];
+      }
+    }
+    float zt4[4], pzo[4], zzo[4];
+    f4a(ld4(a.zzin + ro + x), zt4);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float zn = Az * zt4[c] + Bz * (d2u[c] + dp[c]);
+      pzo[c] = Az * pc[c] + Bz * d1u[c];
+      zzo[c] = zn;
+      if (x + c < g.NX) du[c] += kk[c] * (dp[c] + zn);
+    }
+    st4(a.pzout + ro + x, pzo);
+    st4(a.zzout + ro + x, zzo);
+  }
   grid_dep_wait();  // the addition lands on the stencil kernel's output
-  red4(a.un + ro + x, du);
+  if constexpr (OWN)
+    red4_nonzero(a.un + ro + x, du);
+  else
+    red4(a.un + ro + x, du);
 }
 
 // (row, group) pair t of the x part: row t / ngr, group t % ngr of the two
@@ -197,10 +273,10 @@ __device__ __forceinline__ bool x_pair(const AcFixArgs& a, int bl, int* z, int* 
   return r < a.g.NZ;
 }
 
-template <bool NC>
+template <bool NC, bool OWN>
 __device__ __forceinline__ void fwd_x(const AcFixArgs& a, int s, int bl) {
   int z, x;
-  if (x_pair(a, bl, &z, &x)) fwd_x_group<NC>(a, s, z, x);
+  if (x_pair(a, bl, &z, &x)) fwd_x_group<NC, OWN>(a, s, z, x);
 }
 
 __device__ __forceinline__ void fwd_rec(const AcFixArgs& a, int s, int bl) {
@@ -312,12 +388,13 @@ __device__ __forceinline__ void bwd_z_chunk(const AcFixArgs& a, size_t so, int x
   }
 }
 
-template <bool NC>
+template <bool NC, bool OWN>
 __device__ __forceinline__ void bwd_z(const AcFixArgs& a, int s, int bl) {
   const Geom& g = a.g;
   const int ch = bl / a.zbx;
   const int x = (bl - ch * a.zbx) * FT + ftid();
   if (x >= g.NX) return;
+  if (OWN && x_group_col(a, x)) return;  // the x part owns those columns
   const int lo_end = band_lo_end(g.P, g.NZ), hi_start = band_hi_start(g.P, g.nz, g.NZ);
   constexpr int ZCH = ZCH_B;
   const int nlo = (lo_end + ZCH - 1) / ZCH;
@@ -334,7 +411,7 @@ __device__ __forceinline__ void bwd_z(const AcFixArgs& a, int s, int bl) {
     bwd_z_chunk<NC, false>(a, so, x, zs, ze);
 }
 
-template <bool NC>
+template <bool NC, bool OWN>
 __device__ __forceinline__ void bwd_x_group(const AcFixArgs& a, int s, int z, int x) {
   const Geom& g = a.g;
   const size_t ro = (size_t)s * g.fstride + z * g.NXp;
@@ -370,16 +447,69 @@ __device__ __forceinline__ void bwd_x_group(const AcFixArgs& a, int s, int z, in
   }
   st4(a.pxout + ro + x, po);
   st4(a.zxout + ro + x, zo);
+  if (OWN && (z < band_lo_end(g.P, g.NZ) || z >= band_hi_start(g.P, g.nz, g.NZ))) {
+    // a row of the z band: this group also owns its cells' z terms (the
+    // z part's arithmetic, as sums streamed over the 9 rows, 4 columns at
+    // a time)
+    const bool zb = z_border(g, z);
+    float sC[4] = {0.f, 0.f, 0.f, 0.f}, sB[4] = {0.f, 0.f, 0.f, 0.f};
+    float sG[4] = {0.f, 0.f, 0.f, 0.f}, mz[4] = {0.f, 0.f, 0.f, 0.f};
+    float p4[4] = {0.f, 0.f, 0.f, 0.f};
+    const size_t so = (size_t)s * g.fstride + x;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int zz = z - 4 + k;
+      if (zz < 0 || zz >= g.NZ) continue;  // zero outside the grid
+      float m[4], zv[4], pv[4];
+      const size_t o = so + (size_t)zz * g.NXp;
+      f4a(ldf4<NC>(a.u + o), m);
+      f4a(ldf4<NC>(a.zzin + o), zv);
+      f4a(ldf4<NC>(a.pzin + o), pv);
+      const float b = __ldg(a.bz + zz);
+      const bool gb = z_border(g, zz);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float Cv = b * (m[c] + zv[c]);
+        sC[c] += kD2w(k) * Cv;
+        sB[c] += kD1w(k) * (b * pv[c]);
+        sG[c] += gb ? kD1w(k) * (m[c] + Cv) : 0.f;
+        if (k == 4) {
+          mz[c] = m[c] + zv[c];
+          p4[c] = pv[c];
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (x + c < g.NX) du[c] += kk[c] * (sC[c] - sB[c]);
+    if (zb) {
+      const float Az = __ldg(a.az + z);
+      float pzo[4], zzo[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        pzo[c] = Az * p4[c] - sG[c];
+        zzo[c] = Az * mz[c];
+      }
+      st4(a.pzout + ro + x, pzo);
+      st4(a.zzout + ro + x, zzo);
+    }
+  }
   grid_dep_wait();  // mu^n is the stencil kernel's output
-  red4(a.un + ro + x, du);
+  if constexpr (OWN)
+    red4_nonzero(a.un + ro + x, du);
+  else
+    red4(a.un + ro + x, du);
 }
 
-template <bool NC>
+template <bool NC, bool OWN>
 __device__ __forceinline__ void bwd_x(const AcFixArgs& a, int s, int bl) {
   int z, x;
-  if (x_pair(a, bl, &z, &x)) bwd_x_group<NC>(a, s, z, x);
+  if (x_pair(a, bl, &z, &x)) bwd_x_group<NC, OWN>(a, s, z, x);
 }
 
+
+// residual injection mu^n(r) += K(r) res^{n-1}(r) (outside deterministic
+// mode; there the stencil kernel injects it)
 __device__ __forceinline__ void bwd_rec(const AcFixArgs& a, int s, int bl) {
   const Geom& g = a.g;
   const int r = bl * FT + ftid();

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
     fwd_body<IN_BZ, true>(a, c, bx, G, T, desc, utab, smem_raw);
 }
 
-template <int NP>
+template <int NP, bool INJ>
 __global__ void __launch_bounds__(BWD_THREADS, 1)
     ac_in_bwd_kernel(const __grid_constant__ StepBatch<AcInBwdArgs, NP> m) {
   int bx, G;  // this CTA's index and the CTA count of its problem
@@ -49,12 +49,65 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
   __shared__ UnitDesc utab[kUnitTable];
   const StepCtl c{a.n, a.do_adj, a.do_img, a.do_rec};
   if (a.bz == IN_BZ_SMALL)  // uniform over the CTA: one problem per CTA
-    bwd_body<IN_BZ_SMALL, true>(a, c, bx, G, T, desc, utab, smem_raw);
+    bwd_body<IN_BZ_SMALL, true, INJ>(a, c, bx, G, T, desc, utab, smem_raw);
   else
-    bwd_body<IN_BZ, true>(a, c, bx, G, T, desc, utab, smem_raw);
+    bwd_body<IN_BZ, true, INJ>(a, c, bx, G, T, desc, utab, smem_raw);
+}
+
+// Receiver lists of the backward units, one block per shot: for each tile
+// (in chunks of the block's threads) the count of the shot's receivers in it,
+// an exclusive scan over the tiles, then each tile's receivers in receiver
+// order.  Every receiver lies in exactly one tile, so shot s's entries fill
+// rlist[s nrec, (s + 1) nrec).
+constexpr int kRecThreads = 256;
+__global__ void __launch_bounds__(kRecThreads) rec_tiles_kernel(const Geom g,
+                                                                const int32_t* rec, int bz,
+                                                                int ntx, int2* rtile,
+                                                                int4* rlist) {
+  __shared__ int scan[kRecThreads];
+  const int s = blockIdx.x, S = g.nshot;
+  const int ntz = (g.NZ + bz - 1) / bz, T = ntz * ntx;
+  const int32_t* r = rec + 2 * (size_t)s * g.nrec;
+  int carry = 0;
+  for (int t0 = 0; t0 < T; t0 += kRecThreads) {
+    const int t = t0 + threadIdx.x;
+    const int z0 = (t / ntx) * bz, x0 = (t % ntx) * IN_BX;
+    int cnt = 0;
+    if (t < T)
+      for (int i = 0; i < g.nrec; ++i) {
+        const int rz = r[2 * i] + g.P, rx = r[2 * i + 1] + g.P;
+        cnt += rz >= z0 && rz < z0 + bz && rx >= x0 && rx < x0 + IN_BX;
+      }
+    scan[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int d = 1; d < kRecThreads; d <<= 1) {  // inclusive scan
+      const int v = threadIdx.x >= d ? scan[threadIdx.x - d] : 0;
+      __syncthreads();
+      scan[threadIdx.x] += v;
+      __syncthreads();
+    }
+    const int off = s * g.nrec + carry + scan[threadIdx.x] - cnt;
+    if (t < T) {
+      rtile[(size_t)t * S + s] = make_int2(off, cnt);
+      int k = 0;
+      for (int i = 0; i < g.nrec && k < cnt; ++i) {
+        const int rz = r[2 * i] + g.P, rx = r[2 * i + 1] + g.P;
+        if (rz >= z0 && rz < z0 + bz && rx >= x0 && rx < x0 + IN_BX)
+          rlist[off + k++] = make_int4(i, rz, rx, 0);
+      }
+    }
+    carry += scan[kRecThreads - 1];
+    __syncthreads();  // scan[] reused by the next chunk
+  }
 }
 
 }  // namespace
+
+void launch_rec_tiles(const Geom& g, const int32_t* rec, int bz, int ntx, int2* rtile,
+                      int4* rlist, cudaStream_t st) {
+  if (g.nshot <= 0 || g.nrec <= 0) return;
+  rec_tiles_kernel<<<g.nshot, kRecThreads, 0, st>>>(g, rec, bz, ntx, rtile, rlist);
+}
 
 int device_sms() {
   static const int n = [] {  // thread-safe one-time initialisation
@@ -75,10 +128,10 @@ void set_fwd_attr() {
   }();
   (void)attr;
 }
-template <int NP>
+template <int NP, bool INJ>
 void set_bwd_attr() {
   static const bool attr = [] {  // thread-safe one-time initialisation
-    cudaFuncSetAttribute(ac_in_bwd_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(ac_in_bwd_kernel<NP, INJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kBwdSmem);
     return true;
   }();
@@ -100,13 +153,18 @@ void launch_ac_in_fwd(const AcInFwdArgs& a, cudaStream_t st) {
 
 void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st) {
   if (a.units <= 0) return;
-  set_bwd_attr<1>();
+  const bool inj = a.rtile != nullptr;
+  if (inj)
+    set_bwd_attr<1, true>();
+  else
+    set_bwd_attr<1, false>();
   int grid = device_sms();
   if (grid > a.units) grid = a.units;
   StepBatch<AcInBwdArgs, 1> m;
   m.p[0] = a;
   void* tok = profile_begin(SWEEP_K_AC_BWD_IN, st);
-  launch_dependent(ac_in_bwd_kernel<1>, dim3(grid), dim3(BWD_THREADS), kBwdSmem, st, m);
+  launch_dependent(inj ? ac_in_bwd_kernel<1, true> : ac_in_bwd_kernel<1, false>, dim3(grid),
+                   dim3(BWD_THREADS), kBwdSmem, st, m);
   profile_end(tok, st);
   note_launches(1);
 }
@@ -151,8 +209,15 @@ void launch_ac_in_fwd_batch(const AcInFwdArgs* a, int np, cudaStream_t st) {
 void launch_ac_in_bwd_batch(const AcInBwdArgs* a, int np, cudaStream_t st) {
   if (np <= 0) return;
   if (np > kStepBatch) return;
-  set_bwd_attr<kStepBatch>();
-  launch_in_batch(ac_in_bwd_kernel<kStepBatch>, a, np, BWD_THREADS, kBwdSmem, st);
+  bool inj = false;  // deterministic mode: the stencil kernel injects the residual
+  for (int i = 0; i < np; ++i) inj = inj || a[i].rtile != nullptr;
+  if (inj) {
+    set_bwd_attr<kStepBatch, true>();
+    launch_in_batch(ac_in_bwd_kernel<kStepBatch, true>, a, np, BWD_THREADS, kBwdSmem, st);
+  } else {
+    set_bwd_attr<kStepBatch, false>();
+    launch_in_batch(ac_in_bwd_kernel<kStepBatch, false>, a, np, BWD_THREADS, kBwdSmem, st);
+  }
 }
 
 }  // namespace sweep

@@ -233,9 +233,9 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
       const int s = blk / bps;
       const int p = blk - s * bps;
       if (p < a.nbz)
-        fwd_z<false>(a, s, p);
+        fwd_z<false, false>(a, s, p);
       else if (p < a.nbz + a.nbx)
-        fwd_x<false>(a, s, p - a.nbz);
+        fwd_x<false, false>(a, s, p - a.nbz);
       else if (p < a.nbz + a.nbx + a.nbr)
         fwd_rec(a, s, p - a.nbz - a.nbx);
       else
@@ -274,8 +274,10 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
       const AcInBwdArgs& a = L.p[i]->bin[n & 1];
       const StepCtl c{n, n >= 1, n <= nt - 1, n >= 1 && n <= nt - 1};
       const bool ok = S.bz[i] == IN_BZ_SMALL
-                          ? bwd_body<IN_BZ_SMALL, false>(a, c, b, G, S.T, S.desc, S.utab, smem_raw)
-                          : bwd_body<IN_BZ, false>(a, c, b, G, S.T, S.desc, S.utab, smem_raw);
+                          ? bwd_body<IN_BZ_SMALL, false, false>(a, c, b, G, S.T, S.desc,
+                                                                 S.utab, smem_raw)
+                          : bwd_body<IN_BZ, false, false>(a, c, b, G, S.T, S.desc, S.utab,
+                                                           smem_raw);
       if (!ok) {
         if (threadIdx.x == 0) abort_loop(L);
         return;
@@ -329,9 +331,9 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
       const int s = blk / bps;
       const int p = blk - s * bps;
       if (p < a.nbz)
-        bwd_z<false>(a, s, p);
+        bwd_z<false, false>(a, s, p);
       else if (p < a.nbz + a.nbx)
-        bwd_x<false>(a, s, p - a.nbz);
+        bwd_x<false, false>(a, s, p - a.nbz);
       else if (p < a.nbz + a.nbx + a.nbr)
         bwd_rec(a, s, p - a.nbz - a.nbx);
       else

@@ -115,12 +115,13 @@ enum : int {
   U_IMG = 1,   // meets the interior: imaging (backward)
   U_U1 = 4,    // needs u^{n+1} (reconstruction, backward)
   U_SRC = 8,   // holds the source cell
+  U_REC = 16,  // holds receivers (backward): their count is flags >> 8
 };
 struct UnitDesc {
   int s, z0, x0, flags;
   int sz, sx;  // source cell (padded coordinates)
   float fn;    // wavelet sample of this step (0 where not needed)
-  int pad;
+  int rec;     // U_REC: offset of the unit's receivers in rlist
 };
 // Descriptors of a CTA's first kUnitTable units are computed by all its
 // threads in the prologue; later units (large batches) are described by the
@@ -144,7 +145,7 @@ __device__ __forceinline__ UnitDesc make_desc(const Region& R, const Geom& g, co
   d.sz = si.sz;
   d.sx = si.sx;
   d.fn = si.fn;
-  d.pad = 0;
+  d.rec = 0;
   int f = 0;
   if (si.sz >= p.z0 && si.sz < p.z0 + bz && si.sx >= p.x0 && si.sx < p.x0 + IN_BX &&
       in_region(R, si.sz, si.sx))
@@ -152,6 +153,13 @@ __device__ __forceinline__ UnitDesc make_desc(const Region& R, const Geom& g, co
   if (ab) {
     const BwdFlags b = bwd_flags(g, img, c.do_rec != 0, p, bz);
     f |= (b.imgt ? U_IMG : 0) | (b.needu1 ? U_U1 : 0);
+    if (ab->rtile && c.do_adj) {
+      const int2 oc = ab->rtile[unit];
+      if (oc.y > 0) {
+        f |= U_REC | (oc.y << 8);
+        d.rec = oc.x;
+      }
+    }
   }
   d.flags = f;
   return d;
@@ -297,7 +305,9 @@ __device__ __forceinline__ bool fwd_body(const AcInFwdArgs& a, const StepCtl& c,
 }
 
 // -------------------------------------------------------------- backward
-template <int BZ, bool PDL>
+// INJ: deterministic mode, the adjoint warps inject the residual at the
+// unit's receivers (a.rtile / a.rlist) instead of the CPML kernel.
+template <int BZ, bool PDL, bool INJ>
 __device__ __forceinline__ bool bwd_body(const AcInBwdArgs& a, const StepCtl& c, int bx, int G,
                                          ShotTable& T, UnitDesc* desc, UnitDesc* utab,
                                          unsigned char* smem_raw) {
@@ -380,7 +390,50 @@ __device__ __forceinline__ bool bwd_body(const AcInBwdArgs& a, const StepCtl& c,
     const long long so = (long long)d.s * g.fstride;
     if (adj_warp) {
       if (adj) {
-        // mu^n = 2 mu^{n+1} - mu^{n+2} + K Lap mu^{n+1}
+        // mu^n = 2 mu^{n+1} - mu^{n+2} + K Lap mu^{n+1} + K R^T r^{n-1}: the
+        // residual of this warp's receivers gathered first, in receiver
+        // order (a cell holding two receivers takes both)
+        float inj[RPW][4];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q)
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) inj[q][cc] = 0.f;
+        if (INJ && (d.flags & U_REC)) {
+          // the unit's receivers 32 at a time, one per lane; those in this
+          // warp's rows are handed to the lane owning their column, in list
+          // order (a cell holding two receivers takes both, always in the
+          // same order)
+          const int cnt = d.flags >> 8;
+          const int4* rl = a.rlist + d.rec;
+          for (int j0 = 0; j0 < cnt; j0 += 32) {
+            const int j = j0 + lane;
+            int qr = -1, cr = 0;
+            float v = 0.f;
+            if (j < cnt) {
+              const int4 e = rl[j];  // (receiver, z, x)
+              qr = e.y - (d.z0 + r0);
+              cr = e.z - d.x0;
+              if (qr >= 0 && qr < RPW)
+                v = a.res[((long long)d.s * g.nrec + e.x) * g.nt + (c.n - 1)];
+              else
+                qr = -1;
+            }
+            unsigned todo = __ballot_sync(0xffffffffu, qr >= 0);
+            while (todo) {
+              const int src = __ffs(todo) - 1;
+              todo &= todo - 1;
+              const int q2 = __shfl_sync(0xffffffffu, qr, src);
+              const int c2 = __shfl_sync(0xffffffffu, cr, src);
+              const float v2 = __shfl_sync(0xffffffffu, v, src);
+              const float add = (c2 >> 2) == lane ? v2 : 0.f;  // the owning lane's
+#pragma unroll
+              for (int q = 0; q < RPW; ++q)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc)
+                  inj[q][cc] += (q == q2 && cc == (c2 & 3)) ? add : 0.f;
+            }
+          }
+        }
         float wm[9][4];
 #pragma unroll
         for (int j = 0; j < 8; ++j) f4a(lds4(sg.ma, IN_HW, r0 + j, lx + 4), wm[j]);
@@ -404,6 +457,7 @@ __device__ __forceinline__ bool bwd_body(const AcInBwdArgs& a, const StepCtl& c,
                   d2(wm[0][c], wm[1][c], wm[2][c], wm[3][c], wm[4][c], wm[5][c], wm[6][c],
                      wm[7][c], wm[8][c]);
               out[c] = 2.f * wm[4][c] - m2[c] + kk[c] * lap;
+              if (INJ && (d.flags & U_REC)) out[c] += kk[c] * inj[q][c];
             }
             *reinterpret_cast<float4*>(a.mB + so + (long long)gz * g.NXp + gx) =
                 make_float4(out[0], out[1], out[2], out[3]);

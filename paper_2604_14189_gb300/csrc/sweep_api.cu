@@ -123,6 +123,7 @@ struct Layout {
   size_t el_a = 0, el_e[4] = {0, 0, 0, 0}, el_g = 0, el_ck = 0, el_seg = 0;
   int el_C = 0, el_ncp = 0;
   size_t loop = 0, loopbar = 0;   // acoustic time-loop arguments, barrier words
+  size_t rtile = 0, rlist = 0;    // receiver lists of the backward stencil units
   size_t fwd_lo = 0, fwd_hi = 0;  // contiguous range of forward fields
   size_t adj_lo = 0, adj_hi = 0;  // contiguous range of adjoint fields
   size_t total = 0;
@@ -168,8 +169,8 @@ bool valid_problem(const sweep_problem* p) {
   if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return false;
   if (!(p->f_ref >= 0.f) || !std::isfinite(p->f_ref)) return false;
   if (!std::isfinite(p->v_pml)) return false;
-  if (p->flags &
-      ~(SWEEP_F_PADDED_MODEL | SWEEP_F_RESIDUAL_IN | SWEEP_F_ROWS16 | SWEEP_F_ONE_LAUNCH))
+  if (p->flags & ~(SWEEP_F_PADDED_MODEL | SWEEP_F_RESIDUAL_IN | SWEEP_F_ROWS16 |
+                   SWEEP_F_ONE_LAUNCH | SWEEP_F_DETERMINISTIC))
     return false;  // unknown bits
   // keep every index within one shot's field (z * NXp + x, on the padded
   // row pitch) and the count of (tile, shot) units within 32 bits
@@ -242,6 +243,11 @@ Layout layout(const sweep_problem* p, int mode) {
     L.fwd_hi = b.off;
   }
   if (mode == SWEEP_MODE_ADJOINT || mode == SWEEP_MODE_GRADIENT) {
+    // units of the smaller tile height bound those of either
+    const size_t units = (size_t)((g.NZ + IN_BZ_SMALL - 1) / IN_BZ_SMALL) *
+                         ((g.NXp + IN_BX - 1) / IN_BX) * (size_t)g.nshot;
+    L.rtile = b.take(sizeof(int2) * units);
+    L.rlist = b.take(sizeof(int4) * (size_t)g.nshot * g.nrec);
     L.adj_lo = b.off;
     L.m[0] = b.take(F);
     L.m[1] = b.take(F);
@@ -328,6 +334,11 @@ bool map2(CUtensorMap* m, const Geom& g, const float* base, uint32_t bx, uint32_
   return make_tensor_map(m, base, 2, g.NX, g.NZ, 1, g.NXp, (uint64_t)g.fstride, bx, bz, 1);
 }
 
+// Deterministic mode of a problem: one writer per border cell and phase.
+bool deterministic(const sweep_problem* p) {
+  return (p->flags & SWEEP_F_DETERMINISTIC) != 0;
+}
+
 // Rows of the acoustic stencil tiles of a problem.
 int tile_rows(const sweep_problem* p) {
   return (p->flags & SWEEP_F_ROWS16) ? IN_BZ_SMALL : IN_BZ;
@@ -389,6 +400,7 @@ struct AcFwdLoop {
     fx.zxin = fx.zxout = at<float>(ws, L->zex);
     fx.rec = rec;
     fx.data = data;
+    fx.own = deterministic(p);
     fx.status = status;
     return SWEEP_OK;
   }
@@ -432,8 +444,9 @@ int acoustic_forward_loop(const sweep_problem* p, const Layout& L, void* ws,
 // Backward loop: adjoint propagation from the residual `res`; optionally the
 // imaging condition with wavefield reconstruction (gradient) and/or the
 // adjoint source gather (wgrad).  Per step the plain kernel over the whole
-// grid, then one kernel adding both axes' CPML terms of mu^n and the
-// residual injection, and restoring the ring of u^{n-1}.  Steps run
+// grid (it also injects the residual at the receivers, from per-unit
+// receiver lists built once per call), then one kernel adding both axes'
+// CPML terms of mu^n and restoring the ring of u^{n-1}.  Steps run
 // n = nt .. 0; AcBwdLoop::step(n) fills the arguments of step n and says
 // which of the two kernels run.
 struct AcBwdLoop {
@@ -481,6 +494,15 @@ struct AcBwdLoop {
     in.src = src;
     in.wgrad = wg;
     in.status = status;
+    const bool own = deterministic(p);
+    if (own && res && g.nrec > 0) {  // the stencil kernel injects the residual
+      in.res = res;
+      in.rtile = at<int2>(ws, L->rtile);
+      in.rlist = at<int4>(ws, L->rlist);
+      launch_rec_tiles(g, rec, in.bz, in.ntx, const_cast<int2*>(in.rtile),
+                       const_cast<int4*>(in.rlist), st);
+      note_launches(1);
+    }
     fx.g = g;
     fx.K = at<float>(ws, L->K);
     fx.ax = at<float>(ws, L->ax);
@@ -488,7 +510,8 @@ struct AcBwdLoop {
     fx.az = at<float>(ws, L->az);
     fx.bz = at<float>(ws, L->bz);
     fx.rec = rec;
-    fx.res = g.nrec > 0 ? res : nullptr;
+    fx.res = (!own && g.nrec > 0) ? res : nullptr;
+    fx.own = own;
     fx.status = status;
     return SWEEP_OK;
   }
@@ -765,6 +788,10 @@ static int forward_group(const sweep_problem* const* P, const float* const* mode
 static bool one_launch(const sweep_problem* p) {
   return p->physics == SWEEP_ACOUSTIC && (p->flags & SWEEP_F_ONE_LAUNCH);
 }
+// the time-loop kernels run the default mode only
+static bool unsupported_combination(const sweep_problem* p) {
+  return one_launch(p) && deterministic(p);
+}
 
 int sweep_forward(const sweep_problem* p, const float* model, const float* wavelet,
                   const int32_t* src, const int32_t* rec, float* data, void* ws,
@@ -773,6 +800,7 @@ int sweep_forward(const sweep_problem* p, const float* model, const float* wavel
   if (!valid_problem(p) || !model) return SWEEP_EINVAL;
   if (p->nshot > 0 && (!wavelet || !src)) return SWEEP_EINVAL;
   if (p->nshot > 0 && p->nrec > 0 && (!rec || !data)) return SWEEP_EINVAL;
+  if (unsupported_combination(p)) return SWEEP_EUNSUPPORTED;
   int rc = begin(p, SWEEP_MODE_FORWARD, ws, ws_bytes, st);
   if (rc) return rc;
   if (p->nshot == 0) return SWEEP_OK;
@@ -835,6 +863,7 @@ int sweep_gradient(const sweep_problem* p, const float* model, const float* wave
   if (p->nshot > 0 && p->nrec > 0 && (!rec || !d_obs)) return SWEEP_EINVAL;
   if (p->physics == SWEEP_ELASTIC && illum) return SWEEP_EUNSUPPORTED;
   if (one_launch(p) && illum) return SWEEP_EUNSUPPORTED;
+  if (unsupported_combination(p)) return SWEEP_EUNSUPPORTED;
   int rc = begin(p, SWEEP_MODE_GRADIENT, ws, ws_bytes, st);
   if (rc) return rc;
   const Geom g = make_geom(p);
@@ -1097,7 +1126,9 @@ int sweep_forward_batch(int nprob, const sweep_problem* probs, const float* cons
     const sweep_problem* p = &probs[i];
     if (!valid_problem(p)) return SWEEP_EINVAL;
     if (p->physics != SWEEP_ACOUSTIC) return SWEEP_EUNSUPPORTED;
-    if ((p->flags ^ probs[0].flags) & SWEEP_F_ONE_LAUNCH) return SWEEP_EINVAL;
+    if ((p->flags ^ probs[0].flags) & (SWEEP_F_ONE_LAUNCH | SWEEP_F_DETERMINISTIC))
+      return SWEEP_EINVAL;  // the problems of one launch share these modes
+    if (unsupported_combination(p)) return SWEEP_EUNSUPPORTED;
     const int rc = check_ws(p, SWEEP_MODE_FORWARD, ws[i], ws_bytes[i]);
     if (rc) return rc;
     if (!models[i]) return SWEEP_EINVAL;
@@ -1137,7 +1168,9 @@ int sweep_gradient_batch(int nprob, const sweep_problem* probs, const float* con
     const sweep_problem* p = &probs[i];
     if (!valid_problem(p)) return SWEEP_EINVAL;
     if (p->physics != SWEEP_ACOUSTIC) return SWEEP_EUNSUPPORTED;
-    if ((p->flags ^ probs[0].flags) & SWEEP_F_ONE_LAUNCH) return SWEEP_EINVAL;
+    if ((p->flags ^ probs[0].flags) & (SWEEP_F_ONE_LAUNCH | SWEEP_F_DETERMINISTIC))
+      return SWEEP_EINVAL;  // the problems of one launch share these modes
+    if (unsupported_combination(p)) return SWEEP_EUNSUPPORTED;
     const int rc = check_ws(p, SWEEP_MODE_GRADIENT, ws[i], ws_bytes[i]);
     if (rc) return rc;
     if (!models[i] || !grads[i] || !misfits[i]) return SWEEP_EINVAL;

@@ -71,6 +71,14 @@ struct AcInBwdArgs {
   const float* wavelet;
   const int32_t* src;
   float* wgrad;      // [S][nt] or null
+  // receiver injection mu^n(r) += K(r) res^{n-1}(r), done by the stencil
+  // kernel while it forms mu^n (so that each cell has one writer per
+  // phase): per (tile, shot) unit its receivers' (offset, count) in rlist,
+  // entries (receiver index, z, x) in padded coordinates, receiver order.
+  // Null when there is no residual.
+  const float* res;  // [S][nrec][nt]
+  const int2* rtile; // [units]
+  const int4* rlist; // [S * nrec]
   int* status;
   int n;
   int do_adj, do_img, do_rec;
@@ -86,7 +94,9 @@ struct AcInBwdArgs {
 // save = ring slot that receives the ring cells of u^n (gradient mode).
 // Backward: u = mu^{n+1}, un = mu^n, p*in/p*out = psibar^n/^{n-1},
 // z*in/z*out = zetabar^n/^{n-1}, res = residual injected at the receivers
-// (mu^n(r) += K(r) res[n-1]), save/uring = ring restore of u^{n-1}.
+// (mu^n(r) += K(r) res[n-1]; in deterministic mode the backward stencil
+// kernel injects it instead), save/uring = ring restore of u^{n-1}.
+// own: deterministic mode (one owner per border cell).
 struct XBands {  // 4-cell column groups: left [0, gl), right [gr0, ceil(NX/4))
   int gl, gr0, ngr;
 };
@@ -109,7 +119,8 @@ struct AcFixArgs {
   const float* bz;
   const int32_t* rec;
   float* data;
-  const float* res;
+  const float* res;  // backward: residual injected here (null: the stencil
+                     // kernel injects it, deterministic mode)
   float* save;       // forward: ring slot of u^n; backward: ring slot of u^{n-1}
   float* uring;      // backward: the u^{n-1} field whose ring is restored
   const int* status;
@@ -119,6 +130,7 @@ struct AcFixArgs {
   int nbz, nbx, nbr, nbs;
   int zbx, nchz;
   XBands xb;
+  int own;
 };
 void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st);
 void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st);
@@ -164,6 +176,10 @@ void launch_ac_in_bwd(const AcInBwdArgs& a, cudaStream_t st);
 void launch_ac_in_fwd_batch(const AcInFwdArgs* a, int np, cudaStream_t st);
 void launch_ac_in_bwd_batch(const AcInBwdArgs* a, int np, cudaStream_t st);
 int device_sms();
+// Receiver lists of the backward stencil launch's units (acoustic_interior.cu):
+// for tiles of bz rows x IN_BX cells (ntx along x), unit u = tile * S + s.
+void launch_rec_tiles(const Geom& g, const int32_t* rec, int bz, int ntx, int2* rtile,
+                      int4* rlist, cudaStream_t st);
 
 // Time-loop kernels (acoustic_loop.cu): one cooperative launch runs every
 // forward (or backward) step of up to kStepBatch problems, each step as a

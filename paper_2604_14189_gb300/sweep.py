@@ -25,6 +25,7 @@ F_PADDED_MODEL = 0x1
 F_RESIDUAL_IN = 0x2
 F_ROWS16 = 0x4
 F_ONE_LAUNCH = 0x8
+F_DETERMINISTIC = 0x10
 
 OK = 0
 EINVAL, ECFL, EBOUNDS, EWORKSPACE, ECUDA, ETIMEOUT, ENONFINITE, EMODEL, EUNSUPPORTED = (

@@ -102,7 +102,7 @@ def test_workspace_size_and_validation():
                 dict(nz=20000, nx=20000, pml=0, nshot=65535),
                 dict(nshot=65536),
                 # a flag bit the library does not define
-                dict(flags=0x10), dict(flags=-1)):
+                dict(flags=0x20), dict(flags=-1)):
         q = _prob(sweep, **bad)
         assert sweep.lib().sweep_workspace_bytes(ctypes.byref(q), 0) == 0, bad
     assert sweep.lib().sweep_workspace_bytes(ctypes.byref(p), 7) == 0
@@ -211,6 +211,30 @@ def test_one_launch_flag_rules():
     sizes = (ctypes.c_size_t * 2)(1 << 40, 1 << 40)
     assert L.sweep_forward_batch(2, probs, ptrs, ptrs, ptrs, ptrs, ptrs, ptrs, sizes,
                                  None) == sweep.EINVAL
+
+
+def test_deterministic_flag_rules():
+    """SWEEP_F_DETERMINISTIC: same workspace; refused with the time-loop
+    kernels; a batch whose problems disagree on it is refused."""
+    from paper_2604_14189_gb300 import sweep
+    L = sweep.lib()
+    p = _prob(sweep)
+    d = _prob(sweep, flags=sweep.F_DETERMINISTIC)
+    for mode in (0, 1, 2):
+        assert (L.sweep_workspace_bytes(ctypes.byref(d), mode)
+                == L.sweep_workspace_bytes(ctypes.byref(p), mode))
+    both = _prob(sweep, flags=sweep.F_DETERMINISTIC | sweep.F_ONE_LAUNCH)
+    fake = ctypes.c_void_p(1 << 20)
+    big = ctypes.c_size_t(1 << 40)
+    assert L.sweep_forward(ctypes.byref(both), fake, fake, fake, fake, fake, fake, big,
+                           None) == sweep.EUNSUPPORTED
+    assert L.sweep_gradient(ctypes.byref(both), fake, fake, fake, fake, fake, fake, fake, None,
+                            fake, big, None) == sweep.EUNSUPPORTED
+    probs = (sweep.Problem * 2)(p, d)
+    ptrs = (ctypes.c_void_p * 2)(fake, fake)
+    sizes = (ctypes.c_size_t * 2)(1 << 40, 1 << 40)
+    assert L.sweep_gradient_batch(2, probs, ptrs, ptrs, ptrs, ptrs, ptrs, ptrs, ptrs, ptrs,
+                                  sizes, None) == sweep.EINVAL
 
 
 def test_binding_rejects_wrong_sizes_before_any_call():

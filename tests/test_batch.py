@@ -176,6 +176,41 @@ def test_batch_matches_individual_runs(count, fused):
 
 
 @pytest.mark.gpu
+def test_deterministic_batch_equals_individual_runs_bitwise():
+    """In deterministic mode the shared-launch cohort (9 uneven problems,
+    some in 16-row tiles) gives each problem's own gradient and misfit bit
+    for bit."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_14189_gb300 import inputs, sweep
+
+    rng = np.random.default_rng(19)
+    items, refs = [], []
+    dev = "cuda"
+    for k in range(9):
+        nz, nx = int(rng.integers(40, 90)), int(rng.integers(40, 120))
+        pml, nt, ns = int(rng.integers(8, 20)), int(rng.integers(150, 300)), int(rng.integers(1, 4))
+        v = np.clip(1800.0 + 900.0 * np.arange(nz)[:, None] / nz +
+                    80.0 * rng.standard_normal((nz, nx)), 1500.0, 3000.0)
+        src = np.stack([np.full(ns, 2), rng.integers(0, nx, ns)], -1).astype(np.int32)
+        rec = inputs.surface_line(ns, 2, np.arange(0, nx, 2))
+        flags = sweep.F_DETERMINISTIC | (sweep.F_ROWS16 if k % 3 == 0 else 0)
+        p = sweep.problem(nz=nz, nx=nx, pml=pml, dx=10.0, dt=1e-3, nt=nt, nshot=ns,
+                          nrec=rec.shape[1], f_ref=10.0, flags=flags)
+        w = torch.tensor(np.stack([inputs.ricker(10.0, 1e-3, nt)] * ns), dtype=torch.float32,
+                         device=dev)
+        vt = torch.tensor(v, dtype=torch.float32, device=dev)
+        st, rt = torch.tensor(src, device=dev), torch.tensor(rec, device=dev)
+        d_obs = sweep.sweep_forward(p, vt * 1.02, w, st, rt)
+        items.append(batch.Item(p, vt, w, st, rt, d_obs=d_obs))
+        g, J, _ = sweep.sweep_gradient(p, vt, w, st, rt, d_obs)
+        refs.append((g.clone(), float(J)))
+    assert batch.run(items, streams=2) == [0] * len(items)
+    for it, (g, J) in zip(items, refs):
+        assert torch.equal(it.grad, g) and float(it.misfit) == J
+
+
+@pytest.mark.gpu
 def test_forward_batch_matches_individual_runs():
     """Forward modelling of 19 uneven problems as cohorts sharing launches
     (a cohort of 16 and one of 3) equals each problem's own sweep_forward

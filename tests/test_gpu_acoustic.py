@@ -175,6 +175,47 @@ def test_16_row_tiles_match_oracle(sw, shape):
     assert abs(J16.item() - Jref) <= 1e-4 * nd * nr + 0.5e-8 * nd ** 2
 
 
+def test_deterministic_mode_is_bitwise_reproducible(sw):
+    """SWEEP_F_DETERMINISTIC: every cell has one writer per kernel phase (the
+    CPML x part owns the corners of the border band and adds both axes'
+    terms there; the backward stencil kernel injects the residual at the
+    receivers, in receiver order), so two identical runs give bitwise equal
+    seismograms, adjoint sources, gradients, misfits and illumination, in
+    both tile heights, and they meet the oracle like the default mode.
+    Receivers sit in the band rows, on the corners and twice on one cell.
+    (The two tile heights are separate instantiations whose compiled
+    arithmetic may contract differently, so they agree to FP32 rounding.)"""
+    c = case(70, 301, 20, 300, 3, 25, seed=77)
+    c["rec"][:, :6] = [[0, 0], [1, 300], [2, 2], [69, 0], [69, 300], [2, 2]]
+    ref = oracle.acoustic_forward(probs(sw, c)[1], f32(c["v"]), f32(c["w"]), c["src"],
+                                  c["rec"])
+    _, q = probs(sw, c)
+    v, w = cuda(c["v"]), cuda(c["w"])
+    src, rec = cuda(c["src"], torch.int32), cuda(c["rec"], torch.int32)
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal((c["nshot"], c["nrec"], c["nt"]))
+    wref = oracle.acoustic_adjoint(q, f32(c["v"]), f32(r), c["src"], c["rec"])
+    gref, _ = oracle.acoustic_gradient(q, f32(c["v"]), f32(c["w"]), c["src"], c["rec"],
+                                       f32(ref * 1.05))
+    results = {}
+    for rows16 in (False, True):
+        flags = sw.F_DETERMINISTIC | (sw.F_ROWS16 if rows16 else 0)
+        p, _ = probs(sw, dict(c, flags=flags))
+        d = [sw.sweep_forward(p, v, w, src, rec) for _ in range(2)]
+        assert torch.equal(d[0], d[1])
+        assert rel(d[0].cpu().numpy()[:, 0], ref) <= 1e-4
+        wg = [sw.sweep_adjoint(p, v, cuda(r), src, rec) for _ in range(2)]
+        assert torch.equal(wg[0], wg[1])
+        assert rel(wg[0].cpu().numpy(), wref) <= 1e-4
+        out = [sw.sweep_gradient(p, v, w, src, rec, cuda(ref * 1.05), want_illum=True)
+               for _ in range(2)]
+        assert all(torch.equal(a, b) for a, b in zip(out[0], out[1]))
+        assert rel(out[0][0].cpu().numpy(), gref) <= 1e-3
+        results[rows16] = (d[0], wg[0], out[0][0])
+    for a, b in zip(results[False], results[True]):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) <= 1e-5
+
+
 def test_gradient_residual_mode_and_illumination(sw):
     c = case(45, 60, 8, 260, 2, 5, seed=21, flags=0)
     p, q = probs(sw, c)

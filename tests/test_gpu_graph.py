@@ -132,3 +132,35 @@ def test_synchronising_call_breaks_capture(sw):
     s.synchronize()
     ref = sw.sweep_forward(p, t["model"], t["wavelet"], t["src"], t["rec"])
     assert close(out, ref)
+
+
+@pytest.mark.gpu
+def test_deterministic_graph_replay_is_bitwise_equal(sw):
+    """In deterministic mode a graph replay of sweep_gradient equals the
+    direct call bit for bit."""
+    nz, nx, pml, nt, ns = 50, 140, 12, 200, 3
+    rng = np.random.default_rng(12)
+    v = np.clip(1800.0 + 900.0 * np.arange(nz)[:, None] / nz + 80.0 *
+                rng.standard_normal((nz, nx)), 1500.0, 3000.0).astype(np.float32)
+    src = np.stack([np.full(ns, 2), rng.integers(0, nx, ns)], -1).astype(np.int32)
+    recs = np.stack([np.full((ns, 20), 2), np.tile(np.arange(0, nx, 7)[:20], (ns, 1))],
+                    -1).astype(np.int32)
+    p = sw.problem(nz=nz, nx=nx, pml=pml, dx=10.0, dt=1e-3, nt=nt, nshot=ns, nrec=20,
+                   f_ref=12.0, flags=sw.F_DETERMINISTIC)
+    dev = "cuda"
+    tv = torch.tensor(v, device=dev)
+    tw = torch.tensor(np.stack([inputs.ricker(12.0, 1e-3, nt)] * ns), dtype=torch.float32,
+                      device=dev)
+    ts, tr = torch.tensor(src, device=dev), torch.tensor(recs, device=dev)
+    d_obs = sw.sweep_forward(p, tv * 1.02, tw, ts, tr)
+    ws = sw.alloc_workspace(p, sw.MODE_GRADIENT)
+    g = torch.empty_like(tv)
+    J = torch.empty((), dtype=torch.float64, device=dev)
+    s = torch.cuda.Stream()
+    with sw.capture(s) as c:
+        sw.sweep_gradient(p, tv, tw, ts, tr, d_obs, grad=g, misfit=J, ws=ws, stream=s)
+    c.graph.launch(s)
+    s.synchronize()
+    gd, Jd, _ = sw.sweep_gradient(p, tv, tw, ts, tr, d_obs)
+    assert torch.equal(g, gd) and float(J) == float(Jd)
+    c.graph.close()
