@@ -243,12 +243,15 @@ __device__ __forceinline__ bool fwd_body(const AcInFwdArgs& a, const StepCtl& c,
   for (; k < count; ++k) {
     if constexpr (PDL)
       if (k == count - 1) grid_dep_trigger();  // the next kernel may start
+    // one CTA barrier per unit: each thread waits for the stage itself, and
+    // the barrier after the unit both releases the stage and agrees on a
+    // transfer that never landed
     const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
-    if (__syncthreads_or(!got)) break;
     const UnitDesc d = k < kUnitTable ? utab[k] : desc[k % D];
     const Stage& sg = stg[k % D];
     const long long so = (long long)d.s * g.fstride;
     const int gx = d.x0 + lx;
+    if (got) {
     float w[9][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) f4a(lds4(sg.u, IN_HW, r0 + j, lx + 4), w[j]);
@@ -286,7 +289,8 @@ __device__ __forceinline__ bool fwd_body(const AcInFwdArgs& a, const StepCtl& c,
         for (int c = 0; c < 4; ++c) w[j][c] = w[j + 1][c];
       }
     }
-    __syncthreads();  // stage released; this unit's stores visible to the CTA
+    }  // got
+    if (__syncthreads_or(!got)) break;  // stage released
     if (threadIdx.x == 0 && k + D < count) {
       fence_proxy_async_smem();
       issue(k + D);
@@ -384,11 +388,13 @@ __device__ __forceinline__ bool bwd_body(const AcInBwdArgs& a, const StepCtl& c,
     const UnitDesc d = k < kUnitTable ? utab[k] : desc[k % D];
     const bool imgt = d.flags & U_IMG, needu1 = d.flags & U_U1;
     const int gx = d.x0 + lx;
+    // one CTA barrier per unit (see the forward body)
     const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
-    if (__syncthreads_or(!got)) break;
     const Stage& sg = stg[k % D];
     const long long so = (long long)d.s * g.fstride;
-    if (adj_warp) {
+    if (!got) {
+      // a transfer never landed: the barrier below ends the loop
+    } else if (adj_warp) {
       if (adj) {
         // mu^n = 2 mu^{n+1} - mu^{n+2} + K Lap mu^{n+1} + K R^T r^{n-1}: the
         // residual of this warp's receivers gathered first, in receiver
@@ -543,10 +549,10 @@ __device__ __forceinline__ bool bwd_body(const AcInBwdArgs& a, const StepCtl& c,
       }
     }
     // adjoint source gather: f-bar^n = mu^{n+1}(s)
-    if (a.wgrad && threadIdx.x == 0 && c.n < g.nt && (d.flags & U_SRC))
+    if (got && a.wgrad && threadIdx.x == 0 && c.n < g.nt && (d.flags & U_SRC))
       a.wgrad[(long long)d.s * g.nt + c.n] =
           sg.ma[(d.sz - d.z0 + 4) * IN_HW + (d.sx - d.x0 + 4)];
-    __syncthreads();  // stage released; mu^n stores visible to this CTA
+    if (__syncthreads_or(!got)) break;  // stage released
     if (threadIdx.x == 0 && k + D < count) {
       fence_proxy_async_smem();
       issue(k + D);
