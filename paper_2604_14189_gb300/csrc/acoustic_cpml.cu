@@ -40,6 +40,7 @@ namespace {
 template <int NP, bool OWN>
 __global__ void __launch_bounds__(FT, 8)
     ac_fix_fwd_kernel(const __grid_constant__ StepBatch<AcFixArgs, NP> m) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];  // z blocks' windows
   int blk, nblk;  // this block's index and the block count of its problem
   const AcFixArgs& a = m.p[step_problem(m, &blk, &nblk)];
   grid_dep_trigger();
@@ -51,11 +52,11 @@ __global__ void __launch_bounds__(FT, 8)
   // write memory variables nothing else touches during the step; they wait
   // for the stencil kernel only before adding into its output.
   if (b < a.nbz + a.nbx) {
-    if (!*a.status) {
-      if (b < a.nbz)
-        fwd_z<true, OWN>(a, s, b);
-      else
-        fwd_x<true, OWN>(a, s, b - a.nbz);
+    if (b < a.nbz) {  // (the status test is made uniform: the block syncs inside)
+      if (!__syncthreads_or(threadIdx.x == 0 && *a.status != 0))
+        fwd_z_staged<OWN>(a, s, b, smem_raw);
+    } else if (!*a.status) {
+      fwd_x<true, OWN>(a, s, b - a.nbz);
     }
     // One thread always waits, so that this kernel never completes before
     // the stencil kernel does (the next step's kernels rely on that order).
@@ -146,7 +147,7 @@ void launch_ac_fix_fwd(AcFixArgs a, cudaStream_t st) {
   m.p[0] = a;
   void* tok = profile_begin(SWEEP_K_AC_FWD_FR, st);
   launch_dependent(a.own ? ac_fix_fwd_kernel<1, true> : ac_fix_fwd_kernel<1, false>,
-                   dim3(bps * a.g.nshot), dim3(FT), 0, st, m);
+                   dim3(bps * a.g.nshot), dim3(FT), kZStageF + 16, st, m);
   profile_end(tok, st);
   note_launches(1);
 }
@@ -164,7 +165,7 @@ void launch_ac_fix_bwd(AcFixArgs a, cudaStream_t st) {
 }
 
 template <int (*SPLIT)(AcFixArgs&), typename K>
-void launch_fix_batch(K kernel, const AcFixArgs* a, int np, cudaStream_t st) {
+void launch_fix_batch(K kernel, const AcFixArgs* a, int np, size_t smem, cudaStream_t st) {
   if (np <= 0 || np > kStepBatch) return;
   StepBatch<AcFixArgs, kStepBatch> m;
   m.start[0] = 0;
@@ -177,7 +178,7 @@ void launch_fix_batch(K kernel, const AcFixArgs* a, int np, cudaStream_t st) {
     m.start[i + 1] = m.start[i] + c;
   }
   if (m.start[kStepBatch] == 0) return;
-  launch_dependent(kernel, dim3(m.start[kStepBatch]), dim3(FT), 0, st, m);
+  launch_dependent(kernel, dim3(m.start[kStepBatch]), dim3(FT), smem, st, m);
   note_launches(1);
 }
 
@@ -187,14 +188,14 @@ void launch_ac_fix_fwd_batch(const AcFixArgs* a, int np, cudaStream_t st) {
   if (np <= 0) return;
   launch_fix_batch<fix_fwd_split>(a[0].own ? ac_fix_fwd_kernel<kStepBatch, true>
                                            : ac_fix_fwd_kernel<kStepBatch, false>,
-                                  a, np, st);
+                                  a, np, kZStageF + 16, st);
 }
 
 void launch_ac_fix_bwd_batch(const AcFixArgs* a, int np, cudaStream_t st) {
   if (np <= 0) return;
   launch_fix_batch<fix_bwd_split>(a[0].own ? ac_fix_bwd_kernel<kStepBatch, true>
                                            : ac_fix_bwd_kernel<kStepBatch, false>,
-                                  a, np, st);
+                                  a, np, 0, st);
 }
 
 }  // namespace sweep

@@ -10,6 +10,7 @@
 #pragma once
 
 #include "acoustic_common.cuh"
+#include "tma.cuh"
 
 namespace sweep {
 namespace {
@@ -22,8 +23,8 @@ namespace {
 // 64 and 72 registers without spills; unbounded, the backward kernel takes
 // 80 and one block per SM fewer fits.
 constexpr int FT = 128;     // threads per block
-constexpr int ZCH_F = 8;    // rows per thread, forward z part
-constexpr int ZCH_B = 4;    // rows per thread, backward z part
+constexpr int ZCH_F = ZCH_FWD;  // rows per thread, forward z part
+constexpr int ZCH_B = ZCH_BWD;  // rows per thread, backward z part
 
 __device__ __forceinline__ float4 ldg4(const float* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
@@ -192,6 +193,99 @@ __device__ __forceinline__ void fwd_z(const AcFixArgs& a, int s, int bl) {
     fwd_z_chunk<NC, true>(a, so, x, zs, ze);
   else
     fwd_z_chunk<NC, false>(a, so, x, zs, ze);
+}
+
+// Staged forward z chunk (the per-step kernel): the block's 128 columns of
+// one chunk, its row windows copied into shared memory by four TMA copies
+// (u and psi_z on rows zs-4 .. zs+ZCH+3, zeta_z and K on the chunk's rows;
+// rows outside the grid read as zero, as in fwd_z_chunk), then the same
+// arithmetic per column.  smem: kZStageF bytes + one mbarrier.
+constexpr int ZW_F = ZCH_F + 8;
+constexpr uint32_t kZStageF = (2 * ZW_F + 2 * ZCH_F) * FT * 4;
+
+// Issue a z block's copies and wait for them (bounded); false: gave up
+// (SWEEP_ETIMEOUT latched, copies drained).  All threads call it.
+template <int NCOPY>
+__device__ __forceinline__ bool z_stage(const AcFixArgs& a, uint64_t* bar, uint32_t bytes,
+                                        float* const (&dst)[NCOPY],
+                                        const CUtensorMap* const (&map)[NCOPY],
+                                        const int (&y)[NCOPY], int x0, int s) {
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+    mbar_arrive_expect_tx(bar, bytes);
+#pragma unroll
+    for (int i = 0; i < NCOPY; ++i) {
+      if (map[i] == &a.tzK)
+        tma_load_2d(dst[i], map[i], bar, x0, y[i]);
+      else
+        tma_load_3d(dst[i], map[i], bar, x0, y[i], s);
+    }
+  }
+  __syncthreads();  // the barrier is initialised before anyone waits on it
+  const bool got = mbar_wait(bar, 0);
+  if (__syncthreads_or(!got)) {
+    if (threadIdx.x == 0) {
+      latch(const_cast<int*>(a.status), SWEEP_ETIMEOUT);
+      mbar_wait(bar, 0);  // drain (bounded)
+    }
+    __syncthreads();
+    return false;
+  }
+  return true;
+}
+
+template <bool OWN>
+__device__ __forceinline__ void fwd_z_staged(const AcFixArgs& a, int s, int bl,
+                                             unsigned char* smem) {
+  const Geom& g = a.g;
+  const int ch = bl / a.zbx;
+  const int x0 = (bl - ch * a.zbx) * FT, t = ftid(), x = x0 + t;
+  constexpr int ZCH = ZCH_F, ZW = ZW_F;
+  const int nch = (g.P + ZCH - 1) / ZCH;  // chunks per strip
+  const int strip = ch >= nch ? 1 : 0;
+  const int base = strip ? g.P + g.nz : 0;
+  const int zs = base + (ch - strip * nch) * ZCH;
+  const int ze = min(zs + ZCH, base + g.P);
+  float* su = reinterpret_cast<float*>(smem);
+  float* sp = su + ZW * FT;
+  float* sz = sp + ZW * FT;
+  float* sk = sz + ZCH * FT;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sk + ZCH * FT);
+  float* const dst[4] = {su, sp, sz, sk};
+  const CUtensorMap* const map[4] = {&a.tzu, &a.tzp, &a.tzz, &a.tzK};
+  const int y[4] = {zs - 4, zs - 4, zs, zs};
+  if (!z_stage<4>(a, bar, kZStageF, dst, map, y, x0, s)) return;
+  if (x >= g.NX || (OWN && x_group_col(a, x))) return;  // (after the block's waits)
+  const size_t so = (size_t)s * g.fstride + x;
+  float corr[ZCH];
+#pragma unroll
+  for (int q = 0; q < ZCH; ++q) {
+    const int z = zs + q;
+    corr[q] = 0.f;
+    if (z >= ze) break;
+    const float A = __ldg(a.az + z), B = __ldg(a.bz + z);
+    float w[9], p[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      w[k] = su[(q + k) * FT + t];
+      p[k] = sp[(q + k) * FT + t];
+    }
+    const float d2u = d2(w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7], w[8]);
+    const float d1u = d1(w[0], w[1], w[2], w[3], w[5], w[6], w[7], w[8]);
+    const float dp = d1(p[0], p[1], p[2], p[3], p[5], p[6], p[7], p[8]);
+    const float zn = A * sz[q * FT + t] + B * (d2u + dp);
+    const size_t o = so + (size_t)z * g.NXp;
+    a.pzout[o] = A * p[4] + B * d1u;
+    a.zzout[o] = zn;
+    corr[q] = sk[q * FT + t] * (dp + zn);
+  }
+  grid_dep_wait();  // the additions land on the stencil kernel's output
+#pragma unroll
+  for (int q = 0; q < ZCH; ++q) {
+    if (zs + q >= ze) break;
+    if (!OWN || corr[q] != 0.f) atomicAdd(a.un + so + (size_t)(zs + q) * g.NXp, corr[q]);
+  }
 }
 
 template <bool NC, bool OWN>

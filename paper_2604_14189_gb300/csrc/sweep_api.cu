@@ -329,6 +329,14 @@ bool field_maps(const Geom& g, const float* base, CUtensorMap* halo, CUtensorMap
   return ok;
 }
 
+// The CPML z part's copies of a per-shot field [S][NZ][NXp]: boxes of
+// IN_BX columns and `rows` rows.
+bool z_map(const Geom& g, const float* base, CUtensorMap* m, int rows) {
+  const uint64_t S = (uint64_t)(g.nshot > 0 ? g.nshot : 1);
+  return make_tensor_map(m, base, 3, g.NX, g.NZ, S, g.NXp, (uint64_t)g.fstride, IN_BX,
+                         (uint32_t)rows, 1);
+}
+
 // The shared K grid [NZ][NXp] with box (bx, bz).
 bool map2(CUtensorMap* m, const Geom& g, const float* base, uint32_t bx, uint32_t bz) {
   return make_tensor_map(m, base, 2, g.NX, g.NZ, 1, g.NXp, (uint64_t)g.fstride, bx, bz, 1);
@@ -369,6 +377,7 @@ struct AcFwdLoop {
   AcInFwdArgs in{};
   AcFixArgs fx{};
   CUtensorMap tu_h[2], tu_c[2];
+  CUtensorMap zu[2], zp[2];  // CPML z part: u^n and psi_z windows
 
   int init(const sweep_problem* p, const Layout& lay, void* w, const float* wavelet,
            const int32_t* src, const int32_t* rec, float* data, bool save_ring,
@@ -387,6 +396,13 @@ struct AcFwdLoop {
       if (!field_maps(g, at<float>(ws, L->u[b]), &tu_h[b], &tu_c[b], in.bz))
         return SWEEP_ECUDA;
     if (!map2(&in.tK, g, at<float>(ws, L->K), IN_BX, in.bz)) return SWEEP_ECUDA;
+    for (int b = 0; b < 2; ++b)
+      if (!z_map(g, at<float>(ws, L->u[b]), &zu[b], ZCH_FWD + 8) ||
+          !z_map(g, at<float>(ws, L->psz[b]), &zp[b], ZCH_FWD + 8))
+        return SWEEP_ECUDA;
+    if (!z_map(g, at<float>(ws, L->zez), &fx.tzz, ZCH_FWD) ||
+        !map2(&fx.tzK, g, at<float>(ws, L->K), IN_BX, ZCH_FWD))
+      return SWEEP_ECUDA;
     in.wavelet = wavelet;
     in.src = src;
     in.status = status;
@@ -414,6 +430,8 @@ struct AcFwdLoop {
     fx.n = n;
     fx.u = at<float>(ws, L->u[A]);
     fx.un = at<float>(ws, L->u[B]);
+    fx.tzu = zu[A];
+    fx.tzp = zp[A];
     fx.pzin = at<float>(ws, L->psz[A]);
     fx.pzout = at<float>(ws, L->psz[B]);
     fx.pxin = at<float>(ws, L->psx[A]);
@@ -460,6 +478,7 @@ struct AcBwdLoop {
   AcFixArgs fx{};
   CUtensorMap tu_h[2], tu_c[2], tm_h[2], tm_c[2];
 
+
   int init(const sweep_problem* p, const Layout& lay, void* w, const float* wavelet,
            const int32_t* src, const int32_t* rec, const float* res, float* wg, bool img,
            bool illum, cudaStream_t st) {
@@ -488,6 +507,7 @@ struct AcBwdLoop {
     if (!map2(&in.tK, g, at<float>(ws, L->K), IN_BX, in.bz)) return SWEEP_ECUDA;
     if (imaging && !field_maps(g, at<float>(ws, L->graw), nullptr, &in.tG, in.bz))
       return SWEEP_ECUDA;
+
     in.graw = imaging ? at<float>(ws, L->graw) : nullptr;
     in.illum = (imaging && illum) ? at<float>(ws, L->iraw) : nullptr;
     in.wavelet = wavelet;
@@ -541,6 +561,7 @@ struct AcBwdLoop {
       fx.n = n;
       fx.u = at<float>(ws, L->m[B]);
       fx.un = at<float>(ws, L->m[A]);
+
       fx.pzin = at<float>(ws, L->pbz[A]);
       fx.pzout = at<float>(ws, L->pbz[B]);
       fx.zzin = at<float>(ws, L->zbz[A]);

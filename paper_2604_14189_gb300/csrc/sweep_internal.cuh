@@ -97,10 +97,21 @@ struct AcInBwdArgs {
 // (mu^n(r) += K(r) res[n-1]; in deterministic mode the backward stencil
 // kernel injects it instead), save/uring = ring restore of u^{n-1}.
 // own: deterministic mode (one owner per border cell).
+// Rows per z-part chunk of the CPML kernels (forward, backward): chosen by
+// a sweep on GB300; the forward z part's staged copies are 4 rows taller
+// each way.
+constexpr int ZCH_FWD = 8;
+constexpr int ZCH_BWD = 4;
+
 struct XBands {  // 4-cell column groups: left [0, gl), right [gr0, ceil(NX/4))
   int gl, gr0, ngr;
 };
 struct AcFixArgs {
+  // forward z part of the per-step kernel: each block copies its chunk's
+  // row windows into shared memory (TMA, zero outside the grid): u^n and
+  // psi_z with 4 rows above and below the chunk, zeta_z and K on the chunk's
+  // rows; boxes of 128 columns
+  CUtensorMap tzu, tzp, tzz, tzK;
   Geom g;
   const float* u;
   float* un;
