@@ -1370,7 +1370,7 @@ def run_autograd(args, local_rank, emit=True):
            "config": {"workload": "acoustic gradient 301x901 + 40 CPML, nt 3000, 20 shots, "
                                   "through AcousticModelling (forward, then backward = "
                                   "sweep_gradient with the data-space gradient as residual)",
-                      "loss": float(loss)},
+                      "loss": float(loss.detach())},
            "e2e": {"value": val, "unit": "Gpts/s",
                    "h2d_bytes_per_step": (v_h.numel() + wav_h.numel()) * 4,
                    "d2h_bytes_per_step": g_h.numel() * 4},
