@@ -81,8 +81,9 @@ def test_kernel_source_hash_ignores_comments_not_code(monkeypatch):
     with open(path, "w") as f:
         f.write("// a new comment\n/* and a block\n comment */\n" + src.replace("\n", "\n\n", 3))
     assert bench.kernel_source_hash() == base
+    assert "constexpr int FT = 128;" in src
     with open(path, "w") as f:
-        f.write(src.replace("constexpr int ZCH_B = 4;", "constexpr int ZCH_B = 5;"))
+        f.write(src.replace("constexpr int FT = 128;", "constexpr int FT = 64;"))
     assert bench.kernel_source_hash() != base
 
 
