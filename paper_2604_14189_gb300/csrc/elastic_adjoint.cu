@@ -22,46 +22,36 @@
 //            d J / d cl2m += txx-bar Ex + tzz-bar Ez, d J / d clam +=
 //            txx-bar Ez + tzz-bar Ex, d J / d cmu += txz-bar (shear bracket),
 //            d J / d cbx += vx-bar (vx bracket), d J / d cbz likewise.
-// Each half is a pointwise kernel (the adjoint derivative terms into four
-// scratch fields, memory variables, coefficient adjoints) and a gather
-// kernel (the transposed differences of those terms).
+// Each half is one persistent kernel over (tile, shot group) units: a TMA
+// pipeline stages, per shot, the tile with a halo of 2 rows and 4 columns
+// (the fields the half reads around a cell and the coefficients); the
+// block forms the four adjoint difference terms of the half on the whole
+// box in shared memory, then applies their transposed differences to the
+// tile's cells and sums the coefficient adjoints of the group's shots in
+// registers (one addition per unit to the group's accumulators).  Those
+// sums over shots and steps are compensated FP32 sums (double-float,
+// about 44 significant bits), converted to FP64 and summed over the
+// groups by the chain-rule kernel: FP64 arithmetic runs at a small
+// fraction of the FP32 rate on this GPU, and plain FP64 accumulation cost
+// a sixth of the elastic gradient's time.
 //
 // A memory variable and its adjoint stay zero wherever its profile pair
 // (a, b) is zero, i.e. off its border strip (both start at zero and are
-// only ever replaced by a x (...)); the pointwise kernels neither read nor
-// write them there, which is most of the grid.
+// only ever replaced by a x (...)); the kernels read and write them only on
+// units whose box meets a strip.  A unit reads the adjoint memory variables
+// of its halo, which the neighbouring tile's unit replaces in the same
+// launch, so each step reads them from one buffer and writes them to the
+// other (ap_in, ap_out; the caller swaps the two every step).
+#include <algorithm>
+
 #include "elastic_internal.cuh"
+#include "tma.cuh"
 
 namespace sweep {
 namespace {
 
 constexpr float kS1 = 9.0f / 8.0f;
 constexpr float kS2 = -1.0f / 24.0f;
-constexpr int AT = 128;  // threads per block (a row segment of one shot)
-
-struct Fld {
-  const float* f;
-  int NZ, NX, NXp;
-  __device__ __forceinline__ float operator()(int z, int x) const {
-    return (z >= 0 && z < NZ && x >= 0 && x < NX) ? f[z * NXp + x] : 0.f;
-  }
-};
-__device__ __forceinline__ Fld fld(const float* f, const Geom& g, int s) {
-  return Fld{f + (size_t)s * g.fstride, g.NZ, g.NX, g.NXp};
-}
-// staggered differences, as in the forward kernels
-__device__ __forceinline__ float dpx(const Fld& f, int z, int x) {
-  return kS1 * (f(z, x + 1) - f(z, x)) + kS2 * (f(z, x + 2) - f(z, x - 1));
-}
-__device__ __forceinline__ float dmx(const Fld& f, int z, int x) {
-  return kS1 * (f(z, x) - f(z, x - 1)) + kS2 * (f(z, x + 1) - f(z, x - 2));
-}
-__device__ __forceinline__ float dpz(const Fld& f, int z, int x) {
-  return kS1 * (f(z + 1, x) - f(z, x)) + kS2 * (f(z + 2, x) - f(z - 1, x));
-}
-__device__ __forceinline__ float dmz(const Fld& f, int z, int x) {
-  return kS1 * (f(z, x) - f(z - 1, x)) + kS2 * (f(z + 1, x) - f(z - 2, x));
-}
 
 enum { G_L2M = 0, G_LAM = 1, G_MU = 2, G_BX = 3, G_BZ = 4 };
 
@@ -76,77 +66,380 @@ __global__ void el_adj_src_kernel(const ElAdjArgs a) {
   a.wgrad[(size_t)s * g.nt + a.n] = a.src_scale * (a.atxx[c] + a.atzz[c]);
 }
 
-// ------------------------------------------------------- stress, pointwise
-// One thread per cell for all shots: the coefficient adjoints are summed
-// over the shots in FP64 registers and added once per step to the FP64
-// accumulators [5][NZ][NXp] (shot sum and time sum in FP64).
-__global__ void __launch_bounds__(AT) el_adj_str_pt_kernel(const ElAdjArgs a) {
-  if (*a.status) return;
+// ------------------------------------------------------------ fused halves
+constexpr int TA_Z = 16;         // tile rows: a warp per row
+constexpr int TA_X = 128;        // tile columns: a lane per 4 cells
+constexpr int A_H = TA_Z + 4;    // box rows: the tile's +- 2
+constexpr int A_W = TA_X + 8;    // box columns: the tile's +- 4 (16-byte aligned x)
+constexpr int A_BOX = A_H * A_W;
+constexpr int A_G4 = A_W / 4;    // float4 groups per box row
+constexpr int A_THREADS = 32 * TA_Z;
+constexpr int A_STAGES = 2;
+constexpr uint32_t kABox = A_BOX * 4;  // bytes of one staged field
+
+struct __align__(128) AStrStage {  // per shot: adjoint stress, coefficients, forward v
+  float txx[A_BOX], tzz[A_BOX], txz[A_BOX], l2m[A_BOX], lam[A_BOX], mu[A_BOX];
+  float vx[A_BOX], vz[A_BOX];
+};
+struct __align__(128) AVelStage {  // per shot: adjoint velocity, buoyancies, forward tau
+  float vx[A_BOX], vz[A_BOX], cbx[A_BOX], cbz[A_BOX];
+  float txx[A_BOX], tzz[A_BOX], txz[A_BOX];
+};
+struct __align__(128) ATerms {  // the half's four difference terms on the box
+  float t[4][A_BOX];
+};
+static_assert(kABox % 128 == 0, "staged field alignment");
+constexpr size_t kAStrSmem = A_STAGES * sizeof(AStrStage) + sizeof(ATerms) + 8 * A_STAGES;
+constexpr size_t kAVelSmem = A_STAGES * sizeof(AVelStage) + sizeof(ATerms) + 8 * A_STAGES;
+static_assert(kAStrSmem <= 227 * 1024 && kAVelSmem <= 227 * 1024, "shared memory");
+
+enum : int { AU_XS = 1, AU_ZS = 2 };
+struct AUnit {
+  int s, z0, x0, flags, grp;
+  bool valid, first, last;
+};
+
+// Sub-unit j of this CTA: unit blockIdx.x + (j / sg) gridDim.x = (tile,
+// group), shot grp sg + j % sg (past the last shot: an empty sub-unit).
+__device__ __forceinline__ AUnit a_unit(const ElAdjArgs& a, int j) {
   const Geom& g = a.g;
-  const int x = blockIdx.x * AT + threadIdx.x, z = blockIdx.y;
-  if (x >= g.NXp) return;
-  const size_t pc = (size_t)z * g.NXp + x;
-  if (x >= g.NX) {  // zero terms beyond the grid for the gather kernel
-    for (int s = 0; s < g.nshot; ++s) {
-      const size_t c = (size_t)s * g.fstride + pc;
-      a.e0[c] = a.e1[c] = a.e2[c] = a.e3[c] = 0.f;
-    }
-    return;
+  const int i = j / a.sg, k = j - i * a.sg;
+  const int unit = blockIdx.x + i * gridDim.x;
+  const int tile = unit / a.ngrp;
+  AUnit u;
+  u.grp = unit - tile * a.ngrp;
+  const int tz = tile / a.ntx;
+  u.z0 = tz * TA_Z;
+  u.x0 = (tile - tz * a.ntx) * TA_X;
+  u.s = u.grp * a.sg + k;
+  u.valid = u.s < g.nshot;
+  u.first = k == 0;
+  u.last = k == a.sg - 1;
+  int f = 0;  // the box meets a CPML strip (an integer or half-point profile is nonzero)
+  if (g.P > 0 && (u.x0 - 4 < g.P || u.x0 + TA_X + 4 > g.P + g.nx - 1)) f |= AU_XS;
+  if (g.P > 0 && (u.z0 - 2 < g.P || u.z0 + TA_Z + 2 > g.P + g.nz - 1)) f |= AU_ZS;
+  u.flags = f;
+  return u;
+}
+
+__device__ __forceinline__ float4 lda4(const float* t, int r, int c) {
+  return *reinterpret_cast<const float4*>(t + r * A_W + c);
+}
+__device__ __forceinline__ void sta4(float* t, int r, int c, const float* v) {
+  *reinterpret_cast<float4*>(t + r * A_W + c) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void v4(const float4 q, float* o) {
+  o[0] = q.x;
+  o[1] = q.y;
+  o[2] = q.z;
+  o[3] = q.w;
+}
+__device__ __forceinline__ float4 ld4z(const float* p, bool ok) {
+  return ok ? *reinterpret_cast<const float4*>(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void st4v(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+// 12 values of box row r, columns c0 .. c0+11
+__device__ __forceinline__ void row12(const float* t, int r, int c0, float* e) {
+  v4(lda4(t, r, c0), e);
+  v4(lda4(t, r, c0 + 4), e + 4);
+  v4(lda4(t, r, c0 + 8), e + 8);
+}
+// differences at the 4 cells c = 0..3 of a row window e[12] (cell c at
+// e[4 + c]): D+ x and D- x
+__device__ __forceinline__ float wdp(const float* e, int c) {
+  return kS1 * (e[5 + c] - e[4 + c]) + kS2 * (e[6 + c] - e[3 + c]);
+}
+__device__ __forceinline__ float wdm(const float* e, int c) {
+  return kS1 * (e[4 + c] - e[3 + c]) + kS2 * (e[5 + c] - e[2 + c]);
+}
+// and along z from rows R-2 .. R+2 of one column group (m2 .. p2)
+__device__ __forceinline__ float zdp(float m1, float c0, float p1, float p2) {
+  return kS1 * (p1 - c0) + kS2 * (p2 - m1);
+}
+__device__ __forceinline__ float zdm(float m2, float m1, float c0, float p1) {
+  return kS1 * (c0 - m1) + kS2 * (p1 - m2);
+}
+
+// Compensated (double-float) sums: a value is hi + lo, two FP32 numbers;
+// TwoSum (Knuth) adds an FP32 term with its rounding error kept in lo, so
+// a sum keeps about 44 significant bits while every operation runs on the
+// FP32 pipe (FP64 is far slower on this GPU).  __fadd_rn keeps the compiler
+// from reassociating or contracting the error terms.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+// (H, L) += (hi, lo), renormalised so that |L| <= ulp(H) / 2
+__device__ __forceinline__ void df_acc(float& H, float& L, float hi, float lo) {
+  const float s = __fadd_rn(H, hi);
+  const float bp = __fsub_rn(s, H);
+  const float e = __fadd_rn(__fsub_rn(H, __fsub_rn(s, bp)), __fsub_rn(hi, bp));
+  const float l = __fadd_rn(__fadd_rn(L, lo), e);
+  H = __fadd_rn(s, l);
+  L = __fsub_rn(l, __fsub_rn(H, s));
+}
+// Add this thread's 4 cells of one coefficient adjoint to the group's
+// accumulator planes (hi at G, lo at G + fstride)
+__device__ __forceinline__ void df_flush(float* G, long long fstride, const float* hi,
+                                         const float* lo) {
+  float H[4], L[4];
+  v4(*reinterpret_cast<const float4*>(G), H);
+  v4(*reinterpret_cast<const float4*>(G + fstride), L);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) df_acc(H[k], L[k], hi[k], lo[k]);
+  *reinterpret_cast<float4*>(G) = make_float4(H[0], H[1], H[2], H[3]);
+  *reinterpret_cast<float4*>(G + fstride) = make_float4(L[0], L[1], L[2], L[3]);
+}
+
+// The persistent pipeline of both halves: sub-units in order, D stages.
+// body(u, stage, wait) returns false when a transfer never landed.
+template <typename Stage, typename Issue, typename Body>
+__device__ __forceinline__ void a_pipeline(const ElAdjArgs& a, unsigned char* smem_raw,
+                                           Issue issue, Body body) {
+  constexpr int D = A_STAGES;
+  Stage* stg = reinterpret_cast<Stage*>(smem_raw);
+  uint64_t* bar =
+      reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(Stage) + sizeof(ATerms));
+  const int G = gridDim.x;
+  const int nunit = (a.units - (int)blockIdx.x + G - 1) / G;
+  const int count = nunit * a.sg;
+  if (count <= 0) return;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
+    fence_barrier_init();
+    for (int k = 0; k < D && k < count; ++k) issue(stg[k], &bar[k], a_unit(a, k));
   }
-  const float l2m = a.cl2m[pc], lam = a.clam[pc], mu = a.cmu[pc];
-  // profile pairs of p5 (x), p6 (z), p7 (z, half points), p8 (x, half points)
-  const float A5 = a.ax[x], B5 = a.bx[x], A6 = a.az[z], B6 = a.bz[z];
-  const float A7 = a.azh[z], B7 = a.bzh[z], A8 = a.axh[x], B8 = a.bxh[x];
-  const bool o5 = A5 != 0.f || B5 != 0.f, o6 = A6 != 0.f || B6 != 0.f;
-  const bool o7 = A7 != 0.f || B7 != 0.f, o8 = A8 != 0.f || B8 != 0.f;
-  double sl2m = 0.0, slam = 0.0, smu = 0.0;
-  for (int s = 0; s < g.nshot; ++s) {
-    const size_t c = (size_t)s * g.fstride + pc;
-    const float txx = a.atxx[c], tzz = a.atzz[c], txz = a.atxz[c];
-    if (a.gacc) {
-      const Fld vx = fld(a.fvx, g, s), vz = fld(a.fvz, g, s);
-      const float ex = dmx(vx, z, x) + (o5 ? a.fp[4][c] : 0.f);
-      const float ez = dmz(vz, z, x) + (o6 ? a.fp[5][c] : 0.f);
-      const float sxz = dpz(vx, z, x) + (o7 ? a.fp[6][c] : 0.f) + dpx(vz, z, x) +
-                        (o8 ? a.fp[7][c] : 0.f);
-      sl2m += (double)(txx * ex + tzz * ez);
-      slam += (double)(txx * ez + tzz * ex);
-      smu += (double)(txz * sxz);
+  __syncthreads();
+  int k = 0;
+  for (; k < count; ++k) {
+    const AUnit u = a_unit(a, k);
+    const bool ok = body(u, stg[k % D], [&]() {
+      const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
+      return !__syncthreads_or(!got);
+    });
+    if (!ok) break;   // uniform: a transfer never landed
+    __syncthreads();  // stage and terms released
+    if (threadIdx.x == 0 && k + D < count) {
+      fence_proxy_async_smem();
+      issue(stg[k % D], &bar[k % D], a_unit(a, k + D));
     }
-    // txz += cmu (ezx + p7' + exz + p8')
-    const float T = mu * txz;
-    const float P7 = (o7 ? a.ap[6][c] : 0.f) + T, P8 = (o8 ? a.ap[7][c] : 0.f) + T;
-    a.e2[c] = T + B7 * P7;  // ezx-bar
-    a.e3[c] = T + B8 * P8;  // exz-bar
-    if (o7) a.ap[6][c] = A7 * P7;
-    if (o8) a.ap[7][c] = A8 * P8;
-    // txx += cl2m Ex + clam Ez, tzz += clam Ex + cl2m Ez
-    const float Ex = l2m * txx + lam * tzz, Ez = lam * txx + l2m * tzz;
-    const float P5 = (o5 ? a.ap[4][c] : 0.f) + Ex, P6 = (o6 ? a.ap[5][c] : 0.f) + Ez;
-    a.e0[c] = Ex + B5 * P5;  // exx-bar
-    a.e1[c] = Ez + B6 * P6;  // ezz-bar
-    if (o5) a.ap[4][c] = A5 * P5;
-    if (o6) a.ap[5][c] = A6 * P6;
   }
-  if (a.gacc) {
-    double* ga = a.gacc + pc;
-    ga[G_L2M * g.fstride] += sl2m;
-    ga[G_LAM * g.fstride] += slam;
-    ga[G_MU * g.fstride] += smu;
+  if (k < count && threadIdx.x == 0) {
+    latch(const_cast<int*>(a.status), SWEEP_ETIMEOUT);
+    for (int j = k; j < count && j < k + D; ++j) mbar_wait(&bar[j % D], (j / D) & 1);
   }
 }
 
-// ----------------------------------------------------------- stress, gather
-__global__ void __launch_bounds__(AT) el_adj_str_sc_kernel(const ElAdjArgs a) {
+// A replayed forward memory variable holds its value only where its profile
+// pair is nonzero (the snapshot copies nothing elsewhere): read it there, 0
+// elsewhere.  pa, pb: the pair, at cells x .. x+3 (x axis) or row z.
+__device__ __forceinline__ void fp_x(const float* f, const float* pa, const float* pb, int x,
+                                     bool ok, float* o) {
+  float A[4], B[4], v[4];
+  v4(ld4z(pa + x, ok), A);
+  v4(ld4z(pb + x, ok), B);
+  v4(ld4z(f, ok), v);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o[k] = (A[k] != 0.f || B[k] != 0.f) ? v[k] : 0.f;
+}
+__device__ __forceinline__ void fp_z(const float* f, const float* pa, const float* pb, int z,
+                                     bool ok, float* o) {
+  const bool on = ok && (__ldg(pa + z) != 0.f || __ldg(pb + z) != 0.f);
+  v4(ld4z(f, on), o);
+}
+
+// profiles of the 4 cells x .. x+3 (zero outside [0, NX)) and of row z
+struct XProf {
+  float a[4], b[4], ah[4], bh[4];
+};
+__device__ __forceinline__ void x_prof(const ElAdjArgs& a, int x, XProf& p) {
+  const bool ok = x >= 0 && x < a.g.NXp;  // (the arrays are zero on [NX, NXp))
+  v4(ld4z(a.ax + x, ok), p.a);
+  v4(ld4z(a.bx + x, ok), p.b);
+  v4(ld4z(a.axh + x, ok), p.ah);
+  v4(ld4z(a.bxh + x, ok), p.bh);
+}
+
+// ----------------------------------------------------------------- stress
+// The transpose of the stress update: terms exx-bar (t0), ezz-bar (t1),
+// ezx-bar (t2), exz-bar (t3) on the box; v-bar -= D^T of them on the tile;
+// d J / d (cl2m, clam, cmu) from the forward v^{n+1/2} and p5..p8.
+__global__ void __launch_bounds__(A_THREADS, 1)
+    el_adj_str_kernel(const __grid_constant__ ElAdjArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   if (*a.status) return;
   const Geom& g = a.g;
-  const int x = blockIdx.x * AT + threadIdx.x, z = blockIdx.y, s = blockIdx.z;
-  if (x >= g.NX) return;
-  const size_t c = (size_t)s * g.fstride + (size_t)z * g.NXp + x;
-  const Fld exx = fld(a.e0, g, s), ezz = fld(a.e1, g, s), ezx = fld(a.e2, g, s),
-            exz = fld(a.e3, g, s);
-  a.avx[c] -= dpx(exx, z, x) + dmz(ezx, z, x);
-  a.avz[c] -= dpz(ezz, z, x) + dmx(exz, z, x);
+  ATerms& T = *reinterpret_cast<ATerms*>(smem_raw + A_STAGES * sizeof(AStrStage));
+  const bool grad = a.gacc != nullptr;
+  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5, lx = 4 * lane;
+  float acc[3][4], acl[3][4];  // coefficient adjoints of the group's shots (hi, lo)
+  auto issue = [&](AStrStage& sg, uint64_t* b, const AUnit& u) {
+    if (!u.valid) {
+      mbar_arrive_expect_tx(b, 0);  // completes the phase: nothing to copy
+      return;
+    }
+    mbar_arrive_expect_tx(b, (grad ? 8 : 6) * kABox);
+    const int x = u.x0 - 4, y = u.z0 - 2;
+    tma_load_3d(sg.txx, &a.m_atxx, b, x, y, u.s);
+    tma_load_3d(sg.tzz, &a.m_atzz, b, x, y, u.s);
+    tma_load_3d(sg.txz, &a.m_atxz, b, x, y, u.s);
+    tma_load_2d(sg.l2m, &a.m_l2m, b, x, y);
+    tma_load_2d(sg.lam, &a.m_lam, b, x, y);
+    tma_load_2d(sg.mu, &a.m_mu, b, x, y);
+    if (grad) {
+      tma_load_3d(sg.vx, &a.m_fvx, b, x, y, u.s);
+      tma_load_3d(sg.vz, &a.m_fvz, b, x, y, u.s);
+    }
+  };
+  auto body = [&](const AUnit& u, const AStrStage& sg, auto wait) {
+    if (u.first) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[k][c] = acl[k][c] = 0.f;
+    }
+    const size_t so = (size_t)u.s * g.fstride;
+    const bool xs = u.flags & AU_XS, zs = u.flags & AU_ZS;
+    // this thread's tile cells: adjoint velocities (updated) and the forward
+    // memory variables p5..p8 (gradient), loaded before the stage wait
+    const int z = u.z0 + r, x = u.x0 + lx;
+    const bool cell = u.valid && z < g.NZ && x < g.NXp;
+    const size_t ci = so + (size_t)z * g.NXp + x;
+    float vx[4], vz[4];
+    v4(ld4z(a.avx + ci, cell), vx);
+    v4(ld4z(a.avz + ci, cell), vz);
+    if (!wait()) return false;
+    if (u.valid) {
+      // 1. the terms on the whole box; new p5..p8 on the tile's own cells
+      for (int gi = threadIdx.x; gi < A_H * A_G4; gi += A_THREADS) {
+        const int br = gi / A_G4, bc = 4 * (gi - br * A_G4);
+        const int zz = u.z0 - 2 + br, xx = u.x0 - 4 + bc;
+        const bool zin = zz >= 0 && zz < g.NZ;
+        const bool gin = zin && xx >= 0 && xx < g.NXp;  // the group lies in the arrays
+        const size_t c = so + (size_t)zz * g.NXp + xx;
+        float txx[4], tzz[4], txz[4], l2m[4], lam[4], mu[4];
+        v4(lda4(sg.txx, br, bc), txx);
+        v4(lda4(sg.tzz, br, bc), tzz);
+        v4(lda4(sg.txz, br, bc), txz);
+        v4(lda4(sg.l2m, br, bc), l2m);
+        v4(lda4(sg.lam, br, bc), lam);
+        v4(lda4(sg.mu, br, bc), mu);
+        XProf px;
+        float q5[4], q6[4], q7[4], q8[4];
+        x_prof(a, xs ? xx : -4, px);
+        v4(ld4z(a.ap_in[4] + c, gin && xs), q5);
+        v4(ld4z(a.ap_in[7] + c, gin && xs), q8);
+        v4(ld4z(a.ap_in[5] + c, gin && zs), q6);
+        v4(ld4z(a.ap_in[6] + c, gin && zs), q7);
+        const float A6 = zs && zin ? __ldg(a.az + zz) : 0.f, B6 = zs && zin ? __ldg(a.bz + zz) : 0.f;
+        const float A7 = zs && zin ? __ldg(a.azh + zz) : 0.f, B7 = zs && zin ? __ldg(a.bzh + zz) : 0.f;
+        float e0[4], e1[4], e2[4], e3[4], n5[4], n6[4], n7[4], n8[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const bool in = zin && xx + k >= 0 && xx + k < g.NX;
+          // txz += cmu (ezx + p7' + exz + p8')
+          const float Tz = mu[k] * txz[k];
+          const float P7 = q7[k] + Tz, P8 = q8[k] + Tz;
+          e2[k] = in ? Tz + B7 * P7 : 0.f;        // ezx-bar
+          e3[k] = in ? Tz + px.bh[k] * P8 : 0.f;  // exz-bar
+          n7[k] = A7 * P7;
+          n8[k] = px.ah[k] * P8;
+          // txx += cl2m Ex + clam Ez, tzz += clam Ex + cl2m Ez
+          const float Ex = l2m[k] * txx[k] + lam[k] * tzz[k];
+          const float Ez = lam[k] * txx[k] + l2m[k] * tzz[k];
+          const float P5 = q5[k] + Ex, P6 = q6[k] + Ez;
+          e0[k] = in ? Ex + px.b[k] * P5 : 0.f;   // exx-bar
+          e1[k] = in ? Ez + B6 * P6 : 0.f;        // ezz-bar
+          n5[k] = px.a[k] * P5;
+          n6[k] = A6 * P6;
+        }
+        sta4(T.t[0], br, bc, e0);
+        sta4(T.t[1], br, bc, e1);
+        sta4(T.t[2], br, bc, e2);
+        sta4(T.t[3], br, bc, e3);
+        const bool own = gin && br >= 2 && br < 2 + TA_Z && bc >= 4 && bc < 4 + TA_X;
+        if (own && xs) {
+          st4v(a.ap_out[4] + c, n5);
+          st4v(a.ap_out[7] + c, n8);
+        }
+        if (own && zs) {
+          st4v(a.ap_out[5] + c, n6);
+          st4v(a.ap_out[6] + c, n7);
+        }
+      }
+      __syncthreads();
+      // 2. v-bar -= D^T terms on the tile; coefficient adjoints (the forward
+      // memory variables p5..p8 read here: only strip units have them)
+      if (cell) {
+        float f5[4], f6[4], f7[4], f8[4];
+        fp_x(a.fp[4] + ci, a.ax, a.bx, x, grad && xs, f5);
+        fp_x(a.fp[7] + ci, a.axh, a.bxh, x, grad && xs, f8);
+        fp_z(a.fp[5] + ci, a.az, a.bz, z, grad && zs, f6);
+        fp_z(a.fp[6] + ci, a.azh, a.bzh, z, grad && zs, f7);
+        const int R = r + 2;
+        float e[12], f[12];
+        row12(T.t[0], R, lx, e);  // exx-bar
+        row12(T.t[3], R, lx, f);  // exz-bar
+        float m2[4], m1[4], c0[4], p1[4];
+        v4(lda4(T.t[2], R - 2, lx + 4), m2);  // ezx-bar rows R-2 .. R+1
+        v4(lda4(T.t[2], R - 1, lx + 4), m1);
+        v4(lda4(T.t[2], R, lx + 4), c0);
+        v4(lda4(T.t[2], R + 1, lx + 4), p1);
+        float n1[4], n0[4], q1[4], q2[4];
+        v4(lda4(T.t[1], R - 1, lx + 4), n1);  // ezz-bar rows R-1 .. R+2
+        v4(lda4(T.t[1], R, lx + 4), n0);
+        v4(lda4(T.t[1], R + 1, lx + 4), q1);
+        v4(lda4(T.t[1], R + 2, lx + 4), q2);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (x + k >= g.NX) continue;
+          vx[k] -= wdp(e, k) + zdm(m2[k], m1[k], c0[k], p1[k]);
+          vz[k] -= zdp(n1[k], n0[k], q1[k], q2[k]) + wdm(f, k);
+        }
+        st4v(a.avx + ci, vx);
+        st4v(a.avz + ci, vz);
+        if (grad) {
+          float w[12], y[12];
+          row12(sg.vx, R, lx, w);
+          row12(sg.vz, R, lx, y);
+          float xm1[4], xp1[4], xp2[4], zm2[4], zm1[4], zp1[4];
+          v4(lda4(sg.vx, R - 1, lx + 4), xm1);  // vx rows R-1 .. R+2
+          v4(lda4(sg.vx, R + 1, lx + 4), xp1);
+          v4(lda4(sg.vx, R + 2, lx + 4), xp2);
+          v4(lda4(sg.vz, R - 2, lx + 4), zm2);  // vz rows R-2 .. R+1
+          v4(lda4(sg.vz, R - 1, lx + 4), zm1);
+          v4(lda4(sg.vz, R + 1, lx + 4), zp1);
+          float txx[4], tzz[4], txz[4];
+          v4(lda4(sg.txx, R, lx + 4), txx);
+          v4(lda4(sg.tzz, R, lx + 4), tzz);
+          v4(lda4(sg.txz, R, lx + 4), txz);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (x + k >= g.NX) continue;
+            const float ex = wdm(w, k) + f5[k];
+            const float ez = zdm(zm2[k], zm1[k], y[4 + k], zp1[k]) + f6[k];
+            const float sxz = zdp(xm1[k], w[4 + k], xp1[k], xp2[k]) + f7[k] + wdp(y, k) + f8[k];
+            df_add(acc[0][k], acl[0][k], txx[k] * ex + tzz[k] * ez);
+            df_add(acc[1][k], acl[1][k], txx[k] * ez + tzz[k] * ex);
+            df_add(acc[2][k], acl[2][k], txz[k] * sxz);
+          }
+        }
+      }
+    }
+    if (u.last && grad && z < g.NZ && x < g.NXp) {
+      float* ga = a.gacc + (size_t)u.grp * 10 * g.fstride + (size_t)z * g.NXp + x;
+      df_flush(ga + 2 * G_L2M * g.fstride, g.fstride, acc[0], acl[0]);
+      df_flush(ga + 2 * G_LAM * g.fstride, g.fstride, acc[1], acl[1]);
+      df_flush(ga + 2 * G_MU * g.fstride, g.fstride, acc[2], acl[2]);
+    }
+    return true;
+  };
+  a_pipeline<AStrStage>(a, smem_raw, issue, body);
 }
 
 // ---------------------------------------------------------------- receivers
@@ -157,77 +450,178 @@ __global__ void el_adj_rec_kernel(const ElAdjArgs a) {
   if (r >= g.nrec) return;
   const int32_t* q = a.rec + 2 * ((size_t)s * g.nrec + r);
   const size_t c = (size_t)s * g.fstride + (size_t)(q[0] + g.P) * g.NXp + (q[1] + g.P);
-  a.avx[c] += a.res[(((size_t)s * 2 + 0) * g.nrec + r) * g.nt + a.n];
-  a.avz[c] += a.res[(((size_t)s * 2 + 1) * g.nrec + r) * g.nt + a.n];
+  // atomic: several receivers of a shot may share a cell (their residuals
+  // add up, as in the transpose of recording each of them)
+  atomicAdd(a.avx + c, a.res[(((size_t)s * 2 + 0) * g.nrec + r) * g.nt + a.n]);
+  atomicAdd(a.avz + c, a.res[(((size_t)s * 2 + 1) * g.nrec + r) * g.nt + a.n]);
 }
 
-// ----------------------------------------------------- velocity, pointwise
-__global__ void __launch_bounds__(AT) el_adj_vel_pt_kernel(const ElAdjArgs a) {
+// --------------------------------------------------------------- velocity
+// The transpose of the velocity update: terms dxt-bar of Dpx txx (t0), of
+// Dmz txz (t1), of Dmx txz (t2), of Dpz tzz (t3) on the box; tau-bar -= D^T
+// of them on the tile; d J / d (cbx, cbz) from the forward tau^n and p1..p4.
+__global__ void __launch_bounds__(A_THREADS, 1)
+    el_adj_vel_kernel(const __grid_constant__ ElAdjArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   if (*a.status) return;
   const Geom& g = a.g;
-  const int x = blockIdx.x * AT + threadIdx.x, z = blockIdx.y;
-  if (x >= g.NXp) return;
-  const size_t pc = (size_t)z * g.NXp + x;
-  if (x >= g.NX) {
-    for (int s = 0; s < g.nshot; ++s) {
-      const size_t c = (size_t)s * g.fstride + pc;
-      a.e0[c] = a.e1[c] = a.e2[c] = a.e3[c] = 0.f;
+  ATerms& T = *reinterpret_cast<ATerms*>(smem_raw + A_STAGES * sizeof(AVelStage));
+  const bool grad = a.gacc != nullptr;
+  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5, lx = 4 * lane;
+  float acc[2][4], acl[2][4];
+  auto issue = [&](AVelStage& sg, uint64_t* b, const AUnit& u) {
+    if (!u.valid) {
+      mbar_arrive_expect_tx(b, 0);
+      return;
     }
-    return;
-  }
-  const float cbx = a.cbx[pc], cbz = a.cbz[pc];
-  // profile pairs of p1 (x, half points), p2 (z), p3 (x), p4 (z, half points)
-  const float A1 = a.axh[x], B1 = a.bxh[x], A2 = a.az[z], B2 = a.bz[z];
-  const float A3 = a.ax[x], B3 = a.bx[x], A4 = a.azh[z], B4 = a.bzh[z];
-  const bool o1 = A1 != 0.f || B1 != 0.f, o2 = A2 != 0.f || B2 != 0.f;
-  const bool o3 = A3 != 0.f || B3 != 0.f, o4 = A4 != 0.f || B4 != 0.f;
-  double sbx = 0.0, sbz = 0.0;
-  for (int s = 0; s < g.nshot; ++s) {
-    const size_t c = (size_t)s * g.fstride + pc;
-    const float vx = a.avx[c], vz = a.avz[c];
-    if (a.gacc) {
-      const Fld txx = fld(a.ftxx, g, s), tzz = fld(a.ftzz, g, s), txz = fld(a.ftxz, g, s);
-      const float sx = dpx(txx, z, x) + (o1 ? a.fp[0][c] : 0.f) + dmz(txz, z, x) +
-                       (o2 ? a.fp[1][c] : 0.f);
-      const float sz = dmx(txz, z, x) + (o3 ? a.fp[2][c] : 0.f) + dpz(tzz, z, x) +
-                       (o4 ? a.fp[3][c] : 0.f);
-      sbx += (double)(vx * sx);
-      sbz += (double)(vz * sz);
+    mbar_arrive_expect_tx(b, (grad ? 7 : 4) * kABox);
+    const int x = u.x0 - 4, y = u.z0 - 2;
+    tma_load_3d(sg.vx, &a.m_avx, b, x, y, u.s);
+    tma_load_3d(sg.vz, &a.m_avz, b, x, y, u.s);
+    tma_load_2d(sg.cbx, &a.m_cbx, b, x, y);
+    tma_load_2d(sg.cbz, &a.m_cbz, b, x, y);
+    if (grad) {
+      tma_load_3d(sg.txx, &a.m_ftxx, b, x, y, u.s);
+      tma_load_3d(sg.tzz, &a.m_ftzz, b, x, y, u.s);
+      tma_load_3d(sg.txz, &a.m_ftxz, b, x, y, u.s);
     }
-    // vx += cbx (dxt + p1' + dzt + p2')
-    const float Q = cbx * vx;
-    const float P1 = (o1 ? a.ap[0][c] : 0.f) + Q, P2 = (o2 ? a.ap[1][c] : 0.f) + Q;
-    a.e0[c] = Q + B1 * P1;  // dxt-bar (Dpx txx)
-    a.e1[c] = Q + B2 * P2;  // dzt-bar (Dmz txz)
-    if (o1) a.ap[0][c] = A1 * P1;
-    if (o2) a.ap[1][c] = A2 * P2;
-    // vz += cbz (dxt + p3' + dzt + p4')
-    const float Qz = cbz * vz;
-    const float P3 = (o3 ? a.ap[2][c] : 0.f) + Qz, P4 = (o4 ? a.ap[3][c] : 0.f) + Qz;
-    a.e2[c] = Qz + B3 * P3;  // dxt-bar (Dmx txz)
-    a.e3[c] = Qz + B4 * P4;  // dzt-bar (Dpz tzz)
-    if (o3) a.ap[2][c] = A3 * P3;
-    if (o4) a.ap[3][c] = A4 * P4;
-  }
-  if (a.gacc) {
-    double* ga = a.gacc + pc;
-    ga[G_BX * g.fstride] += sbx;
-    ga[G_BZ * g.fstride] += sbz;
-  }
-}
-
-// --------------------------------------------------------- velocity, gather
-__global__ void __launch_bounds__(AT) el_adj_vel_sc_kernel(const ElAdjArgs a) {
-  if (*a.status) return;
-  const Geom& g = a.g;
-  const int x = blockIdx.x * AT + threadIdx.x, z = blockIdx.y, s = blockIdx.z;
-  if (x >= g.NX) return;
-  const size_t c = (size_t)s * g.fstride + (size_t)z * g.NXp + x;
-  const Fld d0 = fld(a.e0, g, s), d1 = fld(a.e1, g, s), d2 = fld(a.e2, g, s),
-            d3 = fld(a.e3, g, s);
-  a.atxx[c] -= dmx(d0, z, x);
-  a.atxz[c] -= dpz(d1, z, x) + dpx(d2, z, x);
-  a.atzz[c] -= dmz(d3, z, x);
+  };
+  auto body = [&](const AUnit& u, const AVelStage& sg, auto wait) {
+    if (u.first) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[k][c] = acl[k][c] = 0.f;
+    }
+    const size_t so = (size_t)u.s * g.fstride;
+    const bool xs = u.flags & AU_XS, zs = u.flags & AU_ZS;
+    const int z = u.z0 + r, x = u.x0 + lx;
+    const bool cell = u.valid && z < g.NZ && x < g.NXp;
+    const size_t ci = so + (size_t)z * g.NXp + x;
+    float txx[4], tzz[4], txz[4];
+    v4(ld4z(a.atxx + ci, cell), txx);
+    v4(ld4z(a.atzz + ci, cell), tzz);
+    v4(ld4z(a.atxz + ci, cell), txz);
+    if (!wait()) return false;
+    if (u.valid) {
+      for (int gi = threadIdx.x; gi < A_H * A_G4; gi += A_THREADS) {
+        const int br = gi / A_G4, bc = 4 * (gi - br * A_G4);
+        const int zz = u.z0 - 2 + br, xx = u.x0 - 4 + bc;
+        const bool zin = zz >= 0 && zz < g.NZ;
+        const bool gin = zin && xx >= 0 && xx < g.NXp;
+        const size_t c = so + (size_t)zz * g.NXp + xx;
+        float vx[4], vz[4], cbx[4], cbz[4];
+        v4(lda4(sg.vx, br, bc), vx);
+        v4(lda4(sg.vz, br, bc), vz);
+        v4(lda4(sg.cbx, br, bc), cbx);
+        v4(lda4(sg.cbz, br, bc), cbz);
+        XProf px;
+        float q1[4], q2[4], q3[4], q4[4];
+        x_prof(a, xs ? xx : -4, px);
+        v4(ld4z(a.ap_in[0] + c, gin && xs), q1);
+        v4(ld4z(a.ap_in[2] + c, gin && xs), q3);
+        v4(ld4z(a.ap_in[1] + c, gin && zs), q2);
+        v4(ld4z(a.ap_in[3] + c, gin && zs), q4);
+        const float A2 = zs && zin ? __ldg(a.az + zz) : 0.f, B2 = zs && zin ? __ldg(a.bz + zz) : 0.f;
+        const float A4 = zs && zin ? __ldg(a.azh + zz) : 0.f, B4 = zs && zin ? __ldg(a.bzh + zz) : 0.f;
+        float d0[4], d1[4], d2[4], d3[4], n1[4], n2[4], n3[4], n4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const bool in = zin && xx + k >= 0 && xx + k < g.NX;
+          // vx += cbx (dxt + p1' + dzt + p2')
+          const float Q = cbx[k] * vx[k];
+          const float P1 = q1[k] + Q, P2 = q2[k] + Q;
+          d0[k] = in ? Q + px.bh[k] * P1 : 0.f;  // dxt-bar (Dpx txx)
+          d1[k] = in ? Q + B2 * P2 : 0.f;        // dzt-bar (Dmz txz)
+          n1[k] = px.ah[k] * P1;
+          n2[k] = A2 * P2;
+          // vz += cbz (dxt + p3' + dzt + p4')
+          const float Qz = cbz[k] * vz[k];
+          const float P3 = q3[k] + Qz, P4 = q4[k] + Qz;
+          d2[k] = in ? Qz + px.b[k] * P3 : 0.f;  // dxt-bar (Dmx txz)
+          d3[k] = in ? Qz + B4 * P4 : 0.f;       // dzt-bar (Dpz tzz)
+          n3[k] = px.a[k] * P3;
+          n4[k] = A4 * P4;
+        }
+        sta4(T.t[0], br, bc, d0);
+        sta4(T.t[1], br, bc, d1);
+        sta4(T.t[2], br, bc, d2);
+        sta4(T.t[3], br, bc, d3);
+        const bool own = gin && br >= 2 && br < 2 + TA_Z && bc >= 4 && bc < 4 + TA_X;
+        if (own && xs) {
+          st4v(a.ap_out[0] + c, n1);
+          st4v(a.ap_out[2] + c, n3);
+        }
+        if (own && zs) {
+          st4v(a.ap_out[1] + c, n2);
+          st4v(a.ap_out[3] + c, n4);
+        }
+      }
+      __syncthreads();
+      if (cell) {
+        const int R = r + 2;
+        {  // tau-bar -= D^T terms
+          float d0[12], d2[12];
+          row12(T.t[0], R, lx, d0);
+          row12(T.t[2], R, lx, d2);
+          float a1[4], a0[4], b1[4], b2[4], m2[4], m1[4], c0[4], p1[4];
+          v4(lda4(T.t[1], R - 1, lx + 4), a1);  // d1 rows R-1 .. R+2
+          v4(lda4(T.t[1], R, lx + 4), a0);
+          v4(lda4(T.t[1], R + 1, lx + 4), b1);
+          v4(lda4(T.t[1], R + 2, lx + 4), b2);
+          v4(lda4(T.t[3], R - 2, lx + 4), m2);  // d3 rows R-2 .. R+1
+          v4(lda4(T.t[3], R - 1, lx + 4), m1);
+          v4(lda4(T.t[3], R, lx + 4), c0);
+          v4(lda4(T.t[3], R + 1, lx + 4), p1);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (x + k >= g.NX) continue;
+            txx[k] -= wdm(d0, k);
+            txz[k] -= zdp(a1[k], a0[k], b1[k], b2[k]) + wdp(d2, k);
+            tzz[k] -= zdm(m2[k], m1[k], c0[k], p1[k]);
+          }
+          st4v(a.atxx + ci, txx);
+          st4v(a.atzz + ci, tzz);
+          st4v(a.atxz + ci, txz);
+        }
+        if (grad) {
+          float f1[4], f2[4], f3[4], f4_[4];  // forward p1..p4 (strip units)
+          fp_x(a.fp[0] + ci, a.axh, a.bxh, x, xs, f1);
+          fp_x(a.fp[2] + ci, a.ax, a.bx, x, xs, f3);
+          fp_z(a.fp[1] + ci, a.az, a.bz, z, zs, f2);
+          fp_z(a.fp[3] + ci, a.azh, a.bzh, z, zs, f4_);
+          float w[12], y[12];
+          row12(sg.txx, R, lx, w);
+          row12(sg.txz, R, lx, y);
+          float tzm1[4], tz0[4], tzp1[4], tzp2[4], xzm2[4], xzm1[4], xzp1[4], avx[4], avz[4];
+          v4(lda4(sg.txz, R - 2, lx + 4), xzm2);  // txz rows R-2 .. R+1
+          v4(lda4(sg.txz, R - 1, lx + 4), xzm1);
+          v4(lda4(sg.txz, R + 1, lx + 4), xzp1);
+          v4(lda4(sg.tzz, R - 1, lx + 4), tzm1);  // tzz rows R-1 .. R+2
+          v4(lda4(sg.tzz, R, lx + 4), tz0);
+          v4(lda4(sg.tzz, R + 1, lx + 4), tzp1);
+          v4(lda4(sg.tzz, R + 2, lx + 4), tzp2);
+          v4(lda4(sg.vx, R, lx + 4), avx);
+          v4(lda4(sg.vz, R, lx + 4), avz);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (x + k >= g.NX) continue;
+            const float sx = wdp(w, k) + f1[k] + zdm(xzm2[k], xzm1[k], y[4 + k], xzp1[k]) + f2[k];
+            const float sz = wdm(y, k) + f3[k] + zdp(tzm1[k], tz0[k], tzp1[k], tzp2[k]) + f4_[k];
+            df_add(acc[0][k], acl[0][k], avx[k] * sx);
+            df_add(acc[1][k], acl[1][k], avz[k] * sz);
+          }
+        }
+      }
+    }
+    if (u.last && grad && z < g.NZ && x < g.NXp) {
+      float* ga = a.gacc + (size_t)u.grp * 10 * g.fstride + (size_t)z * g.NXp + x;
+      df_flush(ga + 2 * G_BX * g.fstride, g.fstride, acc[0], acl[0]);
+      df_flush(ga + 2 * G_BZ * g.fstride, g.fstride, acc[1], acl[1]);
+    }
+    return true;
+  };
+  a_pipeline<AVelStage>(a, smem_raw, issue, body);
 }
 
 // ------------------------------------------------------------ chain rule
@@ -244,13 +638,21 @@ __device__ __forceinline__ double mu_at(const float* model, const Geom& g, int p
   const double vs = mval(model, g, padded, 1, z, x);
   return mval(model, g, padded, 2, z, x) * vs * vs;
 }
-// coefficient adjoint k at padded point (z, x), summed over shots and steps
-__device__ __forceinline__ double gsum(const double* gacc, const Geom& g, int k, int z, int x) {
-  return gacc[(size_t)k * g.fstride + (size_t)z * g.NXp + x];
+// coefficient adjoint k at padded point (z, x), summed over shots and steps:
+// the shot groups' compensated sums [ngrp][5][hi, lo][NZ][NXp], in FP64
+// and in group order
+__device__ __forceinline__ double gsum(const float* gacc, const Geom& g, int ngrp, int k,
+                                       int z, int x) {
+  double t = 0.0;
+  for (int q = 0; q < ngrp; ++q) {
+    const float* G = gacc + ((size_t)q * 10 + 2 * k) * g.fstride + (size_t)z * g.NXp + x;
+    t += (double)G[0] + (double)G[g.fstride];
+  }
+  return t;
 }
 
-__global__ void el_grad_kernel(const Geom g, const double* gacc, const float* model, int padded,
-                               double sc, float* grad, const int* status) {
+__global__ void el_grad_kernel(const Geom g, const float* gacc, int ngrp, const float* model,
+                               int padded, double sc, float* grad, const int* status) {
   if (*status) return;
   const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= g.nx) return;
@@ -258,8 +660,8 @@ __global__ void el_grad_kernel(const Geom g, const double* gacc, const float* mo
   const double vp = mval(model, g, padded, 0, Z, X), vs = mval(model, g, padded, 1, Z, X);
   const double rho = mval(model, g, padded, 2, Z, X), mu = rho * vs * vs;
   // lam = rho (vp^2 - 2 vs^2): cl2m = sc (lam + 2 mu), clam = sc lam
-  const double gl2m = gsum(gacc, g, G_L2M, Z, X);
-  const double glam = sc * (gl2m + gsum(gacc, g, G_LAM, Z, X));
+  const double gl2m = gsum(gacc, g, ngrp, G_L2M, Z, X);
+  const double glam = sc * (gl2m + gsum(gacc, g, ngrp, G_LAM, Z, X));
   double gmu = 2.0 * sc * gl2m;
   double grho = 0.0;
   // cmu at (pz, px) = sc 4 / sum 1/mu over (pz|pz+1) x (px|px+1), clamped
@@ -280,7 +682,7 @@ __global__ void el_grad_kernel(const Geom g, const double* gacc, const float* mo
       }
       if (mult == 0 || zero) continue;
       const double mxz = 4.0 / inv;
-      gmu += mult * sc * gsum(gacc, g, G_MU, pz, px) * mxz * mxz / (4.0 * mu * mu);
+      gmu += mult * sc * gsum(gacc, g, ngrp, G_MU, pz, px) * mxz * mxz / (4.0 * mu * mu);
     }
   // cbx at (Z, px) = sc 2 / (rho(Z, px) + rho(Z, px+1)), cbz likewise in z
   for (int dx = -1; dx <= 0; ++dx) {
@@ -290,7 +692,7 @@ __global__ void el_grad_kernel(const Geom g, const double* gacc, const float* mo
     const int mult = (px == X) + (px1 == X);
     if (!mult) continue;
     const double r2 = mval(model, g, padded, 2, Z, px) + mval(model, g, padded, 2, Z, px1);
-    grho += mult * sc * gsum(gacc, g, G_BX, Z, px) * (-2.0 / (r2 * r2));
+    grho += mult * sc * gsum(gacc, g, ngrp, G_BX, Z, px) * (-2.0 / (r2 * r2));
   }
   for (int dz = -1; dz <= 0; ++dz) {
     const int pz = Z + dz;
@@ -299,7 +701,7 @@ __global__ void el_grad_kernel(const Geom g, const double* gacc, const float* mo
     const int mult = (pz == Z) + (pz1 == Z);
     if (!mult) continue;
     const double r2 = mval(model, g, padded, 2, pz, X) + mval(model, g, padded, 2, pz1, X);
-    grho += mult * sc * gsum(gacc, g, G_BZ, pz, X) * (-2.0 / (r2 * r2));
+    grho += mult * sc * gsum(gacc, g, ngrp, G_BZ, pz, X) * (-2.0 / (r2 * r2));
   }
   const size_t M = (size_t)g.nz * g.nx, o = (size_t)i * g.nx + j;
   grad[o] = (float)(glam * 2.0 * rho * vp);
@@ -359,32 +761,78 @@ void launch_el_snapshot(const ElSnapArgs& a, cudaStream_t st) {
   note_launches(1);
 }
 
+int el_adj_shot_group(const Geom& g) {
+  // units = tiles x groups; halve the group until there are units enough
+  // for about six per SM of a GB300 (fewer shots per group: more FP64
+  // accumulator traffic, one addition per group and step)
+  const long long tiles =
+      (long long)((g.NZ + TA_Z - 1) / TA_Z) * ((g.NXp + TA_X - 1) / TA_X);
+  int sg = std::max(g.nshot, 1);
+  while (sg > 1 && tiles * ((g.nshot + sg - 1) / sg) < 912) sg = (sg + 1) / 2;
+  return sg;
+}
+
+bool el_adj_maps(ElAdjArgs& a) {
+  const Geom& g = a.g;
+  const uint64_t S = (uint64_t)(g.nshot > 0 ? g.nshot : 1);
+  auto f3 = [&](CUtensorMap* m, const float* base) {
+    return make_tensor_map(m, base, 3, g.NX, g.NZ, S, g.NXp, (uint64_t)g.fstride, A_W, A_H, 1);
+  };
+  auto f2 = [&](CUtensorMap* m, const float* base) {
+    return make_tensor_map(m, base, 2, g.NX, g.NZ, 1, g.NXp, (uint64_t)g.fstride, A_W, A_H, 1);
+  };
+  a.sg = el_adj_shot_group(g);
+  a.ngrp = (g.nshot + a.sg - 1) / a.sg;
+  a.ntx = (g.NXp + TA_X - 1) / TA_X;
+  a.units = a.ntx * ((g.NZ + TA_Z - 1) / TA_Z) * a.ngrp;
+  return f3(&a.m_atxx, a.atxx) && f3(&a.m_atzz, a.atzz) && f3(&a.m_atxz, a.atxz) &&
+         f3(&a.m_avx, a.avx) && f3(&a.m_avz, a.avz) && f2(&a.m_l2m, a.cl2m) &&
+         f2(&a.m_lam, a.clam) && f2(&a.m_mu, a.cmu) && f2(&a.m_cbx, a.cbx) &&
+         f2(&a.m_cbz, a.cbz);
+}
+
+bool el_adj_forward_maps(ElAdjArgs& a) {
+  const Geom& g = a.g;
+  const uint64_t S = (uint64_t)(g.nshot > 0 ? g.nshot : 1);
+  auto f3 = [&](CUtensorMap* m, const float* base) {
+    return make_tensor_map(m, base, 3, g.NX, g.NZ, S, g.NXp, (uint64_t)g.fstride, A_W, A_H, 1);
+  };
+  return f3(&a.m_fvx, a.fvx) && f3(&a.m_fvz, a.fvz) && f3(&a.m_ftxx, a.ftxx) &&
+         f3(&a.m_ftzz, a.ftzz) && f3(&a.m_ftxz, a.ftxz);
+}
+
 void launch_el_adj_step(const ElAdjArgs& a, cudaStream_t st) {
   const Geom& g = a.g;
-  const dim3 grid((g.NXp + AT - 1) / AT, g.NZ, g.nshot);
-  const dim3 cells((g.NXp + AT - 1) / AT, g.NZ);  // pointwise kernels: all shots per thread
+  if (a.units <= 0) return;
+  static const bool attr = [] {  // thread-safe one-time initialisation
+    cudaFuncSetAttribute(el_adj_str_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kAStrSmem);
+    cudaFuncSetAttribute(el_adj_vel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kAVelSmem);
+    return true;
+  }();
+  (void)attr;
+  const int grid = std::min(device_sms(), a.units);
   int k = 0;
   if (a.wgrad) {
     el_adj_src_kernel<<<(g.nshot + 127) / 128, 128, 0, st>>>(a);
     ++k;
   }
-  el_adj_str_pt_kernel<<<cells, AT, 0, st>>>(a);
-  el_adj_str_sc_kernel<<<grid, AT, 0, st>>>(a);
-  k += 2;
+  el_adj_str_kernel<<<grid, A_THREADS, kAStrSmem, st>>>(a);
+  ++k;
   if (a.res && g.nrec > 0) {
     el_adj_rec_kernel<<<dim3((g.nrec + 127) / 128, g.nshot), 128, 0, st>>>(a);
     ++k;
   }
-  el_adj_vel_pt_kernel<<<cells, AT, 0, st>>>(a);
-  el_adj_vel_sc_kernel<<<grid, AT, 0, st>>>(a);
-  note_launches(k + 2);
+  el_adj_vel_kernel<<<grid, A_THREADS, kAVelSmem, st>>>(a);
+  note_launches(k + 1);
 }
 
-void launch_el_grad(const Geom& g, const double* gacc, const float* model, int padded, float dx,
-                    float dt, float* grad, const int* status, cudaStream_t st) {
+void launch_el_grad(const Geom& g, const float* gacc, int ngrp, const float* model, int padded,
+                    float dx, float dt, float* grad, const int* status, cudaStream_t st) {
   const double sc = (double)dt / (double)dx;
-  el_grad_kernel<<<dim3((g.nx + 127) / 128, g.nz), 128, 0, st>>>(g, gacc, model, padded, sc,
-                                                                 grad, status);
+  el_grad_kernel<<<dim3((g.nx + 127) / 128, g.nz), 128, 0, st>>>(g, gacc, ngrp, model, padded,
+                                                                 sc, grad, status);
   note_launches(1);
 }
 

@@ -50,19 +50,21 @@ void launch_el_step(const ElStepArgs& a, cudaStream_t st);
 
 // Elastic adjoint step (elastic_adjoint.cu): the transpose of one
 // ElStepArgs step, run backwards in time.  Adjoint state (vx, vz, txx, tzz,
-// txz, p1..p8) in av*, at*, ap; e0..e3 scratch fields [S][NZ][NXp].  With
-// gacc non-null the step also adds d J / d (cl2m, clam, cmu, cbx, cbz),
-// summed over the shots, to the FP64 accumulators gacc [5][NZ][NXp], from
-// the forward state: fvx, fvz = v^{n+1/2} and fp = p1..p8 after step n,
-// ft* = tau^n (before the step).
+// txz) in av*, at*; adjoint memory variables p1..p8 read from ap_in and
+// written to ap_out (two buffers, swapped by the caller every step).  With
+// gacc non-null the step also adds d J / d (cl2m, clam, cmu, cbx, cbz) to
+// the accumulators gacc [ngrp][5][2][NZ][NXp]: compensated FP32 sums (hi,
+// lo planes; shot group q's shots, in shot order, into block q), from the
+// forward state: fvx, fvz = v^{n+1/2} and fp = p1..p8 after step n, ft* =
+// tau^n (before the step).
 struct ElAdjArgs {
   Geom g;
   float *avx, *avz, *atxx, *atzz, *atxz;
-  float* ap[8];
-  float *e0, *e1, *e2, *e3;
+  const float* ap_in[8];
+  float* ap_out[8];
   const float *fvx, *fvz, *ftxx, *ftzz, *ftxz;
   const float* fp[8];
-  double* gacc;
+  float* gacc;
   const float *cbx, *cbz, *cl2m, *clam, *cmu;
   const float *ax, *bx, *axh, *bxh, *az, *bz, *azh, *bzh;
   const float* res;     // [S][2][R][nt] injected at the receivers, or null
@@ -72,7 +74,22 @@ struct ElAdjArgs {
   float src_scale;      // dt / dx^2
   const int* status;
   int n;
+  // TMA descriptors (el_adj_maps; the forward state's by el_adj_forward_maps
+  // whenever fvx .. ftxz change): boxes of a tile +- 2 rows and +- 4 columns
+  CUtensorMap m_atxx, m_atzz, m_atxz, m_avx, m_avz;
+  CUtensorMap m_fvx, m_fvz, m_ftxx, m_ftzz, m_ftxz;
+  CUtensorMap m_l2m, m_lam, m_mu, m_cbx, m_cbz;
+  int sg, ngrp;       // shots per group, groups
+  int units, ntx;     // (tile, group) units of the persistent kernels
 };
+// Shots per group of the adjoint kernels for this geometry (the workspace
+// holds ceil(nshot / group) accumulator blocks).
+int el_adj_shot_group(const Geom& g);
+// Fill the descriptors of the adjoint state and coefficients and the unit
+// counts (false on a driver error); el_adj_forward_maps: those of the
+// forward state fvx, fvz, ftxx, ftzz, ftxz.
+bool el_adj_maps(ElAdjArgs& a);
+bool el_adj_forward_maps(ElAdjArgs& a);
 void launch_el_adj_step(const ElAdjArgs& a, cudaStream_t st);
 // Copy of a forward state for the adjoint (elastic_adjoint.cu): the five
 // wavefields everywhere, each memory variable only where its profile pair
@@ -86,9 +103,9 @@ struct ElSnapArgs {
   const float *ax, *bx, *axh, *bxh, *az, *bz, *azh, *bzh;
 };
 void launch_el_snapshot(const ElSnapArgs& a, cudaStream_t st);
-// d J / d (vp, vs, rho) on interior cells, [3][nz][nx], from the FP64
-// coefficient adjoints; padding held fixed.
-void launch_el_grad(const Geom& g, const double* gacc, const float* model, int padded, float dx,
-                    float dt, float* grad, const int* status, cudaStream_t st);
+// d J / d (vp, vs, rho) on interior cells, [3][nz][nx], from the
+// coefficient adjoints (summed over the groups in FP64); padding held fixed.
+void launch_el_grad(const Geom& g, const float* gacc, int ngrp, const float* model, int padded,
+                    float dx, float dt, float* grad, const int* status, cudaStream_t st);
 
 }  // namespace sweep

@@ -120,7 +120,8 @@ struct Layout {
   // elastic adjoint state (same 13 fields in the same order), scratch, the
   // per-shot coefficient adjoints, and the checkpoints / segment states of
   // the forward replay (each a copy of the range [fwd_lo, fwd_hi))
-  size_t el_a = 0, el_e[4] = {0, 0, 0, 0}, el_g = 0, el_ck = 0, el_seg = 0;
+  size_t el_a = 0, el_ap2 = 0, el_g = 0, el_ck = 0, el_seg = 0;
+  int el_ngrp = 0;  // FP64 accumulator blocks of the adjoint kernels
   int el_C = 0, el_ncp = 0;
   size_t loop = 0, loopbar = 0;   // acoustic time-loop arguments, barrier words
   size_t rtile = 0, rlist = 0;    // receiver lists of the backward stencil units
@@ -211,7 +212,7 @@ Layout layout(const sweep_problem* p, int mode) {
       L.adj_lo = b.off;
       L.el_a = b.take(L.fwd_hi - L.fwd_lo);
       L.adj_hi = b.off;
-      for (int i = 0; i < 4; ++i) L.el_e[i] = b.take(F);
+      L.el_ap2 = b.take(8 * F);  // second buffer of the adjoint memory variables
     }
     if (mode == SWEEP_MODE_GRADIENT) {
       // sqrt(nt) checkpoints of the forward state, and one segment of
@@ -220,7 +221,10 @@ Layout layout(const sweep_problem* p, int mode) {
       while ((long long)C * C < g.nt) ++C;
       L.el_C = C;
       L.el_ncp = (g.nt + C - 1) / C;
-      L.el_g = b.take(5 * sizeof(double) * (size_t)g.fstride);  // FP64, summed over shots
+      const int sg = el_adj_shot_group(g);
+      L.el_ngrp = (g.nshot + sg - 1) / sg;
+      // per shot group: compensated FP32 sums (hi and lo planes)
+      L.el_g = b.take((size_t)L.el_ngrp * 10 * sizeof(float) * (size_t)g.fstride);
       L.data = b.take(sizeof(float) * (size_t)g.nshot * 2 * g.nrec * g.nt);
       L.el_ck = b.take((L.fwd_hi - L.fwd_lo) * (size_t)L.el_ncp);
       L.el_seg = b.take((L.fwd_hi - L.fwd_lo) * (size_t)C);
@@ -699,11 +703,22 @@ int elastic_reverse_loop(const sweep_problem* p, const Layout& L, void* ws, cons
   a.atxx = state_field(L, adj, 2);
   a.atzz = state_field(L, adj, 3);
   a.atxz = state_field(L, adj, 4);
-  for (int i = 0; i < 8; ++i) a.ap[i] = state_field(L, adj, 5 + i);
-  a.e0 = at<float>(ws, L.el_e[0]);
-  a.e1 = at<float>(ws, L.el_e[1]);
-  a.e2 = at<float>(ws, L.el_e[2]);
-  a.e3 = at<float>(ws, L.el_e[3]);
+  // adjoint memory variables: the state's p1..p8 and a second buffer,
+  // read from one and written to the other, swapped every step
+  float* apb[2][8];
+  for (int i = 0; i < 8; ++i) {
+    apb[0][i] = state_field(L, adj, 5 + i);
+    apb[1][i] = at<float>(ws, L.el_ap2) + (size_t)i * g.fstride * g.nshot;
+  }
+  cudaMemsetAsync(at<char>(ws, L.el_ap2), 0, 8 * sizeof(float) * (size_t)g.fstride * g.nshot,
+                  st);
+  int cur = 0;
+  auto set_ap = [&]() {
+    for (int i = 0; i < 8; ++i) {
+      a.ap_in[i] = apb[cur][i];
+      a.ap_out[i] = apb[cur ^ 1][i];
+    }
+  };
   a.cbx = at<float>(ws, L.el_par[0]);
   a.cbz = at<float>(ws, L.el_par[1]);
   a.cl2m = at<float>(ws, L.el_par[2]);
@@ -723,15 +738,18 @@ int elastic_reverse_loop(const sweep_problem* p, const Layout& L, void* ws, cons
   a.wgrad = wgrad;
   a.src_scale = (float)((double)p->dt / ((double)p->dx * p->dx));
   a.status = at<int>(ws, L.status);
+  if (!el_adj_maps(a)) return SWEEP_ECUDA;
   if (!gradient) {
     for (int n = g.nt - 1; n >= 0; --n) {
       a.n = n;
+      set_ap();
       launch_el_adj_step(a, st);
+      cur ^= 1;
     }
     return SWEEP_OK;
   }
-  a.gacc = at<double>(ws, L.el_g);
-  cudaMemsetAsync(a.gacc, 0, 5 * sizeof(double) * (size_t)g.fstride, st);
+  a.gacc = at<float>(ws, L.el_g);
+  cudaMemsetAsync(a.gacc, 0, (size_t)a.ngrp * 10 * sizeof(float) * (size_t)g.fstride, st);
   char* state = at<char>(ws, L.fwd_lo);
   char* ck = at<char>(ws, L.el_ck);
   char* seg = at<char>(ws, L.el_seg);
@@ -767,8 +785,11 @@ int elastic_reverse_loop(const sweep_problem* p, const Layout& L, void* ws, cons
       a.ftxx = state_field(L, before, 2);
       a.ftzz = state_field(L, before, 3);
       a.ftxz = state_field(L, before, 4);
+      if (!el_adj_forward_maps(a)) return SWEEP_ECUDA;
       a.n = n;
+      set_ap();
       launch_el_adj_step(a, st);
+      cur ^= 1;
     }
   }
   return SWEEP_OK;
@@ -915,8 +936,9 @@ int sweep_gradient(const sweep_problem* p, const float* model, const float* wave
     note_launches(2);
     rc = elastic_reverse_loop(p, L, ws, wavelet, src, rec, d, nullptr, true, st);
     if (rc) return rc;
-    launch_el_grad(g, at<double>(ws, L.el_g), model, (p->flags & SWEEP_F_PADDED_MODEL) ? 1 : 0,
-                   p->dx, p->dt, grad, at<int>(ws, L.status), st);
+    launch_el_grad(g, at<float>(ws, L.el_g), L.el_ngrp, model,
+                   (p->flags & SWEEP_F_PADDED_MODEL) ? 1 : 0, p->dx, p->dt, grad,
+                   at<int>(ws, L.status), st);
     return cuda_rc(cudaGetLastError());
   }
   launch_setup(setup_args(p, L, ws, model, src, rec), st);

@@ -230,3 +230,49 @@ def test_elastic_gradient_layered_fluid_top(sw, golden):
     for k in range(3):
         assert np.abs(gref[k]).max() > 0
         assert rel(g[k], gref[k]) <= 1e-3, (k, rel(g[k], gref[k]))
+
+
+def test_elastic_adjoint_kernels_multi_unit_vs_oracle(sw):
+    """The adjoint kernels' pipeline beyond one unit per CTA: 129x133 + 11
+    (20 tiles of 16 x 128), 93 shots, so the shots go in groups of 2 (47
+    groups, the last with one shot and an empty slot) and every CTA runs
+    12-14 (tile, shot) steps through its two stages; nt 60 (segments of 8,
+    the last one short).  Receivers within 6 cells of the source, clipped to
+    the grid, so that shots near an edge have several receivers on one cell
+    (their residuals must add up).  Gradient per parameter and wavelet
+    adjoint, whole and per shot, against the FP64 oracle."""
+    nz, nx, pml, nt, nshot, nrec = 129, 133, 11, 60, 93, 7
+    rng = np.random.default_rng(21)
+    m = random_model(nz, nx, 21)
+    src = np.stack([rng.integers(2, nz - 2, nshot), rng.integers(2, nx - 2, nshot)], -1)
+    # receivers within 6 cells of their shot's source, so that every shot's
+    # adjoint wave reaches its source within nt steps
+    off = rng.integers(-6, 7, (nshot, nrec, 2))
+    rec = np.stack([np.clip(src[:, None, 0] + off[..., 0], 0, nz - 1),
+                    np.clip(src[:, None, 1] + off[..., 1], 0, nx - 1)], -1)
+    dt, dx, f0 = 4e-4, 5.0, 25.0
+    w = np.stack([inputs.ricker(f0 * (1 + 0.01 * (k % 7)), dt, nt) for k in range(nshot)]) * 1e6
+    mt = m.copy()
+    mt[0, 30:60, 20:50] *= 1.04
+    mt[1, 70:100, 60:110] *= 0.95
+    mt[2, 10:40, 90:120] *= 1.05
+    kw = dict(nz=nz, nx=nx, pml=pml, dx=dx, dt=dt, nt=nt, nshot=nshot, nrec=nrec, f_ref=f0,
+              v_pml=4000.0)
+    p = sw.problem(sw.ELASTIC, **kw)
+    q = oracle.make_problem(1, nz, nx, pml, np.float32(dx), np.float32(dt), nt, nshot, nrec,
+                            np.float32(f0), v_pml=4000.0)
+    dobs = oracle.elastic_forward(q, f32(mt), f32(w), src, rec).astype(np.float32)
+    mtt, wt, st, rt = _tensors(sw, m, w, src, rec)
+    g, J, _ = sw.sweep_gradient(p, mtt, wt, st, rt, torch.tensor(dobs, device="cuda"))
+    g = g.cpu().numpy()
+    gref, Jref = oracle.elastic_gradient(q, f32(m), f32(w), src, rec, dobs.astype(np.float64))
+    assert abs(float(J) - Jref) <= 2e-3 * Jref, (float(J), Jref)
+    for k in range(3):
+        assert np.abs(gref[k]).max() > 0
+        assert rel(g[k], gref[k]) <= 1e-3, (k, rel(g[k], gref[k]))
+    adj = rng.standard_normal((nshot, 2, nrec, nt)).astype(np.float32)
+    wg = sw.sweep_adjoint(p, mtt, torch.tensor(adj, device="cuda"), st, rt).cpu().numpy()
+    ref = oracle.elastic_adjoint(q, f32(m), adj.astype(np.float64), src, rec)
+    assert rel(wg, ref) <= 1e-4, rel(wg, ref)
+    per_shot = [rel(wg[s], ref[s]) for s in range(nshot)]
+    assert max(per_shot) <= 1e-3, max(per_shot)
