@@ -93,7 +93,7 @@ constexpr size_t kAStrSmem = A_STAGES * sizeof(AStrStage) + sizeof(ATerms) + 8 *
 constexpr size_t kAVelSmem = A_STAGES * sizeof(AVelStage) + sizeof(ATerms) + 8 * A_STAGES;
 static_assert(kAStrSmem <= 227 * 1024 && kAVelSmem <= 227 * 1024, "shared memory");
 
-enum : int { AU_XS = 1, AU_ZS = 2 };
+enum : int { AU_XS = 1, AU_ZS = 2, AU_PLAIN = 4 };
 struct AUnit {
   int s, z0, x0, flags, grp;
   bool valid, first, last;
@@ -118,6 +118,11 @@ __device__ __forceinline__ AUnit a_unit(const ElAdjArgs& a, int j) {
   int f = 0;  // the box meets a CPML strip (an integer or half-point profile is nonzero)
   if (g.P > 0 && (u.x0 - 4 < g.P || u.x0 + TA_X + 4 > g.P + g.nx - 1)) f |= AU_XS;
   if (g.P > 0 && (u.z0 - 2 < g.P || u.z0 + TA_Z + 2 > g.P + g.nz - 1)) f |= AU_ZS;
+  // plain: no strip, and the box inside the grid; there every memory
+  // variable and profile is zero, so exz-bar = ezx-bar (stress) and the two
+  // terms of each velocity component are equal
+  if (!f && u.z0 >= 2 && u.z0 + TA_Z + 2 <= g.NZ && u.x0 >= 4 && u.x0 + TA_X + 4 <= g.NX)
+    f |= AU_PLAIN;
   u.flags = f;
   return u;
 }
@@ -314,7 +319,29 @@ __global__ void __launch_bounds__(A_THREADS, 1)
     v4(ld4z(a.avx + ci, cell), vx);
     v4(ld4z(a.avz + ci, cell), vz);
     if (!wait()) return false;
-    if (u.valid) {
+    const bool plain = u.flags & AU_PLAIN;
+    if (u.valid && plain) {
+      // 1. (plain unit) exx-bar, ezz-bar and ezx-bar = exz-bar on the box
+      for (int gi = threadIdx.x; gi < A_H * A_G4; gi += A_THREADS) {
+        const int br = gi / A_G4, bc = 4 * (gi - br * A_G4);
+        float txx[4], tzz[4], txz[4], l2m[4], lam[4], mu[4], e0[4], e1[4], e2[4];
+        v4(lda4(sg.txx, br, bc), txx);
+        v4(lda4(sg.tzz, br, bc), tzz);
+        v4(lda4(sg.txz, br, bc), txz);
+        v4(lda4(sg.l2m, br, bc), l2m);
+        v4(lda4(sg.lam, br, bc), lam);
+        v4(lda4(sg.mu, br, bc), mu);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          e0[k] = l2m[k] * txx[k] + lam[k] * tzz[k];
+          e1[k] = lam[k] * txx[k] + l2m[k] * tzz[k];
+          e2[k] = mu[k] * txz[k];
+        }
+        sta4(T.t[0], br, bc, e0);
+        sta4(T.t[1], br, bc, e1);
+        sta4(T.t[2], br, bc, e2);
+      }
+    } else if (u.valid) {
       // 1. the terms on the whole box; new p5..p8 on the tile's own cells
       for (int gi = threadIdx.x; gi < A_H * A_G4; gi += A_THREADS) {
         const int br = gi / A_G4, bc = 4 * (gi - br * A_G4);
@@ -372,6 +399,8 @@ __global__ void __launch_bounds__(A_THREADS, 1)
           st4v(a.ap_out[6] + c, n7);
         }
       }
+    }
+    if (u.valid) {
       __syncthreads();
       // 2. v-bar -= D^T terms on the tile; coefficient adjoints (the forward
       // memory variables p5..p8 read here: only strip units have them)
@@ -384,7 +413,7 @@ __global__ void __launch_bounds__(A_THREADS, 1)
         const int R = r + 2;
         float e[12], f[12];
         row12(T.t[0], R, lx, e);  // exx-bar
-        row12(T.t[3], R, lx, f);  // exz-bar
+        row12(plain ? T.t[2] : T.t[3], R, lx, f);  // exz-bar
         float m2[4], m1[4], c0[4], p1[4];
         v4(lda4(T.t[2], R - 2, lx + 4), m2);  // ezx-bar rows R-2 .. R+1
         v4(lda4(T.t[2], R - 1, lx + 4), m1);
@@ -503,7 +532,25 @@ __global__ void __launch_bounds__(A_THREADS, 1)
     v4(ld4z(a.atzz + ci, cell), tzz);
     v4(ld4z(a.atxz + ci, cell), txz);
     if (!wait()) return false;
-    if (u.valid) {
+    const bool plain = u.flags & AU_PLAIN;
+    if (u.valid && plain) {
+      // (plain unit) one term per velocity component: d0 = d1, d2 = d3
+      for (int gi = threadIdx.x; gi < A_H * A_G4; gi += A_THREADS) {
+        const int br = gi / A_G4, bc = 4 * (gi - br * A_G4);
+        float vx[4], vz[4], cbx[4], cbz[4], d0[4], d2[4];
+        v4(lda4(sg.vx, br, bc), vx);
+        v4(lda4(sg.vz, br, bc), vz);
+        v4(lda4(sg.cbx, br, bc), cbx);
+        v4(lda4(sg.cbz, br, bc), cbz);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          d0[k] = cbx[k] * vx[k];
+          d2[k] = cbz[k] * vz[k];
+        }
+        sta4(T.t[0], br, bc, d0);
+        sta4(T.t[2], br, bc, d2);
+      }
+    } else if (u.valid) {
       for (int gi = threadIdx.x; gi < A_H * A_G4; gi += A_THREADS) {
         const int br = gi / A_G4, bc = 4 * (gi - br * A_G4);
         const int zz = u.z0 - 2 + br, xx = u.x0 - 4 + bc;
@@ -557,6 +604,8 @@ __global__ void __launch_bounds__(A_THREADS, 1)
           st4v(a.ap_out[3] + c, n4);
         }
       }
+    }
+    if (u.valid) {
       __syncthreads();
       if (cell) {
         const int R = r + 2;
@@ -565,14 +614,16 @@ __global__ void __launch_bounds__(A_THREADS, 1)
           row12(T.t[0], R, lx, d0);
           row12(T.t[2], R, lx, d2);
           float a1[4], a0[4], b1[4], b2[4], m2[4], m1[4], c0[4], p1[4];
-          v4(lda4(T.t[1], R - 1, lx + 4), a1);  // d1 rows R-1 .. R+2
-          v4(lda4(T.t[1], R, lx + 4), a0);
-          v4(lda4(T.t[1], R + 1, lx + 4), b1);
-          v4(lda4(T.t[1], R + 2, lx + 4), b2);
-          v4(lda4(T.t[3], R - 2, lx + 4), m2);  // d3 rows R-2 .. R+1
-          v4(lda4(T.t[3], R - 1, lx + 4), m1);
-          v4(lda4(T.t[3], R, lx + 4), c0);
-          v4(lda4(T.t[3], R + 1, lx + 4), p1);
+          const float* t1 = plain ? T.t[0] : T.t[1];
+          const float* t3 = plain ? T.t[2] : T.t[3];
+          v4(lda4(t1, R - 1, lx + 4), a1);  // d1 rows R-1 .. R+2
+          v4(lda4(t1, R, lx + 4), a0);
+          v4(lda4(t1, R + 1, lx + 4), b1);
+          v4(lda4(t1, R + 2, lx + 4), b2);
+          v4(lda4(t3, R - 2, lx + 4), m2);  // d3 rows R-2 .. R+1
+          v4(lda4(t3, R - 1, lx + 4), m1);
+          v4(lda4(t3, R, lx + 4), c0);
+          v4(lda4(t3, R + 1, lx + 4), p1);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             if (x + k >= g.NX) continue;
