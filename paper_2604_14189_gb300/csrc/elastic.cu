@@ -309,15 +309,15 @@ __global__ void __launch_bounds__(E_THREADS, 1) el_vel_kernel(const __grid_const
         outz[c] = vz[q][c] + bzv[c] * (dxt + dzt);
       }
       const size_t ci = so + (size_t)z * g.NXp + gx;
-      stg4(a.vx + ci, outx);
-      stg4(a.vz + ci, outz);
+      stg4(a.vx_o + ci, outx);
+      stg4(a.vz_o + ci, outz);
       if (xs) {
-        stg4(a.p1 + ci, p1[q]);
-        stg4(a.p3 + ci, p3[q]);
+        stg4(a.p1_o + ci, p1[q]);
+        stg4(a.p3_o + ci, p3[q]);
       }
       if (zs) {
-        stg4(a.p2 + ci, p2[q]);
-        stg4(a.p4 + ci, p4[q]);
+        stg4(a.p2_o + ci, p2[q]);
+        stg4(a.p4_o + ci, p4[q]);
       }
     }
     return true;
@@ -436,16 +436,16 @@ __global__ void __launch_bounds__(E_THREADS, 1) el_str_kernel(const __grid_const
           }
       }
       const size_t ci = so + (size_t)z * g.NXp + gx;
-      stg4(a.txx + ci, txx[q]);
-      stg4(a.tzz + ci, tzz[q]);
-      stg4(a.txz + ci, txz[q]);
+      stg4(a.txx_o + ci, txx[q]);
+      stg4(a.tzz_o + ci, tzz[q]);
+      stg4(a.txz_o + ci, txz[q]);
       if (xs) {
-        stg4(a.p5 + ci, p5[q]);
-        stg4(a.p8 + ci, p8[q]);
+        stg4(a.p5_o + ci, p5[q]);
+        stg4(a.p8_o + ci, p8[q]);
       }
       if (zs) {
-        stg4(a.p6 + ci, p6[q]);
-        stg4(a.p7 + ci, p7[q]);
+        stg4(a.p6_o + ci, p6[q]);
+        stg4(a.p7_o + ci, p7[q]);
       }
     }
     return true;
@@ -464,8 +464,8 @@ __global__ void el_rec_kernel(const ElStepArgs a) {
   if (r >= g.nrec) return;
   const int32_t* q = a.rec + 2 * ((size_t)s * g.nrec + r);
   const size_t c = (size_t)s * g.fstride + (size_t)(q[0] + g.P) * g.NXp + (q[1] + g.P);
-  a.data[(((size_t)s * 2 + 0) * g.nrec + r) * g.nt + a.n] = a.vx[c];
-  a.data[(((size_t)s * 2 + 1) * g.nrec + r) * g.nt + a.n] = a.vz[c];
+  a.data[(((size_t)s * 2 + 0) * g.nrec + r) * g.nt + a.n] = a.vx_o[c];
+  a.data[(((size_t)s * 2 + 1) * g.nrec + r) * g.nt + a.n] = a.vz_o[c];
 }
 
 }  // namespace
@@ -488,8 +488,8 @@ bool el_step_maps(ElStepArgs& a) {
     return make_tensor_map(m, base, 2, g.NX, g.NZ, 1, g.NXp, (uint64_t)g.fstride, TB_X, TB_Z, 1);
   };
   bool ok = f3(&a.m_txx, a.txx, E_HW, TB_Z) && f3(&a.m_txz, a.txz, E_HW, E_HZ) &&
-            f3(&a.m_tzz, a.tzz, TB_X, E_HZ) && f3(&a.m_vx, a.vx, E_HW, E_HZ) &&
-            f3(&a.m_vz, a.vz, E_HW, E_HZ) && f2(&a.m_cbx, a.cbx) && f2(&a.m_cbz, a.cbz) &&
+            f3(&a.m_tzz, a.tzz, TB_X, E_HZ) && f3(&a.m_vx, a.vx_o, E_HW, E_HZ) &&
+            f3(&a.m_vz, a.vz_o, E_HW, E_HZ) && f2(&a.m_cbx, a.cbx) && f2(&a.m_cbz, a.cbz) &&
             f2(&a.m_l2m, a.cl2m) && f2(&a.m_lam, a.clam) && f2(&a.m_mu, a.cmu);
   a.ntx = (g.NXp + TB_X - 1) / TB_X;
   a.units = a.ntx * ((g.NZ + TB_Z - 1) / TB_Z) * g.nshot;

@@ -240,9 +240,9 @@ __device__ __forceinline__ void a_pipeline(const ElAdjArgs& a, unsigned char* sm
   }
 }
 
-// A replayed forward memory variable holds its value only where its profile
-// pair is nonzero (the snapshot copies nothing elsewhere): read it there, 0
-// elsewhere.  pa, pb: the pair, at cells x .. x+3 (x axis) or row z.
+// A replayed forward memory variable is valid only on the tiles that meet
+// its strip (the replay writes it nowhere else): read it where its profile
+// pair is nonzero, 0 elsewhere.  pa, pb: the pair, at cells x .. x+3 (x axis) or row z.
 __device__ __forceinline__ void fp_x(const float* f, const float* pa, const float* pb, int x,
                                      bool ok, float* o) {
   float A[4], B[4], v[4];
@@ -761,56 +761,6 @@ __global__ void el_grad_kernel(const Geom g, const float* gacc, int ngrp, const 
 }
 
 }  // namespace
-
-namespace {
-
-// profile pair of memory variable k (p1..p8): x axis?, half points?
-__device__ __forceinline__ bool snap_on(const ElSnapArgs& a, int k, int z, int x) {
-  const Geom& g = a.g;
-  const bool xaxis = k == 0 || k == 2 || k == 4 || k == 7;
-  const bool half = k == 0 || k == 3 || k == 6 || k == 7;
-  if (!xaxis) {
-    const float A = half ? a.azh[z] : a.az[z], B = half ? a.bzh[z] : a.bz[z];
-    return A != 0.f || B != 0.f;
-  }
-  bool on = false;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    if (x + i < g.NX) {
-      const float A = half ? a.axh[x + i] : a.ax[x + i];
-      const float B = half ? a.bxh[x + i] : a.bx[x + i];
-      on = on || A != 0.f || B != 0.f;
-    }
-  }
-  return on;
-}
-
-// one thread per 4-cell group of a row of one shot
-__global__ void __launch_bounds__(128) el_snapshot_kernel(const ElSnapArgs a) {
-  const Geom& g = a.g;
-  const int x = 4 * (blockIdx.x * 128 + threadIdx.x), z = blockIdx.y, s = blockIdx.z;
-  if (x >= g.NXp) return;
-  const size_t c = (size_t)s * g.fstride + (size_t)z * g.NXp + x;
-#pragma unroll
-  for (int f = 0; f < 5; ++f)
-    *reinterpret_cast<float4*>(a.dst[f] + c) = *reinterpret_cast<const float4*>(a.src[f] + c);
-  if (x >= g.NX) return;
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if (snap_on(a, k, z, x))
-      *reinterpret_cast<float4*>(a.dst[5 + k] + c) =
-          *reinterpret_cast<const float4*>(a.src[5 + k] + c);
-}
-
-}  // namespace
-
-void launch_el_snapshot(const ElSnapArgs& a, cudaStream_t st) {
-  const Geom& g = a.g;
-  if (g.nshot <= 0) return;
-  const dim3 grid((g.NXp / 4 + 127) / 128, g.NZ, g.nshot);
-  el_snapshot_kernel<<<grid, 128, 0, st>>>(a);
-  note_launches(1);
-}
 
 int el_adj_shot_group(const Geom& g) {
   // units = tiles x groups; halve the group until there are units enough

@@ -24,9 +24,15 @@ struct ElParamArgs {
 
 struct ElStepArgs {
   Geom g;
-  float *vx, *vz, *txx, *tzz, *txz;        // [S][NZ][NXp]
+  // state before the step: fields [S][NZ][NXp] and CPML memory variables
+  float *vx, *vz, *txx, *tzz, *txz;
   float *p1, *p2, *p3, *p4;                // velocity CPML memory variables
   float *p5, *p6, *p7, *p8;                // stress CPML memory variables
+  // state after the step (the same buffers for an in-place step; the
+  // gradient's replay writes each step's state into its own slot).  A
+  // memory variable is written on the tiles that meet its strip only.
+  float *vx_o, *vz_o, *txx_o, *tzz_o, *txz_o;
+  float *p1_o, *p2_o, *p3_o, *p4_o, *p5_o, *p6_o, *p7_o, *p8_o;
   const float *cbx, *cbz, *cl2m, *clam, *cmu;
   const float *ax, *bx, *axh, *bxh;        // x profiles (integer, half points)
   const float *az, *bz, *azh, *bzh;        // z profiles
@@ -37,8 +43,9 @@ struct ElStepArgs {
   float src_scale;                         // dt / dx^2
   int* status;
   int n;
-  // TMA descriptors (built by el_step_maps): stress fields with the halos
-  // the velocity kernel needs, velocities with both halos, coefficients
+  // TMA descriptors (built by el_step_maps): stress fields before the step
+  // with the halos the velocity kernel needs, velocities after it (read by
+  // the stress kernel) with both halos, coefficients
   CUtensorMap m_txx, m_txz, m_tzz, m_vx, m_vz;
   CUtensorMap m_cbx, m_cbz, m_l2m, m_lam, m_mu;
   int units, ntx;  // (tile, shot) units of the persistent kernels
@@ -91,18 +98,6 @@ int el_adj_shot_group(const Geom& g);
 bool el_adj_maps(ElAdjArgs& a);
 bool el_adj_forward_maps(ElAdjArgs& a);
 void launch_el_adj_step(const ElAdjArgs& a, cudaStream_t st);
-// Copy of a forward state for the adjoint (elastic_adjoint.cu): the five
-// wavefields everywhere, each memory variable only where its profile pair
-// (a, b) is nonzero (float4 groups meeting that set); elsewhere the
-// variable is zero and the adjoint kernels never read it.  src/dst: fields
-// 0..4 (vx, vz, txx, tzz, txz), 5..12 (p1..p8), each [S][NZ][NXp].
-struct ElSnapArgs {
-  Geom g;
-  const float* src[13];
-  float* dst[13];
-  const float *ax, *bx, *axh, *bxh, *az, *bz, *azh, *bzh;
-};
-void launch_el_snapshot(const ElSnapArgs& a, cudaStream_t st);
 // d J / d (vp, vs, rho) on interior cells, [3][nz][nx], from the
 // coefficient adjoints (summed over the groups in FP64); padding held fixed.
 void launch_el_grad(const Geom& g, const float* gacc, int ngrp, const float* model, int padded,

@@ -625,6 +625,19 @@ float* state_field(const Layout& L, char* state, int k) {  // k: 0..4 fields, 5.
   return reinterpret_cast<float*>(state + (off - L.fwd_lo));
 }
 
+// The step's input state (fields 0..4 and p1..p8 of a state copy at `in`)
+// and where it writes the state after the step.
+void set_step_in(ElStepArgs& a, char* in, const Layout& L) {
+  float** f[13] = {&a.vx, &a.vz, &a.txx, &a.tzz, &a.txz, &a.p1, &a.p2,
+                   &a.p3, &a.p4, &a.p5, &a.p6, &a.p7, &a.p8};
+  for (int i = 0; i < 13; ++i) *f[i] = state_field(L, in, i);
+}
+void set_step_out(ElStepArgs& a, char* out, const Layout& L) {
+  float** f[13] = {&a.vx_o, &a.vz_o, &a.txx_o, &a.tzz_o, &a.txz_o, &a.p1_o, &a.p2_o,
+                   &a.p3_o, &a.p4_o, &a.p5_o, &a.p6_o, &a.p7_o, &a.p8_o};
+  for (int i = 0; i < 13; ++i) *f[i] = state_field(L, out, i);
+}
+
 ElStepArgs elastic_step_args(const sweep_problem* p, const Layout& L, void* ws, char* state,
                              const float* wavelet, const int32_t* src, const int32_t* rec,
                              float* data) {
@@ -637,6 +650,7 @@ ElStepArgs elastic_step_args(const sweep_problem* p, const Layout& L, void* ws, 
   a.txz = state_field(L, state, 4);
   float** ps[8] = {&a.p1, &a.p2, &a.p3, &a.p4, &a.p5, &a.p6, &a.p7, &a.p8};
   for (int i = 0; i < 8; ++i) *ps[i] = state_field(L, state, 5 + i);
+  set_step_out(a, state, L);  // in place
   a.cbx = at<float>(ws, L.el_par[0]);
   a.cbz = at<float>(ws, L.el_par[1]);
   a.cl2m = at<float>(ws, L.el_par[2]);
@@ -755,26 +769,17 @@ int elastic_reverse_loop(const sweep_problem* p, const Layout& L, void* ws, cons
   char* seg = at<char>(ws, L.el_seg);
   ElStepArgs fs = elastic_step_args(p, L, ws, state, wavelet, src, rec, nullptr);
   if (fs.units < 0) return SWEEP_ECUDA;
-  ElSnapArgs sn{};
-  sn.g = g;
-  for (int i = 0; i < 13; ++i) sn.src[i] = state_field(L, state, i);
-  sn.ax = a.ax;
-  sn.bx = a.bx;
-  sn.axh = a.axh;
-  sn.bxh = a.bxh;
-  sn.az = a.az;
-  sn.bz = a.bz;
-  sn.azh = a.azh;
-  sn.bzh = a.bzh;
   for (int k = L.el_ncp - 1; k >= 0; --k) {
     const int n0 = k * L.el_C, n1 = std::min(n0 + L.el_C, g.nt);
-    cudaMemcpyAsync(state, ck + (size_t)k * sb, sb, cudaMemcpyDeviceToDevice, st);
+    // replay the segment from checkpoint k, each step writing the state
+    // after it into its own slot (a memory variable only on the tiles that
+    // meet its strip: the adjoint reads it only where its profile is on)
     for (int n = n0; n < n1; ++n) {
+      set_step_in(fs, n > n0 ? seg + (size_t)(n - n0 - 1) * sb : ck + (size_t)k * sb, L);
+      set_step_out(fs, seg + (size_t)(n - n0) * sb, L);
+      if (!el_step_maps(fs)) return SWEEP_ECUDA;
       fs.n = n;
       launch_el_step(fs, st);
-      // keep the state after step n (memory variables on their strips only)
-      for (int i = 0; i < 13; ++i) sn.dst[i] = state_field(L, seg + (size_t)(n - n0) * sb, i);
-      launch_el_snapshot(sn, st);
     }
     for (int n = n1 - 1; n >= n0; --n) {
       char* after = seg + (size_t)(n - n0) * sb;
