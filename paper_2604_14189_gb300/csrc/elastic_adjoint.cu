@@ -89,8 +89,11 @@ struct __align__(128) ATerms {  // the half's four difference terms on the box
   float t[4][A_BOX];
 };
 static_assert(kABox % 128 == 0, "staged field alignment");
-constexpr size_t kAStrSmem = A_STAGES * sizeof(AStrStage) + sizeof(ATerms) + 8 * A_STAGES;
-constexpr size_t kAVelSmem = A_STAGES * sizeof(AVelStage) + sizeof(ATerms) + 8 * A_STAGES;
+constexpr size_t kATable = 64 * 16;  // unit descriptor table (A_TABLE int4)
+constexpr size_t kAStrSmem =
+    A_STAGES * sizeof(AStrStage) + sizeof(ATerms) + 8 * A_STAGES + kATable;
+constexpr size_t kAVelSmem =
+    A_STAGES * sizeof(AVelStage) + sizeof(ATerms) + 8 * A_STAGES + kATable;
 static_assert(kAStrSmem <= 227 * 1024 && kAVelSmem <= 227 * 1024, "shared memory");
 
 enum : int { AU_XS = 1, AU_ZS = 2, AU_PLAIN = 4 };
@@ -99,11 +102,11 @@ struct AUnit {
   bool valid, first, last;
 };
 
-// Sub-unit j of this CTA: unit blockIdx.x + (j / sg) gridDim.x = (tile,
-// group), shot grp sg + j % sg (past the last shot: an empty sub-unit).
-__device__ __forceinline__ AUnit a_unit(const ElAdjArgs& a, int j) {
+// Unit i of this CTA: unit blockIdx.x + i gridDim.x = (tile, group); its
+// sub-units are the group's shots grp sg + k, k < sg (past the last shot:
+// an empty sub-unit).  The tile part (s, valid, first, last unset).
+__device__ __forceinline__ AUnit a_unit_base(const ElAdjArgs& a, int i) {
   const Geom& g = a.g;
-  const int i = j / a.sg, k = j - i * a.sg;
   const int unit = blockIdx.x + i * gridDim.x;
   const int tile = unit / a.ngrp;
   AUnit u;
@@ -111,10 +114,6 @@ __device__ __forceinline__ AUnit a_unit(const ElAdjArgs& a, int j) {
   const int tz = tile / a.ntx;
   u.z0 = tz * TA_Z;
   u.x0 = (tile - tz * a.ntx) * TA_X;
-  u.s = u.grp * a.sg + k;
-  u.valid = u.s < g.nshot;
-  u.first = k == 0;
-  u.last = k == a.sg - 1;
   int f = 0;  // the box meets a CPML strip (an integer or half-point profile is nonzero)
   if (g.P > 0 && (u.x0 - 4 < g.P || u.x0 + TA_X + 4 > g.P + g.nx - 1)) f |= AU_XS;
   if (g.P > 0 && (u.z0 - 2 < g.P || u.z0 + TA_Z + 2 > g.P + g.nz - 1)) f |= AU_ZS;
@@ -124,6 +123,37 @@ __device__ __forceinline__ AUnit a_unit(const ElAdjArgs& a, int j) {
   if (!f && u.z0 >= 2 && u.z0 + TA_Z + 2 <= g.NZ && u.x0 >= 4 && u.x0 + TA_X + 4 <= g.NX)
     f |= AU_PLAIN;
   u.flags = f;
+  return u;
+}
+
+// Descriptors of this CTA's first A_TABLE units, made once per launch
+// (the tile part, packed: z0, x0, flags, group); later units on the fly.
+constexpr int A_TABLE = 64;
+static_assert(A_TABLE * 16 == kATable, "descriptor table size");
+struct ASub {  // position in this CTA's sub-unit sequence
+  int i, k;    // unit, shot within its group
+  __device__ __forceinline__ void next(int sg) {
+    if (++k == sg) {
+      k = 0;
+      ++i;
+    }
+  }
+};
+__device__ __forceinline__ AUnit a_unit(const ElAdjArgs& a, const int4* tab, ASub q) {
+  AUnit u;
+  if (q.i < A_TABLE) {
+    const int4 t = tab[q.i];
+    u.z0 = t.x;
+    u.x0 = t.y;
+    u.flags = t.z;
+    u.grp = t.w;
+  } else {
+    u = a_unit_base(a, q.i);
+  }
+  u.s = u.grp * a.sg + q.k;
+  u.valid = u.s < a.g.nshot;
+  u.first = q.k == 0;
+  u.last = q.k == a.sg - 1;
   return u;
 }
 
@@ -210,19 +240,30 @@ __device__ __forceinline__ void a_pipeline(const ElAdjArgs& a, unsigned char* sm
   Stage* stg = reinterpret_cast<Stage*>(smem_raw);
   uint64_t* bar =
       reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(Stage) + sizeof(ATerms));
+  int4* tab = reinterpret_cast<int4*>(bar + D);
   const int G = gridDim.x;
   const int nunit = (a.units - (int)blockIdx.x + G - 1) / G;
   const int count = nunit * a.sg;
   if (count <= 0) return;
+  for (int i = threadIdx.x; i < nunit && i < A_TABLE; i += A_THREADS) {
+    const AUnit u = a_unit_base(a, i);
+    tab[i] = make_int4(u.z0, u.x0, u.flags, u.grp);
+  }
+  __syncthreads();
+  ASub qi{0, 0};  // next sub-unit to issue (thread 0)
   if (threadIdx.x == 0) {
     for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
     fence_barrier_init();
-    for (int k = 0; k < D && k < count; ++k) issue(stg[k], &bar[k], a_unit(a, k));
+    for (int k = 0; k < D && k < count; ++k) {
+      issue(stg[k], &bar[k], a_unit(a, tab, qi));
+      qi.next(a.sg);
+    }
   }
   __syncthreads();
+  ASub q{0, 0};
   int k = 0;
   for (; k < count; ++k) {
-    const AUnit u = a_unit(a, k);
+    const AUnit u = a_unit(a, tab, q);
     const bool ok = body(u, stg[k % D], [&]() {
       const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
       return !__syncthreads_or(!got);
@@ -231,8 +272,10 @@ __device__ __forceinline__ void a_pipeline(const ElAdjArgs& a, unsigned char* sm
     __syncthreads();  // stage and terms released
     if (threadIdx.x == 0 && k + D < count) {
       fence_proxy_async_smem();
-      issue(stg[k % D], &bar[k % D], a_unit(a, k + D));
+      issue(stg[k % D], &bar[k % D], a_unit(a, tab, qi));
+      qi.next(a.sg);
     }
+    q.next(a.sg);
   }
   if (k < count && threadIdx.x == 0) {
     latch(const_cast<int*>(a.status), SWEEP_ETIMEOUT);
