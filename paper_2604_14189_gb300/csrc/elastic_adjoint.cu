@@ -807,12 +807,14 @@ __global__ void el_grad_kernel(const Geom g, const float* gacc, int ngrp, const 
 
 int el_adj_shot_group(const Geom& g) {
   // units = tiles x groups; halve the group until there are units enough
-  // for about six per SM of a GB300 (fewer shots per group: more FP64
-  // accumulator traffic, one addition per group and step)
+  // for about twelve per SM of a GB300 (fewer shots per group: more
+  // accumulator traffic, one addition per group and step).  Measured on
+  // the 500x1500 + 40 gradient with 8 shots (481 tiles): groups of 8 shots
+  // 527.6 ms, 4 shots 486.7, 2 shots 480.5, 1 shot 541.4.
   const long long tiles =
       (long long)((g.NZ + TA_Z - 1) / TA_Z) * ((g.NXp + TA_X - 1) / TA_X);
   int sg = std::max(g.nshot, 1);
-  while (sg > 1 && tiles * ((g.nshot + sg - 1) / sg) < 912) sg = (sg + 1) / 2;
+  while (sg > 1 && tiles * ((g.nshot + sg - 1) / sg) < 1824) sg = (sg + 1) / 2;
   return sg;
 }
 

@@ -235,13 +235,13 @@ def test_elastic_gradient_layered_fluid_top(sw, golden):
 def test_elastic_adjoint_kernels_multi_unit_vs_oracle(sw):
     """The adjoint kernels' pipeline beyond one unit per CTA: 129x333 + 11
     (30 tiles of 16 x 128, 7 of them plain: no strip, box inside the grid),
-    92 shots, so the shots go in groups of 3 (31 groups, the last with two
-    shots and an empty slot) and every CTA runs 18-21 (tile, shot) steps
+    121 shots, so the shots go in groups of 2 (61 groups, the last with one
+    shot and an empty slot) and every CTA runs 24-26 (tile, shot) steps
     through its two stages; nt 60 (segments of 8, the last one short).  Receivers within 6 cells of the source, clipped to
     the grid, so that shots near an edge have several receivers on one cell
     (their residuals must add up).  Gradient per parameter and wavelet
     adjoint, whole and per shot, against the FP64 oracle."""
-    nz, nx, pml, nt, nshot, nrec = 129, 333, 11, 60, 92, 7
+    nz, nx, pml, nt, nshot, nrec = 129, 333, 11, 60, 121, 7
     rng = np.random.default_rng(21)
     m = random_model(nz, nx, 21)
     src = np.stack([rng.integers(2, nz - 2, nshot), rng.integers(2, nx - 2, nshot)], -1)
