@@ -218,6 +218,12 @@ __device__ __forceinline__ void df_acc(float& H, float& L, float hi, float lo) {
   H = __fadd_rn(s, l);
   L = __fsub_rn(l, __fsub_rn(H, s));
 }
+// Bring the accumulator planes of this thread's cells into L2 ahead of the
+// flush at the end of the group's last shot (hi at G, lo at G + fstride)
+__device__ __forceinline__ void df_prefetch(const float* G, long long fstride) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(G));
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(G + fstride));
+}
 // Add this thread's 4 cells of one coefficient adjoint to the group's
 // accumulator planes (hi at G, lo at G + fstride)
 __device__ __forceinline__ void df_flush(float* G, long long fstride, const float* hi,
@@ -361,6 +367,13 @@ __global__ void __launch_bounds__(A_THREADS, 1)
     float vx[4], vz[4];
     v4(ld4z(a.avx + ci, cell), vx);
     v4(ld4z(a.avz + ci, cell), vz);
+    const bool flush = u.last && grad && z < g.NZ && x < g.NXp;
+    float* const ga = a.gacc + (size_t)u.grp * 10 * g.fstride + (size_t)z * g.NXp + x;
+    if (flush) {
+      df_prefetch(ga + 2 * G_L2M * g.fstride, g.fstride);
+      df_prefetch(ga + 2 * G_LAM * g.fstride, g.fstride);
+      df_prefetch(ga + 2 * G_MU * g.fstride, g.fstride);
+    }
     if (!wait()) return false;
     const bool plain = u.flags & AU_PLAIN;
     if (u.valid && plain) {
@@ -503,8 +516,7 @@ __global__ void __launch_bounds__(A_THREADS, 1)
         }
       }
     }
-    if (u.last && grad && z < g.NZ && x < g.NXp) {
-      float* ga = a.gacc + (size_t)u.grp * 10 * g.fstride + (size_t)z * g.NXp + x;
+    if (flush) {
       df_flush(ga + 2 * G_L2M * g.fstride, g.fstride, acc[0], acl[0]);
       df_flush(ga + 2 * G_LAM * g.fstride, g.fstride, acc[1], acl[1]);
       df_flush(ga + 2 * G_MU * g.fstride, g.fstride, acc[2], acl[2]);
@@ -574,6 +586,12 @@ __global__ void __launch_bounds__(A_THREADS, 1)
     v4(ld4z(a.atxx + ci, cell), txx);
     v4(ld4z(a.atzz + ci, cell), tzz);
     v4(ld4z(a.atxz + ci, cell), txz);
+    const bool flush = u.last && grad && z < g.NZ && x < g.NXp;
+    float* const ga = a.gacc + (size_t)u.grp * 10 * g.fstride + (size_t)z * g.NXp + x;
+    if (flush) {
+      df_prefetch(ga + 2 * G_BX * g.fstride, g.fstride);
+      df_prefetch(ga + 2 * G_BZ * g.fstride, g.fstride);
+    }
     if (!wait()) return false;
     const bool plain = u.flags & AU_PLAIN;
     if (u.valid && plain) {
@@ -708,8 +726,7 @@ __global__ void __launch_bounds__(A_THREADS, 1)
         }
       }
     }
-    if (u.last && grad && z < g.NZ && x < g.NXp) {
-      float* ga = a.gacc + (size_t)u.grp * 10 * g.fstride + (size_t)z * g.NXp + x;
+    if (flush) {
       df_flush(ga + 2 * G_BX * g.fstride, g.fstride, acc[0], acl[0]);
       df_flush(ga + 2 * G_BZ * g.fstride, g.fstride, acc[1], acl[1]);
     }
