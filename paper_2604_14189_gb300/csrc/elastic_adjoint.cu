@@ -224,6 +224,43 @@ __device__ __forceinline__ void df_prefetch(const float* G, long long fstride) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(G));
   asm volatile("prefetch.global.L2 [%0];" ::"l"(G + fstride));
 }
+__device__ __forceinline__ void pf_l2(const float* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+// Strip units: bring the memory variables that the terms' phase reads (its
+// box groups, adjoint, ap_in[m0], ap_in[m1] on x strips, [m2], [m3] on z
+// strips) and the forward ones of this thread's cells (fp, gradient) into
+// L2 before the stage wait.
+__device__ __forceinline__ void strip_prefetch(const ElAdjArgs& a, const AUnit& u, size_t so,
+                                               size_t ci, bool cell, bool grad, int m0, int m1,
+                                               int m2, int m3) {
+  const Geom& g = a.g;
+  const bool xs = u.flags & AU_XS, zs = u.flags & AU_ZS;
+  for (int gi = threadIdx.x; gi < A_H * A_G4; gi += A_THREADS) {
+    const int br = gi / A_G4, bc = 4 * (gi - br * A_G4);
+    const int zz = u.z0 - 2 + br, xx = u.x0 - 4 + bc;
+    if (zz < 0 || zz >= g.NZ || xx < 0 || xx >= g.NXp) continue;
+    const size_t c = so + (size_t)zz * g.NXp + xx;
+    if (xs) {
+      pf_l2(a.ap_in[m0] + c);
+      pf_l2(a.ap_in[m1] + c);
+    }
+    if (zs) {
+      pf_l2(a.ap_in[m2] + c);
+      pf_l2(a.ap_in[m3] + c);
+    }
+  }
+  if (cell && grad) {
+    if (xs) {
+      pf_l2(a.fp[m0] + ci);
+      pf_l2(a.fp[m1] + ci);
+    }
+    if (zs) {
+      pf_l2(a.fp[m2] + ci);
+      pf_l2(a.fp[m3] + ci);
+    }
+  }
+}
 // Add this thread's 4 cells of one coefficient adjoint to the group's
 // accumulator planes (hi at G, lo at G + fstride)
 __device__ __forceinline__ void df_flush(float* G, long long fstride, const float* hi,
@@ -239,9 +276,9 @@ __device__ __forceinline__ void df_flush(float* G, long long fstride, const floa
 
 // The persistent pipeline of both halves: sub-units in order, D stages.
 // body(u, stage, wait) returns false when a transfer never landed.
-template <typename Stage, typename Issue, typename Body>
+template <typename Stage, typename Issue, typename Body, typename Ahead>
 __device__ __forceinline__ void a_pipeline(const ElAdjArgs& a, unsigned char* smem_raw,
-                                           Issue issue, Body body) {
+                                           Issue issue, Body body, Ahead ahead) {
   constexpr int D = A_STAGES;
   Stage* stg = reinterpret_cast<Stage*>(smem_raw);
   uint64_t* bar =
@@ -267,6 +304,7 @@ __device__ __forceinline__ void a_pipeline(const ElAdjArgs& a, unsigned char* sm
   }
   __syncthreads();
   ASub q{0, 0};
+  ahead(a_unit(a, tab, q));
   int k = 0;
   for (; k < count; ++k) {
     const AUnit u = a_unit(a, tab, q);
@@ -274,7 +312,12 @@ __device__ __forceinline__ void a_pipeline(const ElAdjArgs& a, unsigned char* sm
       const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
       return !__syncthreads_or(!got);
     });
-    if (!ok) break;   // uniform: a transfer never landed
+    if (!ok) break;  // uniform: a transfer never landed
+    if (k + 1 < count) {  // the next sub-unit's global reads, into L2
+      ASub qn = q;
+      qn.next(a.sg);
+      ahead(a_unit(a, tab, qn));
+    }
     __syncthreads();  // stage and terms released
     if (threadIdx.x == 0 && k + D < count) {
       fence_proxy_async_smem();
@@ -369,11 +412,6 @@ __global__ void __launch_bounds__(A_THREADS, 1)
     v4(ld4z(a.avz + ci, cell), vz);
     const bool flush = u.last && grad && z < g.NZ && x < g.NXp;
     float* const ga = a.gacc + (size_t)u.grp * 10 * g.fstride + (size_t)z * g.NXp + x;
-    if (flush) {
-      df_prefetch(ga + 2 * G_L2M * g.fstride, g.fstride);
-      df_prefetch(ga + 2 * G_LAM * g.fstride, g.fstride);
-      df_prefetch(ga + 2 * G_MU * g.fstride, g.fstride);
-    }
     if (!wait()) return false;
     const bool plain = u.flags & AU_PLAIN;
     if (u.valid && plain) {
@@ -523,7 +561,25 @@ __global__ void __launch_bounds__(A_THREADS, 1)
     }
     return true;
   };
-  a_pipeline<AStrStage>(a, smem_raw, issue, body);
+  // global reads of a sub-unit, brought into L2 while the one before runs
+  auto ahead = [&](const AUnit& u) {
+    const int z = u.z0 + r, x = u.x0 + lx;
+    const size_t so = (size_t)u.s * g.fstride;
+    const size_t ci = so + (size_t)z * g.NXp + x;
+    const bool cell = u.valid && z < g.NZ && x < g.NXp;
+    if (u.last && grad && z < g.NZ && x < g.NXp) {
+      const float* ga = a.gacc + (size_t)u.grp * 10 * g.fstride + (size_t)z * g.NXp + x;
+      df_prefetch(ga + 2 * G_L2M * g.fstride, g.fstride);
+      df_prefetch(ga + 2 * G_LAM * g.fstride, g.fstride);
+      df_prefetch(ga + 2 * G_MU * g.fstride, g.fstride);
+    }
+    if (cell) {  // the adjoint velocities it updates
+      pf_l2(a.avx + ci);
+      pf_l2(a.avz + ci);
+    }
+    if (u.valid && !(u.flags & AU_PLAIN)) strip_prefetch(a, u, so, ci, cell, grad, 4, 7, 5, 6);
+  };
+  a_pipeline<AStrStage>(a, smem_raw, issue, body, ahead);
 }
 
 // ---------------------------------------------------------------- receivers
@@ -588,10 +644,6 @@ __global__ void __launch_bounds__(A_THREADS, 1)
     v4(ld4z(a.atxz + ci, cell), txz);
     const bool flush = u.last && grad && z < g.NZ && x < g.NXp;
     float* const ga = a.gacc + (size_t)u.grp * 10 * g.fstride + (size_t)z * g.NXp + x;
-    if (flush) {
-      df_prefetch(ga + 2 * G_BX * g.fstride, g.fstride);
-      df_prefetch(ga + 2 * G_BZ * g.fstride, g.fstride);
-    }
     if (!wait()) return false;
     const bool plain = u.flags & AU_PLAIN;
     if (u.valid && plain) {
@@ -732,7 +784,24 @@ __global__ void __launch_bounds__(A_THREADS, 1)
     }
     return true;
   };
-  a_pipeline<AVelStage>(a, smem_raw, issue, body);
+  auto ahead = [&](const AUnit& u) {
+    const int z = u.z0 + r, x = u.x0 + lx;
+    const size_t so = (size_t)u.s * g.fstride;
+    const size_t ci = so + (size_t)z * g.NXp + x;
+    const bool cell = u.valid && z < g.NZ && x < g.NXp;
+    if (u.last && grad && z < g.NZ && x < g.NXp) {
+      const float* ga = a.gacc + (size_t)u.grp * 10 * g.fstride + (size_t)z * g.NXp + x;
+      df_prefetch(ga + 2 * G_BX * g.fstride, g.fstride);
+      df_prefetch(ga + 2 * G_BZ * g.fstride, g.fstride);
+    }
+    if (cell) {  // the adjoint stresses it updates
+      pf_l2(a.atxx + ci);
+      pf_l2(a.atzz + ci);
+      pf_l2(a.atxz + ci);
+    }
+    if (u.valid && !(u.flags & AU_PLAIN)) strip_prefetch(a, u, so, ci, cell, grad, 0, 2, 1, 3);
+  };
+  a_pipeline<AVelStage>(a, smem_raw, issue, body, ahead);
 }
 
 // ------------------------------------------------------------ chain rule
