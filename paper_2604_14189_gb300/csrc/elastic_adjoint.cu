@@ -90,10 +90,9 @@ struct __align__(128) ATerms {  // the half's four difference terms on the box
 };
 static_assert(kABox % 128 == 0, "staged field alignment");
 constexpr size_t kATable = 64 * 16;  // unit descriptor table (A_TABLE int4)
-constexpr size_t kAStrSmem =
-    A_STAGES * sizeof(AStrStage) + sizeof(ATerms) + 8 * A_STAGES + kATable;
-constexpr size_t kAVelSmem =
-    A_STAGES * sizeof(AVelStage) + sizeof(ATerms) + 8 * A_STAGES + kATable;
+static_assert(A_STAGES <= 2, "16 bytes of barriers");
+constexpr size_t kAStrSmem = A_STAGES * sizeof(AStrStage) + sizeof(ATerms) + 16 + kATable;
+constexpr size_t kAVelSmem = A_STAGES * sizeof(AVelStage) + sizeof(ATerms) + 16 + kATable;
 static_assert(kAStrSmem <= 227 * 1024 && kAVelSmem <= 227 * 1024, "shared memory");
 
 enum : int { AU_XS = 1, AU_ZS = 2, AU_PLAIN = 4 };
@@ -283,7 +282,7 @@ __device__ __forceinline__ void a_pipeline(const ElAdjArgs& a, unsigned char* sm
   Stage* stg = reinterpret_cast<Stage*>(smem_raw);
   uint64_t* bar =
       reinterpret_cast<uint64_t*>(smem_raw + D * sizeof(Stage) + sizeof(ATerms));
-  int4* tab = reinterpret_cast<int4*>(bar + D);
+  int4* tab = reinterpret_cast<int4*>(bar + 2);  // (barriers: 16 bytes reserved)
   const int G = gridDim.x;
   const int nunit = (a.units - (int)blockIdx.x + G - 1) / G;
   const int count = nunit * a.sg;
