@@ -547,6 +547,16 @@ def alg_bytes_elastic_fwd(c):
     return 60 * c["N_pad"] + 32 * (c["N_x"] + c["N_z"])
 
 
+def alg_bytes_elastic_adj(c, nshot):
+    """Algorithmic bytes of one fused elastic transposed step per shot: the
+    adjoint state (5 fields) read and written, the forward state (5 fields)
+    read, the 5 coefficients and the compensated coefficient-adjoint sums
+    (5 x hi, lo, read and written) once per step for all shots, 4 adjoint
+    memory variables read and written and 4 forward ones read per strip
+    cell per axis."""
+    return 60 * c["N_pad"] + (20 + 80) * c["N_pad"] / nshot + 48 * (c["N_x"] + c["N_z"])
+
+
 def run_elastic(args, rank, world, local_rank, emit=True):
     """Elastic forward (isotropic velocity-stress, 500 x 1500 + 40, 64 shots,
     nt 4000, 750 receivers) or elastic gradient (same grid, 8 shots,
@@ -615,17 +625,19 @@ def run_elastic(args, rank, world, local_rank, emit=True):
     if sweep.status(ws) != sweep.OK:
         raise sweep.SweepError(sweep.status(ws), "timed region")
     value = c["N_pad"] * nt * nshot / (ms_step * 1e-3) / 1e9
-    # per-step kernel time of the forward (velocity + stress kernels)
-    sweep.profile_enable((1 << sweep.K_EL_VEL) | (1 << sweep.K_EL_STR))
-    if not grad_mode:
-        step()
-    else:
-        sweep.sweep_forward(p, model, wav, src, rec)
+    # per-step kernel time of the forward (velocity + stress kernels) and,
+    # for the gradient, of the transposed step
+    sweep.profile_enable((1 << sweep.K_EL_VEL) | (1 << sweep.K_EL_STR) |
+                         (1 << sweep.K_EL_ADJ))
+    step()
     torch.cuda.synchronize()
     vms, vn = sweep.profile_read(sweep.K_EL_VEL)
     sms, sn = sweep.profile_read(sweep.K_EL_STR)
+    ams, an = sweep.profile_read(sweep.K_EL_ADJ)
     sweep.profile_enable(False)
     step_ms = vms / max(vn, 1) + sms / max(sn, 1)
+    adj_ms = ams / max(an, 1)
+    adj_bytes = alg_bytes_elastic_adj(c, nshot) * nshot
     peak, peak_src = peaks()
     achieved = alg_bytes_elastic_fwd(c) * nshot / (step_ms * 1e-3) / 1e9
     # end to end with host buffers
@@ -692,18 +704,37 @@ def run_elastic(args, rank, world, local_rank, emit=True):
                                f"nt {nt}, {nshot} shots, {nrec} receivers (vx, vz), 15 Hz "
                                f"explosive Ricker",
                    "l2": "fields of all shots (%.1f GB) exceed L2" % (ws.numel() / 1e9)},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "elastic forward step (velocity + stress kernels)",
-                     "peak_source": peak_src,
-                     "alg_bytes_per_launch": alg_bytes_elastic_fwd(c) * nshot,
-                     "avg_launch_ms": step_ms},
+        "roofline": ({"bound": "hbm", "achieved": adj_bytes / (adj_ms * 1e-3) / 1e9,
+                      "peak": peak, "unit": "GB/s",
+                      "frac": adj_bytes / (adj_ms * 1e-3) / 1e9 / peak, "traffic": None,
+                      "kernel": "elastic transposed step (stress half, receiver injection, "
+                                "velocity half)",
+                      "peak_source": peak_src, "alg_bytes_per_launch": adj_bytes,
+                      "avg_launch_ms": adj_ms,
+                      "timing": "CUDA events around every transposed step of one profiled "
+                                "gradient after the timed region"}
+                     if grad_mode else
+                     {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                      "frac": achieved / peak, "traffic": None,
+                      "kernel": "elastic forward step (velocity + stress kernels)",
+                      "peak_source": peak_src,
+                      "alg_bytes_per_launch": alg_bytes_elastic_fwd(c) * nshot,
+                      "avg_launch_ms": step_ms}),
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "Gpts/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if grad_mode:
+        # the whole gradient in fused algorithmic bytes: the forward pass, the
+        # replay and the transposed steps
+        path = nt * (2 * alg_bytes_elastic_fwd(c) * nshot + adj_bytes)
+        out["path_roofline"] = {"achieved": path / (ms_step * 1e-3) / 1e9,
+                                "frac": path / (ms_step * 1e-3) / 1e9 / peak,
+                                "note": "fused algorithmic bytes of the forward pass, the "
+                                        "replay and the transposed steps / timed gradient"}
+        out["forward_kernel"] = {"avg_launch_ms": step_ms, "achieved_gbs": achieved}
     if emit and rank == 0:
         print(json.dumps(out), flush=True)
     return out
@@ -1450,7 +1481,8 @@ def run_extras(args, local_rank):
     """The other configurations of the solver, one short run each, attached
     to the headline line: the 200 x 200 single-shot forward, the 20-shot
     gradient through autograd and through the time-loop kernels, the 64-shot
-    elastic forward, the 256-model heterogeneous batch and the plain FWI."""
+    elastic forward, the 8-shot elastic gradient, the 256-model heterogeneous
+    batch and the plain FWI."""
     base = dict(vars(args))
     out = {}
     runs = (
@@ -1460,6 +1492,9 @@ def run_extras(args, local_rank):
          lambda a: run_autograd(a, local_rank, emit=False)),
         ("elastic_forward_500x1500_64shots", dict(steps=1, warmup=1, nt=3000,
                                                   workload="elastic-forward"),
+         lambda a: run_elastic(a, 0, 1, local_rank, emit=False)),
+        ("elastic_gradient_500x1500_8shots", dict(steps=2, warmup=1, nt=3000,
+                                                  workload="elastic-gradient"),
          lambda a: run_elastic(a, 0, 1, local_rank, emit=False)),
         ("acoustic_gradient_one_launch_301x901", dict(steps=1, warmup=1),
          lambda a: run_one_launch(a, local_rank, emit=False)),

@@ -312,7 +312,9 @@ enum {
                               after its last step, so the steps keep
                               their programmatic overlap)                */
   SWEEP_K_AC_BWD_LOOP = 9, /* a whole acoustic backward time loop        */
-  SWEEP_K_COUNT = 10
+  SWEEP_K_EL_ADJ = 10,     /* elastic transposed step (stress half,
+                              receiver injection, velocity half)         */
+  SWEEP_K_COUNT = 11
 };
 int sweep_profile_enable(int mask);
 int sweep_profile_read(int kernel, double* ms, long long* launches);

@@ -949,6 +949,7 @@ void launch_el_adj_step(const ElAdjArgs& a, cudaStream_t st) {
     el_adj_src_kernel<<<(g.nshot + 127) / 128, 128, 0, st>>>(a);
     ++k;
   }
+  void* t = profile_begin(SWEEP_K_EL_ADJ, st);
   el_adj_str_kernel<<<grid, A_THREADS, kAStrSmem, st>>>(a);
   ++k;
   if (a.res && g.nrec > 0) {
@@ -956,6 +957,7 @@ void launch_el_adj_step(const ElAdjArgs& a, cudaStream_t st) {
     ++k;
   }
   el_adj_vel_kernel<<<grid, A_THREADS, kAVelSmem, st>>>(a);
+  profile_end(t, st);
   note_launches(k + 1);
 }
 

@@ -43,6 +43,7 @@ EXPORTS = ("sweep_workspace_bytes", "sweep_forward", "sweep_adjoint", "sweep_gra
            "sweep_forward_batch")
 K_AC_FWD, K_AC_BWD, K_EL_VEL, K_EL_STR = 0, 1, 2, 3
 K_AC_FWD_LOOP, K_AC_BWD_LOOP = 8, 9
+K_EL_ADJ = 10  # elastic transposed step
 
 
 class Problem(ctypes.Structure):
