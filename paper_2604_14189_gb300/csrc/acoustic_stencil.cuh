@@ -384,7 +384,11 @@ __device__ __forceinline__ bool bwd_body(const AcInBwdArgs& a, const StepCtl& c,
   int k = 0;
   for (; k < count; ++k) {
     if constexpr (PDL)
-      if (k == count - 1) grid_dep_trigger();  // the next kernel may start
+      // the next (CPML) kernel may start with this CTA's second-to-last unit:
+      // its blocks fit beside the stencil CTA and issue their loads during
+      // the tail (measured: one unit earlier 230.5 ms per gradient, the last
+      // unit 232.0, two units earlier 233.9)
+      if (k == (count > 1 ? count - 2 : 0)) grid_dep_trigger();
     const UnitDesc d = k < kUnitTable ? utab[k] : desc[k % D];
     const bool imgt = d.flags & U_IMG, needu1 = d.flags & U_U1;
     const int gx = d.x0 + lx;
