@@ -57,6 +57,8 @@ enum { G_L2M = 0, G_LAM = 1, G_MU = 2, G_BX = 3, G_BZ = 4 };
 
 // ------------------------------------------------------------- wavelet
 __global__ void el_adj_src_kernel(const ElAdjArgs a) {
+  grid_dep_wait();
+  grid_dep_trigger();
   if (*a.status) return;
   const Geom& g = a.g;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -291,7 +293,11 @@ __device__ __forceinline__ void a_pipeline(const ElAdjArgs& a, unsigned char* sm
     const AUnit u = a_unit_base(a, i);
     tab[i] = make_int4(u.z0, u.x0, u.flags, u.grp);
   }
-  __syncthreads();
+  // (programmatic launch: the table above overlaps the previous kernel's
+  // tail; everything below reads what earlier kernels wrote)
+  grid_dep_wait();
+  // one reader of the status word, so that the whole block returns together
+  if (__syncthreads_or(threadIdx.x == 0 && *a.status != 0)) return;
   ASub qi{0, 0};  // next sub-unit to issue (thread 0)
   if (threadIdx.x == 0) {
     for (int i = 0; i < D; ++i) mbar_init(&bar[i], 1);
@@ -306,6 +312,7 @@ __device__ __forceinline__ void a_pipeline(const ElAdjArgs& a, unsigned char* sm
   ahead(a_unit(a, tab, q));
   int k = 0;
   for (; k < count; ++k) {
+    if (k == count - 1) grid_dep_trigger();  // the next kernel may start
     const AUnit u = a_unit(a, tab, q);
     const bool ok = body(u, stg[k % D], [&]() {
       const bool got = mbar_wait(&bar[k % D], (k / D) & 1);
@@ -368,7 +375,6 @@ __device__ __forceinline__ void x_prof(const ElAdjArgs& a, int x, XProf& p) {
 __global__ void __launch_bounds__(A_THREADS, 1)
     el_adj_str_kernel(const __grid_constant__ ElAdjArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  if (*a.status) return;
   const Geom& g = a.g;
   ATerms& T = *reinterpret_cast<ATerms*>(smem_raw + A_STAGES * sizeof(AStrStage));
   const bool grad = a.gacc != nullptr;
@@ -583,6 +589,8 @@ __global__ void __launch_bounds__(A_THREADS, 1)
 
 // ---------------------------------------------------------------- receivers
 __global__ void el_adj_rec_kernel(const ElAdjArgs a) {
+  grid_dep_wait();
+  grid_dep_trigger();
   if (*a.status) return;
   const Geom& g = a.g;
   const int r = blockIdx.x * blockDim.x + threadIdx.x, s = blockIdx.y;
@@ -602,7 +610,6 @@ __global__ void el_adj_rec_kernel(const ElAdjArgs a) {
 __global__ void __launch_bounds__(A_THREADS, 1)
     el_adj_vel_kernel(const __grid_constant__ ElAdjArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  if (*a.status) return;
   const Geom& g = a.g;
   ATerms& T = *reinterpret_cast<ATerms*>(smem_raw + A_STAGES * sizeof(AVelStage));
   const bool grad = a.gacc != nullptr;
@@ -946,17 +953,18 @@ void launch_el_adj_step(const ElAdjArgs& a, cudaStream_t st) {
   const int grid = std::min(device_sms(), a.units);
   int k = 0;
   if (a.wgrad) {
-    el_adj_src_kernel<<<(g.nshot + 127) / 128, 128, 0, st>>>(a);
+    launch_dependent(el_adj_src_kernel, dim3((g.nshot + 127) / 128), dim3(128), 0, st, a);
     ++k;
   }
   void* t = profile_begin(SWEEP_K_EL_ADJ, st);
-  el_adj_str_kernel<<<grid, A_THREADS, kAStrSmem, st>>>(a);
+  launch_dependent(el_adj_str_kernel, dim3(grid), dim3(A_THREADS), kAStrSmem, st, a);
   ++k;
   if (a.res && g.nrec > 0) {
-    el_adj_rec_kernel<<<dim3((g.nrec + 127) / 128, g.nshot), 128, 0, st>>>(a);
+    launch_dependent(el_adj_rec_kernel, dim3((g.nrec + 127) / 128, g.nshot), dim3(128), 0, st,
+                     a);
     ++k;
   }
-  el_adj_vel_kernel<<<grid, A_THREADS, kAVelSmem, st>>>(a);
+  launch_dependent(el_adj_vel_kernel, dim3(grid), dim3(A_THREADS), kAVelSmem, st, a);
   profile_end(t, st);
   note_launches(k + 1);
 }
