@@ -316,3 +316,21 @@ def test_dot_binding_checks_out_before_any_launch():
         sweep.sweep_dot(a, a, out=torch.zeros(2, dtype=torch.float64))
     with pytest.raises(ValueError, match="size"):
         sweep.sweep_dot(a, torch.zeros(5, dtype=torch.float32))
+
+
+def test_profile_classes_match_the_header(lib):
+    """The binding's kernel-class constants are the header's SWEEP_K_*
+    values, and a class past SWEEP_K_COUNT is rejected on the host."""
+    from paper_2604_14189_gb300 import sweep
+    txt = open(os.path.join(ROOT, "include", "sweep.h")).read()
+    vals = {k: int(v) for k, v in re.findall(r"\bSWEEP_K_(\w+)\s*=\s*(\d+)", txt)}
+    for name in ("AC_FWD", "AC_BWD", "EL_VEL", "EL_STR", "AC_FWD_LOOP", "AC_BWD_LOOP",
+                 "EL_ADJ"):
+        assert getattr(sweep, "K_" + name) == vals[name], name
+    assert sorted(v for k, v in vals.items() if k != "COUNT") == list(range(vals["COUNT"]))
+    ms, n = ctypes.c_double(0.0), ctypes.c_longlong(0)
+    lib.sweep_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_longlong)]
+    assert lib.sweep_profile_read(vals["COUNT"], ctypes.byref(ms), ctypes.byref(n)) \
+        == sweep.EINVAL
+    assert lib.sweep_profile_read(-1, ctypes.byref(ms), ctypes.byref(n)) == sweep.EINVAL
