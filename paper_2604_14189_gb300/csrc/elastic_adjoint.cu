@@ -18,7 +18,7 @@
 //   receivers: v-bar(r) += residual^n(r)
 //   velocity: Q = cbx vx-bar;  P = p1-bar + Q;  dxt-bar = Q + bxh P;
 //            p1-bar = axh P (p2..p4 alike); txx-bar += -Dmx(dxt-bar), ...
-//   coefficients (summed over shots and steps in FP64):
+//   coefficients (summed over shots and steps; see below for the precision):
 //            d J / d cl2m += txx-bar Ex + tzz-bar Ez, d J / d clam +=
 //            txx-bar Ez + tzz-bar Ex, d J / d cmu += txz-bar (shear bracket),
 //            d J / d cbx += vx-bar (vx bracket), d J / d cbz likewise.
